@@ -1,0 +1,224 @@
+/*
+ * tcw_oracle.c -- plain FP64 CPU oracle for the long-transient (tCW) template
+ * track statistic of Merou, Tenorio & Sintes, "GPU-Accelerated Searches for
+ * Long-Transient Gravitational Waves from Newborn Neutron Stars"
+ * (arXiv:2507.07816).
+ *
+ * THIS IS TEST INFRASTRUCTURE, NOT PART OF THE PRODUCT.  Only the test suite,
+ * the smoke check and the CPU-baseline leg of the benchmark may load it.  It
+ * shares no code, header, table or constant generator with the CUDA library;
+ * the two are compared element by element on the same seeded inputs.
+ *
+ * Everything here is written to be checked against the paper by eye: plain
+ * nested loops, one `pow` per lookup, no tables, no reordering, no blocking.
+ *
+ *   Eq. 1 (Sec. 1)   f_gw(t) = f0 * ((t - T0)/tau + 1)^(1/(1-n))
+ *   Eq. 2 (Sec. 1)   fhat(t) = f_gw(t) * (1 + v(t).nhat / c)
+ *   Sec. 2           the track selects one data bin per segment; the weighted
+ *                    normalized power is summed over the selected bins
+ *   Eq. 4 (Sec. 2)   Psi = (s - <s>) / sigma_s
+ *
+ * Readings of points the paper leaves open:
+ *   - segment time t_j is the caller-supplied segment mid-time;
+ *   - segments with t_j < T0 contribute nothing (Eq. 1 starts at T0);
+ *   - bin k has centre f_min + k*df and the track takes the nearest centre,
+ *     k = floor((fhat - f_min)/df + 1/2) (ties go up);
+ *   - lookups outside [0, Nbin) are skipped and their weight is dropped;
+ *   - normalized power is Exp(1) under noise, so for s = sum w*rho the mean is
+ *     <s> = W1 = sum w and the standard deviation is sigma_s = sqrt(W2),
+ *     W2 = sum w^2, both over the lookups actually summed;
+ *   - detectors are combined inside one sum;
+ *   - Psi = -inf when no lookup is valid (W2 == 0);
+ *   - top-k orders by (Psi descending, template index ascending).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORACLE_C_LIGHT 299792458.0 /* m/s, exact SI value */
+
+/* Eq. 1: GW frequency of the msMagnetar model at detector time t (t >= T0). */
+double oracle_track_frequency(double f0, double tau, double n, double T0, double t)
+{
+    return f0 * pow((t - T0) / tau + 1.0, 1.0 / (1.0 - n));
+}
+
+/* Eq. 2: Doppler-modulated frequency for detector velocity v (m/s) and unit
+ * sky vector nhat (both in the same frame). */
+double oracle_doppler_frequency(double f, const double v[3], const double nhat[3])
+{
+    double vn = v[0] * nhat[0] + v[1] * nhat[1] + v[2] * nhat[2];
+    return f * (1.0 + vn / ORACLE_C_LIGHT);
+}
+
+/* Continuous bin coordinate x = (fhat - f_min)/df; bin k has centre f_min + k*df. */
+double oracle_bin_coordinate(double fhat, double f_min, double df)
+{
+    return (fhat - f_min) / df;
+}
+
+/* Nearest-centre bin index, ties upward. */
+int64_t oracle_bin_index(double fhat, double f_min, double df)
+{
+    return (int64_t)floor(oracle_bin_coordinate(fhat, f_min, df) + 0.5);
+}
+
+/* Eq. 4 with <s> = W1 and sigma_s = sqrt(W2). */
+double oracle_critical_ratio(double S, double W1, double W2)
+{
+    if (W2 <= 0.0) return -INFINITY;
+    return (S - W1) / sqrt(W2);
+}
+
+/*
+ * Statistic of one (sky, template) pair: S = sum w*rho, W1 = sum w,
+ * W2 = sum w^2 over every detector d and segment j whose track bin lies in
+ * the band (Sec. 2, Eq. 1, Eq. 2).
+ *
+ *   rho      [D][Nseg][Nbin]  normalized power (float, converted to double)
+ *   t_mid    [Nseg]           segment mid-times, s (shared by all detectors)
+ *   w        [D][Nseg]        per-detector, per-segment weights (NULL = 1)
+ *   v        [D][Nseg][3]     detector velocity w.r.t. the SSB, m/s
+ *   nhat     [3]              unit vector toward the source
+ */
+static void oracle_pair_stats(const float *rho, int D, int Nseg, int Nbin,
+                              double f_min, double df, const double *t_mid,
+                              const float *w, const double *v,
+                              const double *nhat, double f0, double tau,
+                              double n, double T0, double out[3])
+{
+    double S = 0.0, W1 = 0.0, W2 = 0.0;
+    for (int d = 0; d < D; ++d) {
+        for (int j = 0; j < Nseg; ++j) {
+            double t = t_mid[j];
+            if (t < T0) continue;
+            double f = oracle_track_frequency(f0, tau, n, T0, t);
+            double fh = oracle_doppler_frequency(f, v + ((size_t)d * Nseg + j) * 3, nhat);
+            int64_t k = oracle_bin_index(fh, f_min, df);
+            if (k < 0 || k >= Nbin) continue;
+            double wj = w ? (double)w[(size_t)d * Nseg + j] : 1.0;
+            double r = (double)rho[((size_t)d * Nseg + j) * (size_t)Nbin + (size_t)k];
+            S += wj * r;
+            W1 += wj;
+            W2 += wj * wj;
+        }
+    }
+    out[0] = S;
+    out[1] = W1;
+    out[2] = W2;
+}
+
+/*
+ * Statistics for a list of (sky, template) pairs, or for the full grid when
+ * pairs == NULL (then P is ignored and the output is [S][B], sky-major).
+ * Outputs S_out, W1_out, W2_out, Psi_out (any may be NULL).
+ * nthreads <= 0 uses the OpenMP default.
+ */
+void oracle_search_stats(const float *rho, int D, int Nseg, int Nbin,
+                         double f_min, double df, const double *t_mid,
+                         const float *w, const double *v,
+                         const double *nhat, int n_sky,
+                         const double *f0, const double *tau, const double *n,
+                         int n_tmpl, double T0,
+                         const int64_t *pairs, int64_t P,
+                         double *S_out, double *W1_out, double *W2_out,
+                         double *Psi_out, int nthreads)
+{
+    int64_t total = pairs ? P : (int64_t)n_sky * n_tmpl;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (int64_t i = 0; i < total; ++i) {
+        int64_t s, b;
+        if (pairs) {
+            s = pairs[2 * i];
+            b = pairs[2 * i + 1];
+        } else {
+            s = i / n_tmpl;
+            b = i % n_tmpl;
+        }
+        double st[3];
+        oracle_pair_stats(rho, D, Nseg, Nbin, f_min, df, t_mid, w, v,
+                          nhat + 3 * s, f0[b], tau[b], n[b], T0, st);
+        if (S_out) S_out[i] = st[0];
+        if (W1_out) W1_out[i] = st[1];
+        if (W2_out) W2_out[i] = st[2];
+        if (Psi_out) Psi_out[i] = oracle_critical_ratio(st[0], st[1], st[2]);
+    }
+}
+
+/*
+ * Bin coordinate x (before rounding) of every lookup of the given pairs:
+ * out[i][d][j] = (fhat - f_min)/df, NaN where t_j < T0.  Used by the tests to
+ * find lookups inside the rounding tie band and to compare indices.
+ */
+void oracle_track_coordinates(int D, int Nseg, double f_min, double df,
+                              const double *t_mid, const double *v,
+                              const double *nhat, const double *f0,
+                              const double *tau, const double *n, double T0,
+                              const int64_t *pairs, int64_t P, double *out)
+{
+    for (int64_t i = 0; i < P; ++i) {
+        int64_t s = pairs[2 * i], b = pairs[2 * i + 1];
+        for (int d = 0; d < D; ++d) {
+            for (int j = 0; j < Nseg; ++j) {
+                double *o = out + ((size_t)i * D + d) * Nseg + j;
+                if (t_mid[j] < T0) {
+                    *o = NAN;
+                    continue;
+                }
+                double f = oracle_track_frequency(f0[b], tau[b], n[b], T0, t_mid[j]);
+                double fh = oracle_doppler_frequency(f, v + ((size_t)d * Nseg + j) * 3, nhat + 3 * s);
+                *o = oracle_bin_coordinate(fh, f_min, df);
+            }
+        }
+    }
+}
+
+/* Top-k of one row of Psi by (Psi descending, index ascending). */
+typedef struct {
+    double psi;
+    int64_t idx;
+} oracle_entry;
+
+static int oracle_entry_cmp(const void *a, const void *b)
+{
+    const oracle_entry *x = (const oracle_entry *)a, *y = (const oracle_entry *)b;
+    if (x->psi > y->psi) return -1;
+    if (x->psi < y->psi) return 1;
+    return (x->idx < y->idx) ? -1 : (x->idx > y->idx);
+}
+
+/* psi [rows][B] -> idx_out/val_out [rows][k]; k <= B. */
+void oracle_topk(const double *psi, int64_t rows, int64_t B, int64_t k,
+                 int64_t *idx_out, double *val_out)
+{
+    oracle_entry *e = (oracle_entry *)malloc(sizeof(oracle_entry) * (size_t)B);
+    if (!e) return;
+    for (int64_t r = 0; r < rows; ++r) {
+        for (int64_t b = 0; b < B; ++b) {
+            e[b].psi = psi[r * B + b];
+            e[b].idx = b;
+        }
+        qsort(e, (size_t)B, sizeof(oracle_entry), oracle_entry_cmp);
+        for (int64_t i = 0; i < k; ++i) {
+            idx_out[r * k + i] = e[i].idx;
+            val_out[r * k + i] = e[i].psi;
+        }
+    }
+    free(e);
+}
+
+int oracle_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,324 @@
+"""Seeded synthetic inputs for the tCW track-statistic search.
+
+This module is shared by the tests, the benchmark and the smoke check.  It
+holds none of the search's arithmetic (no Eq. 1 closed form, no Eq. 2
+Doppler factor applied to a template, no statistic): it only draws inputs.
+
+* Detector motion: circular Earth orbit (1 AU, 1 sidereal-ish year of
+  365.25 d) in the ecliptic, rotated to equatorial coordinates by the
+  obliquity, plus diurnal rotation of 465 m/s x cos(latitude) at the sidereal
+  rate.  Positions and velocities are both analytic; the velocity is the exact
+  time derivative of the position.
+* Sky: Fibonacci-sphere lattice (equal area for any count).
+* Banks: cubic lattice and uniform random over (f0, tau, n) (Sec. 2 of the
+  paper; parameter ranges from Sec. 1).
+* Noise: whitened data, so normalized power is Exponential(1).
+* Signals: the source frequency is obtained by integrating the braking law
+  df/dt = -f^n / ((n-1) tau f0^(n-1)) with a fourth-order Runge-Kutta scheme,
+  and the detector-frame frequency by multiplying with the time derivative of
+  the arrival-time delay (r(t).nhat/c), taken by central differences of the
+  detector POSITION.  Neither step evaluates the closed forms the search uses,
+  so an injection recovered by the search is an independent check of them.
+  Power in a signal bin is ((x + mu)^2 + y^2)/2 with x, y ~ N(0, 1), whose mean
+  is 1 + mu^2/2; mu follows h0 ~ f^2 (Eq. 3).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+C_LIGHT = 299792458.0
+AU = 1.495978707e11
+YEAR = 365.25 * 86400.0
+OBLIQUITY = math.radians(23.4393)
+SIDEREAL_RATE = 7.2921159e-5
+ROT_SPEED_EQ = 465.0                      # m/s at the equator
+EARTH_RADIUS = ROT_SPEED_EQ / SIDEREAL_RATE
+ORBIT_RATE = 2.0 * math.pi / YEAR
+GPS_EPOCH0 = 1.4e9                        # start time used by the configs, s
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+# --------------------------------------------------------------------------
+# detector motion
+# --------------------------------------------------------------------------
+@dataclass
+class Detector:
+    latitude: float       # rad
+    longitude: float      # rad (rotation phase at t = 0)
+    orbit_phase: float    # rad (orbital phase at t = 0)
+
+    def _ecl_to_eq(self, x, y, z):
+        ce, se = math.cos(OBLIQUITY), math.sin(OBLIQUITY)
+        return x, ce * y - se * z, se * y + ce * z
+
+    def position(self, t):
+        """Detector position w.r.t. the solar-system barycentre, m, [N][3]."""
+        t = np.asarray(t, np.float64)
+        a = ORBIT_RATE * t + self.orbit_phase
+        ox, oy, oz = self._ecl_to_eq(AU * np.cos(a), AU * np.sin(a), 0.0 * a)
+        b = SIDEREAL_RATE * t + self.longitude
+        cl, sl = math.cos(self.latitude), math.sin(self.latitude)
+        rx = EARTH_RADIUS * cl * np.cos(b)
+        ry = EARTH_RADIUS * cl * np.sin(b)
+        rz = EARTH_RADIUS * sl + 0.0 * b
+        return np.stack([ox + rx, oy + ry, oz + rz], axis=-1)
+
+    def velocity(self, t):
+        """Exact time derivative of position(), m/s, [N][3]."""
+        t = np.asarray(t, np.float64)
+        a = ORBIT_RATE * t + self.orbit_phase
+        vx, vy, vz = self._ecl_to_eq(-AU * ORBIT_RATE * np.sin(a),
+                                     AU * ORBIT_RATE * np.cos(a), 0.0 * a)
+        b = SIDEREAL_RATE * t + self.longitude
+        cl = math.cos(self.latitude)
+        rx = -EARTH_RADIUS * SIDEREAL_RATE * cl * np.sin(b)
+        ry = EARTH_RADIUS * SIDEREAL_RATE * cl * np.cos(b)
+        return np.stack([vx + rx, vy + ry, vz + 0.0 * b], axis=-1)
+
+
+def random_detectors(r: np.random.Generator, count: int):
+    """Detectors with seeded latitude/longitude; they share the orbital phase."""
+    orb = r.uniform(0.0, 2.0 * math.pi)
+    return [Detector(latitude=r.uniform(-1.0, 1.0), longitude=r.uniform(0.0, 2.0 * math.pi),
+                     orbit_phase=orb) for _ in range(count)]
+
+
+def segment_times(n_seg: int, t_sft: float, t_start: float = GPS_EPOCH0):
+    """Segment mid-times t_start + (j + 1/2) T_SFT."""
+    return t_start + (np.arange(n_seg, dtype=np.float64) + 0.5) * t_sft
+
+
+# --------------------------------------------------------------------------
+# sky and banks
+# --------------------------------------------------------------------------
+def fibonacci_sky(count: int):
+    """Unit vectors on a Fibonacci-sphere lattice, [count][3]."""
+    i = np.arange(count, dtype=np.float64) + 0.5
+    z = 1.0 - 2.0 * i / count
+    phi = i * math.pi * (3.0 - math.sqrt(5.0))
+    rxy = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    v = np.stack([rxy * np.cos(phi), rxy * np.sin(phi), z], axis=-1)
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+def random_sky(r: np.random.Generator, count: int):
+    v = r.normal(size=(count, 3))
+    return v / np.linalg.norm(v, axis=1, keepdims=True)
+
+
+@dataclass
+class Bank:
+    f0: np.ndarray
+    tau: np.ndarray
+    n: np.ndarray
+
+    def __len__(self):
+        return int(self.f0.shape[0])
+
+    def subset(self, idx):
+        return Bank(self.f0[idx].copy(), self.tau[idx].copy(), self.n[idx].copy())
+
+
+def lattice_bank(f0_values, tau_values, n_values) -> Bank:
+    """Cubic lattice; f0 varies fastest, then tau, then n."""
+    nn, tt, ff = np.meshgrid(np.asarray(n_values, np.float64),
+                             np.asarray(tau_values, np.float64),
+                             np.asarray(f0_values, np.float64), indexing="ij")
+    return Bank(ff.ravel().copy(), tt.ravel().copy(), nn.ravel().copy())
+
+
+def random_bank(r: np.random.Generator, count: int, f0_range=(500.0, 3000.0),
+                tau_range=(3500.0, 35000.0), n_range=(3.0, 7.0)) -> Bank:
+    """Uniform prior over the box (parameter ranges of Sec. 1)."""
+    return Bank(r.uniform(*f0_range, size=count), r.uniform(*tau_range, size=count),
+                r.uniform(*n_range, size=count))
+
+
+# --------------------------------------------------------------------------
+# data
+# --------------------------------------------------------------------------
+def exponential_noise(r: np.random.Generator, shape):
+    return r.standard_exponential(size=shape, dtype=np.float32)
+
+
+def uniform_weights(r: np.random.Generator, n_det: int, n_seg: int, lo=0.5, hi=1.5):
+    return r.uniform(lo, hi, size=(n_det, n_seg)).astype(np.float32)
+
+
+def spindown_frequency(f0, tau, n, T0, t, max_step=2.0):
+    """Source frequency from RK4 integration of df/dt = -f^n/((n-1) tau f0^(n-1)).
+
+    t must be sorted ascending; values with t < T0 are returned as NaN.
+    """
+    t = np.asarray(t, np.float64)
+    out = np.full(t.shape, np.nan)
+    k = f0 ** (1.0 - n) / ((n - 1.0) * tau)
+
+    def rate(f):
+        return -k * f ** n
+
+    f, tc = float(f0), float(T0)
+    for j, tj in enumerate(t):
+        if tj < T0:
+            continue
+        span = tj - tc
+        steps = max(1, int(math.ceil(span / max_step)))
+        h = span / steps
+        for _ in range(steps):
+            k1 = rate(f)
+            k2 = rate(f + 0.5 * h * k1)
+            k3 = rate(f + 0.5 * h * k2)
+            k4 = rate(f + h * k3)
+            f += h * (k1 + 2.0 * k2 + 2.0 * k3 + k4) / 6.0
+        tc = tj
+        out[j] = f
+    return out
+
+
+def detector_frame_frequency(f_src, det: Detector, nhat, t, h=4.0):
+    """Multiply by d/dt of the arrival-time delay r(t).nhat/c (central differences)."""
+    t = np.asarray(t, np.float64)
+    nhat = np.asarray(nhat, np.float64)
+    dp = det.position(t + h) - det.position(t - h)
+    rate = (dp @ nhat) / (2.0 * h * C_LIGHT)
+    return f_src * (1.0 + rate)
+
+
+def signal_bins(f_det, f_min, df, n_bin):
+    """Bin whose centre f_min + k df is nearest the frequency; -1 when outside."""
+    x = (np.asarray(f_det) - f_min) / df
+    k = np.where(np.isfinite(x), np.rint(x), -1).astype(np.int64)
+    k[(k < 0) | (k >= n_bin)] = -1
+    return k
+
+
+@dataclass
+class Injection:
+    f0: float
+    tau: float
+    n: float
+    nhat: np.ndarray
+    snr: float
+    bins: np.ndarray = field(default=None)   # [D][Nseg], -1 = none
+
+
+def inject(r: np.random.Generator, rho, injection: Injection, detectors, t, T0,
+           f_min, df, weights=None):
+    """Add one signal to rho in place and return its [D][Nseg] bin track.
+
+    mu_j is proportional to (f_j/f0)^2 (h0 ~ f^2, Eq. 3) and scaled so that the
+    expected excess of the weighted sum over its standard deviation is `snr`.
+    """
+    D, n_seg, n_bin = rho.shape
+    f_src = spindown_frequency(injection.f0, injection.tau, injection.n, T0, t)
+    bins = np.full((D, n_seg), -1, np.int64)
+    fdet = np.full((D, n_seg), np.nan)
+    for d, det in enumerate(detectors):
+        fd = detector_frame_frequency(f_src, det, injection.nhat, t)
+        fdet[d] = fd
+        bins[d] = signal_bins(fd, f_min, df, n_bin)
+    ok = bins >= 0
+    if not ok.any():
+        injection.bins = bins
+        return bins
+    w = np.ones((D, n_seg)) if weights is None else np.asarray(weights, np.float64)
+    shape = np.where(ok, (fdet / injection.f0) ** 4, 0.0)    # lambda_j ~ f^4
+    lam_unit = (w * shape).sum() / math.sqrt((w * w * ok).sum())
+    lam0 = injection.snr / lam_unit
+    mu = np.sqrt(2.0 * lam0 * shape)
+    dd, jj = np.nonzero(ok)
+    x = r.normal(size=dd.shape[0])
+    y = r.normal(size=dd.shape[0])
+    rho[dd, jj, bins[dd, jj]] = (((x + mu[dd, jj]) ** 2 + y ** 2) / 2.0).astype(rho.dtype)
+    injection.bins = bins
+    return bins
+
+
+# --------------------------------------------------------------------------
+# workload configurations
+# --------------------------------------------------------------------------
+@dataclass
+class Problem:
+    rho: np.ndarray            # [D][Nseg][Nbin] float32 or float16
+    t_mid: np.ndarray          # [Nseg]
+    weights: np.ndarray        # [D][Nseg] float32 or None
+    velocity: np.ndarray       # [D][Nseg][3]
+    f_min: float
+    df: float
+    T0: float
+    nhat: np.ndarray           # [S][3]
+    bank: Bank
+    injections: list
+    detectors: list
+    name: str = ""
+
+    @property
+    def shape(self):
+        return self.rho.shape
+
+
+def config_small(seed=20250711, n_det=1, n_seg=256, n_bin=4096, t_sft=32.0,
+                 f_min=500.0, n_f0=64, n_tau=16, n_values=(3, 4, 5, 6, 7),
+                 n_sky=1, snr=8.0, weights=False, inject_at=None):
+    """Plain search, 1 detector, 256 x 4096 spectrogram, 5120-template lattice.
+
+    df = 1/T_SFT; band 500-628 Hz; f0 lattice 560 + m 64/63 Hz, tau geometric
+    in [3500, 35000] s, n in {3..7}; one injected track at a lattice point.
+    """
+    r = rng(seed)
+    df = 1.0 / t_sft
+    t = segment_times(n_seg, t_sft)
+    T0 = t[0] - 0.5 * t_sft
+    dets = random_detectors(r, n_det)
+    vel = np.stack([d.velocity(t) for d in dets])
+    rho = exponential_noise(r, (n_det, n_seg, n_bin))
+    w = uniform_weights(r, n_det, n_seg) if weights else None
+    f0s = 560.0 + np.arange(n_f0) * (64.0 / 63.0)
+    taus = np.geomspace(3500.0, 35000.0, n_tau)
+    bank = lattice_bank(f0s, taus, n_values)
+    nhat = random_sky(r, n_sky)
+    injections = []
+    if snr and snr > 0:
+        b = int(r.integers(0, len(bank))) if inject_at is None else int(inject_at)
+        inj = Injection(float(bank.f0[b]), float(bank.tau[b]), float(bank.n[b]),
+                        nhat[int(r.integers(0, n_sky))], snr)
+        inject(r, rho, inj, dets, t, T0, f_min, df, w)
+        inj.template = b
+        injections.append(inj)
+    return Problem(rho, t, w, vel, f_min, df, T0, nhat, bank, injections, dets,
+                   name="plain-1det-256x4096-lattice5120")
+
+
+def config_full(seed=20250712, n_det=2, n_seg=10000, n_bin=10000, t_sft=4.0,
+                f_min=500.0, n_tmpl=200000, n_sky=1024, n_inj=10, snr=8.0,
+                dtype=np.float32, weights=False):
+    """Plain search, 2 detectors, 10000 x 10000 spectrogram (500-3000 Hz),
+    2e5 uniform-random templates x 1024 Fibonacci sky directions, 10 injections."""
+    r = rng(seed)
+    df = 1.0 / t_sft
+    t = segment_times(n_seg, t_sft)
+    T0 = t[0] - 0.5 * t_sft
+    dets = random_detectors(r, n_det)
+    vel = np.stack([d.velocity(t) for d in dets])
+    rho = exponential_noise(r, (n_det, n_seg, n_bin))
+    w = uniform_weights(r, n_det, n_seg) if weights else None
+    bank = random_bank(r, n_tmpl, f0_range=(f_min, f_min + n_bin * df))
+    nhat = fibonacci_sky(n_sky)
+    injections = []
+    for _ in range(n_inj):
+        b = int(r.integers(0, len(bank)))
+        inj = Injection(float(bank.f0[b]), float(bank.tau[b]), float(bank.n[b]),
+                        nhat[int(r.integers(0, n_sky))], snr)
+        inject(r, rho, inj, dets, t, T0, f_min, df, w)
+        inj.template = b
+        injections.append(inj)
+    if dtype != np.float32:
+        rho = rho.astype(dtype)
+    return Problem(rho, t, w, vel, f_min, df, T0, nhat, bank, injections, dets,
+                   name=f"plain-{n_det}det-{n_seg}x{n_bin}-random{n_tmpl}-sky{n_sky}")
