@@ -1,0 +1,182 @@
+/*
+ * tcw.h -- C ABI of the GB300 (sm_103a) long-transient track-statistic search.
+ *
+ * The method is the template-bank search of Merou, Tenorio & Sintes,
+ * "GPU-Accelerated Searches for Long-Transient Gravitational Waves from
+ * Newborn Neutron Stars" (arXiv:2507.07816):
+ *
+ *   Eq. 1  f(t)    = f0 * ((t - T0)/tau + 1)^(1/(1-n))          (Sec. 1)
+ *   Eq. 2  fhat(t) = f(t) * (1 + v(t).nhat / c)                  (Sec. 1)
+ *   Sec. 2 each template selects one bin per SFT segment; the weighted
+ *          normalized power is summed over the selected bins:
+ *          S = sum w rho,  W1 = sum w,  W2 = sum w^2
+ *   Eq. 4  Psi = (S - <S>)/sigma_S = (S - W1)/sqrt(W2)
+ *
+ * Readings of points the paper leaves open, used throughout this library:
+ *   - bin k has centre f_min + k*df; the track takes the nearest centre,
+ *     k = floor((fhat - f_min)/df + 1/2);
+ *   - segments with t_mid < T0 and lookups with k outside [0, n_bin) add
+ *     nothing to S, W1 or W2;
+ *   - detectors are summed into one statistic; Psi = -inf when W2 == 0;
+ *   - top-k per sky orders by (Psi descending, caller template index
+ *     ascending).
+ *
+ * Conventions for every entry point:
+ *   - Return value: TCW_OK (0) or a negative tcw_status; no call aborts or
+ *     exits.  tcw_status_string() names a code; tcw_last_error() returns a
+ *     human-readable message for the most recent failure on a context.
+ *   - Arrays are dense, C order (last index fastest), in the element type
+ *     named in the declaration.
+ *   - Pointer flags: TCW_HOST (0) means host memory; TCW_DEVICE (1) means
+ *     device memory on the context's device.  Host inputs are copied into
+ *     buffers the context owns before the call returns.  Device inputs are
+ *     copied too (device to device), so the caller may free them after the
+ *     call returns.  Outputs are caller-allocated.
+ *   - Thread safety: one context per host thread.  All device work of a
+ *     context runs on its stream, in call order.
+ */
+#ifndef TCW_H
+#define TCW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tcw_ctx tcw_ctx;
+typedef int tcw_status;
+
+enum {
+    TCW_OK = 0,
+    TCW_ERR_INVALID_ARGUMENT = -1, /* bad size, pointer, value or flag */
+    TCW_ERR_CUDA = -2,             /* a CUDA runtime call failed */
+    TCW_ERR_OUT_OF_MEMORY = -3,    /* device allocation failed */
+    TCW_ERR_STATE = -4,            /* a required input has not been loaded */
+    TCW_ERR_UNSUPPORTED = -5,      /* inputs outside what the kernels handle */
+    TCW_ERR_DEVICE = -6,           /* a kernel reported an internal error */
+    TCW_ERR_TIMEOUT = -7           /* a bounded device wait ran out */
+};
+
+enum { TCW_HOST = 0, TCW_DEVICE = 1 };
+enum { TCW_F32 = 0, TCW_F16 = 1 };
+
+/* Search kernels.  TCW_KERNEL_AUTO picks the group kernel when its exactness
+ * conditions hold and the per-lookup kernel otherwise. */
+enum {
+    TCW_KERNEL_AUTO = 0,
+    TCW_KERNEL_GROUP = 1,   /* sky-group candidate-pair kernel (fast path) */
+    TCW_KERNEL_LOOKUP = 2   /* one thread per (sky, template), FP64 per lookup */
+};
+
+/* Options for tcw_set_option. */
+enum {
+    TCW_OPT_KERNEL = 1,        /* one of TCW_KERNEL_* */
+    TCW_OPT_KEEP_STATS = 2,    /* 1: keep S, W1, W2 of the last search for
+                                  tcw_get_statistics (costs 3*4 B per pair) */
+    TCW_OPT_TILE_SEGMENTS = 3  /* segments per tile of the group kernel */
+};
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * to run on, or NULL for a stream the context creates and owns.
+ * Errors: INVALID_ARGUMENT (out == NULL, bad device), CUDA. */
+tcw_status tcw_create(tcw_ctx **out, int device, void *cuda_stream);
+
+/* Free every device buffer and the owned stream.  NULL is accepted. */
+tcw_status tcw_destroy(tcw_ctx *ctx);
+
+/* Set an option (TCW_OPT_*).  Errors: INVALID_ARGUMENT. */
+tcw_status tcw_set_option(tcw_ctx *ctx, int option, int64_t value);
+
+/*
+ * Load the normalized-power spectrogram (Sec. 2: SFT data processed into
+ * normalized power rho_j) of n_det detectors that share segment times.
+ *   rho      [n_det][n_seg][n_bin], dtype TCW_F32 (float) or TCW_F16 (IEEE
+ *            half); bin k of segment j has centre f_min + k*df.
+ *   t_mid    [n_seg] segment mid-times (s), strictly increasing, finite.
+ *   weights  [n_det][n_seg] float, finite and >= 0 (the antenna-pattern and
+ *            noise-floor weights of Sec. 2), or NULL for all ones.
+ *   rho_flags applies to rho; t_mid and weights are always host pointers.
+ * Replaces any previous spectrogram and invalidates the loaded velocities
+ * when n_det or n_seg change.
+ * Errors: INVALID_ARGUMENT (sizes < 1, n_bin > 2^30, df <= 0, non-finite
+ * f_min, unsorted t_mid, bad weights, NULL), OUT_OF_MEMORY, CUDA. */
+tcw_status tcw_load_spectrogram(tcw_ctx *ctx, int n_det, int64_t n_seg, int64_t n_bin,
+                                int dtype, const void *rho, int rho_flags,
+                                double f_min, double df, const double *t_mid,
+                                const float *weights);
+
+/*
+ * Load detector velocities relative to the solar-system barycentre (Eq. 2),
+ *   v [n_det][n_seg][3] double, m/s, same frame as the sky vectors.
+ * Errors: STATE (no spectrogram), INVALID_ARGUMENT (NULL, non-finite,
+ * |v| >= c/100), CUDA. */
+tcw_status tcw_load_velocity(tcw_ctx *ctx, const double *v, int flags);
+
+/*
+ * Define the template bank (Eq. 1 parameters), [n_tmpl] doubles each:
+ * f0 > 0 (Hz), tau > 0 (s), n > 1 (Eq. 1 is singular at n = 1); and the
+ * signal start time T0 (s), shared by the bank.
+ * Errors: INVALID_ARGUMENT (n_tmpl < 1, n_tmpl > 2^31 - 1, NULL, a value out
+ * of range or non-finite), OUT_OF_MEMORY, CUDA. */
+tcw_status tcw_define_bank(tcw_ctx *ctx, int64_t n_tmpl, const double *f0,
+                           const double *tau, const double *n, double T0, int flags);
+
+/*
+ * Define the sky directions: nhat [n_sky][3] double unit vectors toward the
+ * source (|nhat| within 1e-9 of 1).
+ * Errors: INVALID_ARGUMENT (n_sky < 1, NULL, non-unit), OUT_OF_MEMORY, CUDA. */
+tcw_status tcw_define_sky(tcw_ctx *ctx, int64_t n_sky, const double *nhat, int flags);
+
+/*
+ * Run the search (track, Doppler, bin, gather, weighted sum, Psi, top-k) and
+ * write, per sky s in caller order, the k best templates:
+ *   psi_out [n_sky][k] float   Psi, descending
+ *   idx_out [n_sky][k] int64   caller template index (ties: ascending index)
+ * 1 <= k <= min(n_tmpl, 1024).  out_flags: TCW_HOST or TCW_DEVICE for both
+ * outputs.  The call returns after the device work has finished.
+ * Errors: STATE (missing spectrogram, velocity, bank or sky),
+ * INVALID_ARGUMENT, UNSUPPORTED (explicit group kernel requested but its
+ * exactness conditions fail), DEVICE, OUT_OF_MEMORY, CUDA. */
+tcw_status tcw_search(tcw_ctx *ctx, int k, float *psi_out, int64_t *idx_out, int out_flags);
+
+/*
+ * Statistics of the last search, [n_sky][n_tmpl] float in caller order (any
+ * pointer may be NULL): S, W1, W2 need TCW_OPT_KEEP_STATS = 1 during the
+ * search; psi is always available.
+ * Errors: STATE (no search, or stats not kept), INVALID_ARGUMENT, CUDA. */
+tcw_status tcw_get_statistics(tcw_ctx *ctx, float *S_out, float *W1_out, float *W2_out,
+                              float *psi_out, int out_flags);
+
+/*
+ * Bin index chosen by the search kernel for every lookup, written by the
+ * same kernel code with recording switched on:
+ *   bins_out [n_sky][n_tmpl][n_det][n_seg] int32, caller order, -1 where the
+ *   segment precedes T0 or the bin lies outside [0, n_bin).
+ * Meant for small problems (the output has n_sky*n_tmpl*n_det*n_seg entries).
+ * Errors: STATE, INVALID_ARGUMENT (output larger than 2^31 entries), CUDA. */
+tcw_status tcw_track_bins(tcw_ctx *ctx, int32_t *bins_out, int out_flags);
+
+/* Information about the last search. */
+typedef struct {
+    int kernel;                 /* TCW_KERNEL_GROUP or TCW_KERNEL_LOOKUP */
+    int launches;               /* kernels launched by the search */
+    int64_t lookups;            /* n_sky * n_tmpl * n_det * n_seg */
+    int64_t general_path_lanes; /* group-kernel (template, detector, segment,
+                                   sky-group) steps that took the per-sky path */
+    double doppler_bins_max;    /* largest |f * v.nhat/c| / df over the search */
+    double quantum;             /* fixed-point step of the Doppler factor */
+    float search_ms;            /* device time of the search kernel, ms */
+} tcw_info;
+
+tcw_status tcw_get_info(tcw_ctx *ctx, tcw_info *info);
+
+const char *tcw_status_string(tcw_status status);
+const char *tcw_last_error(tcw_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TCW_H */

@@ -1,0 +1,659 @@
+// tcw_api.cu -- C ABI, input validation and the host side of a search.
+//
+// A search (tcw_search) runs, on the context's stream:
+//   1. doppler_kernel   v.nhat/c per (detector, segment, sky)        [Eq. 2]
+//   2. group_kernel     track entries + gather + weighted sums + Psi [Eq. 1, Sec. 2, Eq. 4]
+//      (or lookup_kernel when the group kernel's exactness conditions fail)
+//   3. topk_kernel      per-sky top-k by (Psi desc, caller index asc)
+// The bank is sorted by f0 and the sky by its Doppler factor at the middle
+// segment; both permutations are undone on output.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "tcw_internal.cuh"
+
+using namespace tcw;
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaError_t ensure(size_t n) {
+    if (n <= bytes && p) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMalloc(&p, n ? n : 1);
+    if (e == cudaSuccess) bytes = n;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <typename T>
+  T* as() const { return static_cast<T*>(p); }
+};
+
+}  // namespace
+
+struct tcw_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string last_error;
+  // options
+  int opt_kernel = TCW_KERNEL_AUTO;
+  int keep_stats = 0;
+  int tile_segments = 32;
+  // spectrogram
+  bool have_spec = false;
+  int D = 0;
+  int64_t Nseg = 0, Nbin = 0;
+  int dtype = TCW_F32;
+  double f_min = 0, df = 0;
+  std::vector<double> h_t;
+  DevBuf rho, t_mid, weights;
+  // velocity
+  bool have_vel = false;
+  std::vector<double> h_v;
+  DevBuf vel;
+  // bank
+  bool have_bank = false;
+  int64_t B = 0;
+  int Bpad = 0;
+  double T0 = 0;
+  std::vector<double> h_f0, h_tau, h_n;
+  DevBuf f0, tau, nbr, bank_perm, bank_pos;
+  // sky
+  bool have_sky = false;
+  int64_t S = 0;
+  int Spad = 0, NG = 0;
+  std::vector<double> h_nhat;
+  bool sky_dirty = true;
+  DevBuf nhat_sorted, sky_perm, sky_pos;
+  // derived and outputs
+  DevBuf dq, gbound, psi, st_S, st_W1, st_W2, dev, flags, stage_f, stage_i;
+  bool have_result = false, stats_kept = false;
+  tcw_info info{};
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+tcw_status fail(tcw_ctx* c, tcw_status st, const std::string& msg) {
+  if (c) c->last_error = msg;
+  return st;
+}
+
+tcw_status cuda_fail(tcw_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return fail(c, TCW_ERR_OUT_OF_MEMORY, std::string(what) + ": out of device memory");
+  }
+  return fail(c, TCW_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define TCW_CUDA(c, expr, what)                     \
+  do {                                              \
+    cudaError_t e_ = (expr);                        \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+  } while (0)
+
+// Copy n bytes from caller memory (host or device) into a context buffer.
+cudaError_t upload(tcw_ctx* c, DevBuf& dst, const void* src, size_t n, int flags) {
+  cudaError_t e = dst.ensure(n);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(dst.p, src, n, flags == TCW_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                      c->stream);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(c->stream);
+}
+
+// Bring a small caller array to the host for validation.
+template <typename T>
+cudaError_t fetch(tcw_ctx* c, std::vector<T>& out, const T* src, size_t count, int flags) {
+  out.resize(count);
+  if (flags == TCW_DEVICE)
+    return cudaMemcpy(out.data(), src, count * sizeof(T), cudaMemcpyDeviceToHost);
+  std::memcpy(out.data(), src, count * sizeof(T));
+  return cudaSuccess;
+}
+
+bool finite_all(const std::vector<double>& v) {
+  for (double x : v)
+    if (!std::isfinite(x)) return false;
+  return true;
+}
+
+struct Plan {
+  int kernel = TCW_KERNEL_LOOKUP;
+  double q = 0, inv_q = 0, dmax = 0, fmax_bins = 0, doppler_bins = 0;
+  bool group_ok = false;
+  std::string why;
+};
+
+// Fixed-point step and the exactness conditions of the group kernel.
+Plan make_plan(const tcw_ctx* c) {
+  Plan pl;
+  double vmax = 0;
+  for (size_t i = 0; i + 2 < c->h_v.size(); i += 3)
+    vmax = std::max(vmax, std::sqrt(c->h_v[i] * c->h_v[i] + c->h_v[i + 1] * c->h_v[i + 1] +
+                                    c->h_v[i + 2] * c->h_v[i + 2]));
+  pl.dmax = vmax / kLightSpeed * (1.0 + 1e-12);
+  int e = -60;
+  if (pl.dmax > 0) e = (int)std::ceil(std::log2(pl.dmax / (2147483648.0 - 16777216.0)));
+  e = std::max(e, -80);
+  pl.q = std::ldexp(1.0, e);
+  pl.inv_q = std::ldexp(1.0, -e);
+  double f0max = 0;
+  for (double f : c->h_f0) f0max = std::max(f0max, f);
+  pl.fmax_bins = f0max * (1.0 + pl.dmax) / c->df;
+  pl.doppler_bins = pl.fmax_bins * pl.dmax;
+  const double tie_budget = 0.75 * std::ldexp(1.0, -30);
+  pl.group_ok = true;
+  if (pl.fmax_bins * pl.q * 0.5 > tie_budget) {
+    pl.group_ok = false;
+    pl.why = "fixed-point Doppler step too coarse for the bin width";
+  }
+  if (pl.doppler_bins > 2.9) {
+    pl.group_ok = false;
+    pl.why = "Doppler shift exceeds 2.9 bins";
+  }
+  if (c->Nbin > (int64_t)1 << 30 || c->B > INT32_MAX || c->S > INT32_MAX) {
+    pl.group_ok = false;
+    pl.why = "sizes beyond the group kernel's 32-bit indexing";
+  }
+  pl.kernel = pl.group_ok ? TCW_KERNEL_GROUP : TCW_KERNEL_LOOKUP;
+  return pl;
+}
+
+// Sort the sky by its Doppler factor at the middle segment of detector 0 and
+// upload the sorted, padded copy.
+tcw_status prepare_sky(tcw_ctx* c) {
+  if (!c->sky_dirty) return TCW_OK;
+  const int64_t S = c->S;
+  const int64_t jm = c->Nseg / 2;
+  const double* v = &c->h_v[(size_t)jm * 3];
+  std::vector<double> key(S);
+  for (int64_t s = 0; s < S; ++s)
+    key[s] = v[0] * c->h_nhat[3 * s] + v[1] * c->h_nhat[3 * s + 1] + v[2] * c->h_nhat[3 * s + 2];
+  std::vector<int32_t> perm(S);
+  std::iota(perm.begin(), perm.end(), 0);
+  std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
+  c->NG = (int)((S + kGroupSkies - 1) / kGroupSkies);
+  c->Spad = (int)(((int64_t)c->NG + kGroupLanes - 1) / kGroupLanes) * kSkyPad;
+  std::vector<double> ns((size_t)c->Spad * 3);
+  std::vector<int32_t> pos(S);
+  for (int i = 0; i < c->Spad; ++i) {
+    const int32_t src = perm[std::min<int64_t>(i, S - 1)];
+    for (int a = 0; a < 3; ++a) ns[(size_t)i * 3 + a] = c->h_nhat[(size_t)src * 3 + a];
+  }
+  for (int64_t i = 0; i < S; ++i) pos[perm[i]] = (int32_t)i;
+  TCW_CUDA(c, upload(c, c->nhat_sorted, ns.data(), ns.size() * sizeof(double), TCW_HOST), "sky upload");
+  TCW_CUDA(c, upload(c, c->sky_perm, perm.data(), perm.size() * sizeof(int32_t), TCW_HOST), "sky upload");
+  TCW_CUDA(c, upload(c, c->sky_pos, pos.data(), pos.size() * sizeof(int32_t), TCW_HOST), "sky upload");
+  c->sky_dirty = false;
+  return TCW_OK;
+}
+
+tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
+  if (!c->have_spec) return fail(c, TCW_ERR_STATE, "no spectrogram loaded");
+  if (!c->have_vel) return fail(c, TCW_ERR_STATE, "no velocities loaded");
+  if (!c->have_bank) return fail(c, TCW_ERR_STATE, "no template bank defined");
+  if (!c->have_sky) return fail(c, TCW_ERR_STATE, "no sky defined");
+  tcw_status st = prepare_sky(c);
+  if (st != TCW_OK) return st;
+  Plan pl = make_plan(c);
+  int kernel = c->opt_kernel;
+  if (kernel == TCW_KERNEL_AUTO) kernel = pl.kernel;
+  if (kernel == TCW_KERNEL_GROUP && !pl.group_ok)
+    return fail(c, TCW_ERR_UNSUPPORTED, "group kernel unavailable: " + pl.why);
+
+  const size_t pairs = (size_t)c->Spad * c->Bpad;
+  TCW_CUDA(c, c->psi.ensure(pairs * sizeof(float)), "psi buffer");
+  const bool keep = c->keep_stats != 0;
+  if (keep) {
+    TCW_CUDA(c, c->st_S.ensure(pairs * sizeof(float)), "stats buffer");
+    TCW_CUDA(c, c->st_W1.ensure(pairs * sizeof(float)), "stats buffer");
+    TCW_CUDA(c, c->st_W2.ensure(pairs * sizeof(float)), "stats buffer");
+  }
+  TCW_CUDA(c, c->flags.ensure(64), "flags");
+  TCW_CUDA(c, cudaMemsetAsync(c->flags.p, 0, 64, c->stream), "flags");
+  int launches = 0;
+
+  if (kernel == TCW_KERNEL_GROUP) {
+    const size_t dqn = (size_t)c->D * c->Nseg * c->Spad;
+    TCW_CUDA(c, c->dq.ensure(dqn * sizeof(int32_t)), "doppler table");
+    TCW_CUDA(c, c->gbound.ensure((size_t)c->D * c->Nseg * c->NG * sizeof(float2)), "doppler table");
+    TCW_CUDA(c, c->dev.ensure(pairs * sizeof(float2)), "scratch");
+    DopplerParams dp{};
+    dp.vel = c->vel.as<double>();
+    dp.nhat = c->nhat_sorted.as<double>();
+    dp.n_det = c->D;
+    dp.n_seg = (int)c->Nseg;
+    dp.Spad = c->Spad;
+    dp.NG = c->NG;
+    dp.group = kGroupSkies;
+    dp.inv_q = pl.inv_q;
+    dp.dq = c->dq.as<int32_t>();
+    dp.gbound = c->gbound.as<float2>();
+    TCW_CUDA(c, launch_doppler(dp, c->stream), "doppler_kernel launch");
+    ++launches;
+
+    GroupParams gp{};
+    gp.rho = c->rho.p;
+    gp.n_bin = c->Nbin;
+    gp.n_det = c->D;
+    gp.n_seg = (int)c->Nseg;
+    gp.weights = c->weights.as<float>();
+    gp.t_mid = c->t_mid.as<double>();
+    gp.dq = dp.dq;
+    gp.gbound = dp.gbound;
+    gp.f0 = c->f0.as<double>();
+    gp.tau = c->tau.as<double>();
+    gp.nbr = c->nbr.as<double>();
+    gp.T0 = c->T0;
+    gp.f_min = c->f_min;
+    gp.df = c->df;
+    gp.inv_q = pl.inv_q;
+    gp.B = (int)c->B;
+    gp.Bpad = c->Bpad;
+    gp.S = (int)c->S;
+    gp.Spad = c->Spad;
+    gp.NG = c->NG;
+    gp.psi = c->psi.as<float>();
+    gp.S_out = keep ? c->st_S.as<float>() : nullptr;
+    gp.W1_out = keep ? c->st_W1.as<float>() : nullptr;
+    gp.W2_out = keep ? c->st_W2.as<float>() : nullptr;
+    gp.dev = c->dev.as<float2>();
+    gp.rec = rec_dev;
+    gp.bank_perm = c->bank_perm.as<int32_t>();
+    gp.sky_perm = c->sky_perm.as<int32_t>();
+    gp.n_general = reinterpret_cast<unsigned long long*>(c->flags.as<char>() + 8);
+    gp.err = c->flags.as<int>();
+    TCW_CUDA(c, cudaEventRecord(c->ev0, c->stream), "event");
+    TCW_CUDA(c, launch_group(gp, c->dtype == TCW_F16, record, c->tile_segments, c->stream),
+             "group_kernel launch");
+    TCW_CUDA(c, cudaEventRecord(c->ev1, c->stream), "event");
+    ++launches;
+  } else {
+    LookupParams lp{};
+    lp.rho = c->rho.p;
+    lp.n_bin = c->Nbin;
+    lp.n_det = c->D;
+    lp.n_seg = (int)c->Nseg;
+    lp.weights = c->weights.as<float>();
+    lp.t_mid = c->t_mid.as<double>();
+    lp.vel = c->vel.as<double>();
+    lp.nhat = c->nhat_sorted.as<double>();
+    lp.f0 = c->f0.as<double>();
+    lp.tau = c->tau.as<double>();
+    lp.nbr = c->nbr.as<double>();
+    lp.T0 = c->T0;
+    lp.f_min = c->f_min;
+    lp.df = c->df;
+    lp.B = (int)c->B;
+    lp.Bpad = c->Bpad;
+    lp.S = (int)c->S;
+    lp.Spad = c->Spad;
+    lp.psi = c->psi.as<float>();
+    lp.S_out = keep ? c->st_S.as<float>() : nullptr;
+    lp.W1_out = keep ? c->st_W1.as<float>() : nullptr;
+    lp.W2_out = keep ? c->st_W2.as<float>() : nullptr;
+    lp.rec = rec_dev;
+    lp.bank_perm = c->bank_perm.as<int32_t>();
+    lp.sky_perm = c->sky_perm.as<int32_t>();
+    TCW_CUDA(c, cudaEventRecord(c->ev0, c->stream), "event");
+    TCW_CUDA(c, launch_lookup(lp, c->dtype == TCW_F16, record, c->stream), "lookup_kernel launch");
+    TCW_CUDA(c, cudaEventRecord(c->ev1, c->stream), "event");
+    ++launches;
+  }
+  c->info = tcw_info{};
+  c->info.kernel = kernel;
+  c->info.launches = launches;
+  c->info.lookups = (int64_t)c->S * c->B * c->D * c->Nseg;
+  c->info.doppler_bins_max = pl.doppler_bins;
+  c->info.quantum = pl.q;
+  c->stats_kept = keep;
+  return TCW_OK;
+}
+
+tcw_status finish(tcw_ctx* c) {
+  TCW_CUDA(c, cudaStreamSynchronize(c->stream), "search");
+  int64_t fl[2] = {0, 0};
+  TCW_CUDA(c, cudaMemcpy(fl, c->flags.p, sizeof(fl), cudaMemcpyDeviceToHost), "flags");
+  float ms = 0;
+  cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+  c->info.search_ms = ms;
+  c->info.general_path_lanes = fl[1];
+  if ((int)(fl[0] & 0xffffffff) != 0) {
+    c->have_result = false;
+    return fail(c, TCW_ERR_DEVICE, "search kernel: candidate bins outside the threshold window");
+  }
+  c->have_result = true;
+  return TCW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* tcw_status_string(tcw_status s) {
+  switch (s) {
+    case TCW_OK: return "ok";
+    case TCW_ERR_INVALID_ARGUMENT: return "invalid argument";
+    case TCW_ERR_CUDA: return "CUDA error";
+    case TCW_ERR_OUT_OF_MEMORY: return "out of device memory";
+    case TCW_ERR_STATE: return "required input not loaded";
+    case TCW_ERR_UNSUPPORTED: return "unsupported input";
+    case TCW_ERR_DEVICE: return "device-side error";
+    case TCW_ERR_TIMEOUT: return "device wait timed out";
+    default: return "unknown status";
+  }
+}
+
+const char* tcw_last_error(tcw_ctx* c) { return c ? c->last_error.c_str() : "null context"; }
+
+tcw_status tcw_create(tcw_ctx** out, int device, void* stream) {
+  if (!out) return TCW_ERR_INVALID_ARGUMENT;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess) {
+    cudaGetLastError();
+    return TCW_ERR_CUDA;
+  }
+  if (device < 0 || device >= n) return TCW_ERR_INVALID_ARGUMENT;
+  if (cudaSetDevice(device) != cudaSuccess) return TCW_ERR_CUDA;
+  tcw_ctx* c = new tcw_ctx();
+  c->device = device;
+  if (stream) {
+    c->stream = static_cast<cudaStream_t>(stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return TCW_ERR_CUDA;
+    }
+    c->own_stream = true;
+  }
+  if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return TCW_ERR_CUDA;
+  }
+  *out = c;
+  return TCW_OK;
+}
+
+tcw_status tcw_destroy(tcw_ctx* c) {
+  if (!c) return TCW_OK;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  DevBuf* bufs[] = {&c->rho, &c->t_mid, &c->weights, &c->vel, &c->f0, &c->tau, &c->nbr,
+                    &c->bank_perm, &c->bank_pos, &c->nhat_sorted, &c->sky_perm, &c->sky_pos,
+                    &c->dq, &c->gbound, &c->psi, &c->st_S, &c->st_W1, &c->st_W2, &c->dev,
+                    &c->flags, &c->stage_f, &c->stage_i};
+  for (DevBuf* b : bufs) b->release();
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->own_stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return TCW_OK;
+}
+
+tcw_status tcw_set_option(tcw_ctx* c, int option, int64_t value) {
+  if (!c) return TCW_ERR_INVALID_ARGUMENT;
+  switch (option) {
+    case TCW_OPT_KERNEL:
+      if (value < TCW_KERNEL_AUTO || value > TCW_KERNEL_LOOKUP)
+        return fail(c, TCW_ERR_INVALID_ARGUMENT, "unknown kernel");
+      c->opt_kernel = (int)value;
+      return TCW_OK;
+    case TCW_OPT_KEEP_STATS:
+      c->keep_stats = value ? 1 : 0;
+      return TCW_OK;
+    case TCW_OPT_TILE_SEGMENTS:
+      if (value != 32) return fail(c, TCW_ERR_INVALID_ARGUMENT, "tile_segments must be 32");
+      c->tile_segments = (int)value;
+      return TCW_OK;
+    default:
+      return fail(c, TCW_ERR_INVALID_ARGUMENT, "unknown option");
+  }
+}
+
+tcw_status tcw_load_spectrogram(tcw_ctx* c, int n_det, int64_t n_seg, int64_t n_bin, int dtype,
+                                const void* rho, int rho_flags, double f_min, double df,
+                                const double* t_mid, const float* weights) {
+  if (!c) return TCW_ERR_INVALID_ARGUMENT;
+  if (n_det < 1 || n_det > kMaxDet) return fail(c, TCW_ERR_INVALID_ARGUMENT, "n_det must be in [1, 8]");
+  if (n_seg < 1 || n_seg > INT32_MAX) return fail(c, TCW_ERR_INVALID_ARGUMENT, "n_seg out of range");
+  if (n_bin < 1 || n_bin > ((int64_t)1 << 30)) return fail(c, TCW_ERR_INVALID_ARGUMENT, "n_bin out of range");
+  if (dtype != TCW_F32 && dtype != TCW_F16) return fail(c, TCW_ERR_INVALID_ARGUMENT, "unknown dtype");
+  if (!rho || !t_mid) return fail(c, TCW_ERR_INVALID_ARGUMENT, "null pointer");
+  if (rho_flags != TCW_HOST && rho_flags != TCW_DEVICE) return fail(c, TCW_ERR_INVALID_ARGUMENT, "bad flags");
+  if (!std::isfinite(f_min) || !(df > 0) || !std::isfinite(df))
+    return fail(c, TCW_ERR_INVALID_ARGUMENT, "f_min must be finite and df > 0");
+  cudaSetDevice(c->device);
+  std::vector<double> t(t_mid, t_mid + n_seg);
+  for (int64_t j = 0; j < n_seg; ++j) {
+    if (!std::isfinite(t[j])) return fail(c, TCW_ERR_INVALID_ARGUMENT, "non-finite t_mid");
+    if (j && !(t[j] > t[j - 1])) return fail(c, TCW_ERR_INVALID_ARGUMENT, "t_mid must increase strictly");
+  }
+  std::vector<float> w((size_t)n_det * n_seg, 1.0f);
+  if (weights) {
+    for (size_t i = 0; i < w.size(); ++i) {
+      w[i] = weights[i];
+      if (!std::isfinite(w[i]) || w[i] < 0) return fail(c, TCW_ERR_INVALID_ARGUMENT, "weights must be finite and >= 0");
+    }
+  }
+  const size_t esz = dtype == TCW_F16 ? 2 : 4;
+  const size_t bytes = (size_t)n_det * n_seg * n_bin * esz;
+  TCW_CUDA(c, upload(c, c->rho, rho, bytes, rho_flags), "spectrogram upload");
+  TCW_CUDA(c, upload(c, c->t_mid, t.data(), t.size() * sizeof(double), TCW_HOST), "t_mid upload");
+  TCW_CUDA(c, upload(c, c->weights, w.data(), w.size() * sizeof(float), TCW_HOST), "weights upload");
+  if (c->have_vel && (n_det != c->D || n_seg != c->Nseg)) c->have_vel = false;
+  c->D = n_det;
+  c->Nseg = n_seg;
+  c->Nbin = n_bin;
+  c->dtype = dtype;
+  c->f_min = f_min;
+  c->df = df;
+  c->h_t = std::move(t);
+  c->have_spec = true;
+  c->have_result = false;
+  c->sky_dirty = true;
+  return TCW_OK;
+}
+
+tcw_status tcw_load_velocity(tcw_ctx* c, const double* v, int flags) {
+  if (!c) return TCW_ERR_INVALID_ARGUMENT;
+  if (!c->have_spec) return fail(c, TCW_ERR_STATE, "load the spectrogram first");
+  if (!v) return fail(c, TCW_ERR_INVALID_ARGUMENT, "null pointer");
+  if (flags != TCW_HOST && flags != TCW_DEVICE) return fail(c, TCW_ERR_INVALID_ARGUMENT, "bad flags");
+  cudaSetDevice(c->device);
+  const size_t n = (size_t)c->D * c->Nseg * 3;
+  std::vector<double> hv;
+  TCW_CUDA(c, fetch(c, hv, v, n, flags), "velocity fetch");
+  for (size_t i = 0; i < n; i += 3) {
+    if (!std::isfinite(hv[i]) || !std::isfinite(hv[i + 1]) || !std::isfinite(hv[i + 2]))
+      return fail(c, TCW_ERR_INVALID_ARGUMENT, "non-finite velocity");
+    if (std::sqrt(hv[i] * hv[i] + hv[i + 1] * hv[i + 1] + hv[i + 2] * hv[i + 2]) >= kLightSpeed / 100)
+      return fail(c, TCW_ERR_INVALID_ARGUMENT, "velocity must be below c/100");
+  }
+  TCW_CUDA(c, upload(c, c->vel, hv.data(), n * sizeof(double), TCW_HOST), "velocity upload");
+  c->h_v = std::move(hv);
+  c->have_vel = true;
+  c->have_result = false;
+  c->sky_dirty = true;
+  return TCW_OK;
+}
+
+tcw_status tcw_define_bank(tcw_ctx* c, int64_t n_tmpl, const double* f0, const double* tau,
+                           const double* n, double T0, int flags) {
+  if (!c) return TCW_ERR_INVALID_ARGUMENT;
+  if (n_tmpl < 1 || n_tmpl > INT32_MAX - 64) return fail(c, TCW_ERR_INVALID_ARGUMENT, "n_tmpl out of range");
+  if (!f0 || !tau || !n) return fail(c, TCW_ERR_INVALID_ARGUMENT, "null pointer");
+  if (flags != TCW_HOST && flags != TCW_DEVICE) return fail(c, TCW_ERR_INVALID_ARGUMENT, "bad flags");
+  if (!std::isfinite(T0)) return fail(c, TCW_ERR_INVALID_ARGUMENT, "non-finite T0");
+  cudaSetDevice(c->device);
+  std::vector<double> hf, ht, hn;
+  TCW_CUDA(c, fetch(c, hf, f0, (size_t)n_tmpl, flags), "bank fetch");
+  TCW_CUDA(c, fetch(c, ht, tau, (size_t)n_tmpl, flags), "bank fetch");
+  TCW_CUDA(c, fetch(c, hn, n, (size_t)n_tmpl, flags), "bank fetch");
+  if (!finite_all(hf) || !finite_all(ht) || !finite_all(hn))
+    return fail(c, TCW_ERR_INVALID_ARGUMENT, "non-finite template parameter");
+  for (int64_t b = 0; b < n_tmpl; ++b) {
+    if (!(hf[b] > 0)) return fail(c, TCW_ERR_INVALID_ARGUMENT, "f0 must be > 0");
+    if (!(ht[b] > 0)) return fail(c, TCW_ERR_INVALID_ARGUMENT, "tau must be > 0");
+    if (!(hn[b] > 1)) return fail(c, TCW_ERR_INVALID_ARGUMENT, "n must be > 1 (Eq. 1 is singular at n = 1)");
+  }
+  std::vector<int32_t> perm(n_tmpl);
+  std::iota(perm.begin(), perm.end(), 0);
+  std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) { return hf[a] < hf[b]; });
+  const int Bpad = (int)((n_tmpl + kGroupTmplPerCta - 1) / kGroupTmplPerCta) * kGroupTmplPerCta;
+  std::vector<double> sf(Bpad), st(Bpad), sn(Bpad);
+  std::vector<int32_t> pos(n_tmpl), permp(Bpad);
+  for (int i = 0; i < Bpad; ++i) {
+    const int32_t src = perm[std::min<int64_t>(i, n_tmpl - 1)];
+    sf[i] = hf[src];
+    st[i] = ht[src];
+    sn[i] = hn[src];
+    permp[i] = src;
+  }
+  for (int64_t i = 0; i < n_tmpl; ++i) pos[perm[i]] = (int32_t)i;
+  TCW_CUDA(c, upload(c, c->f0, sf.data(), Bpad * sizeof(double), TCW_HOST), "bank upload");
+  TCW_CUDA(c, upload(c, c->tau, st.data(), Bpad * sizeof(double), TCW_HOST), "bank upload");
+  TCW_CUDA(c, upload(c, c->nbr, sn.data(), Bpad * sizeof(double), TCW_HOST), "bank upload");
+  TCW_CUDA(c, upload(c, c->bank_perm, permp.data(), Bpad * sizeof(int32_t), TCW_HOST), "bank upload");
+  TCW_CUDA(c, upload(c, c->bank_pos, pos.data(), n_tmpl * sizeof(int32_t), TCW_HOST), "bank upload");
+  c->B = n_tmpl;
+  c->Bpad = Bpad;
+  c->T0 = T0;
+  c->h_f0 = std::move(hf);
+  c->h_tau = std::move(ht);
+  c->h_n = std::move(hn);
+  c->have_bank = true;
+  c->have_result = false;
+  return TCW_OK;
+}
+
+tcw_status tcw_define_sky(tcw_ctx* c, int64_t n_sky, const double* nhat, int flags) {
+  if (!c) return TCW_ERR_INVALID_ARGUMENT;
+  if (n_sky < 1 || n_sky > (int64_t)1 << 24) return fail(c, TCW_ERR_INVALID_ARGUMENT, "n_sky out of range");
+  if (!nhat) return fail(c, TCW_ERR_INVALID_ARGUMENT, "null pointer");
+  if (flags != TCW_HOST && flags != TCW_DEVICE) return fail(c, TCW_ERR_INVALID_ARGUMENT, "bad flags");
+  cudaSetDevice(c->device);
+  std::vector<double> h;
+  TCW_CUDA(c, fetch(c, h, nhat, (size_t)n_sky * 3, flags), "sky fetch");
+  for (int64_t s = 0; s < n_sky; ++s) {
+    const double x = h[3 * s], y = h[3 * s + 1], z = h[3 * s + 2];
+    if (!std::isfinite(x) || !std::isfinite(y) || !std::isfinite(z))
+      return fail(c, TCW_ERR_INVALID_ARGUMENT, "non-finite sky vector");
+    if (std::fabs(std::sqrt(x * x + y * y + z * z) - 1.0) > 1e-9)
+      return fail(c, TCW_ERR_INVALID_ARGUMENT, "sky vectors must be unit (within 1e-9)");
+  }
+  c->S = n_sky;
+  c->h_nhat = std::move(h);
+  c->have_sky = true;
+  c->sky_dirty = true;
+  c->have_result = false;
+  return TCW_OK;
+}
+
+tcw_status tcw_search(tcw_ctx* c, int k, float* psi_out, int64_t* idx_out, int out_flags) {
+  if (!c) return TCW_ERR_INVALID_ARGUMENT;
+  if (!psi_out || !idx_out) return fail(c, TCW_ERR_INVALID_ARGUMENT, "null output");
+  if (out_flags != TCW_HOST && out_flags != TCW_DEVICE) return fail(c, TCW_ERR_INVALID_ARGUMENT, "bad flags");
+  if (!c->have_bank) return fail(c, TCW_ERR_STATE, "no template bank defined");
+  if (k < 1 || k > 1024 || (int64_t)k > c->B)
+    return fail(c, TCW_ERR_INVALID_ARGUMENT, "k must be in [1, min(n_tmpl, 1024)]");
+  cudaSetDevice(c->device);
+  tcw_status st = run_search(c, false, nullptr);
+  if (st != TCW_OK) return st;
+  float* dpsi = psi_out;
+  int64_t* didx = idx_out;
+  const size_t n = (size_t)c->S * k;
+  if (out_flags == TCW_HOST) {
+    TCW_CUDA(c, c->stage_f.ensure(n * sizeof(float)), "staging");
+    TCW_CUDA(c, c->stage_i.ensure(n * sizeof(int64_t)), "staging");
+    dpsi = c->stage_f.as<float>();
+    didx = c->stage_i.as<int64_t>();
+  }
+  TCW_CUDA(c, launch_topk(c->psi.as<float>(), c->Bpad, (int)c->B, (int)c->S, k,
+                          c->bank_perm.as<int32_t>(), c->sky_perm.as<int32_t>(), dpsi, didx, c->stream),
+           "topk_kernel launch");
+  c->info.launches += 1;
+  if (out_flags == TCW_HOST) {
+    TCW_CUDA(c, cudaMemcpyAsync(psi_out, dpsi, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream), "copy out");
+    TCW_CUDA(c, cudaMemcpyAsync(idx_out, didx, n * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream), "copy out");
+  }
+  return finish(c);
+}
+
+tcw_status tcw_get_statistics(tcw_ctx* c, float* S_out, float* W1_out, float* W2_out, float* psi_out,
+                              int out_flags) {
+  if (!c) return TCW_ERR_INVALID_ARGUMENT;
+  if (out_flags != TCW_HOST && out_flags != TCW_DEVICE) return fail(c, TCW_ERR_INVALID_ARGUMENT, "bad flags");
+  if (!c->have_result) return fail(c, TCW_ERR_STATE, "no completed search");
+  if ((S_out || W1_out || W2_out) && !c->stats_kept)
+    return fail(c, TCW_ERR_STATE, "statistics not kept (set TCW_OPT_KEEP_STATS before searching)");
+  cudaSetDevice(c->device);
+  const size_t n = (size_t)c->S * c->B;
+  float* outs[4] = {S_out, W1_out, W2_out, psi_out};
+  DevBuf* srcs[4] = {&c->st_S, &c->st_W1, &c->st_W2, &c->psi};
+  for (int i = 0; i < 4; ++i) {
+    if (!outs[i]) continue;
+    float* dst = outs[i];
+    if (out_flags == TCW_HOST) {
+      TCW_CUDA(c, c->stage_f.ensure(n * sizeof(float)), "staging");
+      dst = c->stage_f.as<float>();
+    }
+    TCW_CUDA(c, launch_unpermute(srcs[i]->as<float>(), c->Spad, c->Bpad, (int)c->S, (int)c->B,
+                                 c->sky_pos.as<int32_t>(), c->bank_pos.as<int32_t>(), dst, c->stream),
+             "unpermute launch");
+    if (out_flags == TCW_HOST)
+      TCW_CUDA(c, cudaMemcpyAsync(outs[i], dst, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream), "copy out");
+    TCW_CUDA(c, cudaStreamSynchronize(c->stream), "statistics");
+  }
+  return TCW_OK;
+}
+
+tcw_status tcw_track_bins(tcw_ctx* c, int32_t* bins_out, int out_flags) {
+  if (!c) return TCW_ERR_INVALID_ARGUMENT;
+  if (!bins_out) return fail(c, TCW_ERR_INVALID_ARGUMENT, "null output");
+  if (out_flags != TCW_HOST && out_flags != TCW_DEVICE) return fail(c, TCW_ERR_INVALID_ARGUMENT, "bad flags");
+  if (!c->have_spec || !c->have_bank || !c->have_sky) return fail(c, TCW_ERR_STATE, "inputs not loaded");
+  const int64_t n = c->S * c->B * c->D * c->Nseg;
+  if (n > INT32_MAX) return fail(c, TCW_ERR_INVALID_ARGUMENT, "problem too large for tcw_track_bins");
+  cudaSetDevice(c->device);
+  int32_t* dst = bins_out;
+  DevBuf tmp;
+  if (out_flags == TCW_HOST) {
+    TCW_CUDA(c, tmp.ensure((size_t)n * sizeof(int32_t)), "bins buffer");
+    dst = tmp.as<int32_t>();
+  }
+  tcw_status st = run_search(c, true, dst);
+  if (st == TCW_OK && out_flags == TCW_HOST) {
+    cudaError_t e = cudaMemcpyAsync(bins_out, dst, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) st = cuda_fail(c, e, "copy out");
+  }
+  if (st == TCW_OK) st = finish(c);
+  cudaStreamSynchronize(c->stream);
+  tmp.release();
+  return st;
+}
+
+tcw_status tcw_get_info(tcw_ctx* c, tcw_info* info) {
+  if (!c || !info) return TCW_ERR_INVALID_ARGUMENT;
+  *info = c->info;
+  return TCW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,129 @@
+// tcw_internal.cuh -- shared declarations of the sm_103a track-statistic library.
+//
+// Method (arXiv:2507.07816): Eq. 1 track, Eq. 2 Doppler factor, nearest-bin
+// lookup of the normalized power, weighted sum over segments (Sec. 2) and the
+// critical ratio of Eq. 4.  The kernels are organised around one exact
+// reformulation of the bin decision:
+//
+//   a sky s lands above the boundary between bins K and K+1 (frequency
+//   c_K = f_min + (K + 1/2) df) iff  fhat >= c_K  iff  v.nhat/c >= c_K/f - 1.
+//
+// The left side depends on (detector, segment, sky) only, the right side on
+// (template, segment, K) only.  Both are rounded once to an integer grid of
+// step q (the left with floor, the right with round), so the decision becomes
+// one int32 compare per lookup and differs from the exact real decision only
+// when the track lies within F*q/2 bins of the boundary, F = f/df.  The host
+// picks q so that F*q/2 stays below 0.75 * 2^-30 bins.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/tcw.h"
+
+namespace tcw {
+
+constexpr double kLightSpeed = 299792458.0;  // m/s
+constexpr int kMaxDet = 8;
+
+// Bin window of the group kernel, relative to a per-(template, segment) base
+// bin: candidates base + m for m in [kMLo, kMHi]; threshold i separates
+// base + kMLo + i from base + kMLo + i + 1.
+constexpr int kMLo = -4;
+constexpr int kMHi = 4;
+constexpr int kNThr = kMHi - kMLo;  // 8 thresholds
+
+// Precomputed per (template, segment): 48 bytes, lives in shared memory.
+struct __align__(16) TrackEntry {
+  int base;      // base bin (nearest centre of the undoppled track); INT_MIN = no lookups
+  float C;       // (f - f_min)/df - base, fp32 estimate
+  float F;       // f/df, fp32 estimate
+  int pad;
+  int th[kNThr]; // round(threshold/q), clamped to int32
+};
+
+struct GroupParams {
+  const void* rho;         // [D][Nseg][Nbin] float or half
+  int64_t n_bin;
+  int n_det;
+  int n_seg;
+  const float* weights;    // [D][Nseg]
+  const double* t_mid;     // [Nseg]
+  const int32_t* dq;       // [D][Nseg][Spad] floor(v.nhat/c / q)
+  const float2* gbound;    // [D][Nseg][NG] min/max of v.nhat/c over each sky group
+  const double* f0;        // sorted bank, [Bpad]
+  const double* tau;
+  const double* nbr;
+  double T0, f_min, df, inv_q;
+  int B, Bpad, S, Spad, NG;
+  float* psi;              // [Spad][Bpad]
+  float* S_out;            // optional [Spad][Bpad]
+  float* W1_out;
+  float* W2_out;
+  float2* dev;             // scratch [Bpad][Spad]: per-sky weight sums of per-sky-path lookups
+  int32_t* rec;            // optional [S][B][D][Nseg], caller order
+  const int32_t* bank_perm;  // sorted -> caller template index
+  const int32_t* sky_perm;   // sorted -> caller sky index
+  unsigned long long* n_general;
+  int* err;
+};
+
+struct LookupParams {
+  const void* rho;
+  int64_t n_bin;
+  int n_det;
+  int n_seg;
+  const float* weights;
+  const double* t_mid;
+  const double* vel;       // [D][Nseg][3]
+  const double* nhat;      // sorted sky [Spad][3]
+  const double* f0;
+  const double* tau;
+  const double* nbr;
+  double T0, f_min, df;
+  int B, Bpad, S, Spad;
+  float* psi;
+  float* S_out;
+  float* W1_out;
+  float* W2_out;
+  int32_t* rec;
+  const int32_t* bank_perm;
+  const int32_t* sky_perm;
+};
+
+struct DopplerParams {
+  const double* vel;       // [D][Nseg][3]
+  const double* nhat;      // [Spad][3] sorted
+  int n_det, n_seg, Spad, NG, group;
+  double inv_q;
+  int32_t* dq;
+  float2* gbound;
+};
+
+// launchers (return cudaError_t of the launch)
+cudaError_t launch_doppler(const DopplerParams& p, cudaStream_t st);
+cudaError_t launch_group(const GroupParams& p, bool half, bool record, int tile_segments,
+                         cudaStream_t st);
+cudaError_t launch_lookup(const LookupParams& p, bool half, bool record, cudaStream_t st);
+cudaError_t launch_topk(const float* psi, int Bpad, int B, int S, int k, const int32_t* bank_perm,
+                        const int32_t* sky_perm, float* psi_out, int64_t* idx_out,
+                        cudaStream_t st);
+cudaError_t launch_unpermute(const float* src, int Spad, int Bpad, int S, int B,
+                             const int32_t* sky_pos, const int32_t* bank_pos, float* dst,
+                             cudaStream_t st);
+
+// group-kernel geometry (shared by the host planner and the kernel)
+constexpr int kGroupSkies = 16;     // skies per thread
+constexpr int kGroupTmpl = 2;       // templates per thread
+constexpr int kGroupUnits = 4;      // template pairs per CTA
+constexpr int kGroupWarps = 2;      // warps per unit
+constexpr int kGroupLanes = 32 * kGroupWarps;             // sky groups per CTA
+constexpr int kGroupThreads = kGroupUnits * kGroupLanes;  // 256
+constexpr int kGroupTmplPerCta = kGroupUnits * kGroupTmpl;  // 8
+constexpr int kSkyPad = kGroupSkies * kGroupLanes;        // 1024
+
+}  // namespace tcw

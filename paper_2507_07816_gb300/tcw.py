@@ -1,0 +1,232 @@
+"""Python binding of the C ABI in ``include/tcw.h`` (argument marshalling only).
+
+Every step of the search runs in the CUDA library ``_build/libtcw.so``; this
+module converts numpy arrays (host memory) or CUDA torch tensors (device
+memory) into pointers and sizes, and raises ``TcwError`` on a non-zero status.
+There is no CPU fallback: without the library every call fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+OK = 0
+HOST, DEVICE = 0, 1
+F32, F16 = 0, 1
+KERNEL_AUTO, KERNEL_GROUP, KERNEL_LOOKUP = 0, 1, 2
+OPT_KERNEL, OPT_KEEP_STATS, OPT_TILE_SEGMENTS = 1, 2, 3
+
+_lock = threading.Lock()
+_lib = None
+
+
+class TcwError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"tcw status {status}: {message}")
+        self.status = status
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int), ("launches", ctypes.c_int), ("lookups", ctypes.c_int64),
+                ("general_path_lanes", ctypes.c_int64), ("doppler_bins_max", ctypes.c_double),
+                ("quantum", ctypes.c_double), ("search_ms", ctypes.c_float)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True):
+    """Load the CUDA library, compiling it first when it is missing or stale."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(path):
+            raise TcwError(-100, f"CUDA library not built: {path}")
+        lib = ctypes.CDLL(path)
+        p, i, i64, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+        sig = {
+            "tcw_create": [ctypes.POINTER(p), i, p],
+            "tcw_destroy": [p],
+            "tcw_set_option": [p, i, i64],
+            "tcw_load_spectrogram": [p, i, i64, i64, i, p, i, d, d, p, p],
+            "tcw_load_velocity": [p, p, i],
+            "tcw_define_bank": [p, i64, p, p, p, d, i],
+            "tcw_define_sky": [p, i64, p, i],
+            "tcw_search": [p, i, p, p, i],
+            "tcw_get_statistics": [p, p, p, p, p, i],
+            "tcw_track_bins": [p, p, i],
+            "tcw_get_info": [p, ctypes.POINTER(_Info)],
+        }
+        for name, args in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = i
+        lib.tcw_status_string.argtypes = [i]
+        lib.tcw_status_string.restype = ctypes.c_char_p
+        lib.tcw_last_error.argtypes = [p]
+        lib.tcw_last_error.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def _is_torch(a):
+    return type(a).__module__.startswith("torch")
+
+
+def _arg(a, dtype):
+    """(pointer, flags, keepalive) for a numpy array or a CUDA torch tensor."""
+    if a is None:
+        return None, HOST, None
+    if _is_torch(a):
+        if not a.is_cuda:
+            a = a.detach().cpu().numpy()
+        else:
+            import torch
+            tdt = {np.float32: torch.float32, np.float64: torch.float64, np.float16: torch.float16,
+                   np.int64: torch.int64, np.int32: torch.int32}[np.dtype(dtype).type]
+            if a.dtype != tdt:
+                raise TypeError(f"expected {tdt}, got {a.dtype}")
+            a = a.contiguous()
+            return ctypes.c_void_p(a.data_ptr()), DEVICE, a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr.ctypes.data_as(ctypes.c_void_p), HOST, arr
+
+
+@dataclass
+class Info:
+    kernel: int
+    launches: int
+    lookups: int
+    general_path_lanes: int
+    doppler_bins_max: float
+    quantum: float
+    search_ms: float
+
+
+class Search:
+    """One search context (``tcw_ctx``) on one CUDA device and stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self._lib = load_library()
+        self._h = ctypes.c_void_p()
+        st = None if stream is None else ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+        self._check(self._lib.tcw_create(ctypes.byref(self._h), int(device), st), ctx=False)
+        self.n_sky = self.n_tmpl = self.n_det = self.n_seg = self.n_bin = 0
+
+    def _check(self, status, ctx=True):
+        if status != OK:
+            msg = self._lib.tcw_status_string(status).decode()
+            if ctx and self._h:
+                msg += ": " + self._lib.tcw_last_error(self._h).decode()
+            raise TcwError(status, msg)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.tcw_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_option(self, option: int, value: int):
+        self._check(self._lib.tcw_set_option(self._h, option, int(value)))
+
+    def load_spectrogram(self, rho, f_min, df, t_mid, weights=None):
+        dt = np.float16 if str(getattr(rho, "dtype", "")).endswith("float16") else np.float32
+        D, Nseg, Nbin = rho.shape
+        rp, rf, keep = _arg(rho, dt)
+        t = np.ascontiguousarray(np.asarray(t_mid, np.float64))
+        w = None if weights is None else np.ascontiguousarray(np.asarray(weights, np.float32))
+        if w is not None and w.shape != (D, Nseg):
+            raise ValueError("weights must be [n_det][n_seg]")
+        if t.shape != (Nseg,):
+            raise ValueError("t_mid must be [n_seg]")
+        self._check(self._lib.tcw_load_spectrogram(
+            self._h, int(D), int(Nseg), int(Nbin), F16 if dt == np.float16 else F32, rp, rf,
+            float(f_min), float(df), t.ctypes.data_as(ctypes.c_void_p),
+            None if w is None else w.ctypes.data_as(ctypes.c_void_p)))
+        self.n_det, self.n_seg, self.n_bin = int(D), int(Nseg), int(Nbin)
+
+    def load_velocity(self, v):
+        if tuple(v.shape) != (self.n_det, self.n_seg, 3):
+            raise ValueError("velocity must be [n_det][n_seg][3]")
+        p, f, keep = _arg(v, np.float64)
+        self._check(self._lib.tcw_load_velocity(self._h, p, f))
+
+    def define_bank(self, f0, tau, n, T0):
+        a = [_arg(x, np.float64) for x in (f0, tau, n)]
+        if not (len(f0) == len(tau) == len(n)):
+            raise ValueError("bank arrays differ in length")
+        if len({x[1] for x in a}) != 1:
+            raise ValueError("bank arrays must all be on the host or all on the device")
+        self._check(self._lib.tcw_define_bank(self._h, int(len(f0)), a[0][0], a[1][0], a[2][0],
+                                              float(T0), a[0][1]))
+        self.n_tmpl = int(len(f0))
+
+    def define_sky(self, nhat):
+        p, f, keep = _arg(nhat, np.float64)
+        self._check(self._lib.tcw_define_sky(self._h, int(nhat.shape[0]), p, f))
+        self.n_sky = int(nhat.shape[0])
+
+    def search(self, k, psi_out=None, idx_out=None):
+        """Top-k per sky: returns (psi [S][k] float32, idx [S][k] int64).
+
+        With torch CUDA tensors as outputs the results stay on the device."""
+        if psi_out is None:
+            psi_out = np.empty((self.n_sky, k), np.float32)
+            idx_out = np.empty((self.n_sky, k), np.int64)
+        pp, pf, _ = _arg(psi_out, np.float32)
+        ip, iff, _ = _arg(idx_out, np.int64)
+        if pf != iff:
+            raise ValueError("outputs must both be host or both device")
+        if pf == HOST and (not isinstance(psi_out, np.ndarray) or psi_out.dtype != np.float32
+                           or not psi_out.flags.c_contiguous):
+            raise TypeError("host outputs must be C-contiguous numpy arrays")
+        self._check(self._lib.tcw_search(self._h, int(k), pp, ip, pf))
+        return psi_out, idx_out
+
+    def statistics(self, which=("S", "W1", "W2", "psi")):
+        outs = {w: np.empty((self.n_sky, self.n_tmpl), np.float32) for w in which}
+        ptr = {w: (outs[w].ctypes.data_as(ctypes.c_void_p) if w in outs else None)
+               for w in ("S", "W1", "W2", "psi")}
+        self._check(self._lib.tcw_get_statistics(self._h, ptr["S"], ptr["W1"], ptr["W2"],
+                                                 ptr["psi"], HOST))
+        return outs
+
+    def track_bins(self):
+        out = np.empty((self.n_sky, self.n_tmpl, self.n_det, self.n_seg), np.int32)
+        self._check(self._lib.tcw_track_bins(self._h, out.ctypes.data_as(ctypes.c_void_p), HOST))
+        return out
+
+    def info(self) -> Info:
+        i = _Info()
+        self._check(self._lib.tcw_get_info(self._h, ctypes.byref(i)))
+        return Info(i.kernel, i.launches, i.lookups, i.general_path_lanes, i.doppler_bins_max,
+                    i.quantum, i.search_ms)
+
+    def load_problem(self, prob):
+        """Load an object with rho, f_min, df, t_mid, weights, velocity, bank, T0, nhat."""
+        self.load_spectrogram(prob.rho, prob.f_min, prob.df, prob.t_mid, prob.weights)
+        self.load_velocity(prob.velocity)
+        self.define_bank(prob.bank.f0, prob.bank.tau, prob.bank.n, prob.T0)
+        self.define_sky(prob.nhat)
