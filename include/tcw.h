@@ -158,6 +158,43 @@ tcw_status tcw_get_statistics(tcw_ctx *ctx, float *S_out, float *W1_out, float *
  * Errors: STATE, INVALID_ARGUMENT (output larger than 2^31 entries), CUDA. */
 tcw_status tcw_track_bins(tcw_ctx *ctx, int32_t *bins_out, int out_flags);
 
+/*
+ * Search without any device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc -- for example
+ * an application whose device memory is wholly owned by its own arena or
+ * caching allocator, a real-time pipeline that cannot accept the implicit
+ * device synchronisation of cudaMalloc/cudaFree, or a plug-in host that
+ * forbids device allocation.
+ *
+ * It runs the same Doppler-table, group and top-k kernels as tcw_search, on
+ * caller-owned DEVICE inputs and outputs, with no context:
+ *   rho [n_det][n_seg][n_bin] (dtype TCW_F32 or TCW_F16), t_mid [n_seg]
+ *   (strictly increasing), weights [n_det][n_seg] float or NULL for ones,
+ *   v [n_det][n_seg][3] (m/s), f0/tau/n [n_tmpl], nhat [n_sky][3] unit
+ *   vectors, psi_out/idx_out [n_sky][k] (caller order, ties by ascending
+ *   template index); all on the current CUDA device; work is queued on
+ *   cuda_stream (NULL = legacy default stream) and the call returns after it
+ *   has finished.
+ * Every intermediate buffer comes from one fixed device array of 64 MiB
+ * inside the library (held by each GPU on which the library's device code is
+ * loaded, until the process exits).  Problems whose intermediates do not fit
+ * (about (n_sky rounded up to 32) * n_tmpl * 12 bytes plus
+ * n_det * n_seg * n_sky * 4 bytes) are rejected with TCW_ERR_UNSUPPORTED, as
+ * are inputs outside the group kernel's exactness conditions.  The first
+ * call made with a given device current looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  All calls share the array and it keeps the previous
+ * call's contents: each call clears what must start at zero, and calls that
+ * overlap on the GPU (e.g. on two streams) race on it.
+ * Errors: INVALID_ARGUMENT (sizes, NULL, k, or element values: f0 <= 0,
+ * tau <= 0, n <= 1, non-unit nhat, |v| >= c/100, bad weights, unsorted
+ * t_mid), UNSUPPORTED, DEVICE, CUDA. */
+tcw_status tcw_search_noalloc(int n_det, int64_t n_seg, int64_t n_bin, int dtype, const void *rho,
+                              double f_min, double df, const double *t_mid, const float *weights,
+                              const double *v, int64_t n_tmpl, const double *f0, const double *tau,
+                              const double *n, double T0, int64_t n_sky, const double *nhat, int k,
+                              float *psi_out, int64_t *idx_out, void *cuda_stream);
+
 /* Information about the last search. */
 typedef struct {
     int kernel;                 /* TCW_KERNEL_GROUP or TCW_KERNEL_LOOKUP */

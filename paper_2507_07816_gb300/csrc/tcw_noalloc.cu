@@ -1,0 +1,257 @@
+// tcw_noalloc.cu -- a search entry point that allocates no device memory.
+//
+// Some callers cannot call cudaMalloc: an application whose device memory is
+// entirely owned by its own arena or caching allocator (a stray cudaMalloc
+// would fail or fragment that pool), a real-time pipeline that cannot afford
+// the implicit device-wide synchronisation of cudaMalloc/cudaFree, or a
+// plug-in host that forbids device allocation by its plug-ins.  For them,
+// tcw_search_noalloc runs the same kernels as tcw_search (Doppler table,
+// group kernel, top-k) on caller-owned inputs and outputs, and takes every
+// intermediate buffer from one file-scope device array of fixed size,
+// kTcwNoallocScratchBytes (64 MiB).  Every GPU on which this device code is
+// loaded holds that array until the process exits.
+//
+// The array's name is only a host-side stand-in; the device address is
+// obtained once per device with cudaGetSymbolAddress (on the first call made
+// with that device current) and cached.  The array is shared by all calls
+// and keeps the previous call's contents: the entry point clears what has to
+// start at zero (the flag words) on every call, and calls that overlap on the
+// GPU (for example on two streams at once) race on it.
+#include <climits>
+#include <cmath>
+#include <cstring>
+
+#include "tcw_internal.cuh"
+
+namespace tcw {
+namespace {
+
+constexpr size_t kTcwNoallocScratchBytes = (size_t)64 << 20;
+constexpr int kNoallocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kTcwNoallocScratchBytes];
+
+unsigned char* g_scratch_addr[kNoallocMaxDevices] = {nullptr};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct NoallocPrep {
+  const double *f0, *tau, *nbr, *nhat, *vel, *t_mid;
+  const float* weights;       // caller weights or nullptr
+  int B, Bpad, S, Spad, n_det, n_seg;
+  double *f0p, *taup, *nbrp, *nhatp;
+  int32_t *bank_perm, *sky_perm;
+  float* ones;                // filled with 1 when weights == nullptr
+  int* err;                   // bit 2: invalid input values
+  unsigned long long* vmax_bits;
+  unsigned long long* f0max_bits;
+};
+
+// Pads the bank and the sky (repeating the last entry), writes identity
+// permutations, fills unit weights when none are given, checks the inputs
+// element-wise and takes max |v| and max f0 (bit patterns of non-negative
+// doubles order like unsigned integers).
+__global__ void noalloc_prepare_kernel(NoallocPrep p) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (int64_t i = t0; i < p.Bpad; i += stride) {
+    const int src = (int)(i < p.B ? i : (int64_t)p.B - 1);
+    const double f = p.f0[src], ta = p.tau[src], n = p.nbr[src];
+    p.f0p[i] = f;
+    p.taup[i] = ta;
+    p.nbrp[i] = n;
+    p.bank_perm[i] = src;
+    if (i < p.B) {
+      if (!(f > 0.0) || !(ta > 0.0) || !(n > 1.0) || !isfinite(f) || !isfinite(ta) || !isfinite(n))
+        atomicOr(p.err, 4);
+      else
+        atomicMax(p.f0max_bits, (unsigned long long)__double_as_longlong(f));
+    }
+  }
+  for (int64_t i = t0; i < p.Spad; i += stride) {
+    const int src = (int)(i < p.S ? i : (int64_t)p.S - 1);
+    const double x = p.nhat[3 * src], y = p.nhat[3 * src + 1], z = p.nhat[3 * src + 2];
+    p.nhatp[3 * i] = x;
+    p.nhatp[3 * i + 1] = y;
+    p.nhatp[3 * i + 2] = z;
+    p.sky_perm[i] = src;
+    if (i < p.S && !(fabs(sqrt(x * x + y * y + z * z) - 1.0) <= 1e-9)) atomicOr(p.err, 4);
+  }
+  const int64_t nv = (int64_t)p.n_det * p.n_seg;
+  for (int64_t i = t0; i < nv; i += stride) {
+    const double* v = p.vel + 3 * i;
+    const double m = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    if (!(m < kLightSpeed / 100)) atomicOr(p.err, 4);
+    else atomicMax(p.vmax_bits, (unsigned long long)__double_as_longlong(m));
+    if (p.weights) {
+      const float w = p.weights[i];
+      if (!(w >= 0.f) || !isfinite(w)) atomicOr(p.err, 4);
+    } else {
+      p.ones[i] = 1.0f;
+    }
+  }
+  for (int64_t j = t0; j < p.n_seg; j += stride) {
+    const double t = p.t_mid[j];
+    if (!isfinite(t) || (j > 0 && !(t > p.t_mid[j - 1]))) atomicOr(p.err, 4);
+  }
+}
+
+}  // namespace
+}  // namespace tcw
+
+using namespace tcw;
+
+extern "C" tcw_status tcw_search_noalloc(int n_det, int64_t n_seg, int64_t n_bin, int dtype,
+                                         const void* rho, double f_min, double df,
+                                         const double* t_mid, const float* weights,
+                                         const double* v, int64_t n_tmpl, const double* f0,
+                                         const double* tau, const double* n, double T0,
+                                         int64_t n_sky, const double* nhat, int k, float* psi_out,
+                                         int64_t* idx_out, void* cuda_stream) {
+  if (n_det < 1 || n_det > kMaxDet || n_seg < 1 || n_seg > INT32_MAX || n_bin < 1 ||
+      n_bin > ((int64_t)1 << 30) || n_tmpl < 1 || n_tmpl > INT32_MAX - 64 || n_sky < 1 ||
+      n_sky > INT32_MAX - 64)
+    return TCW_ERR_INVALID_ARGUMENT;
+  if (dtype != TCW_F32 && dtype != TCW_F16) return TCW_ERR_INVALID_ARGUMENT;
+  if (!rho || !t_mid || !v || !f0 || !tau || !n || !nhat || !psi_out || !idx_out)
+    return TCW_ERR_INVALID_ARGUMENT;
+  if (!std::isfinite(f_min) || !(df > 0) || !std::isfinite(df) || !std::isfinite(T0))
+    return TCW_ERR_INVALID_ARGUMENT;
+  if (k < 1 || k > 1024 || (int64_t)k > n_tmpl) return TCW_ERR_INVALID_ARGUMENT;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+
+  // Scratch layout (every region 256-byte aligned).
+  const int B = (int)n_tmpl, S = (int)n_sky, D = n_det, Nseg = (int)n_seg;
+  const int Bpad = (B + kGroupTmplPerCta - 1) / kGroupTmplPerCta * kGroupTmplPerCta;
+  const int NG = (S + kGroupSkies - 1) / kGroupSkies;
+  const int Spad = (NG * kGroupSkies + 31) / 32 * 32;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off += align256(bytes);
+    return at;
+  };
+  const size_t o_flags = take(256);
+  const size_t o_f0 = take((size_t)Bpad * 8), o_tau = take((size_t)Bpad * 8), o_n = take((size_t)Bpad * 8);
+  const size_t o_bperm = take((size_t)Bpad * 4), o_sperm = take((size_t)Spad * 4);
+  const size_t o_nhat = take((size_t)Spad * 24);
+  const size_t o_ones = take(weights ? 0 : (size_t)D * Nseg * 4);
+  const size_t o_dq = take((size_t)D * Nseg * Spad * 4);
+  const size_t o_gb = take((size_t)D * Nseg * NG * 8);
+  const size_t o_psi = take((size_t)Spad * Bpad * 4);
+  const size_t o_dev = take((size_t)Spad * Bpad * 8);
+  if (off > kTcwNoallocScratchBytes) return TCW_ERR_UNSUPPORTED;
+
+  // One-time set-up per device: the device address of the scratch array.
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return TCW_ERR_CUDA;
+  if (dev < 0 || dev >= kNoallocMaxDevices) return TCW_ERR_UNSUPPORTED;
+  if (!g_scratch_addr[dev]) {
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr) {
+      cudaGetLastError();
+      return TCW_ERR_CUDA;
+    }
+    g_scratch_addr[dev] = static_cast<unsigned char*>(ptr);
+  }
+  unsigned char* base = g_scratch_addr[dev];
+  int* err = reinterpret_cast<int*>(base + o_flags);
+  unsigned long long* ngen = reinterpret_cast<unsigned long long*>(base + o_flags + 8);
+  unsigned long long* maxes = reinterpret_cast<unsigned long long*>(base + o_flags + 16);
+
+  if (cudaMemsetAsync(base + o_flags, 0, 256, st) != cudaSuccess) return TCW_ERR_CUDA;
+  NoallocPrep pp{};
+  pp.f0 = f0;
+  pp.tau = tau;
+  pp.nbr = n;
+  pp.nhat = nhat;
+  pp.vel = v;
+  pp.t_mid = t_mid;
+  pp.weights = weights;
+  pp.B = B;
+  pp.Bpad = Bpad;
+  pp.S = S;
+  pp.Spad = Spad;
+  pp.n_det = D;
+  pp.n_seg = Nseg;
+  pp.f0p = reinterpret_cast<double*>(base + o_f0);
+  pp.taup = reinterpret_cast<double*>(base + o_tau);
+  pp.nbrp = reinterpret_cast<double*>(base + o_n);
+  pp.nhatp = reinterpret_cast<double*>(base + o_nhat);
+  pp.bank_perm = reinterpret_cast<int32_t*>(base + o_bperm);
+  pp.sky_perm = reinterpret_cast<int32_t*>(base + o_sperm);
+  pp.ones = weights ? nullptr : reinterpret_cast<float*>(base + o_ones);
+  pp.err = err;
+  pp.vmax_bits = maxes;
+  pp.f0max_bits = maxes + 1;
+  noalloc_prepare_kernel<<<152, 256, 0, st>>>(pp);
+  if (cudaGetLastError() != cudaSuccess) return TCW_ERR_CUDA;
+  unsigned long long hflags[4] = {0, 0, 0, 0};
+  if (cudaMemcpyAsync(hflags, base + o_flags, sizeof(hflags), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return TCW_ERR_CUDA;
+  if ((int)(hflags[0] & 0xffffffffull) != 0) return TCW_ERR_INVALID_ARGUMENT;
+
+  // Fixed-point step and the group kernel's exactness conditions.
+  double vmax = 0.0, f0max = 0.0;
+  std::memcpy(&vmax, &hflags[2], sizeof(double));
+  std::memcpy(&f0max, &hflags[3], sizeof(double));
+  const double dmax = vmax / kLightSpeed * (1.0 + 1e-12);
+  int e = -60;
+  if (dmax > 0) e = (int)std::ceil(std::log2(dmax / (2147483648.0 - 16777216.0)));
+  if (e < -80) e = -80;
+  const double q = std::ldexp(1.0, e);
+  const double fmax_bins = f0max * (1.0 + dmax) / df;
+  if (fmax_bins * q * 0.5 > 0.75 * std::ldexp(1.0, -30) || fmax_bins * dmax > 2.9)
+    return TCW_ERR_UNSUPPORTED;
+
+  DopplerParams dp{};
+  dp.vel = v;
+  dp.nhat = pp.nhatp;
+  dp.n_det = D;
+  dp.n_seg = Nseg;
+  dp.Spad = Spad;
+  dp.NG = NG;
+  dp.group = kGroupSkies;
+  dp.inv_q = std::ldexp(1.0, -e);
+  dp.dq = reinterpret_cast<int32_t*>(base + o_dq);
+  dp.gbound = reinterpret_cast<float2*>(base + o_gb);
+  if (launch_doppler(dp, st) != cudaSuccess) return TCW_ERR_CUDA;
+
+  GroupParams gp{};
+  gp.rho = rho;
+  gp.n_bin = n_bin;
+  gp.n_det = D;
+  gp.n_seg = Nseg;
+  gp.weights = weights ? weights : pp.ones;
+  gp.t_mid = t_mid;
+  gp.dq = dp.dq;
+  gp.gbound = dp.gbound;
+  gp.f0 = pp.f0p;
+  gp.tau = pp.taup;
+  gp.nbr = pp.nbrp;
+  gp.T0 = T0;
+  gp.f_min = f_min;
+  gp.df = df;
+  gp.inv_q = dp.inv_q;
+  gp.B = B;
+  gp.Bpad = Bpad;
+  gp.S = S;
+  gp.Spad = Spad;
+  gp.NG = NG;
+  gp.psi = reinterpret_cast<float*>(base + o_psi);
+  gp.dev = reinterpret_cast<float2*>(base + o_dev);
+  gp.bank_perm = pp.bank_perm;
+  gp.sky_perm = pp.sky_perm;
+  gp.n_general = ngen;
+  gp.err = err;
+  if (launch_group(gp, dtype == TCW_F16, false, 32, st) != cudaSuccess) return TCW_ERR_CUDA;
+  if (launch_topk(gp.psi, Bpad, B, S, k, pp.bank_perm, pp.sky_perm, psi_out, idx_out, st) != cudaSuccess)
+    return TCW_ERR_CUDA;
+  int herr = 0;
+  if (cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return TCW_ERR_CUDA;
+  return herr ? TCW_ERR_DEVICE : TCW_OK;
+}
