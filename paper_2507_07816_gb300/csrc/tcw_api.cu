@@ -60,6 +60,7 @@ struct tcw_ctx {
   int dtype = TCW_F32;
   double f_min = 0, df = 0;
   std::vector<double> h_t;
+  bool unit_weights = true;
   DevBuf rho, t_mid, weights;
   // velocity
   bool have_vel = false;
@@ -80,7 +81,7 @@ struct tcw_ctx {
   bool sky_dirty = true;
   DevBuf nhat_sorted, sky_perm, sky_pos;
   // derived and outputs
-  DevBuf dq, gbound, psi, st_S, st_W1, st_W2, dev, flags, stage_f, stage_i;
+  DevBuf dq, gmid, psi, st_S, st_W1, st_W2, dev, flags, stage_f, stage_i;
   bool have_result = false, stats_kept = false;
   tcw_info info{};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -136,9 +137,40 @@ bool finite_all(const std::vector<double>& v) {
 struct Plan {
   int kernel = TCW_KERNEL_LOOKUP;
   double q = 0, inv_q = 0, dmax = 0, fmax_bins = 0, doppler_bins = 0;
+  int nterms = 0;
   bool group_ok = false;
   std::string why;
 };
+
+// Length of the binomial series sum_k binom(r, k) delta^k that gives 1/f(t_j)
+// from the tile anchor to below 2^-56 relative, for every template and tile;
+// 0 when more than kMaxSeriesTerms terms would be needed.
+int series_terms(const tcw_ctx* c) {
+  const int TS = 32;
+  double tau_min = INFINITY, r_max = 0;
+  for (size_t b = 0; b < c->h_tau.size(); ++b) {
+    tau_min = std::min(tau_min, c->h_tau[b]);
+    r_max = std::max(r_max, 1.0 / (c->h_n[b] - 1.0));
+  }
+  double dmax = 0;
+  const int64_t N = c->Nseg;
+  for (int64_t j0 = 0; j0 < N; j0 += TS) {
+    const int64_t jn = std::min<int64_t>(TS, N - j0);
+    const double ta = std::max(c->h_t[j0 + (jn - 1) / 2], c->T0);
+    for (int64_t j = j0; j < j0 + jn; ++j) {
+      if (c->h_t[j] < c->T0) continue;
+      dmax = std::max(dmax, std::fabs(c->h_t[j] - ta) / (tau_min + (ta - c->T0)));
+    }
+  }
+  if (dmax >= 0.5) return 0;
+  double bound = 1.0, pw = 1.0;
+  for (int k = 0; k <= kMaxSeriesTerms; ++k) {
+    if (bound * pw < std::ldexp(1.0, -56)) return std::max(k, 1);
+    bound *= (r_max + k) / (k + 1);
+    pw *= dmax;
+  }
+  return 0;
+}
 
 // Fixed-point step and the exactness conditions of the group kernel.
 Plan make_plan(const tcw_ctx* c) {
@@ -153,9 +185,12 @@ Plan make_plan(const tcw_ctx* c) {
   e = std::max(e, -80);
   pl.q = std::ldexp(1.0, e);
   pl.inv_q = std::ldexp(1.0, -e);
+  // tracks only fall (Eq. 1), and lookups outside the band are never made, so
+  // the largest f/df that reaches the bin decision is bounded by both
   double f0max = 0;
   for (double f : c->h_f0) f0max = std::max(f0max, f);
-  pl.fmax_bins = f0max * (1.0 + pl.dmax) / c->df;
+  const double fband = c->f_min + ((double)c->Nbin + 5.0) * c->df;
+  pl.fmax_bins = std::min(f0max, fband) * (1.0 + pl.dmax) / c->df;
   pl.doppler_bins = pl.fmax_bins * pl.dmax;
   const double tie_budget = 0.75 * std::ldexp(1.0, -30);
   pl.group_ok = true;
@@ -171,6 +206,7 @@ Plan make_plan(const tcw_ctx* c) {
     pl.group_ok = false;
     pl.why = "sizes beyond the group kernel's 32-bit indexing";
   }
+  pl.nterms = series_terms(c);
   pl.kernel = pl.group_ok ? TCW_KERNEL_GROUP : TCW_KERNEL_LOOKUP;
   return pl;
 }
@@ -232,7 +268,7 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
   if (kernel == TCW_KERNEL_GROUP) {
     const size_t dqn = (size_t)c->D * c->Nseg * c->Spad;
     TCW_CUDA(c, c->dq.ensure(dqn * sizeof(int32_t)), "doppler table");
-    TCW_CUDA(c, c->gbound.ensure((size_t)c->D * c->Nseg * c->NG * sizeof(float2)), "doppler table");
+    TCW_CUDA(c, c->gmid.ensure((size_t)c->D * c->Nseg * c->NG * sizeof(float)), "doppler table");
     TCW_CUDA(c, c->dev.ensure(pairs * sizeof(float2)), "scratch");
     DopplerParams dp{};
     dp.vel = c->vel.as<double>();
@@ -244,10 +280,23 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
     dp.group = kGroupSkies;
     dp.inv_q = pl.inv_q;
     dp.dq = c->dq.as<int32_t>();
-    dp.gbound = c->gbound.as<float2>();
+    dp.gmid = c->gmid.as<float>();
+    dp.spread_max = reinterpret_cast<unsigned*>(c->flags.as<char>() + 16);
     TCW_CUDA(c, launch_doppler(dp, c->stream), "doppler_kernel launch");
     ++launches;
-
+    // the candidate pair of a sky group must cover the whole group
+    unsigned spread_bits = 0;
+    TCW_CUDA(c, cudaMemcpyAsync(&spread_bits, dp.spread_max, 4, cudaMemcpyDeviceToHost, c->stream), "spread");
+    TCW_CUDA(c, cudaStreamSynchronize(c->stream), "spread");
+    float spread = 0;
+    std::memcpy(&spread, &spread_bits, 4);
+    if (pl.fmax_bins * (double)spread * 0.5 + 0.02 > 0.45) {
+      if (c->opt_kernel == TCW_KERNEL_GROUP)
+        return fail(c, TCW_ERR_UNSUPPORTED, "group kernel unavailable: sky groups span too many bins");
+      kernel = TCW_KERNEL_LOOKUP;
+    }
+  }
+  if (kernel == TCW_KERNEL_GROUP) {
     GroupParams gp{};
     gp.rho = c->rho.p;
     gp.n_bin = c->Nbin;
@@ -255,8 +304,8 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
     gp.n_seg = (int)c->Nseg;
     gp.weights = c->weights.as<float>();
     gp.t_mid = c->t_mid.as<double>();
-    gp.dq = dp.dq;
-    gp.gbound = dp.gbound;
+    gp.dq = c->dq.as<int32_t>();
+    gp.gmid = c->gmid.as<float>();
     gp.f0 = c->f0.as<double>();
     gp.tau = c->tau.as<double>();
     gp.nbr = c->nbr.as<double>();
@@ -264,6 +313,7 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
     gp.f_min = c->f_min;
     gp.df = c->df;
     gp.inv_q = pl.inv_q;
+    gp.nterms = pl.nterms;
     gp.B = (int)c->B;
     gp.Bpad = c->Bpad;
     gp.S = (int)c->S;
@@ -280,7 +330,7 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
     gp.n_general = reinterpret_cast<unsigned long long*>(c->flags.as<char>() + 8);
     gp.err = c->flags.as<int>();
     TCW_CUDA(c, cudaEventRecord(c->ev0, c->stream), "event");
-    TCW_CUDA(c, launch_group(gp, c->dtype == TCW_F16, record, c->tile_segments, c->stream),
+    TCW_CUDA(c, launch_group(gp, c->dtype == TCW_F16, record, !c->unit_weights, c->stream),
              "group_kernel launch");
     TCW_CUDA(c, cudaEventRecord(c->ev1, c->stream), "event");
     ++launches;
@@ -398,7 +448,7 @@ tcw_status tcw_destroy(tcw_ctx* c) {
   cudaStreamSynchronize(c->stream);
   DevBuf* bufs[] = {&c->rho, &c->t_mid, &c->weights, &c->vel, &c->f0, &c->tau, &c->nbr,
                     &c->bank_perm, &c->bank_pos, &c->nhat_sorted, &c->sky_perm, &c->sky_pos,
-                    &c->dq, &c->gbound, &c->psi, &c->st_S, &c->st_W1, &c->st_W2, &c->dev,
+                    &c->dq, &c->gmid, &c->psi, &c->st_S, &c->st_W1, &c->st_W2, &c->dev,
                     &c->flags, &c->stage_f, &c->stage_i};
   for (DevBuf* b : bufs) b->release();
   if (c->ev0) cudaEventDestroy(c->ev0);
@@ -466,6 +516,9 @@ tcw_status tcw_load_spectrogram(tcw_ctx* c, int n_det, int64_t n_seg, int64_t n_
   c->f_min = f_min;
   c->df = df;
   c->h_t = std::move(t);
+  c->unit_weights = true;
+  for (float x : w)
+    if (x != 1.0f) c->unit_weights = false;
   c->have_spec = true;
   c->have_result = false;
   c->sky_dirty = true;

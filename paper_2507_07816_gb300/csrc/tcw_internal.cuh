@@ -38,13 +38,25 @@ constexpr int kMHi = 4;
 constexpr int kNThr = kMHi - kMLo;  // 8 thresholds
 
 // Precomputed per (template, segment): 48 bytes, lives in shared memory.
+//   F, Cm  fp32 estimates that choose the candidate bin pair: for a sky group
+//          whose mean Doppler factor is g, the pair starts at
+//          base + round(F*g + Cm)   (Cm = (f - f_min)/df - base - 1/2)
+//   kb     base - kMagicBits, so that base + round(y) = kb + bits(y + kMagic)
+//   cls    kEntryNone / kEntryInside / kEntryEdge
+//   th[i]  round((c_K/f - 1)/q) with c_K = f_min + (K + 1/2) df, K = base + kMLo + i
 struct __align__(16) TrackEntry {
-  int base;      // base bin (nearest centre of the undoppled track); INT_MIN = no lookups
-  float C;       // (f - f_min)/df - base, fp32 estimate
-  float F;       // f/df, fp32 estimate
-  int pad;
-  int th[kNThr]; // round(threshold/q), clamped to int32
+  float F;
+  float Cm;
+  int kb;
+  int cls;
+  int th[kNThr];
 };
+
+constexpr int kEntryNone = 0;    // segment before T0, or every candidate bin outside the band
+constexpr int kEntryInside = 1;  // every candidate bin inside the band
+constexpr int kEntryEdge = 2;    // candidates straddle a band edge
+constexpr float kMagic = 12582912.0f;     // 1.5 * 2^23: x + kMagic rounds x to an integer
+constexpr int kMagicBits = 0x4B400000;    // bit pattern of kMagic
 
 struct GroupParams {
   const void* rho;         // [D][Nseg][Nbin] float or half
@@ -54,17 +66,18 @@ struct GroupParams {
   const float* weights;    // [D][Nseg]
   const double* t_mid;     // [Nseg]
   const int32_t* dq;       // [D][Nseg][Spad] floor(v.nhat/c / q)
-  const float2* gbound;    // [D][Nseg][NG] min/max of v.nhat/c over each sky group
+  const float* gmid;       // [D][Nseg][NG] mid-range of v.nhat/c over each sky group
   const double* f0;        // sorted bank, [Bpad]
   const double* tau;
   const double* nbr;
   double T0, f_min, df, inv_q;
+  int nterms;              // binomial-series length for the track; 0 = pow per entry
   int B, Bpad, S, Spad, NG;
   float* psi;              // [Spad][Bpad]
   float* S_out;            // optional [Spad][Bpad]
   float* W1_out;
   float* W2_out;
-  float2* dev;             // scratch [Bpad][Spad]: per-sky weight sums of per-sky-path lookups
+  float2* dev;             // scratch [Bpad][Spad]: per-sky weight sums at band edges
   int32_t* rec;            // optional [S][B][D][Nseg], caller order
   const int32_t* bank_perm;  // sorted -> caller template index
   const int32_t* sky_perm;   // sorted -> caller sky index
@@ -101,12 +114,15 @@ struct DopplerParams {
   int n_det, n_seg, Spad, NG, group;
   double inv_q;
   int32_t* dq;
-  float2* gbound;
+  float* gmid;
+  unsigned* spread_max;    // float bits of max (hi - lo) of v.nhat/c over the groups
 };
+
+constexpr int kMaxSeriesTerms = 24;
 
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_doppler(const DopplerParams& p, cudaStream_t st);
-cudaError_t launch_group(const GroupParams& p, bool half, bool record, int tile_segments,
+cudaError_t launch_group(const GroupParams& p, bool half, bool record, bool weighted,
                          cudaStream_t st);
 cudaError_t launch_lookup(const LookupParams& p, bool half, bool record, cudaStream_t st);
 cudaError_t launch_topk(const float* psi, int Bpad, int B, int S, int k, const int32_t* bank_perm,

@@ -137,7 +137,7 @@ extern "C" tcw_status tcw_search_noalloc(int n_det, int64_t n_seg, int64_t n_bin
   const size_t o_nhat = take((size_t)Spad * 24);
   const size_t o_ones = take(weights ? 0 : (size_t)D * Nseg * 4);
   const size_t o_dq = take((size_t)D * Nseg * Spad * 4);
-  const size_t o_gb = take((size_t)D * Nseg * NG * 8);
+  const size_t o_gb = take((size_t)D * Nseg * NG * 4);
   const size_t o_psi = take((size_t)Spad * Bpad * 4);
   const size_t o_dev = take((size_t)Spad * Bpad * 8);
   if (off > kTcwNoallocScratchBytes) return TCW_ERR_UNSUPPORTED;
@@ -202,7 +202,7 @@ extern "C" tcw_status tcw_search_noalloc(int n_det, int64_t n_seg, int64_t n_bin
   if (dmax > 0) e = (int)std::ceil(std::log2(dmax / (2147483648.0 - 16777216.0)));
   if (e < -80) e = -80;
   const double q = std::ldexp(1.0, e);
-  const double fmax_bins = f0max * (1.0 + dmax) / df;
+  const double fmax_bins = std::fmin(f0max, f_min + ((double)n_bin + 5.0) * df) * (1.0 + dmax) / df;
   if (fmax_bins * q * 0.5 > 0.75 * std::ldexp(1.0, -30) || fmax_bins * dmax > 2.9)
     return TCW_ERR_UNSUPPORTED;
 
@@ -216,38 +216,74 @@ extern "C" tcw_status tcw_search_noalloc(int n_det, int64_t n_seg, int64_t n_bin
   dp.group = kGroupSkies;
   dp.inv_q = std::ldexp(1.0, -e);
   dp.dq = reinterpret_cast<int32_t*>(base + o_dq);
-  dp.gbound = reinterpret_cast<float2*>(base + o_gb);
+  dp.gmid = reinterpret_cast<float*>(base + o_gb);
+  dp.spread_max = reinterpret_cast<unsigned*>(base + o_flags + 32);
   if (launch_doppler(dp, st) != cudaSuccess) return TCW_ERR_CUDA;
-
-  GroupParams gp{};
-  gp.rho = rho;
-  gp.n_bin = n_bin;
-  gp.n_det = D;
-  gp.n_seg = Nseg;
-  gp.weights = weights ? weights : pp.ones;
-  gp.t_mid = t_mid;
-  gp.dq = dp.dq;
-  gp.gbound = dp.gbound;
-  gp.f0 = pp.f0p;
-  gp.tau = pp.taup;
-  gp.nbr = pp.nbrp;
-  gp.T0 = T0;
-  gp.f_min = f_min;
-  gp.df = df;
-  gp.inv_q = dp.inv_q;
-  gp.B = B;
-  gp.Bpad = Bpad;
-  gp.S = S;
-  gp.Spad = Spad;
-  gp.NG = NG;
-  gp.psi = reinterpret_cast<float*>(base + o_psi);
-  gp.dev = reinterpret_cast<float2*>(base + o_dev);
-  gp.bank_perm = pp.bank_perm;
-  gp.sky_perm = pp.sky_perm;
-  gp.n_general = ngen;
-  gp.err = err;
-  if (launch_group(gp, dtype == TCW_F16, false, 32, st) != cudaSuccess) return TCW_ERR_CUDA;
-  if (launch_topk(gp.psi, Bpad, B, S, k, pp.bank_perm, pp.sky_perm, psi_out, idx_out, st) != cudaSuccess)
+  unsigned spread_bits = 0;
+  if (cudaMemcpyAsync(&spread_bits, dp.spread_max, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return TCW_ERR_CUDA;
+  float spread = 0.f;
+  std::memcpy(&spread, &spread_bits, 4);
+  float* psi = reinterpret_cast<float*>(base + o_psi);
+  const float* wts = weights ? weights : pp.ones;
+  if (fmax_bins * (double)spread * 0.5 + 0.02 <= 0.45) {
+    GroupParams gp{};
+    gp.rho = rho;
+    gp.n_bin = n_bin;
+    gp.n_det = D;
+    gp.n_seg = Nseg;
+    gp.weights = wts;
+    gp.t_mid = t_mid;
+    gp.dq = dp.dq;
+    gp.gmid = dp.gmid;
+    gp.f0 = pp.f0p;
+    gp.tau = pp.taup;
+    gp.nbr = pp.nbrp;
+    gp.T0 = T0;
+    gp.f_min = f_min;
+    gp.df = df;
+    gp.inv_q = dp.inv_q;
+    gp.nterms = 0;
+    gp.B = B;
+    gp.Bpad = Bpad;
+    gp.S = S;
+    gp.Spad = Spad;
+    gp.NG = NG;
+    gp.psi = psi;
+    gp.dev = reinterpret_cast<float2*>(base + o_dev);
+    gp.bank_perm = pp.bank_perm;
+    gp.sky_perm = pp.sky_perm;
+    gp.n_general = ngen;
+    gp.err = err;
+    if (launch_group(gp, dtype == TCW_F16, false, true, st) != cudaSuccess) return TCW_ERR_CUDA;
+  } else {
+    // sky groups too wide for one candidate pair: per-lookup FP64 kernel
+    LookupParams lp{};
+    lp.rho = rho;
+    lp.n_bin = n_bin;
+    lp.n_det = D;
+    lp.n_seg = Nseg;
+    lp.weights = wts;
+    lp.t_mid = t_mid;
+    lp.vel = v;
+    lp.nhat = pp.nhatp;
+    lp.f0 = pp.f0p;
+    lp.tau = pp.taup;
+    lp.nbr = pp.nbrp;
+    lp.T0 = T0;
+    lp.f_min = f_min;
+    lp.df = df;
+    lp.B = B;
+    lp.Bpad = Bpad;
+    lp.S = S;
+    lp.Spad = Spad;
+    lp.psi = psi;
+    lp.bank_perm = pp.bank_perm;
+    lp.sky_perm = pp.sky_perm;
+    if (launch_lookup(lp, dtype == TCW_F16, false, st) != cudaSuccess) return TCW_ERR_CUDA;
+  }
+  if (launch_topk(psi, Bpad, B, S, k, pp.bank_perm, pp.sky_perm, psi_out, idx_out, st) != cudaSuccess)
     return TCW_ERR_CUDA;
   int herr = 0;
   if (cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||

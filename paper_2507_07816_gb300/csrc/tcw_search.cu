@@ -1,11 +1,12 @@
 // tcw_search.cu -- sm_103a kernels of the track-statistic search.
 //
 //   doppler_kernel  Eq. 2 factor per (detector, segment, sky): v.nhat/c in FP64,
-//                   stored as floor(./q) int32 plus fp32 min/max per sky group
-//   group_kernel    the hot loop: per (template, segment) track entry in FP64
-//                   (Eq. 1), then per (detector, sky group) a candidate bin
-//                   pair, two gathers and one int32 compare + predicated add
-//                   per sky (Sec. 2 weighted sum), Psi of Eq. 4 in the epilogue
+//                   stored as floor(./q) int32 plus the fp32 mid-range per sky group
+//   group_kernel    the hot loop: per 32-segment tile, FP64 track entries (Eq. 1)
+//                   from one pow per template and a short binomial series; then
+//                   per (template, detector, segment, sky group) one candidate
+//                   bin pair, two gathers, and per sky one int32 compare +
+//                   predicated add (Sec. 2 weighted sum); Psi of Eq. 4 at the end
 //   lookup_kernel   one thread per (sky, template), FP64 per lookup; used when
 //                   the group kernel's exactness conditions do not hold
 //   unpermute_kernel  sorted -> caller order for the statistics getter
@@ -16,27 +17,23 @@
 namespace tcw {
 namespace {
 
-constexpr float kDelta = 1e-3f;  // slack (bins) on the fp32 candidate estimate
-
 __device__ __forceinline__ float load_rho(const float* row, int64_t k) { return __ldg(row + k); }
 __device__ __forceinline__ float load_rho(const __half* row, int64_t k) {
   return __half2float(__ldg(row + k));
-}
-
-__device__ __forceinline__ int clamp_round_int(double x) {
-  if (x >= 2147483647.0) return INT_MAX;
-  if (x <= -2147483647.0) return -INT_MAX;
-  return __double2int_rn(x);
 }
 
 // ---------------------------------------------------------------------------
 // Doppler tables (Eq. 2): one thread per (detector, segment, sorted sky).
 // Sky groups are `group` consecutive sorted skies; group is a power of two
 // <= 32 and Spad is a multiple of 32, so a group never straddles a warp.
+// Writes floor(v.nhat/c / q) per sky, the fp32 mid-range of v.nhat/c per group
+// and the largest group range (one atomic per block).
 // ---------------------------------------------------------------------------
 __global__ void doppler_kernel(DopplerParams p) {
+  __shared__ float s_red[32];
   const int64_t total = (int64_t)p.n_det * p.n_seg * p.Spad;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  float spread = 0.f;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
     const int s = (int)(i % p.Spad);
     const int64_t dj = i / p.Spad;
@@ -50,57 +47,102 @@ __global__ void doppler_kernel(DopplerParams p) {
       lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, off));
       hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, off));
     }
-    if (s % p.group == 0 && s / p.group < p.NG) p.gbound[dj * p.NG + s / p.group] = make_float2(lo, hi);
+    if (s % p.group == 0 && s / p.group < p.NG) {
+      p.gmid[dj * p.NG + s / p.group] = 0.5f * (lo + hi);
+      spread = fmaxf(spread, hi - lo);
+    }
+  }
+  for (int off = 16; off > 0; off >>= 1) spread = fmaxf(spread, __shfl_xor_sync(0xffffffffu, spread, off));
+  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = spread;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float m = threadIdx.x < (blockDim.x >> 5) ? s_red[threadIdx.x] : 0.f;
+    for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if (threadIdx.x == 0) atomicMax(p.spread_max, __float_as_uint(m));
   }
 }
 
 // ---------------------------------------------------------------------------
-// Track entry of one (sorted template b, segment j), Eq. 1 in FP64.
-//   base  nearest bin of the undoppled track f
-//   C, F  fp32 estimates used only to choose candidate bins (slack kDelta)
-//   th[i] round((c_K/f - 1)/q), c_K = f_min + (K + 1/2) df, K = base + kMLo + i
-// base = INT_MIN marks an entry without lookups: the segment precedes T0, or
-// every candidate bin base + m, |m| <= 4, is outside [0, n_bin).
+// Track entry of one (sorted template b, segment j) from the tile anchor
+// (Eq. 1 in FP64): 1/f(t_j) = h_a (1 + delta)^r with r = 1/(n-1),
+// delta = (t_j - t_a)/(tau + t_a - T0), evaluated by a binomial series of
+// p.nterms terms (coefficients in coef[]), or by pow when p.nterms == 0.
+// The thresholds theta_K = c_K/f - 1 = (f_min h - 1) + (K + 1/2) df h are put
+// on the q grid through a 64-bit fixed-point chain with 8 extra bits.
 // ---------------------------------------------------------------------------
-__device__ void compute_entry(const GroupParams& p, int b, int j, TrackEntry& e) {
-  if (j >= p.n_seg) { e.base = INT_MIN; return; }
-  const double t = p.t_mid[j];
-  if (t < p.T0) { e.base = INT_MIN; return; }
-  const double f = p.f0[b] * pow((t - p.T0) / p.tau[b] + 1.0, 1.0 / (1.0 - p.nbr[b]));
-  const double x = (f - p.f_min) / p.df;
-  if (!(x > -5.0 && x < (double)p.n_bin + 4.0)) { e.base = INT_MIN; return; }
-  const double bf = floor(x + 0.5);
-  e.base = (int)bf;
-  e.C = (float)(x - bf);
-  e.F = (float)(f / p.df);
-  e.pad = 0;
-  const double h = 1.0 / f;
+__device__ __forceinline__ void compute_entry(const GroupParams& p, const double* coef, double ha,
+                                              double dt, int b, int j, bool valid, float fmin_f,
+                                              float inv_df_f, TrackEntry& e) {
+  if (!valid) {
+    e.cls = kEntryNone;
+    return;
+  }
+  double h;
+  if (p.nterms > 0) {
+    const double d = dt;
+    double R = coef[p.nterms - 1];
+    for (int k = p.nterms - 2; k >= 0; --k) R = fma(R, d, coef[k]);
+    h = ha * R;
+  } else {
+    h = pow((p.t_mid[j] - p.T0) / p.tau[b] + 1.0, 1.0 / (p.nbr[b] - 1.0)) / p.f0[b];
+  }
+  const float f = __frcp_rn((float)h);
+  const float x = (f - fmin_f) * inv_df_f;
+  const int base = __float2int_rn(x);
+  if (!(base >= -kMHi && (int64_t)base < p.n_bin - kMLo)) {
+    e.cls = kEntryNone;
+    return;
+  }
+  e.cls = (base + kMLo >= 0 && (int64_t)base + kMHi <= p.n_bin - 1) ? kEntryInside : kEntryEdge;
+  e.F = f * inv_df_f;
+  e.Cm = (x - (float)base) - 0.5f;
+  e.kb = base - kMagicBits;
+  const double Q = p.df * h;
+  const double A0 = fma((double)(base + kMLo) + 0.5, Q, fma(p.f_min, h, -1.0));
+  const double sc = p.inv_q * 256.0;
+  const long long a = __double2ll_rn(A0 * sc), st = __double2ll_rn(Q * sc);
 #pragma unroll
   for (int i = 0; i < kNThr; ++i) {
-    const double c = p.f_min + (bf + (double)(kMLo + i) + 0.5) * p.df;
-    e.th[i] = clamp_round_int(fma(c, h, -1.0) * p.inv_q);
+    long long v = (a + (long long)i * st + 128) >> 8;
+    v = v > 2147483647LL ? 2147483647LL : (v < -2147483647LL ? -2147483647LL : v);
+    e.th[i] = (int)v;
   }
 }
 
-template <typename RhoT, bool RECORD, int TS>
+template <typename RhoT, bool RECORD, bool WEIGHTED, int TS>
 __global__ void __launch_bounds__(kGroupThreads, 2) group_kernel(GroupParams p) {
-  constexpr int G = kGroupSkies, T = kGroupTmpl, NE = kGroupTmplPerCta * TS;
+  constexpr int G = kGroupSkies, T = kGroupTmpl, TPC = kGroupTmplPerCta, NE = TPC * TS;
   __shared__ TrackEntry ent[NE];
+  __shared__ double coef[TPC][kMaxSeriesTerms];
+  __shared__ double s_ha[TPC], s_iota[TPC], s_w1[TPC], s_w2[TPC];
+  __shared__ double s_dt[TS];
   __shared__ float wsm[kMaxDet * TS];
   const int tid = threadIdx.x;
   const int u = tid / kGroupLanes, l = tid % kGroupLanes;
   const int g = blockIdx.y * kGroupLanes + l;
   const bool gval = g < p.NG;
   const int s0 = g * G;
-  const int bcta = blockIdx.x * kGroupTmplPerCta;
+  const int bcta = blockIdx.x * TPC;
   const int bt0 = u * T;
   const RhoT* rho = static_cast<const RhoT*>(p.rho);
+  const float fmin_f = (float)p.f_min, inv_df_f = (float)(1.0 / p.df);
+
+  if (tid < TPC) {
+    const double r = 1.0 / (p.nbr[bcta + tid] - 1.0);
+    double c = 1.0;
+    for (int k = 0; k < p.nterms; ++k) {
+      coef[tid][k] = c;
+      c = c * (r - k) / (k + 1);
+    }
+    s_w1[tid] = 0.0;
+    s_w2[tid] = 0.0;
+  }
 
   float tot[T][G];
-  double gw[T], w1[T], w2[T];
+  double gw[T];
 #pragma unroll
   for (int t = 0; t < T; ++t) {
-    gw[t] = w1[t] = w2[t] = 0.0;
+    gw[t] = 0.0;
 #pragma unroll
     for (int s = 0; s < G; ++s) tot[t][s] = 0.f;
   }
@@ -108,23 +150,52 @@ __global__ void __launch_bounds__(kGroupThreads, 2) group_kernel(GroupParams p) 
   unsigned long long ngen = 0;
 
   for (int j0 = 0; j0 < p.n_seg; j0 += TS) {
+    const int jn = min(TS, p.n_seg - j0);
+    const double ta = fmax(p.t_mid[j0 + (jn - 1) / 2], p.T0);
     __syncthreads();
-    for (int e = tid; e < NE; e += kGroupThreads) compute_entry(p, bcta + e / TS, j0 + e % TS, ent[e]);
+    if (tid < TPC) {
+      const int b = bcta + tid;
+      const double tau = p.tau[b];
+      s_ha[tid] = pow((ta - p.T0) / tau + 1.0, 1.0 / (p.nbr[b] - 1.0)) / p.f0[b];
+      s_iota[tid] = 1.0 / (tau + (ta - p.T0));
+    } else if (tid >= 32 && tid < 32 + TS) {
+      const int jj = tid - 32;
+      s_dt[jj] = jj < jn ? p.t_mid[j0 + jj] - ta : 0.0;
+    }
     for (int e = tid; e < p.n_det * TS; e += kGroupThreads) {
       const int d = e / TS, j = j0 + e % TS;
       wsm[e] = (j < p.n_seg) ? p.weights[(int64_t)d * p.n_seg + j] : 0.f;
     }
     __syncthreads();
+    for (int e = tid; e < NE; e += kGroupThreads) {
+      const int bt = e / TS, jj = e % TS, j = j0 + jj;
+      const bool valid = jj < jn && p.t_mid[j] >= p.T0;
+      compute_entry(p, coef[bt], s_ha[bt], s_dt[jj] * s_iota[bt], bcta + bt, j, valid, fmin_f,
+                    inv_df_f, ent[e]);
+    }
+    __syncthreads();
+    if (tid < TPC) {
+      double a1 = 0.0, a2 = 0.0;
+      for (int jj = 0; jj < jn; ++jj) {
+        if (ent[tid * TS + jj].cls != kEntryInside) continue;
+        for (int d = 0; d < p.n_det; ++d) {
+          const double w = wsm[d * TS + jj];
+          a1 += w;
+          a2 += w * w;
+        }
+      }
+      s_w1[tid] += a1;
+      s_w2[tid] += a2;
+    }
     if (!gval) continue;
 
-    float acc[T][G], gt[T], w1t[T], w2t[T];
+    float acc[T][G], gt[T];
 #pragma unroll
     for (int t = 0; t < T; ++t) {
-      gt[t] = w1t[t] = w2t[t] = 0.f;
+      gt[t] = 0.f;
 #pragma unroll
       for (int s = 0; s < G; ++s) acc[t][s] = 0.f;
     }
-    const int jn = min(TS, p.n_seg - j0);
     for (int jj = 0; jj < jn; ++jj) {
       const int j = j0 + jj;
       for (int d = 0; d < p.n_det; ++d) {
@@ -140,54 +211,49 @@ __global__ void __launch_bounds__(kGroupThreads, 2) group_kernel(GroupParams p) 
           dq[4 * v + 2] = x.z;
           dq[4 * v + 3] = x.w;
         }
-        const float2 gb = __ldg(p.gbound + dj * p.NG + g);
+        const float gm = __ldg(p.gmid + dj * p.NG + g);
         const RhoT* row = rho + dj * p.n_bin;
 #pragma unroll
         for (int t = 0; t < T; ++t) {
           const int b = bcta + bt0 + t;
           const TrackEntry& e = ent[(bt0 + t) * TS + jj];
-          const int base = e.base;
+          const int cls = e.cls;
           int32_t* rp = nullptr;
-          if (RECORD) {
-            if (b < p.B) rp = p.rec + ((int64_t)p.bank_perm[b] * p.n_det + d) * p.n_seg + j;
-          }
-          if (base == INT_MIN) {
+          if (RECORD && b < p.B) rp = p.rec + ((int64_t)p.bank_perm[b] * p.n_det + d) * p.n_seg + j;
+          const int64_t rstride = (int64_t)p.B * p.n_det * p.n_seg;
+          if (cls == kEntryNone) {
             if (RECORD && rp) {
 #pragma unroll
               for (int s = 0; s < G; ++s)
-                if (s0 + s < p.S) rp[(int64_t)p.sky_perm[s0 + s] * p.B * p.n_det * p.n_seg] = -1;
+                if (s0 + s < p.S) rp[(int64_t)p.sky_perm[s0 + s] * rstride] = -1;
             }
             continue;
           }
-          const float ylo = fmaf(e.F, gb.x, e.C), yhi = fmaf(e.F, gb.y, e.C);
-          const int n0 = __float2int_rn(ylo - kDelta), n1 = __float2int_rn(yhi + kDelta);
-          const int K0 = base + n0;
-          if (n1 - n0 <= 1 && n0 >= kMLo && n0 < kMHi && K0 >= 0 && (int64_t)K0 + 1 < p.n_bin) {
-            // candidate pair (K0, K0 + 1): every sky of the group is in one of them
+          const int zb = __float_as_int(fmaf(e.F, gm, e.Cm) + kMagic);
+          const int K0 = e.kb + zb;
+          const int th = e.th[zb - kMagicBits - kMLo];
+          if (cls == kEntryInside) {
             const float rlo = load_rho(row, K0), rhi = load_rho(row, K0 + 1);
-            const int th = e.th[n0 - kMLo];
-            gt[t] = fmaf(wd, rlo, gt[t]);
-            w1t[t] += wd;
-            w2t[t] = fmaf(wd, wd, w2t[t]);
-            const float dw = wd * (rhi - rlo);
+            float dw;
+            if (WEIGHTED) {
+              gt[t] = fmaf(wd, rlo, gt[t]);
+              dw = wd * (rhi - rlo);
+            } else {
+              gt[t] += rlo;
+              dw = rhi - rlo;
+            }
 #pragma unroll
             for (int s = 0; s < G; ++s) {
               if (dq[s] >= th) acc[t][s] += dw;
               if (RECORD && rp && s0 + s < p.S)
-                rp[(int64_t)p.sky_perm[s0 + s] * p.B * p.n_det * p.n_seg] = K0 + (dq[s] >= th ? 1 : 0);
-            }
-          } else if ((int64_t)base + n1 < 0 || (int64_t)base + n0 >= p.n_bin) {
-            if (RECORD && rp) {
-#pragma unroll
-              for (int s = 0; s < G; ++s)
-                if (s0 + s < p.S) rp[(int64_t)p.sky_perm[s0 + s] * p.B * p.n_det * p.n_seg] = -1;
+                rp[(int64_t)p.sky_perm[s0 + s] * rstride] = K0 + (dq[s] >= th ? 1 : 0);
             }
           } else {
-            // per-sky path: band edge, or a group spread over more than two bins
-            if (n0 < kMLo || n1 > kMHi) {
-              atomicOr(p.err, 1);
-              continue;
-            }
+            // band edge: per-sky validity and per-sky weight sums
+            const bool vlo = (unsigned)K0 < (unsigned)p.n_bin;
+            const bool vhi = (unsigned)(K0 + 1) < (unsigned)p.n_bin;
+            const float rlo = vlo ? load_rho(row, K0) : 0.f;
+            const float rhi = vhi ? load_rho(row, K0 + 1) : 0.f;
             ++ngen;
             float2* dvp = p.dev + (int64_t)b * p.Spad + s0;
             if (!(touched & (1u << t))) {
@@ -197,14 +263,12 @@ __global__ void __launch_bounds__(kGroupThreads, 2) group_kernel(GroupParams p) 
             }
 #pragma unroll
             for (int s = 0; s < G; ++s) {
-              int m = n0;
-              for (int i = n0; i < n1; ++i) m += (dq[s] >= e.th[i - kMLo]) ? 1 : 0;
-              const int K = base + m;
-              const bool ok = K >= 0 && (int64_t)K < p.n_bin;
+              const bool up = dq[s] >= th;
+              const bool ok = up ? vhi : vlo;
               if (RECORD && rp && s0 + s < p.S)
-                rp[(int64_t)p.sky_perm[s0 + s] * p.B * p.n_det * p.n_seg] = ok ? K : -1;
+                rp[(int64_t)p.sky_perm[s0 + s] * rstride] = ok ? K0 + (up ? 1 : 0) : -1;
               if (ok) {
-                acc[t][s] = fmaf(wd, load_rho(row, K), acc[t][s]);
+                acc[t][s] = fmaf(wd, up ? rhi : rlo, acc[t][s]);
                 float2 dv = dvp[s];
                 dv.x += wd;
                 dv.y = fmaf(wd, wd, dv.y);
@@ -218,19 +282,18 @@ __global__ void __launch_bounds__(kGroupThreads, 2) group_kernel(GroupParams p) 
 #pragma unroll
     for (int t = 0; t < T; ++t) {
       gw[t] += (double)gt[t];
-      w1[t] += (double)w1t[t];
-      w2[t] += (double)w2t[t];
 #pragma unroll
       for (int s = 0; s < G; ++s) tot[t][s] += acc[t][s];
     }
   }
-
+  __syncthreads();
   if (!gval) return;
   if (ngen) atomicAdd(p.n_general, ngen);
 #pragma unroll
   for (int t = 0; t < T; ++t) {
     const int b = bcta + bt0 + t;
-    const double base_num = gw[t] - w1[t];
+    const double w1 = s_w1[bt0 + t], w2 = s_w2[bt0 + t];
+    const double base_num = gw[t] - w1;
 #pragma unroll
     for (int s = 0; s < G; ++s) {
       const int sk = s0 + s;
@@ -240,8 +303,8 @@ __global__ void __launch_bounds__(kGroupThreads, 2) group_kernel(GroupParams p) 
         dv1 = dv.x;
         dv2 = dv.y;
       }
-      const float W1 = (float)(w1[t] + (double)dv1);
-      const float W2 = (float)(w2[t] + (double)dv2);
+      const float W1 = (float)(w1 + (double)dv1);
+      const float W2 = (float)(w2 + (double)dv2);
       const float num = (float)(base_num - (double)dv1) + tot[t][s];
       const int64_t o = (int64_t)sk * p.Bpad + b;
       p.psi[o] = W2 > 0.f ? num * rsqrtf(W2) : -INFINITY;
@@ -317,18 +380,20 @@ cudaError_t launch_doppler(const DopplerParams& p, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_group(const GroupParams& p, bool half, bool record, int tile_segments,
+cudaError_t launch_group(const GroupParams& p, bool half, bool record, bool weighted,
                          cudaStream_t st) {
-  (void)tile_segments;
-  const dim3 grid((unsigned)(p.Bpad / kGroupTmplPerCta), (unsigned)((p.NG + kGroupLanes - 1) / kGroupLanes));
+  const dim3 grid((unsigned)(p.Bpad / kGroupTmplPerCta),
+                  (unsigned)((p.NG + kGroupLanes - 1) / kGroupLanes));
   constexpr int TS = 32;
+#define TCW_GROUP(R, REC, W) group_kernel<R, REC, W, TS><<<grid, kGroupThreads, 0, st>>>(p)
   if (half) {
-    if (record) group_kernel<__half, true, TS><<<grid, kGroupThreads, 0, st>>>(p);
-    else group_kernel<__half, false, TS><<<grid, kGroupThreads, 0, st>>>(p);
+    if (record) { if (weighted) TCW_GROUP(__half, true, true); else TCW_GROUP(__half, true, false); }
+    else { if (weighted) TCW_GROUP(__half, false, true); else TCW_GROUP(__half, false, false); }
   } else {
-    if (record) group_kernel<float, true, TS><<<grid, kGroupThreads, 0, st>>>(p);
-    else group_kernel<float, false, TS><<<grid, kGroupThreads, 0, st>>>(p);
+    if (record) { if (weighted) TCW_GROUP(float, true, true); else TCW_GROUP(float, true, false); }
+    else { if (weighted) TCW_GROUP(float, false, true); else TCW_GROUP(float, false, false); }
   }
+#undef TCW_GROUP
   return cudaGetLastError();
 }
 
