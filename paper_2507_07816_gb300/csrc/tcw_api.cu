@@ -76,7 +76,7 @@ struct tcw_ctx {
   // sky
   bool have_sky = false;
   int64_t S = 0;
-  int Spad = 0, NG = 0;
+  int Spad = 0, NG = 0, NGpad = 0;
   std::vector<double> h_nhat;
   bool sky_dirty = true;
   DevBuf nhat_sorted, sky_perm, sky_pos;
@@ -206,6 +206,14 @@ Plan make_plan(const tcw_ctx* c) {
     pl.group_ok = false;
     pl.why = "sizes beyond the group kernel's 32-bit indexing";
   }
+  if (c->D > kMaxStageDet) {
+    pl.group_ok = false;
+    pl.why = "more detectors than the group kernel stages";
+  }
+  if ((int64_t)c->D * c->Nseg * c->Nbin * (c->dtype == TCW_F16 ? 2 : 4) < 64) {
+    pl.group_ok = false;
+    pl.why = "power map smaller than one staged window";
+  }
   pl.nterms = series_terms(c);
   pl.kernel = pl.group_ok ? TCW_KERNEL_GROUP : TCW_KERNEL_LOOKUP;
   return pl;
@@ -226,6 +234,7 @@ tcw_status prepare_sky(tcw_ctx* c) {
   std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
   c->NG = (int)((S + kGroupSkies - 1) / kGroupSkies);
   c->Spad = (int)(((int64_t)c->NG + kGroupLanes - 1) / kGroupLanes) * kSkyPad;
+  c->NGpad = c->Spad / kGroupSkies;
   std::vector<double> ns((size_t)c->Spad * 3);
   std::vector<int32_t> pos(S);
   for (int i = 0; i < c->Spad; ++i) {
@@ -268,7 +277,7 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
   if (kernel == TCW_KERNEL_GROUP) {
     const size_t dqn = (size_t)c->D * c->Nseg * c->Spad;
     TCW_CUDA(c, c->dq.ensure(dqn * sizeof(int32_t)), "doppler table");
-    TCW_CUDA(c, c->gmid.ensure((size_t)c->D * c->Nseg * c->NG * sizeof(float)), "doppler table");
+    TCW_CUDA(c, c->gmid.ensure((size_t)c->D * c->Nseg * c->NGpad * sizeof(float)), "doppler table");
     TCW_CUDA(c, c->dev.ensure(pairs * sizeof(float2)), "scratch");
     DopplerParams dp{};
     dp.vel = c->vel.as<double>();
@@ -277,6 +286,7 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
     dp.n_seg = (int)c->Nseg;
     dp.Spad = c->Spad;
     dp.NG = c->NG;
+    dp.NGpad = c->NGpad;
     dp.group = kGroupSkies;
     dp.inv_q = pl.inv_q;
     dp.dq = c->dq.as<int32_t>();
@@ -300,6 +310,8 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
     GroupParams gp{};
     gp.rho = c->rho.p;
     gp.n_bin = c->Nbin;
+    gp.pitch = c->Nbin;
+    gp.total_elems = (int64_t)c->D * c->Nseg * c->Nbin;
     gp.n_det = c->D;
     gp.n_seg = (int)c->Nseg;
     gp.weights = c->weights.as<float>();
@@ -319,6 +331,7 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
     gp.S = (int)c->S;
     gp.Spad = c->Spad;
     gp.NG = c->NG;
+    gp.NGpad = c->NGpad;
     gp.psi = c->psi.as<float>();
     gp.S_out = keep ? c->st_S.as<float>() : nullptr;
     gp.W1_out = keep ? c->st_W1.as<float>() : nullptr;

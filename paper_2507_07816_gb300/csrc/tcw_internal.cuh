@@ -37,18 +37,26 @@ constexpr int kMLo = -4;
 constexpr int kMHi = 4;
 constexpr int kNThr = kMHi - kMLo;  // 8 thresholds
 
-// Precomputed per (template, segment): 48 bytes, lives in shared memory.
+// Precomputed per (template, segment): 80 bytes, lives in shared memory.
 //   F, Cm  fp32 estimates that choose the candidate bin pair: for a sky group
 //          whose mean Doppler factor is g, the pair starts at
-//          base + round(F*g + Cm)   (Cm = (f - f_min)/df - base - 1/2)
-//   kb     base - kMagicBits, so that base + round(y) = kb + bits(y + kMagic)
+//          base + n0 with n0 = round(F*g + Cm)   (Cm = (f - f_min)/df - base - 1/2),
+//          computed as zb = bits(F*g + Cm + kMagic), n0 = zb - kMagicBits
+//   tha    shared address of th[] minus 4*(kMagicBits + kMLo): threshold of
+//          the pair is at tha + 4*zb
 //   cls    kEntryNone / kEntryInside / kEntryEdge
+//   wa[d]  shared address of detector d's staged power window minus
+//          elem*(kMagicBits + woff_d): power of bin base + n0 is at wa[d] + elem*zb
+//   kb     base - kMagicBits, so that base + n0 = kb + zb
 //   th[i]  round((c_K/f - 1)/q) with c_K = f_min + (K + 1/2) df, K = base + kMLo + i
 struct __align__(16) TrackEntry {
   float F;
   float Cm;
-  int kb;
+  uint32_t tha;
   int cls;
+  uint32_t wa[4];
+  int kb;
+  int pad[3];
   int th[kNThr];
 };
 
@@ -59,20 +67,22 @@ constexpr float kMagic = 12582912.0f;     // 1.5 * 2^23: x + kMagic rounds x to 
 constexpr int kMagicBits = 0x4B400000;    // bit pattern of kMagic
 
 struct GroupParams {
-  const void* rho;         // [D][Nseg][Nbin] float or half
-  int64_t n_bin;
-  int n_det;
+  const void* rho;         // [D][Nseg][pitch] float or half, 16-byte aligned base
+  int64_t n_bin;           // bins per row that belong to the band
+  int64_t pitch;           // elements between rows (>= n_bin)
+  int64_t total_elems;     // D * Nseg * pitch
+  int n_det;               // <= kMaxStageDet
   int n_seg;
   const float* weights;    // [D][Nseg]
   const double* t_mid;     // [Nseg]
-  const int32_t* dq;       // [D][Nseg][Spad] floor(v.nhat/c / q)
-  const float* gmid;       // [D][Nseg][NG] mid-range of v.nhat/c over each sky group
+  const int32_t* dq;       // [D][Nseg][4][NGpad][4] floor(v.nhat/c / q), sky s = 16 g + 4 v + k
+  const float* gmid;       // [D][Nseg][NGpad] mid-range of v.nhat/c over each sky group
   const double* f0;        // sorted bank, [Bpad]
   const double* tau;
   const double* nbr;
   double T0, f_min, df, inv_q;
   int nterms;              // binomial-series length for the track; 0 = pow per entry
-  int B, Bpad, S, Spad, NG;
+  int B, Bpad, S, Spad, NG, NGpad;
   float* psi;              // [Spad][Bpad]
   float* S_out;            // optional [Spad][Bpad]
   float* W1_out;
@@ -82,7 +92,7 @@ struct GroupParams {
   const int32_t* bank_perm;  // sorted -> caller template index
   const int32_t* sky_perm;   // sorted -> caller sky index
   unsigned long long* n_general;
-  int* err;
+  int* err;                // bit 0: window, bit 1: a bounded wait ran out
 };
 
 struct LookupParams {
@@ -111,7 +121,7 @@ struct LookupParams {
 struct DopplerParams {
   const double* vel;       // [D][Nseg][3]
   const double* nhat;      // [Spad][3] sorted
-  int n_det, n_seg, Spad, NG, group;
+  int n_det, n_seg, Spad, NG, NGpad, group;
   double inv_q;
   int32_t* dq;
   float* gmid;
@@ -119,6 +129,12 @@ struct DopplerParams {
 };
 
 constexpr int kMaxSeriesTerms = 24;
+constexpr int kMaxStageDet = 4;          // detectors the group kernel stages in shared memory
+constexpr int kStages = 4;               // depth of the Doppler-table ring
+constexpr int kTileSegments = 32;
+
+// dynamic shared memory of the group kernel for D detectors
+size_t group_smem_bytes(int n_det);
 
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_doppler(const DopplerParams& p, cudaStream_t st);

@@ -124,7 +124,8 @@ extern "C" tcw_status tcw_search_noalloc(int n_det, int64_t n_seg, int64_t n_bin
   const int B = (int)n_tmpl, S = (int)n_sky, D = n_det, Nseg = (int)n_seg;
   const int Bpad = (B + kGroupTmplPerCta - 1) / kGroupTmplPerCta * kGroupTmplPerCta;
   const int NG = (S + kGroupSkies - 1) / kGroupSkies;
-  const int Spad = (NG * kGroupSkies + 31) / 32 * 32;
+  const int NGpad = (NG + kGroupLanes - 1) / kGroupLanes * kGroupLanes;
+  const int Spad = NGpad * kGroupSkies;
   size_t off = 0;
   auto take = [&](size_t bytes) {
     const size_t at = off;
@@ -137,7 +138,7 @@ extern "C" tcw_status tcw_search_noalloc(int n_det, int64_t n_seg, int64_t n_bin
   const size_t o_nhat = take((size_t)Spad * 24);
   const size_t o_ones = take(weights ? 0 : (size_t)D * Nseg * 4);
   const size_t o_dq = take((size_t)D * Nseg * Spad * 4);
-  const size_t o_gb = take((size_t)D * Nseg * NG * 4);
+  const size_t o_gb = take((size_t)D * Nseg * NGpad * 4);
   const size_t o_psi = take((size_t)Spad * Bpad * 4);
   const size_t o_dev = take((size_t)Spad * Bpad * 8);
   if (off > kTcwNoallocScratchBytes) return TCW_ERR_UNSUPPORTED;
@@ -213,6 +214,7 @@ extern "C" tcw_status tcw_search_noalloc(int n_det, int64_t n_seg, int64_t n_bin
   dp.n_seg = Nseg;
   dp.Spad = Spad;
   dp.NG = NG;
+  dp.NGpad = NGpad;
   dp.group = kGroupSkies;
   dp.inv_q = std::ldexp(1.0, -e);
   dp.dq = reinterpret_cast<int32_t*>(base + o_dq);
@@ -227,10 +229,15 @@ extern "C" tcw_status tcw_search_noalloc(int n_det, int64_t n_seg, int64_t n_bin
   std::memcpy(&spread, &spread_bits, 4);
   float* psi = reinterpret_cast<float*>(base + o_psi);
   const float* wts = weights ? weights : pp.ones;
-  if (fmax_bins * (double)spread * 0.5 + 0.02 <= 0.45) {
+  const size_t esz = dtype == TCW_F16 ? 2 : 4;
+  const bool group_ok = fmax_bins * (double)spread * 0.5 + 0.02 <= 0.45 && D <= kMaxStageDet &&
+                        ((uintptr_t)rho % 16) == 0 && (size_t)D * Nseg * n_bin * esz >= 64;
+  if (group_ok) {
     GroupParams gp{};
     gp.rho = rho;
     gp.n_bin = n_bin;
+    gp.pitch = n_bin;
+    gp.total_elems = (int64_t)D * Nseg * n_bin;
     gp.n_det = D;
     gp.n_seg = Nseg;
     gp.weights = wts;
@@ -250,6 +257,7 @@ extern "C" tcw_status tcw_search_noalloc(int n_det, int64_t n_seg, int64_t n_bin
     gp.S = S;
     gp.Spad = Spad;
     gp.NG = NG;
+    gp.NGpad = NGpad;
     gp.psi = psi;
     gp.dev = reinterpret_cast<float2*>(base + o_dev);
     gp.bank_perm = pp.bank_perm;
