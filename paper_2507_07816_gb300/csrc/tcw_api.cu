@@ -81,7 +81,7 @@ struct tcw_ctx {
   bool sky_dirty = true;
   DevBuf nhat_sorted, sky_perm, sky_pos;
   // derived and outputs
-  DevBuf dq, gmid, psi, st_S, st_W1, st_W2, dev, flags, stage_f, stage_i;
+  DevBuf dq, psi, st_S, st_W1, st_W2, dev, flags, stage_f, stage_i;
   bool have_result = false, stats_kept = false;
   tcw_info info{};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -275,9 +275,8 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
   int launches = 0;
 
   if (kernel == TCW_KERNEL_GROUP) {
-    const size_t dqn = (size_t)c->D * c->Nseg * c->Spad;
-    TCW_CUDA(c, c->dq.ensure(dqn * sizeof(int32_t)), "doppler table");
-    TCW_CUDA(c, c->gmid.ensure((size_t)c->D * c->Nseg * c->NGpad * sizeof(float)), "doppler table");
+    const size_t blkn = (size_t)(c->Spad / kSkyPad) * c->Nseg * c->D * kBlockWords;
+    TCW_CUDA(c, c->dq.ensure(blkn * sizeof(int32_t)), "doppler table");
     TCW_CUDA(c, c->dev.ensure(pairs * sizeof(float2)), "scratch");
     DopplerParams dp{};
     dp.vel = c->vel.as<double>();
@@ -286,11 +285,9 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
     dp.n_seg = (int)c->Nseg;
     dp.Spad = c->Spad;
     dp.NG = c->NG;
-    dp.NGpad = c->NGpad;
     dp.group = kGroupSkies;
     dp.inv_q = pl.inv_q;
-    dp.dq = c->dq.as<int32_t>();
-    dp.gmid = c->gmid.as<float>();
+    dp.blk = c->dq.as<int32_t>();
     dp.spread_max = reinterpret_cast<unsigned*>(c->flags.as<char>() + 16);
     TCW_CUDA(c, launch_doppler(dp, c->stream), "doppler_kernel launch");
     ++launches;
@@ -316,8 +313,7 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
     gp.n_seg = (int)c->Nseg;
     gp.weights = c->weights.as<float>();
     gp.t_mid = c->t_mid.as<double>();
-    gp.dq = c->dq.as<int32_t>();
-    gp.gmid = c->gmid.as<float>();
+    gp.blk = c->dq.as<int32_t>();
     gp.f0 = c->f0.as<double>();
     gp.tau = c->tau.as<double>();
     gp.nbr = c->nbr.as<double>();
@@ -461,7 +457,7 @@ tcw_status tcw_destroy(tcw_ctx* c) {
   cudaStreamSynchronize(c->stream);
   DevBuf* bufs[] = {&c->rho, &c->t_mid, &c->weights, &c->vel, &c->f0, &c->tau, &c->nbr,
                     &c->bank_perm, &c->bank_pos, &c->nhat_sorted, &c->sky_perm, &c->sky_pos,
-                    &c->dq, &c->gmid, &c->psi, &c->st_S, &c->st_W1, &c->st_W2, &c->dev,
+                    &c->dq, &c->psi, &c->st_S, &c->st_W1, &c->st_W2, &c->dev,
                     &c->flags, &c->stage_f, &c->stage_i};
   for (DevBuf* b : bufs) b->release();
   if (c->ev0) cudaEventDestroy(c->ev0);

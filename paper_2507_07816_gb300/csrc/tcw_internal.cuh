@@ -75,8 +75,7 @@ struct GroupParams {
   int n_seg;
   const float* weights;    // [D][Nseg]
   const double* t_mid;     // [Nseg]
-  const int32_t* dq;       // [D][Nseg][4][NGpad][4] floor(v.nhat/c / q), sky s = 16 g + 4 v + k
-  const float* gmid;       // [D][Nseg][NGpad] mid-range of v.nhat/c over each sky group
+  const int32_t* blk;      // Doppler blocks [NGpad/64][Nseg][D][kBlockWords], see kBlockWords
   const double* f0;        // sorted bank, [Bpad]
   const double* tau;
   const double* nbr;
@@ -118,13 +117,18 @@ struct LookupParams {
   const int32_t* sky_perm;
 };
 
+// One Doppler block per (sky chunk of 1024 sorted skies, segment, detector):
+//   words [0, 1024): floor(v.nhat/c / q) of sky 16 g + 4 v + k at (v * 64 + g) * 4 + k
+//   words [1024, 1088): fp32 mid-range of v.nhat/c over sky group g (bits)
+// so that one bulk copy moves a chunk's segment for every detector.
+constexpr int kBlockWords = 1088;
+
 struct DopplerParams {
   const double* vel;       // [D][Nseg][3]
   const double* nhat;      // [Spad][3] sorted
-  int n_det, n_seg, Spad, NG, NGpad, group;
+  int n_det, n_seg, Spad, NG, group;
   double inv_q;
-  int32_t* dq;
-  float* gmid;
+  int32_t* blk;            // [Spad/1024][Nseg][D][kBlockWords]
   unsigned* spread_max;    // float bits of max (hi - lo) of v.nhat/c over the groups
 };
 

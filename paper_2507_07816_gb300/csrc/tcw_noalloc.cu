@@ -137,8 +137,7 @@ extern "C" tcw_status tcw_search_noalloc(int n_det, int64_t n_seg, int64_t n_bin
   const size_t o_bperm = take((size_t)Bpad * 4), o_sperm = take((size_t)Spad * 4);
   const size_t o_nhat = take((size_t)Spad * 24);
   const size_t o_ones = take(weights ? 0 : (size_t)D * Nseg * 4);
-  const size_t o_dq = take((size_t)D * Nseg * Spad * 4);
-  const size_t o_gb = take((size_t)D * Nseg * NGpad * 4);
+  const size_t o_dq = take((size_t)(Spad / kSkyPad) * Nseg * D * kBlockWords * 4);
   const size_t o_psi = take((size_t)Spad * Bpad * 4);
   const size_t o_dev = take((size_t)Spad * Bpad * 8);
   if (off > kTcwNoallocScratchBytes) return TCW_ERR_UNSUPPORTED;
@@ -214,11 +213,9 @@ extern "C" tcw_status tcw_search_noalloc(int n_det, int64_t n_seg, int64_t n_bin
   dp.n_seg = Nseg;
   dp.Spad = Spad;
   dp.NG = NG;
-  dp.NGpad = NGpad;
   dp.group = kGroupSkies;
   dp.inv_q = std::ldexp(1.0, -e);
-  dp.dq = reinterpret_cast<int32_t*>(base + o_dq);
-  dp.gmid = reinterpret_cast<float*>(base + o_gb);
+  dp.blk = reinterpret_cast<int32_t*>(base + o_dq);
   dp.spread_max = reinterpret_cast<unsigned*>(base + o_flags + 32);
   if (launch_doppler(dp, st) != cudaSuccess) return TCW_ERR_CUDA;
   unsigned spread_bits = 0;
@@ -242,8 +239,7 @@ extern "C" tcw_status tcw_search_noalloc(int n_det, int64_t n_seg, int64_t n_bin
     gp.n_seg = Nseg;
     gp.weights = wts;
     gp.t_mid = t_mid;
-    gp.dq = dp.dq;
-    gp.gmid = dp.gmid;
+    gp.blk = dp.blk;
     gp.f0 = pp.f0p;
     gp.tau = pp.taup;
     gp.nbr = pp.nbrp;

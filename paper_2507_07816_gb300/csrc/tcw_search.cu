@@ -37,20 +37,22 @@ __global__ void doppler_kernel(DopplerParams p) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
     const int s = (int)(i % p.Spad);
     const int64_t dj = i / p.Spad;
+    const int d = (int)(dj / p.n_seg), j = (int)(dj % p.n_seg);
     const double* v = p.vel + dj * 3;
     const double* n = p.nhat + (int64_t)s * 3;
     const double dD = (v[0] * n[0] + v[1] * n[1] + v[2] * n[2]) / kLightSpeed;
     const double qd = floor(dD * p.inv_q);
-    const int sg = s >> 4, sv = (s >> 2) & 3, sk = s & 3;
-    p.dq[((dj * 4 + sv) * p.NGpad + sg) * 4 + sk] = (int32_t)fmax(fmin(qd, 2147483647.0), -2147483648.0);
+    const int c = s >> 10, gl = (s >> 4) & 63, sv = (s >> 2) & 3, sk = s & 3;
+    int32_t* blk = p.blk + (((int64_t)c * p.n_seg + j) * p.n_det + d) * kBlockWords;
+    blk[(sv * 64 + gl) * 4 + sk] = (int32_t)fmax(fmin(qd, 2147483647.0), -2147483648.0);
     float lo = (float)dD, hi = lo;
     for (int off = 1; off < p.group; off <<= 1) {
       lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, off));
       hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, off));
     }
-    if (s % p.group == 0 && s / p.group < p.NG) {
-      p.gmid[dj * p.NGpad + s / p.group] = 0.5f * (lo + hi);
-      spread = fmaxf(spread, hi - lo);
+    if (s % p.group == 0) {
+      blk[1024 + gl] = __float_as_int(0.5f * (lo + hi));
+      if (s / p.group < p.NG) spread = fmaxf(spread, hi - lo);
     }
   }
   for (int off = 16; off > 0; off >>= 1) spread = fmaxf(spread, __shfl_xor_sync(0xffffffffu, spread, off));
@@ -67,7 +69,7 @@ __global__ void doppler_kernel(DopplerParams p) {
 // Shared-memory staging: mbarriers and bulk asynchronous copies (PTX).
 // ---------------------------------------------------------------------------
 constexpr int kMaxSpin = 1 << 26;              // bound on every mbarrier wait
-constexpr int kStageDetBytes = kGroupLanes * 16 * 4 + kGroupLanes * 4;  // dq slabs + gmid
+constexpr int kStageDetBytes = kBlockWords * 4;  // one Doppler block per detector
 constexpr int kWinBytes = 64;                  // staged power window per (entry, detector)
 
 __device__ __forceinline__ uint32_t smem_addr(const void* ptr) {
@@ -164,14 +166,14 @@ __device__ __forceinline__ void pred_add(float& acc, int q, int th, float dw) {
 // p.nterms terms (coefficients in coef[]), or by pow when p.nterms == 0.
 // The thresholds theta_K = c_K/f - 1 = (f_min h - 1) + (K + 1/2) df h are put
 // on the q grid through a 64-bit fixed-point chain with 8 extra bits.
-// Also issues the bulk copies of the 64-byte power windows around the track
-// (one per detector) and returns the bytes requested.
+// Also issues the asynchronous copies (16 bytes each) of the 64-byte power
+// windows around the track, one window per detector, and returns their bytes.
 // ---------------------------------------------------------------------------
 template <typename RhoT>
 __device__ __forceinline__ uint32_t compute_entry(const GroupParams& p, const double* coef,
                                                   double ha, double delta, int b, int j,
                                                   bool valid, float fmin_f, float inv_df_f,
-                                                  TrackEntry& e, uint32_t win_dst, uint32_t wbar) {
+                                                  TrackEntry& e, uint32_t win_dst) {
   if (!valid) {
     e.cls = kEntryNone;
     return 0;
@@ -218,7 +220,10 @@ __device__ __forceinline__ uint32_t compute_entry(const GroupParams& p, const do
     const int woff = (int)(gs - row - base);
     const uint32_t dst = win_dst + d * kWinBytes;
     e.wa[d] = dst - (uint32_t)sizeof(RhoT) * (uint32_t)(kMagicBits + woff);
-    bulk_g2s(dst, rho + gs, kWinBytes, wbar);
+    const char* src = reinterpret_cast<const char*>(rho + gs);
+#pragma unroll
+    for (int c = 0; c < kWinBytes / 16; ++c)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + 16 * c), "l"(src + 16 * c) : "memory");
   }
   return (uint32_t)(p.n_det * kWinBytes);
 }
@@ -281,23 +286,16 @@ __global__ void __launch_bounds__(kGroupThreads, 2) group_kernel(GroupParams p) 
   }
   __syncthreads();
 
-  // producer (thread 0): fill f of the Doppler ring = segment f, stage f % kStages
-  const size_t dq_slab = (size_t)p.NGpad * 16;  // bytes per (d, j, v) row of the dq table
+  // producer (thread 0): fill f of the Doppler ring = segment f, stage f % kStages,
+  // one bulk copy of the sky chunk's blocks for every detector
+  const int32_t* blk_c = p.blk + (int64_t)blockIdx.y * p.n_seg * D * kBlockWords;
   auto issue_fill = [&](int f) -> bool {
     const int st = f % kStages;
     if (!mbar_wait(bar_empty + 8 * st, ((f / kStages) & 1) ^ 1, p.err)) return false;
     fence_proxy_async();
     const uint32_t full = bar_full + 8 * st;
     mbar_arrive_expect_tx(full, stage_bytes);
-    const uint32_t dst0 = ring_addr + st * stage_bytes;
-    for (int d = 0; d < D; ++d) {
-      const int64_t dj = (int64_t)d * p.n_seg + f;
-      const uint32_t dst = dst0 + d * kStageDetBytes;
-      const unsigned char* src =
-          reinterpret_cast<const unsigned char*>(p.dq) + (size_t)dj * 4 * dq_slab + (size_t)g0 * 16;
-      for (int v = 0; v < 4; ++v) bulk_g2s(dst + v * kGroupLanes * 16, src + v * dq_slab, kGroupLanes * 16, full);
-      bulk_g2s(dst + 4 * kGroupLanes * 16, p.gmid + dj * p.NGpad + g0, kGroupLanes * 4, full);
-    }
+    bulk_g2s(ring_addr + st * stage_bytes, blk_c + (int64_t)f * D * kBlockWords, stage_bytes, full);
     return true;
   };
   int issued = 0;
@@ -345,8 +343,10 @@ __global__ void __launch_bounds__(kGroupThreads, 2) group_kernel(GroupParams p) 
       const bool valid = jj < jn && p.t_mid[min(j, p.n_seg - 1)] >= p.T0;
       const uint32_t bytes = compute_entry<RhoT>(
           p, coef + bt * kMaxSeriesTerms, s_ha[bt], s_dt[jj] * s_iota[bt], bcta + bt, j, valid, fmin_f,
-          inv_df_f, ent[e], smem_addr(smem + L.win) + e * D * kWinBytes, bar_win);
-      mbar_arrive_expect_tx(bar_win, bytes);
+          inv_df_f, ent[e], smem_addr(smem + L.win) + e * D * kWinBytes);
+      (void)bytes;
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      mbar_arrive(bar_win);
     }
     if (!mbar_wait(bar_win, tile & 1, p.err)) { ok = false; break; }
     if (tid < TPC) {
