@@ -81,7 +81,7 @@ struct tcw_ctx {
   bool sky_dirty = true;
   DevBuf nhat_sorted, sky_perm, sky_pos;
   // derived and outputs
-  DevBuf dq, psi, st_S, st_W1, st_W2, dev, flags, stage_f, stage_i;
+  DevBuf dq, anchors, psi, st_S, st_W1, st_W2, dev, flags, stage_f, stage_i;
   bool have_result = false, stats_kept = false;
   tcw_info info{};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -328,6 +328,13 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
     gp.Spad = c->Spad;
     gp.NG = c->NG;
     gp.NGpad = c->NGpad;
+    gp.n_chunks = c->Spad / kSkyPad;
+    gp.n_items = gp.n_chunks * (c->Bpad / kGroupTmplPerCta);
+    gp.n_tiles = (int)((c->Nseg + kTileSegments - 1) / kTileSegments);
+    if (pl.nterms > 0) {
+      TCW_CUDA(c, c->anchors.ensure((size_t)c->Bpad * gp.n_tiles * 2 * sizeof(double)), "anchors");
+      gp.anchors = c->anchors.as<double>();
+    }
     gp.psi = c->psi.as<float>();
     gp.S_out = keep ? c->st_S.as<float>() : nullptr;
     gp.W1_out = keep ? c->st_W1.as<float>() : nullptr;
@@ -339,6 +346,10 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
     gp.n_general = reinterpret_cast<unsigned long long*>(c->flags.as<char>() + 8);
     gp.err = c->flags.as<int>();
     TCW_CUDA(c, cudaEventRecord(c->ev0, c->stream), "event");
+    if (pl.nterms > 0) {
+      TCW_CUDA(c, launch_anchors(gp, c->anchors.as<double>(), c->stream), "anchor_kernel launch");
+      ++launches;
+    }
     TCW_CUDA(c, launch_group(gp, c->dtype == TCW_F16, record, !c->unit_weights, c->stream),
              "group_kernel launch");
     TCW_CUDA(c, cudaEventRecord(c->ev1, c->stream), "event");
@@ -457,7 +468,7 @@ tcw_status tcw_destroy(tcw_ctx* c) {
   cudaStreamSynchronize(c->stream);
   DevBuf* bufs[] = {&c->rho, &c->t_mid, &c->weights, &c->vel, &c->f0, &c->tau, &c->nbr,
                     &c->bank_perm, &c->bank_pos, &c->nhat_sorted, &c->sky_perm, &c->sky_pos,
-                    &c->dq, &c->psi, &c->st_S, &c->st_W1, &c->st_W2, &c->dev,
+                    &c->dq, &c->anchors, &c->psi, &c->st_S, &c->st_W1, &c->st_W2, &c->dev,
                     &c->flags, &c->stage_f, &c->stage_i};
   for (DevBuf* b : bufs) b->release();
   if (c->ev0) cudaEventDestroy(c->ev0);

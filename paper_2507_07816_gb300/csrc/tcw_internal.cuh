@@ -81,7 +81,12 @@ struct GroupParams {
   const double* nbr;
   double T0, f_min, df, inv_q;
   int nterms;              // binomial-series length for the track; 0 = pow per entry
+  const double* anchors;   // [Bpad][n_tiles][2]: 1/f and 1/(tau + t_a - T0) at each tile's
+                           // anchor t_a; read only when nterms > 0
+  int n_tiles;             // ceil(Nseg / kTileSegments)
   int B, Bpad, S, Spad, NG, NGpad;
+  int n_chunks;            // Spad / 1024 sky chunks
+  int n_items;             // n_chunks * Bpad / 8 work items; item i runs on CTA i mod grid
   float* psi;              // [Spad][Bpad]
   float* S_out;            // optional [Spad][Bpad]
   float* W1_out;
@@ -133,12 +138,13 @@ struct DopplerParams {
 };
 
 constexpr int kMaxSeriesTerms = 24;
-constexpr int kMaxStageDet = 4;          // detectors the group kernel stages in shared memory
-constexpr int kStages = 4;               // depth of the Doppler-table ring
+constexpr int kMaxStageDet = 2;          // detectors the group kernel stages in shared memory
 constexpr int kTileSegments = 32;
 
 // dynamic shared memory of the group kernel for D detectors
 size_t group_smem_bytes(int n_det);
+// tile anchors of every (sorted template, tile) into anchors[Bpad * n_tiles * 2]
+cudaError_t launch_anchors(const GroupParams& p, double* anchors, cudaStream_t st);
 
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_doppler(const DopplerParams& p, cudaStream_t st);
@@ -155,11 +161,10 @@ cudaError_t launch_unpermute(const float* src, int Spad, int Bpad, int S, int B,
 // group-kernel geometry (shared by the host planner and the kernel)
 constexpr int kGroupSkies = 16;     // skies per thread
 constexpr int kGroupTmpl = 2;       // templates per thread
-constexpr int kGroupUnits = 4;      // template pairs per CTA
+constexpr int kGroupUnits = 4;      // template pairs per work item
 constexpr int kGroupWarps = 2;      // warps per unit
 constexpr int kGroupLanes = 32 * kGroupWarps;             // sky groups per CTA
-constexpr int kGroupThreads = kGroupUnits * kGroupLanes;  // 256
-constexpr int kGroupTmplPerCta = kGroupUnits * kGroupTmpl;  // 8
+constexpr int kGroupTmplPerCta = kGroupUnits * kGroupTmpl;  // 8 templates per work item
 constexpr int kSkyPad = kGroupSkies * kGroupLanes;        // 1024
 
 }  // namespace tcw

@@ -254,6 +254,9 @@ extern "C" tcw_status tcw_search_noalloc(int n_det, int64_t n_seg, int64_t n_bin
     gp.Spad = Spad;
     gp.NG = NG;
     gp.NGpad = NGpad;
+    gp.n_chunks = Spad / kSkyPad;
+    gp.n_items = gp.n_chunks * (Bpad / kGroupTmplPerCta);
+    gp.n_tiles = (int)((n_seg + kTileSegments - 1) / kTileSegments);
     gp.psi = psi;
     gp.dev = reinterpret_cast<float2*>(base + o_dev);
     gp.bank_perm = pp.bank_perm;

@@ -1,0 +1,473 @@
+// tcw_persist.cu -- the hot loop: a persistent, warp-specialised group kernel.
+//
+// One CTA per SM walks its share of the work items (item i runs on CTA
+// i mod gridDim.x); an item is 8 sorted templates x one chunk of 1024 sorted
+// sky directions x every segment and detector.
+//
+//   producer warps (3)   warp w owns every third batch of 4 segments: the
+//                        8 x 4 track entries in FP64 (Eq. 1, one lane per
+//                        entry, from the tile anchors of anchor_kernel), their
+//                        64-byte power windows (16-byte async copies), the
+//                        segment weights, and one bulk copy of the chunk's
+//                        Doppler blocks per segment (Eq. 2 factor on the
+//                        fixed-point grid) into a 16-stage shared-memory ring
+//   consumer warps (8)   per segment: for each detector and each of two
+//                        templates, the candidate bin pair of the lane's
+//                        16-sky group, two window reads, and per sky one int32
+//                        compare + one predicated add (Sec. 2 weighted sum),
+//                        plus the weight sums W1, W2; Psi of Eq. 4 at the end
+//                        of the item
+//
+// Ring stage q holds segment q mod Nseg of the CTA's (q / Nseg)-th item, so
+// both sides derive every index from q alone.  The ring is driven by
+// mbarriers (full: one producer arrival + the bulk-copy bytes; empty: one
+// arrival per consumer warp); every wait is bounded.
+#include <climits>
+
+#include "tcw_internal.cuh"
+#include "tcw_ptx.cuh"
+
+namespace tcw {
+namespace {
+
+constexpr int kPT = kGroupTmplPerCta;             // templates per work item
+constexpr int kConsumerWarps = 8;
+constexpr int kConsumers = kConsumerWarps * 32;   // 4 template pairs x 64 sky groups
+constexpr int kProducerWarps = 3;
+constexpr int kThreads = kConsumers + kProducerWarps * 32;
+constexpr int kBatch = 32 / kPT;                  // segments per producer batch (one lane per entry)
+constexpr int kRing = 16;                         // ring stages
+constexpr int kTileSeg = kTileSegments;           // fp32 partial-sum tile and anchor spacing
+static_assert(kPT == 8 && kBatch == 4, "geometry");
+static_assert(kConsumers == (kPT / 2) * kGroupLanes, "two templates per consumer thread");
+static_assert(kRing >= (kProducerWarps + 1) * kBatch, "every producer's batch fits the ring");
+
+struct PersistLayout {
+  size_t ent, win, hdr, stage, coef, bar, total;
+  __host__ __device__ explicit PersistLayout(int D) {
+    ent = (size_t)D * kStageDetBytes;                 // Doppler blocks first (bulk-copy target)
+    win = ent + (size_t)kPT * sizeof(TrackEntry);
+    hdr = win + (size_t)kPT * D * kWinBytes;          // segment weight of each detector
+    stage = (hdr + 16 + 127) & ~(size_t)127;
+    coef = stage * kRing;
+    bar = coef + (size_t)kProducerWarps * kPT * kMaxSeriesTerms * 8;
+    total = bar + (size_t)2 * kRing * 8;
+  }
+};
+
+// Tile anchor of a tile's segments: the middle segment's time, or T0 when
+// that is earlier.
+__device__ __forceinline__ double tile_anchor_time(const GroupParams& p, int ti) {
+  const int j0 = ti * kTileSeg;
+  const int jn = min(kTileSeg, p.n_seg - j0);
+  return fmax(p.t_mid[j0 + (jn - 1) / 2], p.T0);
+}
+
+// ---------------------------------------------------------------------------
+// Tile anchors (Eq. 1 in FP64), one thread per (sorted template, tile):
+//   anchors[b][ti] = { 1/f(t_a) = (1 + (t_a - T0)/tau)^(1/(n-1)) / f0,
+//                      1/(tau + t_a - T0) }
+// ---------------------------------------------------------------------------
+__global__ void anchor_kernel(GroupParams p, double* anchors) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)p.Bpad * p.n_tiles) return;
+  const int b = (int)(i / p.n_tiles), ti = (int)(i % p.n_tiles);
+  const double ta = tile_anchor_time(p, ti);
+  const double tau = p.tau[b];
+  anchors[i * 2] = pow((ta - p.T0) / tau + 1.0, 1.0 / (p.nbr[b] - 1.0)) / p.f0[b];
+  anchors[i * 2 + 1] = 1.0 / (tau + (ta - p.T0));
+}
+
+// ---------------------------------------------------------------------------
+// Track entry of one (sorted template b, segment j) from its tile anchor:
+// 1/f(t_j) = h_a (1 + delta)^r with r = 1/(n-1), delta = (t_j - t_a) iota_a,
+// by a binomial series of p.nterms terms (coefficients coef[]), or by pow when
+// p.nterms == 0.  The thresholds theta_K = c_K/f - 1 =
+// (f_min h - 1) + (K + 1/2) df h go on the q grid through a 64-bit fixed-point
+// chain with 8 extra bits.  Issues the 16-byte asynchronous copies of the
+// 64-byte power windows around the track.
+// ---------------------------------------------------------------------------
+template <typename RhoT>
+__device__ __forceinline__ void compute_entry(const GroupParams& p, const double* coef, int b, int j,
+                                              float fmin_f, float inv_df_f, TrackEntry& e,
+                                              uint32_t win_dst) {
+  const double tj = p.t_mid[j];
+  if (!(tj >= p.T0)) {
+    e.cls = kEntryNone;
+    return;
+  }
+  double h;
+  if (p.nterms > 0) {
+    const int ti = j / kTileSeg;
+    const double2 an = reinterpret_cast<const double2*>(p.anchors)[(int64_t)b * p.n_tiles + ti];
+    const double delta = (tj - tile_anchor_time(p, ti)) * an.y;
+    double R = coef[p.nterms - 1];
+    for (int k = p.nterms - 2; k >= 0; --k) R = fma(R, delta, coef[k]);
+    h = an.x * R;
+  } else {
+    h = pow((tj - p.T0) / p.tau[b] + 1.0, 1.0 / (p.nbr[b] - 1.0)) / p.f0[b];
+  }
+  const float f = __frcp_rn((float)h);
+  const float x = (f - fmin_f) * inv_df_f;
+  const int base = __float2int_rn(x);
+  if (!(base >= -kMHi && (int64_t)base < p.n_bin - kMLo)) {
+    e.cls = kEntryNone;
+    return;
+  }
+  e.cls = (base + kMLo >= 0 && (int64_t)base + kMHi <= p.n_bin - 1) ? kEntryInside : kEntryEdge;
+  e.F = f * inv_df_f;
+  e.Cm = (x - (float)base) - 0.5f;
+  e.kb = base - kMagicBits;
+  e.tha = smem_addr(&e.th[0]) - 4u * (uint32_t)(kMagicBits + kMLo);
+  const double Q = p.df * h;
+  const double A0 = fma((double)(base + kMLo) + 0.5, Q, fma(p.f_min, h, -1.0));
+  const double sc = p.inv_q * 256.0;
+  const long long a = __double2ll_rn(A0 * sc), st = __double2ll_rn(Q * sc);
+#pragma unroll
+  for (int i = 0; i < kNThr; ++i) {
+    long long v = (a + (long long)i * st + 128) >> 8;
+    v = v > 2147483647LL ? 2147483647LL : (v < -2147483647LL ? -2147483647LL : v);
+    e.th[i] = (int)v;
+  }
+  // power windows: 64 bytes from a 16-byte boundary at or below bin base + kMLo,
+  // clamped into the array (the valid candidates stay inside the window)
+  constexpr int64_t E = 16 / sizeof(RhoT), W = kWinBytes / sizeof(RhoT);
+  const RhoT* rho = static_cast<const RhoT*>(p.rho);
+  for (int d = 0; d < p.n_det; ++d) {
+    const int64_t row = ((int64_t)d * p.n_seg + j) * p.pitch;
+    int64_t gs = row + base + kMLo;
+    gs -= ((gs % E) + E) % E;
+    gs = gs < 0 ? 0 : (gs > p.total_elems - W ? p.total_elems - W : gs);
+    const int woff = (int)(gs - row - base);
+    const uint32_t dst = win_dst + d * kWinBytes;
+    e.wa[d] = dst - (uint32_t)sizeof(RhoT) * (uint32_t)(kMagicBits + woff);
+    const char* src = reinterpret_cast<const char*>(rho + gs);
+#pragma unroll
+    for (int c = 0; c < kWinBytes / 16; ++c) cp_async16(dst + 16 * c, src + 16 * c);
+  }
+}
+
+template <typename RhoT, bool RECORD, bool WEIGHTED, int DT>
+__global__ void __launch_bounds__(kThreads, 1) group_kernel(GroupParams p) {
+  constexpr int G = kGroupSkies;
+  constexpr uint32_t ESZ = sizeof(RhoT);
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int D = DT > 0 ? DT : p.n_det;
+  const PersistLayout L(D);
+  const uint32_t smem0 = smem_addr(smem);
+  const uint32_t bar_full = smem0 + (uint32_t)L.bar;
+  const uint32_t bar_empty = bar_full + kRing * 8;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const uint32_t dq_bytes = (uint32_t)(D * kStageDetBytes);
+  const int n_seg = p.n_seg;
+
+  if (tid == 0) {
+    for (int i = 0; i < kRing; ++i) {
+      mbar_init(bar_full + 8 * i, 1);
+      mbar_init(bar_empty + 8 * i, kConsumerWarps);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  if (tid >= kConsumers) {
+    // ======================= producer warps =======================
+    // Batches are numbered in ring order; warp pw takes n = pw, pw + 3, ...
+    // Each warp fills its batches in increasing order, so a stage it waits
+    // for was last used by an earlier batch and the waits cannot deadlock.
+    const int pw = (tid - kConsumers) >> 5;
+    const int lt = lane % kPT, lk = lane / kPT;   // template and segment slot of this lane
+    double* coef = reinterpret_cast<double*>(smem + L.coef) + pw * kPT * kMaxSeriesTerms;
+    const float fmin_f = (float)p.f_min, inv_df_f = (float)(1.0 / p.df);
+    const int bpi = (n_seg + kBatch - 1) / kBatch;   // batches per item
+    long long coef_item = -1;
+    for (long long n = pw;; n += kProducerWarps) {
+      const long long ki = n / bpi;
+      const long long item = blockIdx.x + ki * gridDim.x;
+      if (item >= p.n_items) break;
+      const int jb = (int)(n % bpi) * kBatch;
+      const int nb = min(kBatch, n_seg - jb);
+      const long long q0 = ki * n_seg + jb;           // ring position of the batch's first segment
+      const int chunk = (int)(item % p.n_chunks);
+      const int b0 = (int)(item / p.n_chunks) * kPT;
+      if (coef_item != item) {
+        __syncwarp();
+        if (lane < kPT) {
+          const double r = 1.0 / (p.nbr[b0 + lane] - 1.0);
+          double c = 1.0;
+          for (int k = 0; k < p.nterms; ++k) {
+            coef[lane * kMaxSeriesTerms + k] = c;
+            c = c * (r - k) / (k + 1);
+          }
+        }
+        coef_item = item;
+        __syncwarp();
+      }
+      int ok = 1;
+      if (lane == 0) {
+        for (int k = 0; k < nb && ok; ++k) {
+          const long long q = q0 + k;
+          ok = mbar_wait(bar_empty + 8 * (unsigned)(q % kRing), (unsigned)(((q / kRing) & 1) ^ 1), p.err);
+        }
+      }
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      fence_proxy_async();
+      if (lk < nb) {
+        const int j = jb + lk;
+        const unsigned s = (unsigned)((q0 + lk) % kRing);
+        unsigned char* st = smem + s * L.stage;
+        TrackEntry& e = *reinterpret_cast<TrackEntry*>(st + L.ent + lt * sizeof(TrackEntry));
+        compute_entry<RhoT>(p, coef + lt * kMaxSeriesTerms, b0 + lt, j, fmin_f, inv_df_f, e,
+                            smem0 + s * (uint32_t)L.stage + (uint32_t)L.win + lt * D * kWinBytes);
+        if (lt < D) reinterpret_cast<float*>(st + L.hdr)[lt] = p.weights[(int64_t)lt * n_seg + j];
+      }
+      cp_async_wait_all();
+      __syncwarp();
+      if (lane == 0) {
+        for (int k = 0; k < nb; ++k) {
+          const long long q = q0 + k;
+          const unsigned s = (unsigned)(q % kRing);
+          const uint32_t full = bar_full + 8 * s;
+          mbar_arrive_expect_tx(full, dq_bytes);
+          bulk_g2s(smem0 + s * (uint32_t)L.stage,
+                   p.blk + (((int64_t)chunk * n_seg + jb + k) * D) * kBlockWords, dq_bytes, full);
+        }
+      }
+    }
+    return;
+  }
+
+  // ======================= consumer warps =======================
+  const int u = tid / kGroupLanes, l = tid % kGroupLanes;  // template pair, sky group in the chunk
+  unsigned long long ngen = 0;
+  long long q = 0;
+  bool ok = true;
+  for (long long item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
+    const int chunk = (int)(item % p.n_chunks);
+    const int b0 = (int)(item / p.n_chunks) * kPT;
+    const int g = chunk * kGroupLanes + l;
+    const bool gval = g < p.NG;
+    const int s0 = g * G;
+    float acc[2][G], tot[2][G], gt[2], w1t[2], w2t[2];
+    double gw[2], w1[2], w2[2];
+    unsigned touched = 0;
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      gt[t] = w1t[t] = w2t[t] = 0.f;
+      gw[t] = w1[t] = w2[t] = 0.0;
+#pragma unroll
+      for (int k = 0; k < G; ++k) acc[t][k] = tot[t][k] = 0.f;
+    }
+    for (int j = 0; j < n_seg; ++j, ++q) {
+      const unsigned s = (unsigned)(q % kRing);
+      if (!mbar_wait(bar_full + 8 * s, (unsigned)((q / kRing) & 1), p.err)) {
+        ok = false;
+        break;
+      }
+      const uint32_t sb = smem0 + s * (uint32_t)L.stage;
+      if (gval) {
+        const uint32_t stage = sb + l * 16;
+        const uint32_t e0 = sb + (uint32_t)L.ent + (uint32_t)(2 * u * (int)sizeof(TrackEntry));
+        const uint32_t e1 = e0 + (uint32_t)sizeof(TrackEntry);
+        const float4 h0 = lds_f4(e0), h1 = lds_f4(e1);
+        const int4 wa0 = lds_v4(e0 + 16), wa1 = lds_v4(e1 + 16);
+        const int c0 = __float_as_int(h0.w), c1 = __float_as_int(h1.w);
+        const float4 wseg = lds_f4(sb + (uint32_t)L.hdr);
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          const float wd = WEIGHTED ? (d == 0 ? wseg.x : wseg.y) : 1.0f;
+          const uint32_t sd = stage + d * kStageDetBytes;
+          const float gm = lds_f32(sd - l * 16 + 4 * kGroupLanes * 16 + l * 4);
+          int th0 = INT_MAX, th1 = INT_MAX;
+          float dw0 = 0.f, dw1 = 0.f;
+          const int zb0 = __float_as_int(fmaf(h0.x, gm, h0.y) + kMagic);
+          const int zb1 = __float_as_int(fmaf(h1.x, gm, h1.y) + kMagic);
+          const uint32_t wd0 = (uint32_t)(d == 0 ? wa0.x : wa0.y);
+          const uint32_t wd1 = (uint32_t)(d == 0 ? wa1.x : wa1.y);
+          if (c0 == kEntryInside) {
+            th0 = (int)lds_u32(__float_as_uint(h0.z) + 4u * (uint32_t)zb0);
+            const uint32_t a = wd0 + ESZ * (uint32_t)zb0;
+            const float rlo = lds_pow(a, RhoT()), rhi = lds_pow(a + ESZ, RhoT());
+            gt[0] = fmaf(wd, rlo, gt[0]);
+            dw0 = wd * (rhi - rlo);
+            w1t[0] += wd;
+            w2t[0] = fmaf(wd, wd, w2t[0]);
+          }
+          if (c1 == kEntryInside) {
+            th1 = (int)lds_u32(__float_as_uint(h1.z) + 4u * (uint32_t)zb1);
+            const uint32_t a = wd1 + ESZ * (uint32_t)zb1;
+            const float rlo = lds_pow(a, RhoT()), rhi = lds_pow(a + ESZ, RhoT());
+            gt[1] = fmaf(wd, rlo, gt[1]);
+            dw1 = wd * (rhi - rlo);
+            w1t[1] += wd;
+            w2t[1] = fmaf(wd, wd, w2t[1]);
+          }
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            const int4 qv = lds_v4(sd + v * kGroupLanes * 16);
+            pred_add(acc[0][4 * v + 0], qv.x, th0, dw0);
+            pred_add(acc[1][4 * v + 0], qv.x, th1, dw1);
+            pred_add(acc[0][4 * v + 1], qv.y, th0, dw0);
+            pred_add(acc[1][4 * v + 1], qv.y, th1, dw1);
+            pred_add(acc[0][4 * v + 2], qv.z, th0, dw0);
+            pred_add(acc[1][4 * v + 2], qv.z, th1, dw1);
+            pred_add(acc[0][4 * v + 3], qv.w, th0, dw0);
+            pred_add(acc[1][4 * v + 3], qv.w, th1, dw1);
+          }
+          if (RECORD || c0 == kEntryEdge || c1 == kEntryEdge) {
+            // rare: band-edge entries, and recording of the chosen bins
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+              const int c = t ? c1 : c0;
+              const int zb = t ? zb1 : zb0;
+              const uint32_t tha = __float_as_uint(t ? h1.z : h0.z);
+              const uint32_t wdt = t ? wd1 : wd0;
+              const uint32_t ea = t ? e1 : e0;
+              const int b = b0 + 2 * u + t;
+              int32_t* rp = nullptr;
+              const int64_t rstride = (int64_t)p.B * D * n_seg;
+              if (RECORD && b < p.B) rp = p.rec + ((int64_t)p.bank_perm[b] * D + d) * n_seg + j;
+              if (c == kEntryNone) {
+                if (RECORD && rp)
+                  for (int k = 0; k < G; ++k)
+                    if (s0 + k < p.S) rp[(int64_t)p.sky_perm[s0 + k] * rstride] = -1;
+                continue;
+              }
+              const int K0 = (int)lds_u32(ea + 32) + zb;  // kb
+              const int th = (int)lds_u32(tha + 4u * (uint32_t)zb);
+              if (c == kEntryInside) {
+                if (RECORD && rp)
+                  for (int k = 0; k < G; ++k) {
+                    const int qk = (int)lds_u32(sd + (k >> 2) * kGroupLanes * 16 + (k & 3) * 4);
+                    if (s0 + k < p.S) rp[(int64_t)p.sky_perm[s0 + k] * rstride] = K0 + (qk >= th ? 1 : 0);
+                  }
+                continue;
+              }
+              const bool vlo = (unsigned)K0 < (unsigned)p.n_bin;
+              const bool vhi = (unsigned)(K0 + 1) < (unsigned)p.n_bin;
+              const uint32_t a = wdt + ESZ * (uint32_t)zb;
+              const float rlo = vlo ? lds_pow(a, RhoT()) : 0.f;
+              const float rhi = vhi ? lds_pow(a + ESZ, RhoT()) : 0.f;
+              ++ngen;
+              float2* dvp = p.dev + (int64_t)b * p.Spad + s0;
+              if (!(touched & (1u << t))) {
+                touched |= 1u << t;
+                for (int k = 0; k < G; ++k) dvp[k] = make_float2(0.f, 0.f);
+              }
+#pragma unroll
+              for (int k = 0; k < G; ++k) {
+                const int qk = (int)lds_u32(sd + (k >> 2) * kGroupLanes * 16 + (k & 3) * 4);
+                const bool up = qk >= th;
+                const bool okb = up ? vhi : vlo;
+                if (RECORD && rp && s0 + k < p.S)
+                  rp[(int64_t)p.sky_perm[s0 + k] * rstride] = okb ? K0 + (up ? 1 : 0) : -1;
+                if (okb) {
+                  acc[t][k] = fmaf(wd, up ? rhi : rlo, acc[t][k]);
+                  float2 dv = dvp[k];
+                  dv.x += wd;
+                  dv.y = fmaf(wd, wd, dv.y);
+                  dvp[k] = dv;
+                }
+              }
+            }
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(bar_empty + 8 * s);
+      if (j % kTileSeg == kTileSeg - 1 || j == n_seg - 1) {
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          gw[t] += (double)gt[t];
+          w1[t] += (double)w1t[t];
+          w2[t] += (double)w2t[t];
+          gt[t] = w1t[t] = w2t[t] = 0.f;
+#pragma unroll
+          for (int k = 0; k < G; ++k) {
+            tot[t][k] += acc[t][k];
+            acc[t][k] = 0.f;
+          }
+        }
+      }
+    }
+    if (!ok || !gval) continue;
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int b = b0 + 2 * u + t;
+      const double base_num = gw[t] - w1[t];
+#pragma unroll
+      for (int k = 0; k < G; ++k) {
+        const int sk = s0 + k;
+        float dv1 = 0.f, dv2 = 0.f;
+        if (touched & (1u << t)) {
+          const float2 dv = p.dev[(int64_t)b * p.Spad + sk];
+          dv1 = dv.x;
+          dv2 = dv.y;
+        }
+        const float W1 = (float)(w1[t] + (double)dv1);
+        const float W2 = (float)(w2[t] + (double)dv2);
+        const float num = (float)(base_num - (double)dv1) + tot[t][k];
+        const int64_t o = (int64_t)sk * p.Bpad + b;
+        p.psi[o] = W2 > 0.f ? num * rsqrtf(W2) : -INFINITY;
+        if (p.S_out) {
+          p.S_out[o] = (float)gw[t] + tot[t][k];
+          p.W1_out[o] = W1;
+          p.W2_out[o] = W2;
+        }
+      }
+    }
+  }
+  if (ngen) atomicAdd(p.n_general, ngen);
+}
+
+}  // namespace
+
+size_t group_smem_bytes(int n_det) { return PersistLayout(n_det).total; }
+
+cudaError_t launch_anchors(const GroupParams& p, double* anchors, cudaStream_t st) {
+  const int64_t total = (int64_t)p.Bpad * p.n_tiles;
+  if (total == 0) return cudaSuccess;
+  const int threads = 128;
+  anchor_kernel<<<(unsigned)((total + threads - 1) / threads), threads, 0, st>>>(p, anchors);
+  return cudaGetLastError();
+}
+
+template <typename R, bool REC, bool WT, int DT>
+cudaError_t launch_group_t(const GroupParams& p, int grid, size_t smem, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(group_kernel<R, REC, WT, DT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  group_kernel<R, REC, WT, DT><<<grid, kThreads, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_group_r(const GroupParams& p, bool record, bool weighted, int grid, size_t smem,
+                           cudaStream_t st) {
+  if (record) return launch_group_t<R, true, true, 0>(p, grid, smem, st);
+  if (weighted) {
+    if (p.n_det == 1) return launch_group_t<R, false, true, 1>(p, grid, smem, st);
+    return launch_group_t<R, false, true, 2>(p, grid, smem, st);
+  }
+  if (p.n_det == 1) return launch_group_t<R, false, false, 1>(p, grid, smem, st);
+  return launch_group_t<R, false, false, 2>(p, grid, smem, st);
+}
+
+// Needs 1 <= p.n_det <= kMaxStageDet, and the anchors of launch_anchors when p.nterms > 0.
+cudaError_t launch_group(const GroupParams& p, bool half, bool record, bool weighted,
+                         cudaStream_t st) {
+  if (p.n_det < 1 || p.n_det > kMaxStageDet) return cudaErrorInvalidValue;
+  if (p.n_items <= 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int grid = p.n_items < sms ? p.n_items : sms;
+  const size_t smem = PersistLayout(p.n_det).total;
+  return half ? launch_group_r<__half>(p, record, weighted, grid, smem, st)
+              : launch_group_r<float>(p, record, weighted, grid, smem, st);
+}
+
+}  // namespace tcw
