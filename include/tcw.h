@@ -75,7 +75,17 @@ enum {
     TCW_OPT_KERNEL = 1,        /* one of TCW_KERNEL_* */
     TCW_OPT_KEEP_STATS = 2,    /* 1: keep S, W1, W2 of the last search for
                                   tcw_get_statistics (costs 3*4 B per pair) */
-    TCW_OPT_TILE_SEGMENTS = 3  /* segments per tile of the group kernel */
+    TCW_OPT_TILE_SEGMENTS = 3, /* segments per tile of the group kernel: the spacing of
+                                  the FP64 track anchors and of the fp32 partial sums;
+                                  a power of two in [8, 128], default 32 */
+    TCW_OPT_BANK_CHUNK = 4,    /* groups of 8 sorted templates per work item of the
+                                  group kernel, in [1, 4096], default 1 */
+    TCW_OPT_AUTOTUNE = 5,      /* batched search: 1 (default) = choose the bank chunk
+                                  and tile length by timing candidates on a sample of
+                                  the batch; 0 = use TCW_OPT_BANK_CHUNK and
+                                  TCW_OPT_TILE_SEGMENTS */
+    TCW_OPT_BATCH_MEMORY = 6   /* batched search: bytes of Psi and anchor buffers per
+                                  wave of events (default 48 GiB, minimum 1 MiB) */
 };
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
@@ -194,6 +204,75 @@ tcw_status tcw_search_noalloc(int n_det, int64_t n_seg, int64_t n_bin, int dtype
                               const double *v, int64_t n_tmpl, const double *f0, const double *tau,
                               const double *n, double T0, int64_t n_sky, const double *nhat, int k,
                               float *psi_out, int64_t *idx_out, void *cuda_stream);
+
+/*
+ * Batched search.  The paper searches one event at a time; this form runs
+ * many events -- spectrograms of uneven length, each with its own segment
+ * times, detector velocities, weights, signal start T0 (Eq. 1) and sky list --
+ * against the context's template bank (tcw_define_bank; its T0 is not used
+ * here) in one persistent group-kernel launch per wave of events, recorded
+ * once as a CUDA graph and replayed by every tcw_search_batched call.
+ *
+ * tcw_load_events copies every event (host or device memory per `flags`)
+ * into context buffers:
+ *   rho [n_det][n_seg][n_bin] of `dtype`, t_mid [n_seg] strictly increasing,
+ *   weights [n_det][n_seg] >= 0 or NULL for ones, velocity [n_det][n_seg][3]
+ *   in m/s (|v| < c/100), nhat [n_sky][3] unit vectors (within 1e-9).
+ * Errors: INVALID_ARGUMENT (names the event and the field), UNSUPPORTED
+ * (n_det > 2, or a power map smaller than 64 bytes), OUT_OF_MEMORY, CUDA.
+ *
+ * tcw_search_batched writes, for every event in order and every sky of that
+ * event in the caller's order, the top k of Psi (Eq. 4):
+ *   psi_out [total_sky][k], idx_out [total_sky][k] (caller template index),
+ *   total_sky = sum of the events' n_sky; ordering as in tcw_search.
+ * The first call after loading (or after a bank or option change) plans the
+ * batch, runs the autotuner (TCW_OPT_AUTOTUNE) and records the graph; later
+ * calls with the same k only replay it.  There is no per-lookup fallback: a
+ * batch outside the group kernel's exactness conditions is UNSUPPORTED.
+ * Errors: STATE (no events or bank), INVALID_ARGUMENT (k, pointers, flags),
+ * UNSUPPORTED, OUT_OF_MEMORY, DEVICE, CUDA. */
+typedef struct {
+    const void *rho;
+    const double *t_mid;
+    const float *weights;
+    const double *velocity;
+    const double *nhat;
+    int64_t n_seg;
+    int64_t n_sky;
+    double T0;
+} tcw_event;
+
+tcw_status tcw_load_events(tcw_ctx *ctx, int n_det, int64_t n_bin, int dtype, double f_min,
+                           double df, const tcw_event *events, int n_events, int flags);
+tcw_status tcw_search_batched(tcw_ctx *ctx, int k, float *psi_out, int64_t *idx_out,
+                              int out_flags);
+
+/* What the last batched search ran. */
+typedef struct {
+    int n_events;
+    int waves;                  /* group-kernel launches per search */
+    int bank_chunk;             /* groups of 8 templates per work item */
+    int tile_segments;          /* anchor spacing / fp32 partial-sum length */
+    int autotuned;              /* 1 if the two above came from the autotuner */
+    int n_candidates;           /* shapes timed by the autotuner */
+    int n_items;                /* work items over all waves */
+    int graph_kernels;          /* kernel nodes in the replayed graph */
+    int64_t total_sky;
+    int64_t lookups;            /* sum over events of n_sky * n_tmpl * n_det * n_seg */
+    int64_t general_path_lanes;
+    double tune_ms;             /* host wall time of the autotuner */
+    double best_rate;           /* sums/s of the winning shape on the autotuner's sample */
+    double default_rate;        /* sums/s of bank_chunk 1, tile 32 on the same sample */
+    double quantum;             /* fixed-point step of the Doppler factor */
+    float search_ms;            /* device time of the last graph replay, ms */
+} tcw_batch_info;
+
+tcw_status tcw_get_batch_info(tcw_ctx *ctx, tcw_batch_info *info);
+
+/* The autotuner's measurements: up to max_results (bank_chunk, tile_segments,
+ * sums/s) rows; *n_results = rows available.  Errors: STATE, INVALID_ARGUMENT. */
+tcw_status tcw_get_tune_results(tcw_ctx *ctx, int max_results, int *bank_chunk,
+                                int *tile_segments, double *sums_per_s, int *n_results);
 
 /* Information about the last search. */
 typedef struct {

@@ -15,124 +15,11 @@
 #include <string>
 #include <vector>
 
-#include "tcw_internal.cuh"
+#include "tcw_context.cuh"
 
 using namespace tcw;
 
 namespace {
-
-struct DevBuf {
-  void* p = nullptr;
-  size_t bytes = 0;
-  cudaError_t ensure(size_t n) {
-    if (n <= bytes && p) return cudaSuccess;
-    if (p) cudaFree(p);
-    p = nullptr;
-    bytes = 0;
-    cudaError_t e = cudaMalloc(&p, n ? n : 1);
-    if (e == cudaSuccess) bytes = n;
-    return e;
-  }
-  void release() {
-    if (p) cudaFree(p);
-    p = nullptr;
-    bytes = 0;
-  }
-  template <typename T>
-  T* as() const { return static_cast<T*>(p); }
-};
-
-}  // namespace
-
-struct tcw_ctx {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  std::string last_error;
-  // options
-  int opt_kernel = TCW_KERNEL_AUTO;
-  int keep_stats = 0;
-  int tile_segments = 32;
-  // spectrogram
-  bool have_spec = false;
-  int D = 0;
-  int64_t Nseg = 0, Nbin = 0;
-  int dtype = TCW_F32;
-  double f_min = 0, df = 0;
-  std::vector<double> h_t;
-  bool unit_weights = true;
-  DevBuf rho, t_mid, weights;
-  // velocity
-  bool have_vel = false;
-  std::vector<double> h_v;
-  DevBuf vel;
-  // bank
-  bool have_bank = false;
-  int64_t B = 0;
-  int Bpad = 0;
-  double T0 = 0;
-  std::vector<double> h_f0, h_tau, h_n;
-  DevBuf f0, tau, nbr, bank_perm, bank_pos;
-  // sky
-  bool have_sky = false;
-  int64_t S = 0;
-  int Spad = 0, NG = 0, NGpad = 0;
-  std::vector<double> h_nhat;
-  bool sky_dirty = true;
-  DevBuf nhat_sorted, sky_perm, sky_pos;
-  // derived and outputs
-  DevBuf dq, anchors, psi, st_S, st_W1, st_W2, dev, flags, stage_f, stage_i;
-  bool have_result = false, stats_kept = false;
-  tcw_info info{};
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-};
-
-namespace {
-
-tcw_status fail(tcw_ctx* c, tcw_status st, const std::string& msg) {
-  if (c) c->last_error = msg;
-  return st;
-}
-
-tcw_status cuda_fail(tcw_ctx* c, cudaError_t e, const char* what) {
-  if (e == cudaErrorMemoryAllocation) {
-    cudaGetLastError();
-    return fail(c, TCW_ERR_OUT_OF_MEMORY, std::string(what) + ": out of device memory");
-  }
-  return fail(c, TCW_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
-}
-
-#define TCW_CUDA(c, expr, what)                     \
-  do {                                              \
-    cudaError_t e_ = (expr);                        \
-    if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
-  } while (0)
-
-// Copy n bytes from caller memory (host or device) into a context buffer.
-cudaError_t upload(tcw_ctx* c, DevBuf& dst, const void* src, size_t n, int flags) {
-  cudaError_t e = dst.ensure(n);
-  if (e != cudaSuccess) return e;
-  e = cudaMemcpyAsync(dst.p, src, n, flags == TCW_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                      c->stream);
-  if (e != cudaSuccess) return e;
-  return cudaStreamSynchronize(c->stream);
-}
-
-// Bring a small caller array to the host for validation.
-template <typename T>
-cudaError_t fetch(tcw_ctx* c, std::vector<T>& out, const T* src, size_t count, int flags) {
-  out.resize(count);
-  if (flags == TCW_DEVICE)
-    return cudaMemcpy(out.data(), src, count * sizeof(T), cudaMemcpyDeviceToHost);
-  std::memcpy(out.data(), src, count * sizeof(T));
-  return cudaSuccess;
-}
-
-bool finite_all(const std::vector<double>& v) {
-  for (double x : v)
-    if (!std::isfinite(x)) return false;
-  return true;
-}
 
 struct Plan {
   int kernel = TCW_KERNEL_LOOKUP;
@@ -142,34 +29,13 @@ struct Plan {
   std::string why;
 };
 
-// Length of the binomial series sum_k binom(r, k) delta^k that gives 1/f(t_j)
-// from the tile anchor to below 2^-56 relative, for every template and tile;
-// 0 when more than kMaxSeriesTerms terms would be needed.
 int series_terms(const tcw_ctx* c) {
-  const int TS = 32;
   double tau_min = INFINITY, r_max = 0;
   for (size_t b = 0; b < c->h_tau.size(); ++b) {
     tau_min = std::min(tau_min, c->h_tau[b]);
     r_max = std::max(r_max, 1.0 / (c->h_n[b] - 1.0));
   }
-  double dmax = 0;
-  const int64_t N = c->Nseg;
-  for (int64_t j0 = 0; j0 < N; j0 += TS) {
-    const int64_t jn = std::min<int64_t>(TS, N - j0);
-    const double ta = std::max(c->h_t[j0 + (jn - 1) / 2], c->T0);
-    for (int64_t j = j0; j < j0 + jn; ++j) {
-      if (c->h_t[j] < c->T0) continue;
-      dmax = std::max(dmax, std::fabs(c->h_t[j] - ta) / (tau_min + (ta - c->T0)));
-    }
-  }
-  if (dmax >= 0.5) return 0;
-  double bound = 1.0, pw = 1.0;
-  for (int k = 0; k <= kMaxSeriesTerms; ++k) {
-    if (bound * pw < std::ldexp(1.0, -56)) return std::max(k, 1);
-    bound *= (r_max + k) / (k + 1);
-    pw *= dmax;
-  }
-  return 0;
+  return series_terms_for(c->h_t.data(), c->Nseg, c->T0, c->tile_segments, tau_min, r_max);
 }
 
 // Fixed-point step and the exactness conditions of the group kernel.
@@ -277,7 +143,6 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
   if (kernel == TCW_KERNEL_GROUP) {
     const size_t blkn = (size_t)(c->Spad / kSkyPad) * c->Nseg * c->D * kBlockWords;
     TCW_CUDA(c, c->dq.ensure(blkn * sizeof(int32_t)), "doppler table");
-    TCW_CUDA(c, c->dev.ensure(pairs * sizeof(float2)), "scratch");
     DopplerParams dp{};
     dp.vel = c->vel.as<double>();
     dp.nhat = c->nhat_sorted.as<double>();
@@ -304,41 +169,85 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
     }
   }
   if (kernel == TCW_KERNEL_GROUP) {
+    const int tile_shift = ilog2(c->tile_segments);
+    const int n_tiles = (int)((c->Nseg + c->tile_segments - 1) / c->tile_segments);
+    const int n_chunks = c->Spad / kSkyPad;
+    if (c->grid == 0) TCW_CUDA(c, group_grid(&c->grid), "device query");
+    const int64_t key[4] = {n_chunks, c->Bpad, c->bank_chunk, c->grid};
+    if (!std::equal(key, key + 4, c->items_key)) {
+      // bank chunks of bank_chunk groups of 8 templates x sky chunks, spread evenly over the CTAs
+      std::vector<int4> items;
+      std::vector<int64_t> cost;
+      const int groups = c->Bpad / kGroupTmplPerCta;
+      for (int g0 = 0; g0 < groups; g0 += c->bank_chunk)
+        for (int ch = 0; ch < n_chunks; ++ch) {
+          const int ng = std::min(c->bank_chunk, groups - g0);
+          items.push_back(make_int4(0, ch, g0 * kGroupTmplPerCta, ng));
+          cost.push_back((int64_t)ng * c->Nseg);
+        }
+      std::vector<int4> order;
+      std::vector<int> cta;
+      schedule_items(items, cost, c->grid, order, cta);
+      const size_t ib = order.size() * sizeof(int4), cb = cta.size() * sizeof(int);
+      TCW_CUDA(c, c->items.ensure(ib + cb), "schedule");
+      TCW_CUDA(c, cudaMemcpyAsync(c->items.p, order.data(), ib, cudaMemcpyHostToDevice, c->stream), "schedule");
+      TCW_CUDA(c, cudaMemcpyAsync(c->items.as<char>() + ib, cta.data(), cb, cudaMemcpyHostToDevice, c->stream),
+               "schedule");
+      TCW_CUDA(c, cudaStreamSynchronize(c->stream), "schedule");
+      std::copy(key, key + 4, c->items_key);
+      c->n_items = (int)order.size();
+    }
+    TCW_CUDA(c, c->dev.ensure(group_dev_elems(c->grid) * sizeof(float2)), "scratch");
+    EventDesc ev{};
+    ev.rho = c->rho.p;
+    ev.weights = c->weights.as<float>();
+    ev.t_mid = c->t_mid.as<double>();
+    ev.blk = c->dq.as<int32_t>();
+    ev.psi = c->psi.as<float>();
+    ev.S_out = keep ? c->st_S.as<float>() : nullptr;
+    ev.W1_out = keep ? c->st_W1.as<float>() : nullptr;
+    ev.W2_out = keep ? c->st_W2.as<float>() : nullptr;
+    ev.total_elems = (int64_t)c->D * c->Nseg * c->Nbin;
+    ev.T0 = c->T0;
+    ev.n_seg = (int)c->Nseg;
+    ev.n_tiles = n_tiles;
+    ev.S = (int)c->S;
+    ev.Spad = c->Spad;
+    ev.NG = c->NG;
+    AnchorParams ap{};
+    if (pl.nterms > 0) {
+      TCW_CUDA(c, c->anchors.ensure((size_t)c->Bpad * n_tiles * 2 * sizeof(double)), "anchors");
+      ev.anchors = c->anchors.as<double>();
+      ap.t_mid = ev.t_mid;
+      ap.f0 = c->f0.as<double>();
+      ap.tau = c->tau.as<double>();
+      ap.nbr = c->nbr.as<double>();
+      ap.T0 = c->T0;
+      ap.n_seg = ev.n_seg;
+      ap.n_tiles = n_tiles;
+      ap.tile_shift = tile_shift;
+      ap.Bpad = c->Bpad;
+      ap.anchors = c->anchors.as<double>();
+    }
+    TCW_CUDA(c, c->evtab.ensure(sizeof(EventDesc)), "event table");
+    TCW_CUDA(c, cudaMemcpyAsync(c->evtab.p, &ev, sizeof(ev), cudaMemcpyHostToDevice, c->stream), "event table");
     GroupParams gp{};
-    gp.rho = c->rho.p;
+    gp.events = c->evtab.as<EventDesc>();
+    gp.items = c->items.as<int4>();
+    gp.cta_items = reinterpret_cast<const int*>(c->items.as<char>() + (size_t)c->n_items * sizeof(int4));
     gp.n_bin = c->Nbin;
     gp.pitch = c->Nbin;
-    gp.total_elems = (int64_t)c->D * c->Nseg * c->Nbin;
     gp.n_det = c->D;
-    gp.n_seg = (int)c->Nseg;
-    gp.weights = c->weights.as<float>();
-    gp.t_mid = c->t_mid.as<double>();
-    gp.blk = c->dq.as<int32_t>();
     gp.f0 = c->f0.as<double>();
     gp.tau = c->tau.as<double>();
     gp.nbr = c->nbr.as<double>();
-    gp.T0 = c->T0;
     gp.f_min = c->f_min;
     gp.df = c->df;
     gp.inv_q = pl.inv_q;
     gp.nterms = pl.nterms;
+    gp.tile_shift = tile_shift;
     gp.B = (int)c->B;
     gp.Bpad = c->Bpad;
-    gp.S = (int)c->S;
-    gp.Spad = c->Spad;
-    gp.NG = c->NG;
-    gp.NGpad = c->NGpad;
-    gp.n_chunks = c->Spad / kSkyPad;
-    gp.n_items = gp.n_chunks * (c->Bpad / kGroupTmplPerCta);
-    gp.n_tiles = (int)((c->Nseg + kTileSegments - 1) / kTileSegments);
-    if (pl.nterms > 0) {
-      TCW_CUDA(c, c->anchors.ensure((size_t)c->Bpad * gp.n_tiles * 2 * sizeof(double)), "anchors");
-      gp.anchors = c->anchors.as<double>();
-    }
-    gp.psi = c->psi.as<float>();
-    gp.S_out = keep ? c->st_S.as<float>() : nullptr;
-    gp.W1_out = keep ? c->st_W1.as<float>() : nullptr;
-    gp.W2_out = keep ? c->st_W2.as<float>() : nullptr;
     gp.dev = c->dev.as<float2>();
     gp.rec = rec_dev;
     gp.bank_perm = c->bank_perm.as<int32_t>();
@@ -347,10 +256,10 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
     gp.err = c->flags.as<int>();
     TCW_CUDA(c, cudaEventRecord(c->ev0, c->stream), "event");
     if (pl.nterms > 0) {
-      TCW_CUDA(c, launch_anchors(gp, c->anchors.as<double>(), c->stream), "anchor_kernel launch");
+      TCW_CUDA(c, launch_anchors(ap, c->stream), "anchor_kernel launch");
       ++launches;
     }
-    TCW_CUDA(c, launch_group(gp, c->dtype == TCW_F16, record, !c->unit_weights, c->stream),
+    TCW_CUDA(c, launch_group(gp, c->grid, c->dtype == TCW_F16, record, !c->unit_weights, c->stream),
              "group_kernel launch");
     TCW_CUDA(c, cudaEventRecord(c->ev1, c->stream), "event");
     ++launches;
@@ -469,8 +378,9 @@ tcw_status tcw_destroy(tcw_ctx* c) {
   DevBuf* bufs[] = {&c->rho, &c->t_mid, &c->weights, &c->vel, &c->f0, &c->tau, &c->nbr,
                     &c->bank_perm, &c->bank_pos, &c->nhat_sorted, &c->sky_perm, &c->sky_pos,
                     &c->dq, &c->anchors, &c->psi, &c->st_S, &c->st_W1, &c->st_W2, &c->dev,
-                    &c->flags, &c->stage_f, &c->stage_i};
+                    &c->flags, &c->stage_f, &c->stage_i, &c->evtab, &c->items};
   for (DevBuf* b : bufs) b->release();
+  batch_free(c);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -490,8 +400,20 @@ tcw_status tcw_set_option(tcw_ctx* c, int option, int64_t value) {
       c->keep_stats = value ? 1 : 0;
       return TCW_OK;
     case TCW_OPT_TILE_SEGMENTS:
-      if (value != 32) return fail(c, TCW_ERR_INVALID_ARGUMENT, "tile_segments must be 32");
+      if (value < 8 || value > 128 || (value & (value - 1)))
+        return fail(c, TCW_ERR_INVALID_ARGUMENT, "tile_segments must be a power of two in [8, 128]");
       c->tile_segments = (int)value;
+      return TCW_OK;
+    case TCW_OPT_BANK_CHUNK:
+      if (value < 1 || value > 4096) return fail(c, TCW_ERR_INVALID_ARGUMENT, "bank_chunk must be in [1, 4096]");
+      c->bank_chunk = (int)value;
+      return TCW_OK;
+    case TCW_OPT_AUTOTUNE:
+      c->autotune = value ? 1 : 0;
+      return TCW_OK;
+    case TCW_OPT_BATCH_MEMORY:
+      if (value < ((int64_t)1 << 20)) return fail(c, TCW_ERR_INVALID_ARGUMENT, "batch_memory must be >= 1 MiB");
+      c->batch_memory = value;
       return TCW_OK;
     default:
       return fail(c, TCW_ERR_INVALID_ARGUMENT, "unknown option");
@@ -608,6 +530,7 @@ tcw_status tcw_define_bank(tcw_ctx* c, int64_t n_tmpl, const double* f0, const d
   TCW_CUDA(c, upload(c, c->bank_pos, pos.data(), n_tmpl * sizeof(int32_t), TCW_HOST), "bank upload");
   c->B = n_tmpl;
   c->Bpad = Bpad;
+  ++c->bank_epoch;
   c->T0 = T0;
   c->h_f0 = std::move(hf);
   c->h_tau = std::move(ht);

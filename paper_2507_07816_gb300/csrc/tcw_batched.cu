@@ -1,0 +1,734 @@
+// tcw_batched.cu -- batched search over many events.
+//
+// Each event has its own spectrogram (uneven segment counts), segment times,
+// detector velocities, weights, signal start T0 (Eq. 1) and sky list; all
+// events are searched against the context's template bank.  One search is a
+// CUDA graph, replayed on every call:
+//
+//   doppler_kernel  x event      Eq. 2 factor tables
+//   anchor_kernel   x event      FP64 tile anchors of Eq. 1
+//   group_kernel    x wave       ONE persistent launch over the wave's
+//                                (event, sky chunk, bank chunk) work items,
+//                                spread over the CTAs longest-first
+//   topk_kernel     x event      per-sky top-k of Eq. 4's Psi
+//
+// A wave is a run of events whose Psi and anchor buffers fit the memory
+// budget (TCW_OPT_BATCH_MEMORY); small batches are a single wave.  The bank
+// chunk (templates per work item) and the tile length (anchor spacing and
+// fp32 partial-sum length) are chosen by an autotuner that times every
+// candidate shape on a sample of the batch and keeps the fastest.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <numeric>
+
+#include "tcw_context.cuh"
+
+namespace tcw {
+
+namespace {
+
+struct EventHost {
+  int64_t n_seg = 0, n_sky = 0;
+  double T0 = 0;
+  std::vector<double> t, v;   // segment times, velocities (planning)
+  bool unit_w = true;
+  int Spad = 0, NG = 0, n_chunks = 0;
+  size_t o_rho = 0, o_t = 0, o_w = 0, o_v = 0, o_nhat = 0, o_perm = 0, o_blk = 0;  // byte offsets
+  size_t o_anchor = 0, o_psi = 0;  // byte offsets in the wave buffers
+  int64_t out_row = 0;             // first output row (sum of earlier events' n_sky)
+  int wave = 0;
+};
+
+struct TuneResult {
+  int bank_chunk, tile;
+  double rate;  // sums/s on the probe
+};
+
+size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
+
+}  // namespace
+
+struct BatchState {
+  // inputs
+  int D = 0, dtype = TCW_F32;
+  int64_t n_bin = 0;
+  double f_min = 0, df = 0;
+  std::vector<EventHost> ev;
+  bool unit_weights = true;
+  int64_t total_sky = 0;
+  DevBuf rho, small, blk, anchors, psi, out_psi, out_idx, evtab, items, dev, flags;
+  // plan
+  bool planned = false;
+  double q = 0, inv_q = 0, doppler_bins = 0;
+  int nterms = 0, tile = 32, bank_chunk = 1, grid = 0, waves = 1;
+  std::vector<int> wave_items;     // item offset of each wave in `items`, plus the end
+  std::vector<int> wave_cta;       // offset (in ints) of each wave's CTA table
+  int64_t lookups = 0;
+  // autotuner
+  bool tuned = false;
+  int64_t tune_key[4] = {-1, -1, -1, -1};
+  std::vector<TuneResult> tune;
+  double tune_ms = 0;
+  // graph
+  cudaGraphExec_t exec = nullptr;
+  int graph_k = 0, graph_nodes = 0;
+  int64_t graph_mem = 0;           // wave budget the graph was recorded with
+  // last search
+  bool have_result = false;
+  int last_k = 0;
+  float search_ms = 0;
+  int64_t general = 0;
+};
+
+void batch_free(tcw_ctx* c) {
+  if (!c->batch) return;
+  BatchState* b = c->batch;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  DevBuf* bufs[] = {&b->rho, &b->small, &b->blk, &b->anchors, &b->psi, &b->out_psi,
+                    &b->out_idx, &b->evtab, &b->items, &b->dev, &b->flags};
+  for (DevBuf* d : bufs) d->release();
+  delete b;
+  c->batch = nullptr;
+}
+
+namespace {
+
+void drop_graph(BatchState* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  b->exec = nullptr;
+  b->graph_k = 0;
+}
+
+template <typename T>
+T* at(DevBuf& buf, size_t off) {
+  return reinterpret_cast<T*>(buf.as<char>() + off);
+}
+
+// Fixed-point step, exactness conditions and series length for the whole
+// batch (the same reasoning as the single-event planner).
+tcw_status plan_batch(tcw_ctx* c, BatchState* b) {
+  double vmax = 0;
+  for (const EventHost& e : b->ev)
+    for (size_t i = 0; i + 2 < e.v.size(); i += 3)
+      vmax = std::max(vmax, std::sqrt(e.v[i] * e.v[i] + e.v[i + 1] * e.v[i + 1] + e.v[i + 2] * e.v[i + 2]));
+  const double dmax = vmax / kLightSpeed * (1.0 + 1e-12);
+  int ex = -60;
+  if (dmax > 0) ex = (int)std::ceil(std::log2(dmax / (2147483648.0 - 16777216.0)));
+  ex = std::max(ex, -80);
+  b->q = std::ldexp(1.0, ex);
+  b->inv_q = std::ldexp(1.0, -ex);
+  double f0max = 0;
+  for (double f : c->h_f0) f0max = std::max(f0max, f);
+  const double fband = b->f_min + ((double)b->n_bin + 5.0) * b->df;
+  const double fmax_bins = std::min(f0max, fband) * (1.0 + dmax) / b->df;
+  b->doppler_bins = fmax_bins * dmax;
+  if (fmax_bins * b->q * 0.5 > 0.75 * std::ldexp(1.0, -30))
+    return fail(c, TCW_ERR_UNSUPPORTED, "batched search: fixed-point Doppler step too coarse for the bin width");
+  if (b->doppler_bins > 2.9) return fail(c, TCW_ERR_UNSUPPORTED, "batched search: Doppler shift exceeds 2.9 bins");
+  if (b->n_bin > (int64_t)1 << 30 || c->B > INT32_MAX)
+    return fail(c, TCW_ERR_UNSUPPORTED, "batched search: sizes beyond 32-bit indexing");
+  // Doppler blocks of every event, and the widest sky group they hold
+  TCW_CUDA(c, cudaMemsetAsync(b->flags.p, 0, b->flags.bytes, c->stream), "flags");
+  for (size_t i = 0; i < b->ev.size(); ++i) {
+    EventHost& e = b->ev[i];
+    DopplerParams dp{};
+    dp.vel = at<double>(b->small, e.o_v);
+    dp.nhat = at<double>(b->small, e.o_nhat);
+    dp.n_det = b->D;
+    dp.n_seg = (int)e.n_seg;
+    dp.Spad = e.Spad;
+    dp.NG = e.NG;
+    dp.group = kGroupSkies;
+    dp.inv_q = b->inv_q;
+    dp.blk = at<int32_t>(b->blk, e.o_blk);
+    dp.spread_max = at<unsigned>(b->flags, 64 + 4 * i);
+    TCW_CUDA(c, launch_doppler(dp, c->stream), "doppler_kernel launch");
+  }
+  std::vector<float> spread(b->ev.size());
+  TCW_CUDA(c, cudaMemcpyAsync(spread.data(), at<char>(b->flags, 64), spread.size() * 4, cudaMemcpyDeviceToHost,
+                              c->stream), "spread");
+  TCW_CUDA(c, cudaStreamSynchronize(c->stream), "spread");
+  for (size_t i = 0; i < spread.size(); ++i)
+    if (fmax_bins * (double)spread[i] * 0.5 + 0.02 > 0.45)
+      return fail(c, TCW_ERR_UNSUPPORTED,
+                  "batched search: sky groups of event " + std::to_string(i) + " span too many bins");
+  b->lookups = 0;
+  for (const EventHost& e : b->ev) b->lookups += e.n_sky * c->B * b->D * e.n_seg;
+  TCW_CUDA(c, group_grid(&b->grid), "device query");
+  TCW_CUDA(c, b->dev.ensure(group_dev_elems(b->grid) * sizeof(float2)), "scratch");
+  b->planned = true;
+  return TCW_OK;
+}
+
+int batch_series_terms(const tcw_ctx* c, const BatchState* b, int tile) {
+  double tau_min = INFINITY, r_max = 0;
+  for (size_t i = 0; i < c->h_tau.size(); ++i) {
+    tau_min = std::min(tau_min, c->h_tau[i]);
+    r_max = std::max(r_max, 1.0 / (c->h_n[i] - 1.0));
+  }
+  int nt = 1;
+  for (const EventHost& e : b->ev) {
+    const int n = series_terms_for(e.t.data(), e.n_seg, e.T0, tile, tau_min, r_max);
+    if (n == 0) return 0;
+    nt = std::max(nt, n);
+  }
+  return nt;
+}
+
+int n_tiles_of(int64_t n_seg, int tile) { return (int)((n_seg + tile - 1) / tile); }
+
+// Split the events into waves whose Psi and anchor buffers fit `budget` bytes
+// and lay out those buffers.  Returns the per-wave buffer sizes.
+void layout_waves(const tcw_ctx* c, BatchState* b, int tile, bool anchors, size_t* psi_bytes,
+                  size_t* anchor_bytes) {
+  const size_t budget = (size_t)c->batch_memory;
+  size_t psi_w = 0, anc_w = 0, psi_max = 0, anc_max = 0;
+  int wave = 0;
+  for (EventHost& e : b->ev) {
+    const size_t p = align256((size_t)e.Spad * c->Bpad * 4);
+    const size_t a = anchors ? align256((size_t)c->Bpad * n_tiles_of(e.n_seg, tile) * 16) : 0;
+    if ((psi_w + anc_w) > 0 && psi_w + anc_w + p + a > budget) {
+      ++wave;
+      psi_w = anc_w = 0;
+    }
+    e.wave = wave;
+    e.o_psi = psi_w;
+    e.o_anchor = anc_w;
+    psi_w += p;
+    anc_w += a;
+    psi_max = std::max(psi_max, psi_w);
+    anc_max = std::max(anc_max, anc_w);
+  }
+  b->waves = wave + 1;
+  *psi_bytes = psi_max;
+  *anchor_bytes = anc_max;
+}
+
+EventDesc make_desc(const tcw_ctx* c, BatchState* b, const EventHost& e, int tile, bool anchors) {
+  EventDesc d{};
+  d.rho = at<char>(b->rho, e.o_rho);
+  d.weights = at<float>(b->small, e.o_w);
+  d.t_mid = at<double>(b->small, e.o_t);
+  d.blk = at<int32_t>(b->blk, e.o_blk);
+  d.anchors = anchors ? at<double>(b->anchors, e.o_anchor) : nullptr;
+  d.psi = at<float>(b->psi, e.o_psi);
+  d.total_elems = (int64_t)b->D * e.n_seg * b->n_bin;
+  d.T0 = e.T0;
+  d.n_seg = (int)e.n_seg;
+  d.n_tiles = n_tiles_of(e.n_seg, tile);
+  d.S = (int)e.n_sky;
+  d.Spad = e.Spad;
+  d.NG = e.NG;
+  (void)c;
+  return d;
+}
+
+// Work items of the events of wave w over `groups_limit` groups of 8
+// templates, bank_chunk groups per item, scheduled longest-first.
+void wave_items(const tcw_ctx* c, const BatchState* b, int w, int bank_chunk, int groups_limit,
+                std::vector<int4>& order, std::vector<int>& cta, int64_t* sums) {
+  std::vector<int4> items;
+  std::vector<int64_t> cost;
+  const int groups = std::min(groups_limit, c->Bpad / kGroupTmplPerCta);
+  *sums = 0;
+  for (size_t i = 0; i < b->ev.size(); ++i) {
+    const EventHost& e = b->ev[i];
+    if (e.wave != w) continue;
+    for (int g0 = 0; g0 < groups; g0 += bank_chunk)
+      for (int ch = 0; ch < e.n_chunks; ++ch) {
+        const int ng = std::min(bank_chunk, groups - g0);
+        items.push_back(make_int4((int)i, ch, g0 * kGroupTmplPerCta, ng));
+        cost.push_back((int64_t)ng * e.n_seg);
+        const int64_t skies = std::min<int64_t>(kSkyPad, e.n_sky - (int64_t)ch * kSkyPad);
+        *sums += (int64_t)ng * kGroupTmplPerCta * skies * b->D * e.n_seg;
+      }
+  }
+  schedule_items(items, cost, b->grid, order, cta);
+}
+
+GroupParams base_params(const tcw_ctx* c, BatchState* b, int tile, int nterms) {
+  GroupParams gp{};
+  gp.events = b->evtab.as<EventDesc>();
+  gp.n_bin = b->n_bin;
+  gp.pitch = b->n_bin;
+  gp.n_det = b->D;
+  gp.f0 = c->f0.as<double>();
+  gp.tau = c->tau.as<double>();
+  gp.nbr = c->nbr.as<double>();
+  gp.f_min = b->f_min;
+  gp.df = b->df;
+  gp.inv_q = b->inv_q;
+  gp.nterms = nterms;
+  gp.tile_shift = ilog2(tile);
+  gp.B = (int)c->B;
+  gp.Bpad = c->Bpad;
+  gp.dev = b->dev.as<float2>();
+  gp.bank_perm = c->bank_perm.as<int32_t>();
+  gp.n_general = at<unsigned long long>(b->flags, 8);
+  gp.err = b->flags.as<int>();
+  return gp;
+}
+
+// Buffers and event table for (tile, anchors); items are uploaded by the caller.
+tcw_status prepare_shape(tcw_ctx* c, BatchState* b, int tile, int nterms) {
+  size_t psi_bytes = 0, anc_bytes = 0;
+  layout_waves(c, b, tile, nterms > 0, &psi_bytes, &anc_bytes);
+  TCW_CUDA(c, b->psi.ensure(psi_bytes), "Psi buffer");
+  if (nterms > 0) TCW_CUDA(c, b->anchors.ensure(anc_bytes), "anchor buffer");
+  std::vector<EventDesc> tab;
+  for (const EventHost& e : b->ev) tab.push_back(make_desc(c, b, e, tile, nterms > 0));
+  TCW_CUDA(c, b->evtab.ensure(tab.size() * sizeof(EventDesc)), "event table");
+  TCW_CUDA(c, cudaMemcpyAsync(b->evtab.p, tab.data(), tab.size() * sizeof(EventDesc), cudaMemcpyHostToDevice,
+                              c->stream), "event table");
+  TCW_CUDA(c, cudaStreamSynchronize(c->stream), "event table");
+  return TCW_OK;
+}
+
+cudaError_t launch_wave_anchors(const tcw_ctx* c, BatchState* b, int w, int tile, cudaStream_t st) {
+  for (const EventHost& e : b->ev) {
+    if (e.wave != w) continue;
+    AnchorParams ap{};
+    ap.t_mid = at<double>(b->small, e.o_t);
+    ap.f0 = c->f0.as<double>();
+    ap.tau = c->tau.as<double>();
+    ap.nbr = c->nbr.as<double>();
+    ap.T0 = e.T0;
+    ap.n_seg = (int)e.n_seg;
+    ap.n_tiles = n_tiles_of(e.n_seg, tile);
+    ap.tile_shift = ilog2(tile);
+    ap.Bpad = c->Bpad;
+    ap.anchors = at<double>(b->anchors, e.o_anchor);
+    cudaError_t err = launch_anchors(ap, st);
+    if (err != cudaSuccess) return err;
+  }
+  return cudaSuccess;
+}
+
+// Upload the item lists of every wave (concatenated) for one shape.
+tcw_status upload_items(tcw_ctx* c, BatchState* b, int bank_chunk, int groups_limit, int64_t* sums) {
+  std::vector<int4> all;
+  std::vector<int> ctas;
+  b->wave_items.assign(1, 0);
+  b->wave_cta.clear();
+  *sums = 0;
+  for (int w = 0; w < b->waves; ++w) {
+    std::vector<int4> order;
+    std::vector<int> cta;
+    int64_t s = 0;
+    wave_items(c, b, w, bank_chunk, groups_limit, order, cta, &s);
+    *sums += s;
+    all.insert(all.end(), order.begin(), order.end());
+    b->wave_items.push_back((int)all.size());
+    b->wave_cta.push_back((int)ctas.size());
+    for (int& x : cta) x += b->wave_items[w];
+    ctas.insert(ctas.end(), cta.begin(), cta.end());
+  }
+  const size_t ib = all.size() * sizeof(int4), cb = ctas.size() * sizeof(int);
+  TCW_CUDA(c, b->items.ensure(ib + cb), "schedule");
+  TCW_CUDA(c, cudaMemcpyAsync(b->items.p, all.data(), ib, cudaMemcpyHostToDevice, c->stream), "schedule");
+  TCW_CUDA(c, cudaMemcpyAsync(b->items.as<char>() + ib, ctas.data(), cb, cudaMemcpyHostToDevice, c->stream),
+           "schedule");
+  TCW_CUDA(c, cudaStreamSynchronize(c->stream), "schedule");
+  return TCW_OK;
+}
+
+GroupParams wave_params(const tcw_ctx* c, BatchState* b, int w, int tile, int nterms) {
+  GroupParams gp = base_params(c, b, tile, nterms);
+  const size_t ib = (size_t)b->wave_items.back() * sizeof(int4);
+  gp.items = b->items.as<int4>();
+  gp.cta_items = reinterpret_cast<const int*>(b->items.as<char>() + ib) + b->wave_cta[w];
+  return gp;
+}
+
+// Autotuner: every (bank chunk, tile) candidate runs the group kernel over the
+// first probe_groups groups of 8 templates of every event (wave by wave); the
+// candidate with the highest sums/s wins, ties going to the earlier one.
+tcw_status autotune(tcw_ctx* c, BatchState* b) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const int groups = c->Bpad / kGroupTmplPerCta;
+  const int probe_groups = std::min(groups, std::max(64, groups / 32));
+  const int chunks[] = {1, 8, 64};
+  const int tiles[] = {32, 16, 64};
+  b->tune.clear();
+  cudaEvent_t e0, e1;
+  TCW_CUDA(c, cudaEventCreate(&e0), "event");
+  TCW_CUDA(c, cudaEventCreate(&e1), "event");
+  tcw_status st = TCW_OK;
+  for (int tile : tiles) {
+    const int nterms = batch_series_terms(c, b, tile);
+    if ((st = prepare_shape(c, b, tile, nterms)) != TCW_OK) break;
+    for (int w = 0; w < b->waves && nterms > 0; ++w) {
+      cudaError_t err = launch_wave_anchors(c, b, w, tile, c->stream);
+      if (err != cudaSuccess) {
+        st = cuda_fail(c, err, "anchor_kernel launch");
+        break;
+      }
+    }
+    if (st != TCW_OK) break;
+    for (int bc : chunks) {
+      if (bc > probe_groups && bc != 1) continue;
+      int64_t sums = 0;
+      if ((st = upload_items(c, b, bc, probe_groups, &sums)) != TCW_OK) break;
+      float best = INFINITY;
+      for (int rep = 0; rep < 2 && st == TCW_OK; ++rep) {
+        cudaEventRecord(e0, c->stream);
+        for (int w = 0; w < b->waves; ++w) {
+          const GroupParams gp = wave_params(c, b, w, tile, nterms);
+          cudaError_t err = launch_group(gp, b->grid, b->dtype == TCW_F16, false, !b->unit_weights, c->stream);
+          if (err != cudaSuccess) {
+            st = cuda_fail(c, err, "group_kernel launch");
+            break;
+          }
+        }
+        cudaEventRecord(e1, c->stream);
+        cudaError_t err = cudaEventSynchronize(e1);
+        if (err != cudaSuccess) {
+          st = cuda_fail(c, err, "autotune");
+          break;
+        }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        best = std::min(best, ms);
+      }
+      if (st != TCW_OK) break;
+      b->tune.push_back({bc, tile, (double)sums / (best * 1e-3)});
+    }
+    if (st != TCW_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != TCW_OK) return st;
+  int err_flag = 0;
+  TCW_CUDA(c, cudaMemcpy(&err_flag, b->flags.p, sizeof(int), cudaMemcpyDeviceToHost), "flags");
+  if (err_flag) return fail(c, TCW_ERR_DEVICE, "batched search: device error while autotuning");
+  size_t best = 0;
+  for (size_t i = 1; i < b->tune.size(); ++i)
+    if (b->tune[i].rate > b->tune[best].rate) best = i;
+  b->bank_chunk = b->tune[best].bank_chunk;
+  b->tile = b->tune[best].tile;
+  b->tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  b->tuned = true;
+  return TCW_OK;
+}
+
+// Record one search of the whole batch as a CUDA graph.
+tcw_status capture(tcw_ctx* c, BatchState* b, int k) {
+  drop_graph(b);
+  const int nterms = batch_series_terms(c, b, b->tile);
+  b->nterms = nterms;
+  tcw_status st = prepare_shape(c, b, b->tile, nterms);
+  if (st != TCW_OK) return st;
+  int64_t sums = 0;
+  if ((st = upload_items(c, b, b->bank_chunk, INT32_MAX, &sums)) != TCW_OK) return st;
+  TCW_CUDA(c, b->out_psi.ensure((size_t)b->total_sky * k * sizeof(float)), "output");
+  TCW_CUDA(c, b->out_idx.ensure((size_t)b->total_sky * k * sizeof(int64_t)), "output");
+  TCW_CUDA(c, group_prepare(b->D, b->dtype == TCW_F16, !b->unit_weights), "group_kernel attributes");
+  TCW_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "graph capture");
+  cudaError_t err = cudaMemsetAsync(b->flags.p, 0, 64, c->stream);
+  int nodes = 0;
+  for (size_t i = 0; i < b->ev.size() && err == cudaSuccess; ++i) {
+    const EventHost& e = b->ev[i];
+    DopplerParams dp{};
+    dp.vel = at<double>(b->small, e.o_v);
+    dp.nhat = at<double>(b->small, e.o_nhat);
+    dp.n_det = b->D;
+    dp.n_seg = (int)e.n_seg;
+    dp.Spad = e.Spad;
+    dp.NG = e.NG;
+    dp.group = kGroupSkies;
+    dp.inv_q = b->inv_q;
+    dp.blk = at<int32_t>(b->blk, e.o_blk);
+    dp.spread_max = at<unsigned>(b->flags, 64 + 4 * i);
+    err = launch_doppler(dp, c->stream);
+    ++nodes;
+  }
+  for (int w = 0; w < b->waves && err == cudaSuccess; ++w) {
+    if (nterms > 0) {
+      err = launch_wave_anchors(c, b, w, b->tile, c->stream);
+      for (const EventHost& e : b->ev) nodes += e.wave == w;
+    }
+    if (err != cudaSuccess) break;
+    const GroupParams gp = wave_params(c, b, w, b->tile, nterms);
+    err = launch_group(gp, b->grid, b->dtype == TCW_F16, false, !b->unit_weights, c->stream);
+    ++nodes;
+    for (const EventHost& e : b->ev) {
+      if (e.wave != w || err != cudaSuccess) continue;
+      err = launch_topk(at<float>(b->psi, e.o_psi), c->Bpad, (int)c->B, (int)e.n_sky, k,
+                        c->bank_perm.as<int32_t>(), at<int32_t>(b->small, e.o_perm),
+                        b->out_psi.as<float>() + e.out_row * k, b->out_idx.as<int64_t>() + e.out_row * k,
+                        c->stream);
+      ++nodes;
+    }
+  }
+  cudaGraph_t graph = nullptr;
+  const cudaError_t end = cudaStreamEndCapture(c->stream, &graph);
+  if (err == cudaSuccess) err = end;
+  if (err == cudaSuccess) err = cudaGraphInstantiate(&b->exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (err != cudaSuccess) {
+    b->exec = nullptr;
+    return cuda_fail(c, err, "graph capture");
+  }
+  b->graph_k = k;
+  b->graph_mem = c->batch_memory;
+  b->graph_nodes = nodes;
+  return TCW_OK;
+}
+
+}  // namespace
+}  // namespace tcw
+
+using namespace tcw;
+
+extern "C" {
+
+tcw_status tcw_load_events(tcw_ctx* c, int n_det, int64_t n_bin, int dtype, double f_min, double df,
+                           const tcw_event* events, int n_events, int flags) {
+  if (!c) return TCW_ERR_INVALID_ARGUMENT;
+  if (n_det < 1 || n_det > kMaxDet) return fail(c, TCW_ERR_INVALID_ARGUMENT, "n_det out of range");
+  if (n_bin < 1 || n_bin > ((int64_t)1 << 30)) return fail(c, TCW_ERR_INVALID_ARGUMENT, "n_bin out of range");
+  if (dtype != TCW_F32 && dtype != TCW_F16) return fail(c, TCW_ERR_INVALID_ARGUMENT, "bad dtype");
+  if (!std::isfinite(f_min) || !(df > 0) || !std::isfinite(df))
+    return fail(c, TCW_ERR_INVALID_ARGUMENT, "bad f_min or df");
+  if (!events || n_events < 1 || n_events > 65536) return fail(c, TCW_ERR_INVALID_ARGUMENT, "bad event list");
+  if (flags != TCW_HOST && flags != TCW_DEVICE) return fail(c, TCW_ERR_INVALID_ARGUMENT, "bad flags");
+  cudaSetDevice(c->device);
+  batch_free(c);
+  BatchState* b = new BatchState();
+  c->batch = b;
+  b->D = n_det;
+  b->n_bin = n_bin;
+  b->dtype = dtype;
+  b->f_min = f_min;
+  b->df = df;
+  const size_t esz = dtype == TCW_F16 ? 2 : 4;
+  size_t rho_bytes = 0, small_bytes = 0, blk_bytes = 0;
+  std::vector<std::vector<double>> nhat_sorted(n_events);
+  std::vector<std::vector<int32_t>> perms(n_events);
+  std::vector<std::vector<float>> wts(n_events);
+  auto reject = [&](const std::string& m) {
+    batch_free(c);
+    return fail(c, TCW_ERR_INVALID_ARGUMENT, m);
+  };
+  for (int i = 0; i < n_events; ++i) {
+    const tcw_event& in = events[i];
+    const std::string tag = "event " + std::to_string(i) + ": ";
+    if (!in.rho || !in.t_mid || !in.velocity || !in.nhat) return reject(tag + "null pointer");
+    if (in.n_seg < 1 || in.n_seg > INT32_MAX / 2) return reject(tag + "n_seg out of range");
+    if (in.n_sky < 1 || in.n_sky > ((int64_t)1 << 24)) return reject(tag + "n_sky out of range");
+    if (!std::isfinite(in.T0)) return reject(tag + "non-finite T0");
+    EventHost e;
+    e.n_seg = in.n_seg;
+    e.n_sky = in.n_sky;
+    e.T0 = in.T0;
+    cudaError_t ce = fetch(c, e.t, in.t_mid, (size_t)in.n_seg, flags);
+    if (ce == cudaSuccess) ce = fetch(c, e.v, in.velocity, (size_t)n_det * in.n_seg * 3, flags);
+    std::vector<double> nh;
+    if (ce == cudaSuccess) ce = fetch(c, nh, in.nhat, (size_t)in.n_sky * 3, flags);
+    std::vector<float> w;
+    if (ce == cudaSuccess && in.weights) ce = fetch(c, w, in.weights, (size_t)n_det * in.n_seg, flags);
+    if (ce != cudaSuccess) {
+      batch_free(c);
+      return cuda_fail(c, ce, "event fetch");
+    }
+    if (!finite_all(e.t)) return reject(tag + "non-finite segment time");
+    for (int64_t j = 1; j < in.n_seg; ++j)
+      if (!(e.t[j] > e.t[j - 1])) return reject(tag + "segment times must increase");
+    for (size_t a = 0; a + 2 < e.v.size(); a += 3) {
+      const double s = std::sqrt(e.v[a] * e.v[a] + e.v[a + 1] * e.v[a + 1] + e.v[a + 2] * e.v[a + 2]);
+      if (!std::isfinite(s) || s >= kLightSpeed / 100) return reject(tag + "velocity must be below c/100");
+    }
+    for (int64_t s = 0; s < in.n_sky; ++s) {
+      const double x = nh[3 * s], y = nh[3 * s + 1], z = nh[3 * s + 2];
+      if (!std::isfinite(x) || !std::isfinite(y) || !std::isfinite(z) ||
+          std::fabs(std::sqrt(x * x + y * y + z * z) - 1.0) > 1e-9)
+        return reject(tag + "sky vectors must be unit (within 1e-9)");
+    }
+    if (in.weights) {
+      for (float x : w) {
+        if (!std::isfinite(x) || x < 0) return reject(tag + "weights must be finite and >= 0");
+        if (x != 1.0f) e.unit_w = false;
+      }
+    } else {
+      w.assign((size_t)n_det * in.n_seg, 1.0f);
+    }
+    wts[i] = std::move(w);
+    b->unit_weights = b->unit_weights && e.unit_w;
+    // sky sorted by its Doppler factor at the event's middle segment (detector 0)
+    const double* vm = &e.v[(size_t)(in.n_seg / 2) * 3];
+    std::vector<double> key(in.n_sky);
+    for (int64_t s = 0; s < in.n_sky; ++s) key[s] = vm[0] * nh[3 * s] + vm[1] * nh[3 * s + 1] + vm[2] * nh[3 * s + 2];
+    std::vector<int32_t> perm(in.n_sky);
+    std::iota(perm.begin(), perm.end(), 0);
+    std::stable_sort(perm.begin(), perm.end(), [&](int32_t x, int32_t y) { return key[x] < key[y]; });
+    e.NG = (int)((in.n_sky + kGroupSkies - 1) / kGroupSkies);
+    e.Spad = (int)(((int64_t)e.NG + kGroupLanes - 1) / kGroupLanes) * kSkyPad;
+    e.n_chunks = e.Spad / kSkyPad;
+    std::vector<double> ns((size_t)e.Spad * 3);
+    for (int s = 0; s < e.Spad; ++s) {
+      const int32_t src = perm[std::min<int64_t>(s, in.n_sky - 1)];
+      for (int a = 0; a < 3; ++a) ns[(size_t)s * 3 + a] = nh[(size_t)src * 3 + a];
+    }
+    perm.resize(e.Spad, perm.back());
+    nhat_sorted[i] = std::move(ns);
+    perms[i] = std::move(perm);
+    e.out_row = b->total_sky;
+    b->total_sky += in.n_sky;
+    // layout
+    e.o_rho = rho_bytes;
+    rho_bytes += align256((size_t)n_det * in.n_seg * n_bin * esz);
+    e.o_t = small_bytes;
+    small_bytes += align256((size_t)in.n_seg * 8);
+    e.o_w = small_bytes;
+    small_bytes += align256((size_t)n_det * in.n_seg * 4);
+    e.o_v = small_bytes;
+    small_bytes += align256((size_t)n_det * in.n_seg * 24);
+    e.o_nhat = small_bytes;
+    small_bytes += align256((size_t)e.Spad * 24);
+    e.o_perm = small_bytes;
+    small_bytes += align256((size_t)e.Spad * 4);
+    e.o_blk = blk_bytes;
+    blk_bytes += align256((size_t)e.n_chunks * in.n_seg * n_det * kBlockWords * 4);
+    b->ev.push_back(std::move(e));
+  }
+  if (b->D > kMaxStageDet) {
+    batch_free(c);
+    return fail(c, TCW_ERR_UNSUPPORTED, "batched search: more detectors than the group kernel stages");
+  }
+  const cudaMemcpyKind kind = flags == TCW_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  cudaError_t ce = b->rho.ensure(rho_bytes);
+  if (ce == cudaSuccess) ce = b->small.ensure(small_bytes);
+  if (ce == cudaSuccess) ce = b->blk.ensure(blk_bytes);
+  if (ce == cudaSuccess) ce = b->flags.ensure(64 + 4 * (size_t)n_events);
+  for (int i = 0; i < n_events && ce == cudaSuccess; ++i) {
+    const EventHost& e = b->ev[i];
+    ce = cudaMemcpyAsync(at<char>(b->rho, e.o_rho), events[i].rho, (size_t)n_det * e.n_seg * n_bin * esz, kind,
+                         c->stream);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(at<char>(b->small, e.o_t), e.t.data(), e.t.size() * 8, cudaMemcpyHostToDevice,
+                           c->stream);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(at<char>(b->small, e.o_w), wts[i].data(), wts[i].size() * 4, cudaMemcpyHostToDevice,
+                           c->stream);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(at<char>(b->small, e.o_v), e.v.data(), e.v.size() * 8, cudaMemcpyHostToDevice,
+                           c->stream);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(at<char>(b->small, e.o_nhat), nhat_sorted[i].data(), nhat_sorted[i].size() * 8,
+                           cudaMemcpyHostToDevice, c->stream);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(at<char>(b->small, e.o_perm), perms[i].data(), perms[i].size() * 4,
+                           cudaMemcpyHostToDevice, c->stream);
+    // the host vectors must outlive the copies
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->stream);
+  }
+  if (ce != cudaSuccess) {
+    batch_free(c);
+    return cuda_fail(c, ce, "event upload");
+  }
+  for (EventHost& e : b->ev) {
+    if ((size_t)b->D * e.n_seg * n_bin * esz < 64) {
+      batch_free(c);
+      return fail(c, TCW_ERR_UNSUPPORTED, "batched search: an event's power map is smaller than one window");
+    }
+  }
+  return TCW_OK;
+}
+
+tcw_status tcw_search_batched(tcw_ctx* c, int k, float* psi_out, int64_t* idx_out, int out_flags) {
+  if (!c) return TCW_ERR_INVALID_ARGUMENT;
+  if (!psi_out || !idx_out) return fail(c, TCW_ERR_INVALID_ARGUMENT, "null output");
+  if (out_flags != TCW_HOST && out_flags != TCW_DEVICE) return fail(c, TCW_ERR_INVALID_ARGUMENT, "bad flags");
+  if (!c->batch) return fail(c, TCW_ERR_STATE, "no events loaded");
+  if (!c->have_bank) return fail(c, TCW_ERR_STATE, "no template bank defined");
+  if (k < 1 || k > 1024 || (int64_t)k > c->B)
+    return fail(c, TCW_ERR_INVALID_ARGUMENT, "k must be in [1, min(n_tmpl, 1024)]");
+  cudaSetDevice(c->device);
+  BatchState* b = c->batch;
+  b->have_result = false;
+  // the plan, the tuning and the graph depend on the bank and the options
+  const int64_t key[4] = {c->B, (int64_t)c->bank_epoch, c->autotune ? 1 : 0,
+                          c->autotune ? 0 : ((int64_t)c->bank_chunk << 16 | c->tile_segments)};
+  if (!std::equal(key, key + 4, b->tune_key)) {
+    drop_graph(b);
+    b->planned = b->tuned = false;
+    std::copy(key, key + 4, b->tune_key);
+  }
+  tcw_status st = TCW_OK;
+  if (!b->planned && (st = plan_batch(c, b)) != TCW_OK) return st;
+  if (!b->tuned) {
+    if (c->autotune) {
+      if ((st = autotune(c, b)) != TCW_OK) return st;
+    } else {
+      b->bank_chunk = c->bank_chunk;
+      b->tile = c->tile_segments;
+      b->tune.clear();
+      b->tune_ms = 0;
+      b->tuned = true;
+    }
+    drop_graph(b);
+  }
+  if (!b->exec || b->graph_k != k || b->graph_mem != c->batch_memory) {
+    if ((st = capture(c, b, k)) != TCW_OK) return st;
+  }
+  TCW_CUDA(c, cudaEventRecord(c->ev0, c->stream), "event");
+  TCW_CUDA(c, cudaGraphLaunch(b->exec, c->stream), "graph launch");
+  TCW_CUDA(c, cudaEventRecord(c->ev1, c->stream), "event");
+  const size_t n = (size_t)b->total_sky * k;
+  const cudaMemcpyKind kind = out_flags == TCW_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  TCW_CUDA(c, cudaMemcpyAsync(psi_out, b->out_psi.p, n * sizeof(float), kind, c->stream), "copy out");
+  TCW_CUDA(c, cudaMemcpyAsync(idx_out, b->out_idx.p, n * sizeof(int64_t), kind, c->stream), "copy out");
+  int64_t fl[2] = {0, 0};
+  TCW_CUDA(c, cudaMemcpyAsync(fl, b->flags.p, sizeof(fl), cudaMemcpyDeviceToHost, c->stream), "flags");
+  TCW_CUDA(c, cudaStreamSynchronize(c->stream), "batched search");
+  cudaEventElapsedTime(&b->search_ms, c->ev0, c->ev1);
+  b->general = fl[1];
+  if ((int)(fl[0] & 0xffffffff) != 0) return fail(c, TCW_ERR_DEVICE, "batched search: device-side error");
+  b->have_result = true;
+  b->last_k = k;
+  return TCW_OK;
+}
+
+tcw_status tcw_get_batch_info(tcw_ctx* c, tcw_batch_info* info) {
+  if (!c || !info) return TCW_ERR_INVALID_ARGUMENT;
+  if (!c->batch) return fail(c, TCW_ERR_STATE, "no events loaded");
+  const BatchState* b = c->batch;
+  tcw_batch_info r{};
+  r.n_events = (int)b->ev.size();
+  r.total_sky = b->total_sky;
+  r.waves = b->waves;
+  r.bank_chunk = b->bank_chunk;
+  r.tile_segments = b->tile;
+  r.autotuned = (b->tuned && !b->tune.empty()) ? 1 : 0;
+  r.n_candidates = (int)b->tune.size();
+  r.n_items = b->wave_items.empty() ? 0 : b->wave_items.back();
+  r.graph_kernels = b->graph_nodes;
+  r.tune_ms = b->tune_ms;
+  for (const auto& t : b->tune) {
+    r.best_rate = std::max(r.best_rate, t.rate);
+    if (t.bank_chunk == 1 && t.tile == 32) r.default_rate = t.rate;
+  }
+  r.lookups = b->lookups;
+  r.general_path_lanes = b->general;
+  r.search_ms = b->search_ms;
+  r.quantum = b->q;
+  *info = r;
+  return TCW_OK;
+}
+
+tcw_status tcw_get_tune_results(tcw_ctx* c, int max_results, int* bank_chunk, int* tile_segments,
+                                double* sums_per_s, int* n_results) {
+  if (!c || !n_results) return TCW_ERR_INVALID_ARGUMENT;
+  if (!c->batch) return fail(c, TCW_ERR_STATE, "no events loaded");
+  const BatchState* b = c->batch;
+  *n_results = (int)b->tune.size();
+  for (int i = 0; i < (int)b->tune.size() && i < max_results; ++i) {
+    if (bank_chunk) bank_chunk[i] = b->tune[i].bank_chunk;
+    if (tile_segments) tile_segments[i] = b->tune[i].tile;
+    if (sums_per_s) sums_per_s[i] = b->tune[i].rate;
+  }
+  return TCW_OK;
+}
+
+}  // extern "C"

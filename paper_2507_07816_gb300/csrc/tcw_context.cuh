@@ -1,0 +1,137 @@
+// tcw_context.cuh -- the search context (struct tcw_ctx) and the host helpers
+// shared by the C-ABI entry points: device buffers, error reporting, uploads.
+#pragma once
+
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "tcw_internal.cuh"
+
+namespace tcw {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaError_t ensure(size_t n) {
+    if (n <= bytes && p) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMalloc(&p, n ? n : 1);
+    if (e == cudaSuccess) bytes = n;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <typename T>
+  T* as() const { return static_cast<T*>(p); }
+};
+
+struct BatchState;  // batched search state (tcw_batched.cu)
+
+}  // namespace tcw
+
+struct tcw_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string last_error;
+  // options
+  int opt_kernel = TCW_KERNEL_AUTO;
+  int keep_stats = 0;
+  int tile_segments = 32;
+  int bank_chunk = 1;      // groups of 8 templates per work item
+  int autotune = 1;        // batched search: pick bank_chunk and tile_segments by timing
+  int64_t batch_memory = (int64_t)48 << 30;  // batched search: Psi + anchor bytes per wave
+  unsigned bank_epoch = 0; // bumped by every tcw_define_bank
+  // spectrogram
+  bool have_spec = false;
+  int D = 0;
+  int64_t Nseg = 0, Nbin = 0;
+  int dtype = TCW_F32;
+  double f_min = 0, df = 0;
+  std::vector<double> h_t;
+  bool unit_weights = true;
+  tcw::DevBuf rho, t_mid, weights;
+  // velocity
+  bool have_vel = false;
+  std::vector<double> h_v;
+  tcw::DevBuf vel;
+  // bank
+  bool have_bank = false;
+  int64_t B = 0;
+  int Bpad = 0;
+  double T0 = 0;
+  std::vector<double> h_f0, h_tau, h_n;
+  tcw::DevBuf f0, tau, nbr, bank_perm, bank_pos;
+  // sky
+  bool have_sky = false;
+  int64_t S = 0;
+  int Spad = 0, NG = 0, NGpad = 0;
+  std::vector<double> h_nhat;
+  bool sky_dirty = true;
+  tcw::DevBuf nhat_sorted, sky_perm, sky_pos;
+  // derived and outputs
+  tcw::DevBuf dq, anchors, psi, st_S, st_W1, st_W2, dev, flags, stage_f, stage_i, evtab, items;
+  int64_t items_key[4] = {-1, -1, -1, -1};  // (n_chunks, Bpad, bank_chunk, grid) of the uploaded schedule
+  int grid = 0, n_items = 0;
+  bool have_result = false, stats_kept = false;
+  tcw_info info{};
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  tcw::BatchState* batch = nullptr;  // owned; freed by tcw::batch_free
+};
+
+namespace tcw {
+
+inline tcw_status fail(tcw_ctx* c, tcw_status st, const std::string& msg) {
+  if (c) c->last_error = msg;
+  return st;
+}
+
+inline tcw_status cuda_fail(tcw_ctx* c, cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return fail(c, TCW_ERR_OUT_OF_MEMORY, std::string(what) + ": out of device memory");
+  }
+  return fail(c, TCW_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define TCW_CUDA(c, expr, what)                     \
+  do {                                              \
+    cudaError_t e_ = (expr);                        \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+  } while (0)
+
+// Copy n bytes from caller memory (host or device) into a context buffer.
+inline cudaError_t upload(tcw_ctx* c, DevBuf& dst, const void* src, size_t n, int flags) {
+  cudaError_t e = dst.ensure(n);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(dst.p, src, n, flags == TCW_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                      c->stream);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(c->stream);
+}
+
+// Bring a small caller array to the host for validation.
+template <typename T>
+inline cudaError_t fetch(tcw_ctx* c, std::vector<T>& out, const T* src, size_t count, int flags) {
+  out.resize(count);
+  if (flags == TCW_DEVICE)
+    return cudaMemcpy(out.data(), src, count * sizeof(T), cudaMemcpyDeviceToHost);
+  std::memcpy(out.data(), src, count * sizeof(T));
+  return cudaSuccess;
+}
+
+inline bool finite_all(const std::vector<double>& v) {
+  for (double x : v)
+    if (!std::isfinite(x)) return false;
+  return true;
+}
+
+void batch_free(tcw_ctx* c);
+
+}  // namespace tcw

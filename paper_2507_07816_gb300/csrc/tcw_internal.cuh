@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cstdint>
 #include <string>
 #include <vector>
 
@@ -66,37 +67,59 @@ constexpr int kEntryEdge = 2;    // candidates straddle a band edge
 constexpr float kMagic = 12582912.0f;     // 1.5 * 2^23: x + kMagic rounds x to an integer
 constexpr int kMagicBits = 0x4B400000;    // bit pattern of kMagic
 
-struct GroupParams {
-  const void* rho;         // [D][Nseg][pitch] float or half, 16-byte aligned base
-  int64_t n_bin;           // bins per row that belong to the band
-  int64_t pitch;           // elements between rows (>= n_bin)
-  int64_t total_elems;     // D * Nseg * pitch
-  int n_det;               // <= kMaxStageDet
-  int n_seg;
-  const float* weights;    // [D][Nseg]
-  const double* t_mid;     // [Nseg]
-  const int32_t* blk;      // Doppler blocks [NGpad/64][Nseg][D][kBlockWords], see kBlockWords
-  const double* f0;        // sorted bank, [Bpad]
-  const double* tau;
-  const double* nbr;
-  double T0, f_min, df, inv_q;
-  int nterms;              // binomial-series length for the track; 0 = pow per entry
+// One event of a search: its spectrogram, segment times, Doppler blocks, tile
+// anchors and outputs.  A plain search is a batch of one event.
+struct EventDesc {
+  const void* rho;         // [D][n_seg][pitch] float or half, 16-byte aligned base
+  const float* weights;    // [D][n_seg]
+  const double* t_mid;     // [n_seg]
+  const int32_t* blk;      // Doppler blocks [Spad/1024][n_seg][D][kBlockWords], see kBlockWords
   const double* anchors;   // [Bpad][n_tiles][2]: 1/f and 1/(tau + t_a - T0) at each tile's
                            // anchor t_a; read only when nterms > 0
-  int n_tiles;             // ceil(Nseg / kTileSegments)
-  int B, Bpad, S, Spad, NG, NGpad;
-  int n_chunks;            // Spad / 1024 sky chunks
-  int n_items;             // n_chunks * Bpad / 8 work items; item i runs on CTA i mod grid
   float* psi;              // [Spad][Bpad]
   float* S_out;            // optional [Spad][Bpad]
   float* W1_out;
   float* W2_out;
-  float2* dev;             // scratch [Bpad][Spad]: per-sky weight sums at band edges
-  int32_t* rec;            // optional [S][B][D][Nseg], caller order
+  int64_t total_elems;     // D * n_seg * pitch
+  double T0;
+  int n_seg, n_tiles, S, Spad, NG, pad_;
+};
+
+// Work item of the group kernel: one sky chunk of 1024 sorted directions of
+// one event x `groups` consecutive groups of 8 sorted templates.
+//   x = event, y = sky chunk, z = first sorted template, w = groups
+// CTA i runs items [cta_items[i], cta_items[i + 1]) in order.
+struct GroupParams {
+  const EventDesc* events;
+  const int4* items;
+  const int* cta_items;    // [gridDim.x + 1]
+  int64_t n_bin;           // bins per row that belong to the band
+  int64_t pitch;           // elements between rows (>= n_bin)
+  int n_det;               // <= kMaxStageDet
+  const double* f0;        // sorted bank, [Bpad]
+  const double* tau;
+  const double* nbr;
+  double f_min, df, inv_q;
+  int nterms;              // binomial-series length for the track; 0 = pow per entry
+  int tile_shift;          // tiles of 2^tile_shift segments: anchors and fp32 partial sums
+  int B, Bpad;
+  float2* dev;             // scratch [gridDim.x][8][1024]: per-sky weight sums at band edges
+  int32_t* rec;            // optional [S][B][D][Nseg], caller order (single-event searches)
   const int32_t* bank_perm;  // sorted -> caller template index
-  const int32_t* sky_perm;   // sorted -> caller sky index
+  const int32_t* sky_perm;   // sorted -> caller sky index (event 0)
   unsigned long long* n_general;
   int* err;                // bit 0: window, bit 1: a bounded wait ran out
+};
+
+// Tile anchors of one event for every sorted template.
+struct AnchorParams {
+  const double* t_mid;
+  const double* f0;
+  const double* tau;
+  const double* nbr;
+  double T0;
+  int n_seg, n_tiles, tile_shift, Bpad;
+  double* anchors;         // [Bpad][n_tiles][2]
 };
 
 struct LookupParams {
@@ -139,16 +162,41 @@ struct DopplerParams {
 
 constexpr int kMaxSeriesTerms = 24;
 constexpr int kMaxStageDet = 2;          // detectors the group kernel stages in shared memory
-constexpr int kTileSegments = 32;
+constexpr int kTileShift = 5;           // default tile: 32 segments
 
 // dynamic shared memory of the group kernel for D detectors
 size_t group_smem_bytes(int n_det);
-// tile anchors of every (sorted template, tile) into anchors[Bpad * n_tiles * 2]
-cudaError_t launch_anchors(const GroupParams& p, double* anchors, cudaStream_t st);
+cudaError_t launch_anchors(const AnchorParams& p, cudaStream_t st);
+// per-CTA scratch of the group kernel, in float2 elements
+size_t group_dev_elems(int grid);
+
+// Host helpers of the group kernel (tcw_persist.cu).
+// CTAs of a group-kernel launch on the current device: one per SM.
+cudaError_t group_grid(int* grid);
+// Longest-processing-time-first schedule: items in decreasing cost, each to
+// the CTA with the least work so far (ties: lowest CTA, and equal costs keep
+// their order).  out = the items grouped by CTA, cta_items = [grid + 1] offsets.
+void schedule_items(const std::vector<int4>& items, const std::vector<int64_t>& cost, int grid,
+                    std::vector<int4>& out, std::vector<int>& cta_items);
+// Length of the binomial series sum_k binom(r, k) delta^k that gives 1/f(t_j)
+// from its tile anchor to below 2^-56 relative, for every template (tau >=
+// tau_min, r = 1/(n-1) <= r_max) and tile of `tile` segments; 0 when more
+// than kMaxSeriesTerms terms would be needed.
+int series_terms_for(const double* t_mid, int64_t n_seg, double T0, int tile, double tau_min,
+                     double r_max);
+inline int ilog2(int v) {
+  int r = 0;
+  while ((1 << (r + 1)) <= v) ++r;
+  return r;
+}
 
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_doppler(const DopplerParams& p, cudaStream_t st);
-cudaError_t launch_group(const GroupParams& p, bool half, bool record, bool weighted,
+// Set the shared-memory attribute of the group-kernel variant (also done by
+// launch_group on first use); call before capturing a launch into a graph.
+cudaError_t group_prepare(int n_det, bool half, bool weighted);
+// grid = number of CTAs (the length of p.cta_items minus one); one CTA per SM at most
+cudaError_t launch_group(const GroupParams& p, int grid, bool half, bool record, bool weighted,
                          cudaStream_t st);
 cudaError_t launch_lookup(const LookupParams& p, bool half, bool record, cudaStream_t st);
 cudaError_t launch_topk(const float* psi, int Bpad, int B, int S, int k, const int32_t* bank_perm,

@@ -21,6 +21,8 @@
 #include <cmath>
 #include <cstring>
 
+#include <vector>
+
 #include "tcw_internal.cuh"
 
 namespace tcw {
@@ -139,7 +141,13 @@ extern "C" tcw_status tcw_search_noalloc(int n_det, int64_t n_seg, int64_t n_bin
   const size_t o_ones = take(weights ? 0 : (size_t)D * Nseg * 4);
   const size_t o_dq = take((size_t)(Spad / kSkyPad) * Nseg * D * kBlockWords * 4);
   const size_t o_psi = take((size_t)Spad * Bpad * 4);
-  const size_t o_dev = take((size_t)Spad * Bpad * 8);
+  int grid = 0;
+  if (group_grid(&grid) != cudaSuccess) return TCW_ERR_CUDA;
+  const int n_chunks = Spad / kSkyPad, n_groups = Bpad / kGroupTmplPerCta;
+  const int64_t n_items = (int64_t)n_chunks * n_groups;
+  const size_t o_dev = take(group_dev_elems(grid) * 8);
+  const size_t o_ev = take(sizeof(EventDesc));
+  const size_t o_items = take((size_t)n_items * sizeof(int4) + (size_t)(grid + 1) * sizeof(int));
   if (off > kTcwNoallocScratchBytes) return TCW_ERR_UNSUPPORTED;
 
   // One-time set-up per device: the device address of the scratch array.
@@ -230,40 +238,62 @@ extern "C" tcw_status tcw_search_noalloc(int n_det, int64_t n_seg, int64_t n_bin
   const bool group_ok = fmax_bins * (double)spread * 0.5 + 0.02 <= 0.45 && D <= kMaxStageDet &&
                         ((uintptr_t)rho % 16) == 0 && (size_t)D * Nseg * n_bin * esz >= 64;
   if (group_ok) {
+    // one event; items of one group of 8 templates x one sky chunk, dealt round robin
+    EventDesc ev{};
+    ev.rho = rho;
+    ev.weights = wts;
+    ev.t_mid = t_mid;
+    ev.blk = dp.blk;
+    ev.psi = psi;
+    ev.total_elems = (int64_t)D * Nseg * n_bin;
+    ev.T0 = T0;
+    ev.n_seg = Nseg;
+    ev.n_tiles = (Nseg + 31) / 32;
+    ev.S = S;
+    ev.Spad = Spad;
+    ev.NG = NG;
+    std::vector<int4> items;
+    std::vector<int64_t> cost;
+    items.reserve(n_items);
+    for (int g = 0; g < n_groups; ++g)
+      for (int ch = 0; ch < n_chunks; ++ch) {
+        items.push_back(make_int4(0, ch, g * kGroupTmplPerCta, 1));
+        cost.push_back(Nseg);
+      }
+    std::vector<int4> order;
+    std::vector<int> cta;
+    schedule_items(items, cost, grid, order, cta);
+    unsigned char* it_dst = base + o_items;
+    if (cudaMemcpyAsync(base + o_ev, &ev, sizeof(ev), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(it_dst, order.data(), order.size() * sizeof(int4), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(it_dst + order.size() * sizeof(int4), cta.data(), cta.size() * sizeof(int),
+                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return TCW_ERR_CUDA;
     GroupParams gp{};
-    gp.rho = rho;
+    gp.events = reinterpret_cast<const EventDesc*>(base + o_ev);
+    gp.items = reinterpret_cast<const int4*>(it_dst);
+    gp.cta_items = reinterpret_cast<const int*>(it_dst + order.size() * sizeof(int4));
     gp.n_bin = n_bin;
     gp.pitch = n_bin;
-    gp.total_elems = (int64_t)D * Nseg * n_bin;
     gp.n_det = D;
-    gp.n_seg = Nseg;
-    gp.weights = wts;
-    gp.t_mid = t_mid;
-    gp.blk = dp.blk;
     gp.f0 = pp.f0p;
     gp.tau = pp.taup;
     gp.nbr = pp.nbrp;
-    gp.T0 = T0;
     gp.f_min = f_min;
     gp.df = df;
     gp.inv_q = dp.inv_q;
     gp.nterms = 0;
+    gp.tile_shift = kTileShift;
     gp.B = B;
     gp.Bpad = Bpad;
-    gp.S = S;
-    gp.Spad = Spad;
-    gp.NG = NG;
-    gp.NGpad = NGpad;
-    gp.n_chunks = Spad / kSkyPad;
-    gp.n_items = gp.n_chunks * (Bpad / kGroupTmplPerCta);
-    gp.n_tiles = (int)((n_seg + kTileSegments - 1) / kTileSegments);
-    gp.psi = psi;
     gp.dev = reinterpret_cast<float2*>(base + o_dev);
     gp.bank_perm = pp.bank_perm;
     gp.sky_perm = pp.sky_perm;
     gp.n_general = ngen;
     gp.err = err;
-    if (launch_group(gp, dtype == TCW_F16, false, true, st) != cudaSuccess) return TCW_ERR_CUDA;
+    if (launch_group(gp, grid, dtype == TCW_F16, false, true, st) != cudaSuccess) return TCW_ERR_CUDA;
   } else {
     // sky groups too wide for one candidate pair: per-lookup FP64 kernel
     LookupParams lp{};

@@ -1,28 +1,33 @@
 // tcw_persist.cu -- the hot loop: a persistent, warp-specialised group kernel.
 //
-// One CTA per SM walks its share of the work items (item i runs on CTA
-// i mod gridDim.x); an item is 8 sorted templates x one chunk of 1024 sorted
-// sky directions x every segment and detector.
+// One CTA per SM runs its list of work items in order; an item is one chunk
+// of 1024 sorted sky directions of one event x a run of groups of 8 sorted
+// templates, and each group of 8 templates (a "pass") streams every segment
+// and detector of the event through shared memory:
 //
-//   producer warps (3)   warp w owns every third batch of 4 segments: the
-//                        8 x 4 track entries in FP64 (Eq. 1, one lane per
-//                        entry, from the tile anchors of anchor_kernel), their
-//                        64-byte power windows (16-byte async copies), the
-//                        segment weights, and one bulk copy of the chunk's
-//                        Doppler blocks per segment (Eq. 2 factor on the
-//                        fixed-point grid) into a 16-stage shared-memory ring
+//   producer warps (3)   warp w owns every third batch of 4 segments of the
+//                        CTA's pass sequence: the 8 x 4 track entries in FP64
+//                        (Eq. 1, one lane per entry, from the tile anchors of
+//                        anchor_kernel), their 64-byte power windows (16-byte
+//                        async copies), the segment weights, and one bulk copy
+//                        of the chunk's Doppler blocks per segment (Eq. 2
+//                        factor on the fixed-point grid) into a 16-stage ring
 //   consumer warps (8)   per segment: for each detector and each of two
 //                        templates, the candidate bin pair of the lane's
 //                        16-sky group, two window reads, and per sky one int32
 //                        compare + one predicated add (Sec. 2 weighted sum),
 //                        plus the weight sums W1, W2; Psi of Eq. 4 at the end
-//                        of the item
+//                        of the pass
 //
-// Ring stage q holds segment q mod Nseg of the CTA's (q / Nseg)-th item, so
-// both sides derive every index from q alone.  The ring is driven by
-// mbarriers (full: one producer arrival + the bulk-copy bytes; empty: one
-// arrival per consumer warp); every wait is bounded.
+// Ring position q counts the segments of all passes of the CTA so far, so
+// both sides derive every index from their walk over the item list.  The ring
+// is driven by mbarriers (full: one producer arrival + the bulk-copy bytes;
+// empty: one arrival per consumer warp); every wait is bounded.
+#include <algorithm>
 #include <climits>
+#include <cmath>
+#include <numeric>
+#include <queue>
 
 #include "tcw_internal.cuh"
 #include "tcw_ptx.cuh"
@@ -37,7 +42,6 @@ constexpr int kProducerWarps = 3;
 constexpr int kThreads = kConsumers + kProducerWarps * 32;
 constexpr int kBatch = 32 / kPT;                  // segments per producer batch (one lane per entry)
 constexpr int kRing = 16;                         // ring stages
-constexpr int kTileSeg = kTileSegments;           // fp32 partial-sum tile and anchor spacing
 static_assert(kPT == 8 && kBatch == 4, "geometry");
 static_assert(kConsumers == (kPT / 2) * kGroupLanes, "two templates per consumer thread");
 static_assert(kRing >= (kProducerWarps + 1) * kBatch, "every producer's batch fits the ring");
@@ -55,12 +59,13 @@ struct PersistLayout {
   }
 };
 
-// Tile anchor of a tile's segments: the middle segment's time, or T0 when
-// that is earlier.
-__device__ __forceinline__ double tile_anchor_time(const GroupParams& p, int ti) {
-  const int j0 = ti * kTileSeg;
-  const int jn = min(kTileSeg, p.n_seg - j0);
-  return fmax(p.t_mid[j0 + (jn - 1) / 2], p.T0);
+// Anchor time of tile ti (segments [ti << shift, (ti + 1) << shift)): the
+// middle segment's time, or T0 when that is earlier.
+__device__ __forceinline__ double tile_anchor_time(const double* t_mid, int n_seg, double T0,
+                                                   int shift, int ti) {
+  const int j0 = ti << shift;
+  const int jn = min(1 << shift, n_seg - j0);
+  return fmax(t_mid[j0 + (jn - 1) / 2], T0);
 }
 
 // ---------------------------------------------------------------------------
@@ -68,14 +73,14 @@ __device__ __forceinline__ double tile_anchor_time(const GroupParams& p, int ti)
 //   anchors[b][ti] = { 1/f(t_a) = (1 + (t_a - T0)/tau)^(1/(n-1)) / f0,
 //                      1/(tau + t_a - T0) }
 // ---------------------------------------------------------------------------
-__global__ void anchor_kernel(GroupParams p, double* anchors) {
+__global__ void anchor_kernel(AnchorParams p) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (int64_t)p.Bpad * p.n_tiles) return;
   const int b = (int)(i / p.n_tiles), ti = (int)(i % p.n_tiles);
-  const double ta = tile_anchor_time(p, ti);
+  const double ta = tile_anchor_time(p.t_mid, p.n_seg, p.T0, p.tile_shift, ti);
   const double tau = p.tau[b];
-  anchors[i * 2] = pow((ta - p.T0) / tau + 1.0, 1.0 / (p.nbr[b] - 1.0)) / p.f0[b];
-  anchors[i * 2 + 1] = 1.0 / (tau + (ta - p.T0));
+  p.anchors[i * 2] = pow((ta - p.T0) / tau + 1.0, 1.0 / (p.nbr[b] - 1.0)) / p.f0[b];
+  p.anchors[i * 2 + 1] = 1.0 / (tau + (ta - p.T0));
 }
 
 // ---------------------------------------------------------------------------
@@ -88,24 +93,24 @@ __global__ void anchor_kernel(GroupParams p, double* anchors) {
 // 64-byte power windows around the track.
 // ---------------------------------------------------------------------------
 template <typename RhoT>
-__device__ __forceinline__ void compute_entry(const GroupParams& p, const double* coef, int b, int j,
-                                              float fmin_f, float inv_df_f, TrackEntry& e,
-                                              uint32_t win_dst) {
-  const double tj = p.t_mid[j];
-  if (!(tj >= p.T0)) {
+__device__ __forceinline__ void compute_entry(const GroupParams& p, const EventDesc& ev,
+                                              const double* coef, int b, int j, float fmin_f,
+                                              float inv_df_f, TrackEntry& e, uint32_t win_dst) {
+  const double tj = ev.t_mid[j];
+  if (!(tj >= ev.T0)) {
     e.cls = kEntryNone;
     return;
   }
   double h;
   if (p.nterms > 0) {
-    const int ti = j / kTileSeg;
-    const double2 an = reinterpret_cast<const double2*>(p.anchors)[(int64_t)b * p.n_tiles + ti];
-    const double delta = (tj - tile_anchor_time(p, ti)) * an.y;
+    const int ti = j >> p.tile_shift;
+    const double2 an = reinterpret_cast<const double2*>(ev.anchors)[(int64_t)b * ev.n_tiles + ti];
+    const double delta = (tj - tile_anchor_time(ev.t_mid, ev.n_seg, ev.T0, p.tile_shift, ti)) * an.y;
     double R = coef[p.nterms - 1];
     for (int k = p.nterms - 2; k >= 0; --k) R = fma(R, delta, coef[k]);
     h = an.x * R;
   } else {
-    h = pow((tj - p.T0) / p.tau[b] + 1.0, 1.0 / (p.nbr[b] - 1.0)) / p.f0[b];
+    h = pow((tj - ev.T0) / p.tau[b] + 1.0, 1.0 / (p.nbr[b] - 1.0)) / p.f0[b];
   }
   const float f = __frcp_rn((float)h);
   const float x = (f - fmin_f) * inv_df_f;
@@ -132,12 +137,12 @@ __device__ __forceinline__ void compute_entry(const GroupParams& p, const double
   // power windows: 64 bytes from a 16-byte boundary at or below bin base + kMLo,
   // clamped into the array (the valid candidates stay inside the window)
   constexpr int64_t E = 16 / sizeof(RhoT), W = kWinBytes / sizeof(RhoT);
-  const RhoT* rho = static_cast<const RhoT*>(p.rho);
+  const RhoT* rho = static_cast<const RhoT*>(ev.rho);
   for (int d = 0; d < p.n_det; ++d) {
-    const int64_t row = ((int64_t)d * p.n_seg + j) * p.pitch;
+    const int64_t row = ((int64_t)d * ev.n_seg + j) * p.pitch;
     int64_t gs = row + base + kMLo;
     gs -= ((gs % E) + E) % E;
-    gs = gs < 0 ? 0 : (gs > p.total_elems - W ? p.total_elems - W : gs);
+    gs = gs < 0 ? 0 : (gs > ev.total_elems - W ? ev.total_elems - W : gs);
     const int woff = (int)(gs - row - base);
     const uint32_t dst = win_dst + d * kWinBytes;
     e.wa[d] = dst - (uint32_t)sizeof(RhoT) * (uint32_t)(kMagicBits + woff);
@@ -159,7 +164,8 @@ __global__ void __launch_bounds__(kThreads, 1) group_kernel(GroupParams p) {
   const uint32_t bar_empty = bar_full + kRing * 8;
   const int tid = threadIdx.x, lane = tid & 31;
   const uint32_t dq_bytes = (uint32_t)(D * kStageDetBytes);
-  const int n_seg = p.n_seg;
+  const int it0 = p.cta_items[blockIdx.x], it1 = p.cta_items[blockIdx.x + 1];
+  const int tmask = (1 << p.tile_shift) - 1;
 
   if (tid == 0) {
     for (int i = 0; i < kRing; ++i) {
@@ -172,67 +178,77 @@ __global__ void __launch_bounds__(kThreads, 1) group_kernel(GroupParams p) {
 
   if (tid >= kConsumers) {
     // ======================= producer warps =======================
-    // Batches are numbered in ring order; warp pw takes n = pw, pw + 3, ...
-    // Each warp fills its batches in increasing order, so a stage it waits
-    // for was last used by an earlier batch and the waits cannot deadlock.
+    // Batches of 4 segments are numbered along the CTA's pass sequence; warp
+    // pw takes those with number = pw (mod 3).  Each warp fills its batches
+    // in increasing order, so a stage it waits for was last used by an
+    // earlier batch and the waits cannot deadlock.
     const int pw = (tid - kConsumers) >> 5;
     const int lt = lane % kPT, lk = lane / kPT;   // template and segment slot of this lane
     double* coef = reinterpret_cast<double*>(smem + L.coef) + pw * kPT * kMaxSeriesTerms;
     const float fmin_f = (float)p.f_min, inv_df_f = (float)(1.0 / p.df);
-    const int bpi = (n_seg + kBatch - 1) / kBatch;   // batches per item
-    long long coef_item = -1;
-    for (long long n = pw;; n += kProducerWarps) {
-      const long long ki = n / bpi;
-      const long long item = blockIdx.x + ki * gridDim.x;
-      if (item >= p.n_items) break;
-      const int jb = (int)(n % bpi) * kBatch;
-      const int nb = min(kBatch, n_seg - jb);
-      const long long q0 = ki * n_seg + jb;           // ring position of the batch's first segment
-      const int chunk = (int)(item % p.n_chunks);
-      const int b0 = (int)(item / p.n_chunks) * kPT;
-      if (coef_item != item) {
-        __syncwarp();
-        if (lane < kPT) {
-          const double r = 1.0 / (p.nbr[b0 + lane] - 1.0);
-          double c = 1.0;
-          for (int k = 0; k < p.nterms; ++k) {
-            coef[lane * kMaxSeriesTerms + k] = c;
-            c = c * (r - k) / (k + 1);
+    long long qbase = 0;   // ring position of the pass's first segment
+    int nmod = 0;          // number of the pass's first batch, mod 3
+    bool ok = true;
+    for (int it = it0; it < it1 && ok; ++it) {
+      const int4 item = p.items[it];
+      const EventDesc ev = p.events[item.x];
+      const int n_seg = ev.n_seg;
+      const int bpi = (n_seg + kBatch - 1) / kBatch;   // batches per pass
+      const int32_t* blk = ev.blk + (int64_t)item.y * n_seg * D * kBlockWords;
+      for (int tg = 0; tg < item.w && ok; ++tg) {
+        const int b0 = item.z + tg * kPT;
+        if (p.nterms > 0) {
+          __syncwarp();
+          if (lane < kPT) {
+            const double r = 1.0 / (p.nbr[b0 + lane] - 1.0);
+            double c = 1.0;
+            for (int k = 0; k < p.nterms; ++k) {
+              coef[lane * kMaxSeriesTerms + k] = c;
+              c = c * (r - k) / (k + 1);
+            }
+          }
+          __syncwarp();
+        }
+        for (int jbi = (pw - nmod + kProducerWarps) % kProducerWarps; jbi < bpi; jbi += kProducerWarps) {
+          const int jb = jbi * kBatch;
+          const int nb = min(kBatch, n_seg - jb);
+          const long long q0 = qbase + jb;
+          int okw = 1;
+          if (lane == 0) {
+            for (int k = 0; k < nb && okw; ++k) {
+              const long long q = q0 + k;
+              okw = mbar_wait(bar_empty + 8 * (unsigned)(q % kRing), (unsigned)(((q / kRing) & 1) ^ 1), p.err);
+            }
+          }
+          okw = __shfl_sync(0xffffffffu, okw, 0);
+          if (!okw) {
+            ok = false;
+            break;
+          }
+          fence_proxy_async();
+          if (lk < nb) {
+            const int j = jb + lk;
+            const unsigned s = (unsigned)((q0 + lk) % kRing);
+            unsigned char* st = smem + s * L.stage;
+            TrackEntry& e = *reinterpret_cast<TrackEntry*>(st + L.ent + lt * sizeof(TrackEntry));
+            compute_entry<RhoT>(p, ev, coef + lt * kMaxSeriesTerms, b0 + lt, j, fmin_f, inv_df_f, e,
+                                smem0 + s * (uint32_t)L.stage + (uint32_t)L.win + lt * D * kWinBytes);
+            if (lt < D) reinterpret_cast<float*>(st + L.hdr)[lt] = ev.weights[(int64_t)lt * n_seg + j];
+          }
+          cp_async_wait_all();
+          __syncwarp();
+          if (lane == 0) {
+            for (int k = 0; k < nb; ++k) {
+              const unsigned s = (unsigned)((q0 + k) % kRing);
+              const uint32_t full = bar_full + 8 * s;
+              mbar_arrive_expect_tx(full, dq_bytes);
+              bulk_g2s(smem0 + s * (uint32_t)L.stage, blk + (int64_t)(jb + k) * D * kBlockWords, dq_bytes,
+                       full);
+            }
           }
         }
-        coef_item = item;
-        __syncwarp();
-      }
-      int ok = 1;
-      if (lane == 0) {
-        for (int k = 0; k < nb && ok; ++k) {
-          const long long q = q0 + k;
-          ok = mbar_wait(bar_empty + 8 * (unsigned)(q % kRing), (unsigned)(((q / kRing) & 1) ^ 1), p.err);
-        }
-      }
-      ok = __shfl_sync(0xffffffffu, ok, 0);
-      if (!ok) break;
-      fence_proxy_async();
-      if (lk < nb) {
-        const int j = jb + lk;
-        const unsigned s = (unsigned)((q0 + lk) % kRing);
-        unsigned char* st = smem + s * L.stage;
-        TrackEntry& e = *reinterpret_cast<TrackEntry*>(st + L.ent + lt * sizeof(TrackEntry));
-        compute_entry<RhoT>(p, coef + lt * kMaxSeriesTerms, b0 + lt, j, fmin_f, inv_df_f, e,
-                            smem0 + s * (uint32_t)L.stage + (uint32_t)L.win + lt * D * kWinBytes);
-        if (lt < D) reinterpret_cast<float*>(st + L.hdr)[lt] = p.weights[(int64_t)lt * n_seg + j];
-      }
-      cp_async_wait_all();
-      __syncwarp();
-      if (lane == 0) {
-        for (int k = 0; k < nb; ++k) {
-          const long long q = q0 + k;
-          const unsigned s = (unsigned)(q % kRing);
-          const uint32_t full = bar_full + 8 * s;
-          mbar_arrive_expect_tx(full, dq_bytes);
-          bulk_g2s(smem0 + s * (uint32_t)L.stage,
-                   p.blk + (((int64_t)chunk * n_seg + jb + k) * D) * kBlockWords, dq_bytes, full);
-        }
+        qbase += n_seg;
+        nmod = (nmod + bpi) % kProducerWarps;
       }
     }
     return;
@@ -240,180 +256,186 @@ __global__ void __launch_bounds__(kThreads, 1) group_kernel(GroupParams p) {
 
   // ======================= consumer warps =======================
   const int u = tid / kGroupLanes, l = tid % kGroupLanes;  // template pair, sky group in the chunk
+  float2* const dev_cta = p.dev + (int64_t)blockIdx.x * kPT * kSkyPad;
   unsigned long long ngen = 0;
   long long q = 0;
   bool ok = true;
-  for (long long item = blockIdx.x; item < p.n_items && ok; item += gridDim.x) {
-    const int chunk = (int)(item % p.n_chunks);
-    const int b0 = (int)(item / p.n_chunks) * kPT;
-    const int g = chunk * kGroupLanes + l;
-    const bool gval = g < p.NG;
+  for (int it = it0; it < it1 && ok; ++it) {
+    const int4 item = p.items[it];
+    const EventDesc ev = p.events[item.x];
+    const int n_seg = ev.n_seg;
+    const int g = item.y * kGroupLanes + l;
+    const bool gval = g < ev.NG;
     const int s0 = g * G;
-    float acc[2][G], tot[2][G], gt[2], w1t[2], w2t[2];
-    double gw[2], w1[2], w2[2];
-    unsigned touched = 0;
+    for (int tg = 0; tg < item.w && ok; ++tg) {
+      const int b0 = item.z + tg * kPT;
+      float acc[2][G], tot[2][G], gt[2], w1t[2], w2t[2];
+      double gw[2], w1[2], w2[2];
+      unsigned touched = 0;
 #pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      gt[t] = w1t[t] = w2t[t] = 0.f;
-      gw[t] = w1[t] = w2[t] = 0.0;
+      for (int t = 0; t < 2; ++t) {
+        gt[t] = w1t[t] = w2t[t] = 0.f;
+        gw[t] = w1[t] = w2[t] = 0.0;
 #pragma unroll
-      for (int k = 0; k < G; ++k) acc[t][k] = tot[t][k] = 0.f;
-    }
-    for (int j = 0; j < n_seg; ++j, ++q) {
-      const unsigned s = (unsigned)(q % kRing);
-      if (!mbar_wait(bar_full + 8 * s, (unsigned)((q / kRing) & 1), p.err)) {
-        ok = false;
-        break;
+        for (int k = 0; k < G; ++k) acc[t][k] = tot[t][k] = 0.f;
       }
-      const uint32_t sb = smem0 + s * (uint32_t)L.stage;
-      if (gval) {
-        const uint32_t stage = sb + l * 16;
-        const uint32_t e0 = sb + (uint32_t)L.ent + (uint32_t)(2 * u * (int)sizeof(TrackEntry));
-        const uint32_t e1 = e0 + (uint32_t)sizeof(TrackEntry);
-        const float4 h0 = lds_f4(e0), h1 = lds_f4(e1);
-        const int4 wa0 = lds_v4(e0 + 16), wa1 = lds_v4(e1 + 16);
-        const int c0 = __float_as_int(h0.w), c1 = __float_as_int(h1.w);
-        const float4 wseg = lds_f4(sb + (uint32_t)L.hdr);
+      for (int j = 0; j < n_seg; ++j, ++q) {
+        const unsigned s = (unsigned)(q % kRing);
+        if (!mbar_wait(bar_full + 8 * s, (unsigned)((q / kRing) & 1), p.err)) {
+          ok = false;
+          break;
+        }
+        const uint32_t sb = smem0 + s * (uint32_t)L.stage;
+        if (gval) {
+          const uint32_t stage = sb + l * 16;
+          const uint32_t e0 = sb + (uint32_t)L.ent + (uint32_t)(2 * u * (int)sizeof(TrackEntry));
+          const uint32_t e1 = e0 + (uint32_t)sizeof(TrackEntry);
+          const float4 h0 = lds_f4(e0), h1 = lds_f4(e1);
+          const int4 wa0 = lds_v4(e0 + 16), wa1 = lds_v4(e1 + 16);
+          const int c0 = __float_as_int(h0.w), c1 = __float_as_int(h1.w);
+          const float4 wseg = lds_f4(sb + (uint32_t)L.hdr);
 #pragma unroll
-        for (int d = 0; d < D; ++d) {
-          const float wd = WEIGHTED ? (d == 0 ? wseg.x : wseg.y) : 1.0f;
-          const uint32_t sd = stage + d * kStageDetBytes;
-          const float gm = lds_f32(sd - l * 16 + 4 * kGroupLanes * 16 + l * 4);
-          int th0 = INT_MAX, th1 = INT_MAX;
-          float dw0 = 0.f, dw1 = 0.f;
-          const int zb0 = __float_as_int(fmaf(h0.x, gm, h0.y) + kMagic);
-          const int zb1 = __float_as_int(fmaf(h1.x, gm, h1.y) + kMagic);
-          const uint32_t wd0 = (uint32_t)(d == 0 ? wa0.x : wa0.y);
-          const uint32_t wd1 = (uint32_t)(d == 0 ? wa1.x : wa1.y);
-          if (c0 == kEntryInside) {
-            th0 = (int)lds_u32(__float_as_uint(h0.z) + 4u * (uint32_t)zb0);
-            const uint32_t a = wd0 + ESZ * (uint32_t)zb0;
-            const float rlo = lds_pow(a, RhoT()), rhi = lds_pow(a + ESZ, RhoT());
-            gt[0] = fmaf(wd, rlo, gt[0]);
-            dw0 = wd * (rhi - rlo);
-            w1t[0] += wd;
-            w2t[0] = fmaf(wd, wd, w2t[0]);
-          }
-          if (c1 == kEntryInside) {
-            th1 = (int)lds_u32(__float_as_uint(h1.z) + 4u * (uint32_t)zb1);
-            const uint32_t a = wd1 + ESZ * (uint32_t)zb1;
-            const float rlo = lds_pow(a, RhoT()), rhi = lds_pow(a + ESZ, RhoT());
-            gt[1] = fmaf(wd, rlo, gt[1]);
-            dw1 = wd * (rhi - rlo);
-            w1t[1] += wd;
-            w2t[1] = fmaf(wd, wd, w2t[1]);
-          }
+          for (int d = 0; d < D; ++d) {
+            const float wd = WEIGHTED ? (d == 0 ? wseg.x : wseg.y) : 1.0f;
+            const uint32_t sd = stage + d * kStageDetBytes;
+            const float gm = lds_f32(sd - l * 16 + 4 * kGroupLanes * 16 + l * 4);
+            int th0 = INT_MAX, th1 = INT_MAX;
+            float dw0 = 0.f, dw1 = 0.f;
+            const int zb0 = __float_as_int(fmaf(h0.x, gm, h0.y) + kMagic);
+            const int zb1 = __float_as_int(fmaf(h1.x, gm, h1.y) + kMagic);
+            const uint32_t wd0 = (uint32_t)(d == 0 ? wa0.x : wa0.y);
+            const uint32_t wd1 = (uint32_t)(d == 0 ? wa1.x : wa1.y);
+            if (c0 == kEntryInside) {
+              th0 = (int)lds_u32(__float_as_uint(h0.z) + 4u * (uint32_t)zb0);
+              const uint32_t a = wd0 + ESZ * (uint32_t)zb0;
+              const float rlo = lds_pow(a, RhoT()), rhi = lds_pow(a + ESZ, RhoT());
+              gt[0] = fmaf(wd, rlo, gt[0]);
+              dw0 = wd * (rhi - rlo);
+              w1t[0] += wd;
+              w2t[0] = fmaf(wd, wd, w2t[0]);
+            }
+            if (c1 == kEntryInside) {
+              th1 = (int)lds_u32(__float_as_uint(h1.z) + 4u * (uint32_t)zb1);
+              const uint32_t a = wd1 + ESZ * (uint32_t)zb1;
+              const float rlo = lds_pow(a, RhoT()), rhi = lds_pow(a + ESZ, RhoT());
+              gt[1] = fmaf(wd, rlo, gt[1]);
+              dw1 = wd * (rhi - rlo);
+              w1t[1] += wd;
+              w2t[1] = fmaf(wd, wd, w2t[1]);
+            }
 #pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            const int4 qv = lds_v4(sd + v * kGroupLanes * 16);
-            pred_add(acc[0][4 * v + 0], qv.x, th0, dw0);
-            pred_add(acc[1][4 * v + 0], qv.x, th1, dw1);
-            pred_add(acc[0][4 * v + 1], qv.y, th0, dw0);
-            pred_add(acc[1][4 * v + 1], qv.y, th1, dw1);
-            pred_add(acc[0][4 * v + 2], qv.z, th0, dw0);
-            pred_add(acc[1][4 * v + 2], qv.z, th1, dw1);
-            pred_add(acc[0][4 * v + 3], qv.w, th0, dw0);
-            pred_add(acc[1][4 * v + 3], qv.w, th1, dw1);
-          }
-          if (RECORD || c0 == kEntryEdge || c1 == kEntryEdge) {
-            // rare: band-edge entries, and recording of the chosen bins
+            for (int v = 0; v < 4; ++v) {
+              const int4 qv = lds_v4(sd + v * kGroupLanes * 16);
+              pred_add(acc[0][4 * v + 0], qv.x, th0, dw0);
+              pred_add(acc[1][4 * v + 0], qv.x, th1, dw1);
+              pred_add(acc[0][4 * v + 1], qv.y, th0, dw0);
+              pred_add(acc[1][4 * v + 1], qv.y, th1, dw1);
+              pred_add(acc[0][4 * v + 2], qv.z, th0, dw0);
+              pred_add(acc[1][4 * v + 2], qv.z, th1, dw1);
+              pred_add(acc[0][4 * v + 3], qv.w, th0, dw0);
+              pred_add(acc[1][4 * v + 3], qv.w, th1, dw1);
+            }
+            if (RECORD || c0 == kEntryEdge || c1 == kEntryEdge) {
+              // rare: band-edge entries, and recording of the chosen bins
 #pragma unroll
-            for (int t = 0; t < 2; ++t) {
-              const int c = t ? c1 : c0;
-              const int zb = t ? zb1 : zb0;
-              const uint32_t tha = __float_as_uint(t ? h1.z : h0.z);
-              const uint32_t wdt = t ? wd1 : wd0;
-              const uint32_t ea = t ? e1 : e0;
-              const int b = b0 + 2 * u + t;
-              int32_t* rp = nullptr;
-              const int64_t rstride = (int64_t)p.B * D * n_seg;
-              if (RECORD && b < p.B) rp = p.rec + ((int64_t)p.bank_perm[b] * D + d) * n_seg + j;
-              if (c == kEntryNone) {
-                if (RECORD && rp)
-                  for (int k = 0; k < G; ++k)
-                    if (s0 + k < p.S) rp[(int64_t)p.sky_perm[s0 + k] * rstride] = -1;
-                continue;
-              }
-              const int K0 = (int)lds_u32(ea + 32) + zb;  // kb
-              const int th = (int)lds_u32(tha + 4u * (uint32_t)zb);
-              if (c == kEntryInside) {
-                if (RECORD && rp)
-                  for (int k = 0; k < G; ++k) {
-                    const int qk = (int)lds_u32(sd + (k >> 2) * kGroupLanes * 16 + (k & 3) * 4);
-                    if (s0 + k < p.S) rp[(int64_t)p.sky_perm[s0 + k] * rstride] = K0 + (qk >= th ? 1 : 0);
+              for (int t = 0; t < 2; ++t) {
+                const int c = t ? c1 : c0;
+                const int zb = t ? zb1 : zb0;
+                const uint32_t tha = __float_as_uint(t ? h1.z : h0.z);
+                const uint32_t wdt = t ? wd1 : wd0;
+                const uint32_t ea = t ? e1 : e0;
+                const int b = b0 + 2 * u + t;
+                int32_t* rp = nullptr;
+                const int64_t rstride = (int64_t)p.B * D * n_seg;
+                if (RECORD && b < p.B) rp = p.rec + ((int64_t)p.bank_perm[b] * D + d) * n_seg + j;
+                if (c == kEntryNone) {
+                  if (RECORD && rp)
+                    for (int k = 0; k < G; ++k)
+                      if (s0 + k < ev.S) rp[(int64_t)p.sky_perm[s0 + k] * rstride] = -1;
+                  continue;
+                }
+                const int K0 = (int)lds_u32(ea + 32) + zb;  // kb
+                const int th = (int)lds_u32(tha + 4u * (uint32_t)zb);
+                if (c == kEntryInside) {
+                  if (RECORD && rp)
+                    for (int k = 0; k < G; ++k) {
+                      const int qk = (int)lds_u32(sd + (k >> 2) * kGroupLanes * 16 + (k & 3) * 4);
+                      if (s0 + k < ev.S) rp[(int64_t)p.sky_perm[s0 + k] * rstride] = K0 + (qk >= th ? 1 : 0);
+                    }
+                  continue;
+                }
+                const bool vlo = (unsigned)K0 < (unsigned)p.n_bin;
+                const bool vhi = (unsigned)(K0 + 1) < (unsigned)p.n_bin;
+                const uint32_t a = wdt + ESZ * (uint32_t)zb;
+                const float rlo = vlo ? lds_pow(a, RhoT()) : 0.f;
+                const float rhi = vhi ? lds_pow(a + ESZ, RhoT()) : 0.f;
+                ++ngen;
+                float2* dvp = dev_cta + (2 * u + t) * kSkyPad + l * G;
+                if (!(touched & (1u << t))) {
+                  touched |= 1u << t;
+                  for (int k = 0; k < G; ++k) dvp[k] = make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int k = 0; k < G; ++k) {
+                  const int qk = (int)lds_u32(sd + (k >> 2) * kGroupLanes * 16 + (k & 3) * 4);
+                  const bool up = qk >= th;
+                  const bool okb = up ? vhi : vlo;
+                  if (RECORD && rp && s0 + k < ev.S)
+                    rp[(int64_t)p.sky_perm[s0 + k] * rstride] = okb ? K0 + (up ? 1 : 0) : -1;
+                  if (okb) {
+                    acc[t][k] = fmaf(wd, up ? rhi : rlo, acc[t][k]);
+                    float2 dv = dvp[k];
+                    dv.x += wd;
+                    dv.y = fmaf(wd, wd, dv.y);
+                    dvp[k] = dv;
                   }
-                continue;
-              }
-              const bool vlo = (unsigned)K0 < (unsigned)p.n_bin;
-              const bool vhi = (unsigned)(K0 + 1) < (unsigned)p.n_bin;
-              const uint32_t a = wdt + ESZ * (uint32_t)zb;
-              const float rlo = vlo ? lds_pow(a, RhoT()) : 0.f;
-              const float rhi = vhi ? lds_pow(a + ESZ, RhoT()) : 0.f;
-              ++ngen;
-              float2* dvp = p.dev + (int64_t)b * p.Spad + s0;
-              if (!(touched & (1u << t))) {
-                touched |= 1u << t;
-                for (int k = 0; k < G; ++k) dvp[k] = make_float2(0.f, 0.f);
-              }
-#pragma unroll
-              for (int k = 0; k < G; ++k) {
-                const int qk = (int)lds_u32(sd + (k >> 2) * kGroupLanes * 16 + (k & 3) * 4);
-                const bool up = qk >= th;
-                const bool okb = up ? vhi : vlo;
-                if (RECORD && rp && s0 + k < p.S)
-                  rp[(int64_t)p.sky_perm[s0 + k] * rstride] = okb ? K0 + (up ? 1 : 0) : -1;
-                if (okb) {
-                  acc[t][k] = fmaf(wd, up ? rhi : rlo, acc[t][k]);
-                  float2 dv = dvp[k];
-                  dv.x += wd;
-                  dv.y = fmaf(wd, wd, dv.y);
-                  dvp[k] = dv;
                 }
               }
             }
           }
         }
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(bar_empty + 8 * s);
-      if (j % kTileSeg == kTileSeg - 1 || j == n_seg - 1) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar_empty + 8 * s);
+        if ((j & tmask) == tmask || j == n_seg - 1) {
 #pragma unroll
-        for (int t = 0; t < 2; ++t) {
-          gw[t] += (double)gt[t];
-          w1[t] += (double)w1t[t];
-          w2[t] += (double)w2t[t];
-          gt[t] = w1t[t] = w2t[t] = 0.f;
+          for (int t = 0; t < 2; ++t) {
+            gw[t] += (double)gt[t];
+            w1[t] += (double)w1t[t];
+            w2[t] += (double)w2t[t];
+            gt[t] = w1t[t] = w2t[t] = 0.f;
 #pragma unroll
-          for (int k = 0; k < G; ++k) {
-            tot[t][k] += acc[t][k];
-            acc[t][k] = 0.f;
+            for (int k = 0; k < G; ++k) {
+              tot[t][k] += acc[t][k];
+              acc[t][k] = 0.f;
+            }
           }
         }
       }
-    }
-    if (!ok || !gval) continue;
+      if (!ok || !gval) continue;
 #pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      const int b = b0 + 2 * u + t;
-      const double base_num = gw[t] - w1[t];
+      for (int t = 0; t < 2; ++t) {
+        const int b = b0 + 2 * u + t;
+        const double base_num = gw[t] - w1[t];
+        const float2* dvp = dev_cta + (2 * u + t) * kSkyPad + l * G;
 #pragma unroll
-      for (int k = 0; k < G; ++k) {
-        const int sk = s0 + k;
-        float dv1 = 0.f, dv2 = 0.f;
-        if (touched & (1u << t)) {
-          const float2 dv = p.dev[(int64_t)b * p.Spad + sk];
-          dv1 = dv.x;
-          dv2 = dv.y;
-        }
-        const float W1 = (float)(w1[t] + (double)dv1);
-        const float W2 = (float)(w2[t] + (double)dv2);
-        const float num = (float)(base_num - (double)dv1) + tot[t][k];
-        const int64_t o = (int64_t)sk * p.Bpad + b;
-        p.psi[o] = W2 > 0.f ? num * rsqrtf(W2) : -INFINITY;
-        if (p.S_out) {
-          p.S_out[o] = (float)gw[t] + tot[t][k];
-          p.W1_out[o] = W1;
-          p.W2_out[o] = W2;
+        for (int k = 0; k < G; ++k) {
+          const int sk = s0 + k;
+          float dv1 = 0.f, dv2 = 0.f;
+          if (touched & (1u << t)) {
+            const float2 dv = dvp[k];
+            dv1 = dv.x;
+            dv2 = dv.y;
+          }
+          const float W1 = (float)(w1[t] + (double)dv1);
+          const float W2 = (float)(w2[t] + (double)dv2);
+          const float num = (float)(base_num - (double)dv1) + tot[t][k];
+          const int64_t o = (int64_t)sk * p.Bpad + b;
+          ev.psi[o] = W2 > 0.f ? num * rsqrtf(W2) : -INFINITY;
+          if (ev.S_out) {
+            ev.S_out[o] = (float)gw[t] + tot[t][k];
+            ev.W1_out[o] = W1;
+            ev.W2_out[o] = W2;
+          }
         }
       }
     }
@@ -425,18 +447,91 @@ __global__ void __launch_bounds__(kThreads, 1) group_kernel(GroupParams p) {
 
 size_t group_smem_bytes(int n_det) { return PersistLayout(n_det).total; }
 
-cudaError_t launch_anchors(const GroupParams& p, double* anchors, cudaStream_t st) {
+cudaError_t group_grid(int* grid) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  *grid = sms;
+  return cudaSuccess;
+}
+
+void schedule_items(const std::vector<int4>& items, const std::vector<int64_t>& cost, int grid,
+                    std::vector<int4>& out, std::vector<int>& cta_items) {
+  const size_t n = items.size();
+  std::vector<size_t> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
+  // min-heap of (load, cta)
+  using Slot = std::pair<int64_t, int>;
+  std::priority_queue<Slot, std::vector<Slot>, std::greater<Slot>> heap;
+  for (int i = 0; i < grid; ++i) heap.push({0, i});
+  std::vector<std::vector<size_t>> per(grid);
+  for (size_t i : order) {
+    Slot s = heap.top();
+    heap.pop();
+    per[s.second].push_back(i);
+    s.first += cost[i];
+    heap.push(s);
+  }
+  out.clear();
+  cta_items.assign(grid + 1, 0);
+  for (int c = 0; c < grid; ++c) {
+    for (size_t i : per[c]) out.push_back(items[i]);
+    cta_items[c + 1] = (int)out.size();
+  }
+}
+
+int series_terms_for(const double* t_mid, int64_t n_seg, double T0, int tile, double tau_min,
+                     double r_max) {
+  double dmax = 0;
+  for (int64_t j0 = 0; j0 < n_seg; j0 += tile) {
+    const int64_t jn = std::min<int64_t>(tile, n_seg - j0);
+    const double ta = std::max(t_mid[j0 + (jn - 1) / 2], T0);
+    for (int64_t j = j0; j < j0 + jn; ++j) {
+      if (t_mid[j] < T0) continue;
+      dmax = std::max(dmax, std::fabs(t_mid[j] - ta) / (tau_min + (ta - T0)));
+    }
+  }
+  if (dmax >= 0.5) return 0;
+  double bound = 1.0, pw = 1.0;
+  for (int k = 0; k <= kMaxSeriesTerms; ++k) {
+    if (bound * pw < std::ldexp(1.0, -56)) return std::max(k, 1);
+    bound *= (r_max + k) / (k + 1);
+    pw *= dmax;
+  }
+  return 0;
+}
+size_t group_dev_elems(int grid) { return (size_t)grid * kPT * kSkyPad; }
+
+cudaError_t launch_anchors(const AnchorParams& p, cudaStream_t st) {
   const int64_t total = (int64_t)p.Bpad * p.n_tiles;
   if (total == 0) return cudaSuccess;
   const int threads = 128;
-  anchor_kernel<<<(unsigned)((total + threads - 1) / threads), threads, 0, st>>>(p, anchors);
+  anchor_kernel<<<(unsigned)((total + threads - 1) / threads), threads, 0, st>>>(p);
   return cudaGetLastError();
+}
+
+// The dynamic shared-memory limit of each variant is raised once per device
+// (again when a variant shared by several detector counts needs more).
+template <typename R, bool REC, bool WT, int DT>
+cudaError_t set_smem_t(size_t smem) {
+  constexpr int kDevices = 64;
+  static size_t done[kDevices] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < kDevices && done[dev] >= smem) return cudaSuccess;
+  e = cudaFuncSetAttribute(group_kernel<R, REC, WT, DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+  if (e == cudaSuccess && dev >= 0 && dev < kDevices) done[dev] = smem;
+  return e;
 }
 
 template <typename R, bool REC, bool WT, int DT>
 cudaError_t launch_group_t(const GroupParams& p, int grid, size_t smem, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(group_kernel<R, REC, WT, DT>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = set_smem_t<R, REC, WT, DT>(smem);
   if (e != cudaSuccess) return e;
   group_kernel<R, REC, WT, DT><<<grid, kThreads, smem, st>>>(p);
   return cudaGetLastError();
@@ -454,17 +549,23 @@ cudaError_t launch_group_r(const GroupParams& p, bool record, bool weighted, int
   return launch_group_t<R, false, false, 2>(p, grid, smem, st);
 }
 
+template <typename R>
+cudaError_t prepare_r(int n_det, bool weighted) {
+  const size_t smem = PersistLayout(n_det).total;
+  if (weighted) return n_det == 1 ? set_smem_t<R, false, true, 1>(smem) : set_smem_t<R, false, true, 2>(smem);
+  return n_det == 1 ? set_smem_t<R, false, false, 1>(smem) : set_smem_t<R, false, false, 2>(smem);
+}
+
+cudaError_t group_prepare(int n_det, bool half, bool weighted) {
+  if (n_det < 1 || n_det > kMaxStageDet) return cudaErrorInvalidValue;
+  return half ? prepare_r<__half>(n_det, weighted) : prepare_r<float>(n_det, weighted);
+}
+
 // Needs 1 <= p.n_det <= kMaxStageDet, and the anchors of launch_anchors when p.nterms > 0.
-cudaError_t launch_group(const GroupParams& p, bool half, bool record, bool weighted,
+cudaError_t launch_group(const GroupParams& p, int grid, bool half, bool record, bool weighted,
                          cudaStream_t st) {
   if (p.n_det < 1 || p.n_det > kMaxStageDet) return cudaErrorInvalidValue;
-  if (p.n_items <= 0) return cudaSuccess;
-  int dev = 0, sms = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e != cudaSuccess) return e;
-  const int grid = p.n_items < sms ? p.n_items : sms;
+  if (grid <= 0) return cudaSuccess;
   const size_t smem = PersistLayout(p.n_det).total;
   return half ? launch_group_r<__half>(p, record, weighted, grid, smem, st)
               : launch_group_r<float>(p, record, weighted, grid, smem, st);

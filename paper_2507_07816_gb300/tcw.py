@@ -20,7 +20,8 @@ OK = 0
 HOST, DEVICE = 0, 1
 F32, F16 = 0, 1
 KERNEL_AUTO, KERNEL_GROUP, KERNEL_LOOKUP = 0, 1, 2
-OPT_KERNEL, OPT_KEEP_STATS, OPT_TILE_SEGMENTS = 1, 2, 3
+OPT_KERNEL, OPT_KEEP_STATS, OPT_TILE_SEGMENTS, OPT_BANK_CHUNK = 1, 2, 3, 4
+OPT_AUTOTUNE, OPT_BATCH_MEMORY = 5, 6
 
 _lock = threading.Lock()
 _lib = None
@@ -36,6 +37,23 @@ class _Info(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int), ("launches", ctypes.c_int), ("lookups", ctypes.c_int64),
                 ("general_path_lanes", ctypes.c_int64), ("doppler_bins_max", ctypes.c_double),
                 ("quantum", ctypes.c_double), ("search_ms", ctypes.c_float)]
+
+
+class _Event(ctypes.Structure):
+    _fields_ = [("rho", ctypes.c_void_p), ("t_mid", ctypes.c_void_p), ("weights", ctypes.c_void_p),
+                ("velocity", ctypes.c_void_p), ("nhat", ctypes.c_void_p), ("n_seg", ctypes.c_int64),
+                ("n_sky", ctypes.c_int64), ("T0", ctypes.c_double)]
+
+
+class _BatchInfo(ctypes.Structure):
+    _fields_ = [("n_events", ctypes.c_int), ("waves", ctypes.c_int), ("bank_chunk", ctypes.c_int),
+                ("tile_segments", ctypes.c_int), ("autotuned", ctypes.c_int),
+                ("n_candidates", ctypes.c_int), ("n_items", ctypes.c_int),
+                ("graph_kernels", ctypes.c_int), ("total_sky", ctypes.c_int64),
+                ("lookups", ctypes.c_int64), ("general_path_lanes", ctypes.c_int64),
+                ("tune_ms", ctypes.c_double), ("best_rate", ctypes.c_double),
+                ("default_rate", ctypes.c_double), ("quantum", ctypes.c_double),
+                ("search_ms", ctypes.c_float)]
 
 
 def library_path() -> str:
@@ -67,6 +85,10 @@ def load_library(build_if_missing: bool = True):
             "tcw_get_statistics": [p, p, p, p, p, i],
             "tcw_track_bins": [p, p, i],
             "tcw_get_info": [p, ctypes.POINTER(_Info)],
+            "tcw_load_events": [p, i, i64, i, d, d, ctypes.POINTER(_Event), i, i],
+            "tcw_search_batched": [p, i, p, p, i],
+            "tcw_get_batch_info": [p, ctypes.POINTER(_BatchInfo)],
+            "tcw_get_tune_results": [p, i, p, p, p, p],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -230,3 +252,80 @@ class Search:
         self.load_velocity(prob.velocity)
         self.define_bank(prob.bank.f0, prob.bank.tau, prob.bank.n, prob.T0)
         self.define_sky(prob.nhat)
+
+    # ---------------------------------------------------------------- batched
+    def load_events(self, events, f_min, df):
+        """Load a batch of events for ``search_batched``.
+
+        ``events``: sequence of objects with ``rho`` [D][n_seg][n_bin] (float32
+        or float16; all events the same dtype, D and n_bin), ``t_mid``,
+        ``weights`` (or None), ``velocity`` [D][n_seg][3], ``nhat`` [n_sky][3]
+        and ``T0``.  All arrays on the host (numpy) or all on the device (CUDA
+        torch tensors)."""
+        evs = list(events)
+        if not evs:
+            raise ValueError("no events")
+        dt = np.float16 if str(getattr(evs[0].rho, "dtype", "")).endswith("float16") else np.float32
+        D, _, Nbin = evs[0].rho.shape
+        arr = (_Event * len(evs))()
+        keep = []
+        flags = set()
+        for i, e in enumerate(evs):
+            if e.rho.shape[0] != D or e.rho.shape[2] != Nbin:
+                raise ValueError("events differ in n_det or n_bin")
+            n_seg, n_sky = int(e.rho.shape[1]), int(e.nhat.shape[0])
+            small = [e.t_mid, e.weights, e.velocity, e.nhat]
+            if _is_torch(e.rho) and e.rho.is_cuda:
+                # a device map takes its small arrays along to the same device
+                import torch
+                small = [None if a is None or (_is_torch(a) and a.is_cuda) else
+                         torch.as_tensor(np.ascontiguousarray(a, dtype=t), device=e.rho.device)
+                         for a, t in zip(small, (np.float64, np.float32, np.float64, np.float64))]
+                small = [a if a is not None else b for a, b in
+                         zip(small, [e.t_mid, e.weights, e.velocity, e.nhat])]
+            parts = [_arg(e.rho, dt), _arg(small[0], np.float64),
+                     _arg(small[1], np.float32), _arg(small[2], np.float64),
+                     _arg(small[3], np.float64)]
+            for (ptr, fl, k), a in zip(parts, (e.rho, *small)):
+                if a is not None:
+                    flags.add(fl)
+                keep.append(k)
+            arr[i] = _Event(parts[0][0], parts[1][0], parts[2][0], parts[3][0], parts[4][0], n_seg,
+                            n_sky, float(e.T0))
+        if len(flags) != 1:
+            raise ValueError("event arrays must all be on the host or all on the device")
+        self._check(self._lib.tcw_load_events(self._h, int(D), int(Nbin), F16 if dt == np.float16 else F32,
+                                              float(f_min), float(df), arr, len(evs), flags.pop()))
+        self.batch_sky = [int(e.nhat.shape[0]) for e in evs]
+
+    def search_batched(self, k, psi_out=None, idx_out=None):
+        """Top-k per sky of every event: (psi [total_sky][k], idx [total_sky][k]),
+        events in order, each event's skies in the caller's order."""
+        total = sum(self.batch_sky)
+        if psi_out is None:
+            psi_out = np.empty((total, k), np.float32)
+            idx_out = np.empty((total, k), np.int64)
+        pp, pf, _ = _arg(psi_out, np.float32)
+        ip, iff, _ = _arg(idx_out, np.int64)
+        if pf != iff:
+            raise ValueError("outputs must both be host or both device")
+        if pf == HOST and (not isinstance(psi_out, np.ndarray) or not psi_out.flags.c_contiguous):
+            raise TypeError("host outputs must be C-contiguous numpy arrays")
+        self._check(self._lib.tcw_search_batched(self._h, int(k), pp, ip, pf))
+        return psi_out, idx_out
+
+    def batch_info(self) -> dict:
+        i = _BatchInfo()
+        self._check(self._lib.tcw_get_batch_info(self._h, ctypes.byref(i)))
+        return {name: getattr(i, name) for name, _ in _BatchInfo._fields_}
+
+    def tune_results(self):
+        """Autotuner measurements: list of (bank_chunk, tile_segments, sums/s)."""
+        n = ctypes.c_int()
+        self._check(self._lib.tcw_get_tune_results(self._h, 0, None, None, None, ctypes.byref(n)))
+        m = n.value
+        bc = (ctypes.c_int * max(m, 1))()
+        ts = (ctypes.c_int * max(m, 1))()
+        rt = (ctypes.c_double * max(m, 1))()
+        self._check(self._lib.tcw_get_tune_results(self._h, m, bc, ts, rt, ctypes.byref(n)))
+        return [(bc[i], ts[i], rt[i]) for i in range(m)]

@@ -215,7 +215,17 @@ def inject(r: np.random.Generator, rho, injection: Injection, detectors, t, T0,
     mu_j is proportional to (f_j/f0)^2 (h0 ~ f^2, Eq. 3) and scaled so that the
     expected excess of the weighted sum over its standard deviation is `snr`.
     """
-    D, n_seg, n_bin = rho.shape
+    dd, jj, kk, val = injection_values(r, rho.shape, injection, detectors, t, T0, f_min, df, weights)
+    if dd.size:
+        rho[dd, jj, kk] = val.astype(rho.dtype)
+    return injection.bins
+
+
+def injection_values(r: np.random.Generator, shape, injection: Injection, detectors, t, T0,
+                     f_min, df, weights=None):
+    """The (detector, segment, bin) cells of one injected signal and their new
+    powers ((x + mu)^2 + y^2)/2, x, y ~ N(0, 1); sets injection.bins."""
+    D, n_seg, n_bin = shape
     f_src = spindown_frequency(injection.f0, injection.tau, injection.n, T0, t)
     bins = np.full((D, n_seg), -1, np.int64)
     fdet = np.full((D, n_seg), np.nan)
@@ -224,20 +234,19 @@ def inject(r: np.random.Generator, rho, injection: Injection, detectors, t, T0,
         fdet[d] = fd
         bins[d] = signal_bins(fd, f_min, df, n_bin)
     ok = bins >= 0
+    injection.bins = bins
     if not ok.any():
-        injection.bins = bins
-        return bins
+        e = np.zeros(0, np.int64)
+        return e, e, e, np.zeros(0)
     w = np.ones((D, n_seg)) if weights is None else np.asarray(weights, np.float64)
-    shape = np.where(ok, (fdet / injection.f0) ** 4, 0.0)    # lambda_j ~ f^4
-    lam_unit = (w * shape).sum() / math.sqrt((w * w * ok).sum())
+    lam_shape = np.where(ok, (fdet / injection.f0) ** 4, 0.0)    # lambda_j ~ f^4
+    lam_unit = (w * lam_shape).sum() / math.sqrt((w * w * ok).sum())
     lam0 = injection.snr / lam_unit
-    mu = np.sqrt(2.0 * lam0 * shape)
+    mu = np.sqrt(2.0 * lam0 * lam_shape)
     dd, jj = np.nonzero(ok)
     x = r.normal(size=dd.shape[0])
     y = r.normal(size=dd.shape[0])
-    rho[dd, jj, bins[dd, jj]] = (((x + mu[dd, jj]) ** 2 + y ** 2) / 2.0).astype(rho.dtype)
-    injection.bins = bins
-    return bins
+    return dd, jj, bins[dd, jj], ((x + mu[dd, jj]) ** 2 + y ** 2) / 2.0
 
 
 # --------------------------------------------------------------------------
@@ -322,3 +331,53 @@ def config_full(seed=20250712, n_det=2, n_seg=10000, n_bin=10000, t_sft=4.0,
         rho = rho.astype(dtype)
     return Problem(rho, t, w, vel, f_min, df, T0, nhat, bank, injections, dets,
                    name=f"plain-{n_det}det-{n_seg}x{n_bin}-random{n_tmpl}-sky{n_sky}")
+
+
+def config_batched(seed=20250714, n_events=64, n_seg_range=(2000, 20000), n_bin=10000,
+                   sky_range=(256, 4096), n_tmpl=20000, n_det=1, t_sft=4.0, f_min=500.0,
+                   dtype=np.float16, snr=8.0, weights=False, device=None):
+    """Batched workload: events with uneven spectrograms, each with its own
+    epoch, detector(s), signal start T0 (uniform in the first 10 % of its
+    span), sky list and one injected track, all against one random bank.
+
+    Returns (events, bank): events are Problems sharing `bank`.  With
+    `device` (a torch CUDA device) the noise is drawn on that device by a
+    seeded torch generator and rho is a CUDA tensor; otherwise numpy arrays.
+    """
+    r = rng(seed)
+    df = 1.0 / t_sft
+    bank = random_bank(r, n_tmpl, f0_range=(f_min, f_min + n_bin * df))
+    events = []
+    for i in range(n_events):
+        n_seg = int(r.integers(n_seg_range[0], n_seg_range[1] + 1))
+        t = segment_times(n_seg, t_sft, t_start=GPS_EPOCH0 + float(r.uniform(0.0, 3.0e7)))
+        T0 = float(t[0] - 0.5 * t_sft + r.uniform(0.0, 0.1) * n_seg * t_sft)
+        dets = random_detectors(r, n_det)
+        vel = np.stack([d.velocity(t) for d in dets])
+        n_sky = int(r.integers(sky_range[0], sky_range[1] + 1))
+        nhat = random_sky(r, n_sky)
+        w = uniform_weights(r, n_det, n_seg) if weights else None
+        b = int(r.integers(0, n_tmpl))
+        inj = Injection(float(bank.f0[b]), float(bank.tau[b]), float(bank.n[b]),
+                        nhat[int(r.integers(0, n_sky))], snr)
+        inj.template = b
+        shape = (n_det, n_seg, n_bin)
+        if device is None:
+            rho = exponential_noise(r, shape)
+            inject(r, rho, inj, dets, t, T0, f_min, df, w)
+            if dtype != np.float32:
+                rho = rho.astype(dtype)
+        else:
+            import torch
+            g = torch.Generator(device=device)
+            g.manual_seed(int(seed) * 1000 + i)
+            rho = torch.empty(shape, dtype=torch.float32, device=device).exponential_(generator=g)
+            dd, jj, kk, val = injection_values(r, shape, inj, dets, t, T0, f_min, df, w)
+            if dd.size:
+                idx = tuple(torch.as_tensor(a, device=device) for a in (dd, jj, kk))
+                rho[idx] = torch.as_tensor(val, dtype=torch.float32, device=device)
+            if dtype == np.float16:
+                rho = rho.half()
+        events.append(Problem(rho, t, w, vel, f_min, df, T0, nhat, bank, [inj], dets,
+                              name=f"event{i}-{n_det}det-{n_seg}x{n_bin}-sky{n_sky}"))
+    return events, bank
