@@ -274,6 +274,87 @@ tcw_status tcw_get_batch_info(tcw_ctx *ctx, tcw_batch_info *info);
 tcw_status tcw_get_tune_results(tcw_ctx *ctx, int max_results, int *bank_chunk,
                                 int *tile_segments, double *sums_per_s, int *n_results);
 
+/*
+ * Learned sky triage.  The paper has no learned component: the triage is an
+ * addition that ranks sky patches so that the exhaustive search (Sec. 2,
+ * Eq. 4) runs on the best-ranked ones only.
+ *
+ * A patch is a run of patch_size consecutive skies in the search's
+ * Doppler-sorted order (v_0(t_m).nhat, t_m = the middle segment of detector
+ * 0, ties by caller index); its representative is its middle sky.  The
+ * coarse pass computes Psi of every template at every representative, and
+ * the features of a patch are log(1 + count) over a 128-bin histogram of
+ * those Psi on [psi_lo, psi_hi) (lower values and -inf in bin 0, higher ones
+ * in bin 127).
+ *
+ * The network is an MLP 128 -> 256 -> 256 -> 1 with ReLU after both hidden
+ * layers: y = relu(relu(X W1 + b1) W2 + b2) w3 + b3.  Its parameters are one
+ * packed float32 vector theta[TCW_MLP_PARAMS]:
+ *   W1 [128][256] | b1 [256] | W2 [256][256] | b2 [256] | w3 [256] | b3
+ * and the forward pass reads the weights as bfloat16, wbf[TCW_MLP_WEIGHTS]:
+ *   W1 | W2 | w3 (same element order), with fp32 accumulation.
+ * The tcw_mlp_* calls take DEVICE pointers on the current device, queue work
+ * on `stream` (NULL = legacy default stream) and return without waiting.
+ */
+#define TCW_MLP_PARAMS 99073
+#define TCW_MLP_WEIGHTS 98560
+
+/* wbf = bfloat16(theta weights), round to nearest even. */
+tcw_status tcw_mlp_pack(const float *theta, uint16_t *wbf, void *stream);
+/* X [n][128] -> H1 [n][256], H2 [n][256] (post-ReLU), y [n]. */
+tcw_status tcw_mlp_forward(const uint16_t *wbf, const float *theta, const float *X, int64_t n,
+                           float *H1, float *H2, float *y, void *stream);
+/* Gradient of a loss with dL/dy = dy into grad[TCW_MLP_PARAMS] (packed like
+ * theta; taken at the bfloat16 weights the forward pass used).
+ * work: 2 * n * 256 floats of scratch. */
+tcw_status tcw_mlp_backward(const uint16_t *wbf, const float *X, int64_t n, const float *H1,
+                            const float *H2, const float *dy, float *grad, float *work,
+                            void *stream);
+/* Mean binary cross-entropy with logits: loss[0] = mean(pw*l*softplus(-y) +
+ * (1-l)*softplus(y)), dy = its derivative in y. */
+tcw_status tcw_mlp_bce(const float *y, const float *label, int64_t n, float pos_weight,
+                       float *loss, float *dy, void *stream);
+/* One Adam step (step counts from 1, bias-corrected) on theta with moments
+ * m, v; refreshes wbf from the new theta. */
+tcw_status tcw_mlp_adam(float *theta, float *m, float *v, const float *grad, int64_t step,
+                        float lr, float beta1, float beta2, float eps, uint16_t *wbf,
+                        void *stream);
+
+/* Coarse pass of the loaded search: feat_out [n_patch][128] float32,
+ * n_patch = ceil(n_sky / patch_size); psi_out [n_patch][n_tmpl] (caller
+ * template order) may be NULL.  Errors: STATE, INVALID_ARGUMENT (patch_size
+ * < 1, psi_hi <= psi_lo), UNSUPPORTED (more than 8 detectors), CUDA. */
+tcw_status tcw_triage_features(tcw_ctx *ctx, int patch_size, float psi_lo, float psi_hi,
+                               float *feat_out, float *psi_out, int out_flags);
+
+/* Triaged search: coarse pass, network score per patch, the ceil(frac *
+ * n_patch) best patches searched exhaustively as tcw_search does.
+ * psi_out/idx_out [n_sky][k] as tcw_search for searched skies; rows of
+ * skipped skies hold -inf and -1.  searched_out [n_sky] (may be NULL): 1 for
+ * searched skies.  wbf and theta are device pointers.
+ * Errors: as tcw_search and tcw_triage_features, INVALID_ARGUMENT (frac not
+ * in (0, 1]). */
+tcw_status tcw_search_triaged(tcw_ctx *ctx, const uint16_t *wbf, const float *theta,
+                              int patch_size, float psi_lo, float psi_hi, float frac, int k,
+                              float *psi_out, int64_t *idx_out, int32_t *searched_out,
+                              int out_flags);
+
+typedef struct {
+    int n_patch;
+    int n_selected;             /* patches searched exhaustively */
+    int64_t skies_searched;
+    int64_t lookups_full;       /* sums of the exhaustive search of every sky */
+    int64_t lookups_coarse;     /* sums of the coarse pass */
+    int64_t lookups_searched;   /* sums of the exhaustive search of the selected skies */
+    float coarse_ms, mlp_ms, search_ms;  /* device times */
+} tcw_triage_info;
+
+tcw_status tcw_get_triage_info(tcw_ctx *ctx, tcw_triage_info *info);
+
+/* The search's Doppler-sorted sky order: order_out[i] = caller index of the
+ * i-th sky (host memory, n_sky entries).  Errors: STATE, INVALID_ARGUMENT. */
+tcw_status tcw_sky_order(tcw_ctx *ctx, int32_t *order_out);
+
 /* Information about the last search. */
 typedef struct {
     int kernel;                 /* TCW_KERNEL_GROUP or TCW_KERNEL_LOOKUP */

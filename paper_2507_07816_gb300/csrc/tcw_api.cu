@@ -108,6 +108,7 @@ tcw_status prepare_sky(tcw_ctx* c) {
     for (int a = 0; a < 3; ++a) ns[(size_t)i * 3 + a] = c->h_nhat[(size_t)src * 3 + a];
   }
   for (int64_t i = 0; i < S; ++i) pos[perm[i]] = (int32_t)i;
+  c->h_sky_perm = perm;
   TCW_CUDA(c, upload(c, c->nhat_sorted, ns.data(), ns.size() * sizeof(double), TCW_HOST), "sky upload");
   TCW_CUDA(c, upload(c, c->sky_perm, perm.data(), perm.size() * sizeof(int32_t), TCW_HOST), "sky upload");
   TCW_CUDA(c, upload(c, c->sky_pos, pos.data(), pos.size() * sizeof(int32_t), TCW_HOST), "sky upload");
@@ -321,6 +322,86 @@ tcw_status finish(tcw_ctx* c) {
   return TCW_OK;
 }
 
+// Coarse pass of the triage on the loaded search: features in c->tri_feat
+// ([P][128]) and, when keep_psi, Psi in c->tri_psi ([P][Bpad], sorted bank).
+tcw_status run_coarse(tcw_ctx* c, int patch_size, float lo, float hi, bool keep_psi, int* P_out) {
+  if (!c->have_spec || !c->have_vel || !c->have_bank || !c->have_sky)
+    return fail(c, TCW_ERR_STATE, "inputs not loaded");
+  if (c->D > 8) return fail(c, TCW_ERR_UNSUPPORTED, "coarse pass handles at most 8 detectors");
+  tcw_status st = prepare_sky(c);
+  if (st != TCW_OK) return st;
+  const int P = (int)((c->S + patch_size - 1) / patch_size);
+  const int tile = 64;
+  const int n_tiles = (int)((c->Nseg + tile - 1) / tile);
+  double tau_min = INFINITY, r_max = 0;
+  for (size_t b = 0; b < c->h_tau.size(); ++b) {
+    tau_min = std::min(tau_min, c->h_tau[b]);
+    r_max = std::max(r_max, 1.0 / (c->h_n[b] - 1.0));
+  }
+  const int nterms = series_terms_for(c->h_t.data(), c->Nseg, c->T0, tile, tau_min, r_max);
+  TCW_CUDA(c, c->tri_dop.ensure((size_t)c->D * c->Nseg * P * sizeof(float)), "triage buffers");
+  TCW_CUDA(c, c->tri_hist.ensure((size_t)P * kTriageBins * sizeof(unsigned)), "triage buffers");
+  TCW_CUDA(c, c->tri_feat.ensure((size_t)P * kTriageBins * sizeof(float)), "triage buffers");
+  if (keep_psi) TCW_CUDA(c, c->tri_psi.ensure((size_t)P * c->Bpad * sizeof(float)), "triage buffers");
+  if (nterms > 0) TCW_CUDA(c, c->tri_anchor.ensure((size_t)c->Bpad * n_tiles * 2 * sizeof(double)), "triage buffers");
+  TCW_CUDA(c, cudaMemsetAsync(c->tri_hist.p, 0, (size_t)P * kTriageBins * sizeof(unsigned), c->stream), "triage");
+  PatchDopplerParams dp{};
+  dp.vel = c->vel.as<double>();
+  dp.nhat = c->nhat_sorted.as<double>();
+  dp.n_det = c->D;
+  dp.n_seg = (int)c->Nseg;
+  dp.S = (int)c->S;
+  dp.patch_size = patch_size;
+  dp.P = P;
+  dp.dop = c->tri_dop.as<float>();
+  TCW_CUDA(c, launch_patch_doppler(dp, c->stream), "patch_doppler_kernel launch");
+  if (nterms > 0) {
+    AnchorParams ap{};
+    ap.t_mid = c->t_mid.as<double>();
+    ap.f0 = c->f0.as<double>();
+    ap.tau = c->tau.as<double>();
+    ap.nbr = c->nbr.as<double>();
+    ap.T0 = c->T0;
+    ap.n_seg = (int)c->Nseg;
+    ap.n_tiles = n_tiles;
+    ap.tile_shift = 6;
+    ap.Bpad = c->Bpad;
+    ap.anchors = c->tri_anchor.as<double>();
+    TCW_CUDA(c, launch_anchors(ap, c->stream), "anchor_kernel launch");
+  }
+  CoarseParams cp{};
+  cp.rho = c->rho.p;
+  cp.n_bin = c->Nbin;
+  cp.n_det = c->D;
+  cp.n_seg = (int)c->Nseg;
+  cp.weights = c->weights.as<float>();
+  cp.t_mid = c->t_mid.as<double>();
+  cp.T0 = c->T0;
+  cp.f_min = c->f_min;
+  cp.df = c->df;
+  cp.dop = dp.dop;
+  cp.P = P;
+  cp.f0 = c->f0.as<double>();
+  cp.tau = c->tau.as<double>();
+  cp.nbr = c->nbr.as<double>();
+  cp.B = (int)c->B;
+  cp.Bpad = c->Bpad;
+  cp.anchors = nterms > 0 ? c->tri_anchor.as<double>() : nullptr;
+  cp.n_tiles = n_tiles;
+  cp.nterms = nterms;
+  cp.lo = lo;
+  cp.hi = hi;
+  cp.psi = keep_psi ? c->tri_psi.as<float>() : nullptr;
+  cp.hist = c->tri_hist.as<unsigned>();
+  cp.feat = c->tri_feat.as<float>();
+  TCW_CUDA(c, launch_coarse(cp, c->dtype == TCW_F16, c->stream), "coarse_kernel launch");
+  c->tri_info.n_patch = P;
+  c->tri_info.lookups_coarse = (int64_t)P * c->B * c->D * c->Nseg;
+  c->tri_info.lookups_full = c->S * c->B * c->D * c->Nseg;
+  *P_out = P;
+  return TCW_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -378,7 +459,9 @@ tcw_status tcw_destroy(tcw_ctx* c) {
   DevBuf* bufs[] = {&c->rho, &c->t_mid, &c->weights, &c->vel, &c->f0, &c->tau, &c->nbr,
                     &c->bank_perm, &c->bank_pos, &c->nhat_sorted, &c->sky_perm, &c->sky_pos,
                     &c->dq, &c->anchors, &c->psi, &c->st_S, &c->st_W1, &c->st_W2, &c->dev,
-                    &c->flags, &c->stage_f, &c->stage_i, &c->evtab, &c->items};
+                    &c->flags, &c->stage_f, &c->stage_i, &c->evtab, &c->items, &c->tri_dop,
+                    &c->tri_hist, &c->tri_feat, &c->tri_psi, &c->tri_anchor, &c->tri_h1, &c->tri_h2,
+                    &c->tri_score, &c->tri_sel};
   for (DevBuf* b : bufs) b->release();
   batch_free(c);
   if (c->ev0) cudaEventDestroy(c->ev0);
@@ -523,6 +606,7 @@ tcw_status tcw_define_bank(tcw_ctx* c, int64_t n_tmpl, const double* f0, const d
     permp[i] = src;
   }
   for (int64_t i = 0; i < n_tmpl; ++i) pos[perm[i]] = (int32_t)i;
+  c->h_bank_perm = permp;
   TCW_CUDA(c, upload(c, c->f0, sf.data(), Bpad * sizeof(double), TCW_HOST), "bank upload");
   TCW_CUDA(c, upload(c, c->tau, st.data(), Bpad * sizeof(double), TCW_HOST), "bank upload");
   TCW_CUDA(c, upload(c, c->nbr, sn.data(), Bpad * sizeof(double), TCW_HOST), "bank upload");
@@ -649,6 +733,144 @@ tcw_status tcw_track_bins(tcw_ctx* c, int32_t* bins_out, int out_flags) {
 tcw_status tcw_get_info(tcw_ctx* c, tcw_info* info) {
   if (!c || !info) return TCW_ERR_INVALID_ARGUMENT;
   *info = c->info;
+  return TCW_OK;
+}
+
+tcw_status tcw_triage_features(tcw_ctx* c, int patch_size, float psi_lo, float psi_hi, float* feat_out,
+                               float* psi_out, int out_flags) {
+  if (!c) return TCW_ERR_INVALID_ARGUMENT;
+  if (!feat_out) return fail(c, TCW_ERR_INVALID_ARGUMENT, "null output");
+  if (patch_size < 1 || !(psi_hi > psi_lo) || !std::isfinite(psi_lo) || !std::isfinite(psi_hi))
+    return fail(c, TCW_ERR_INVALID_ARGUMENT, "bad patch size or histogram range");
+  if (out_flags != TCW_HOST && out_flags != TCW_DEVICE) return fail(c, TCW_ERR_INVALID_ARGUMENT, "bad flags");
+  cudaSetDevice(c->device);
+  int P = 0;
+  tcw_status st = run_coarse(c, patch_size, psi_lo, psi_hi, psi_out != nullptr, &P);
+  if (st != TCW_OK) return st;
+  const cudaMemcpyKind kind = out_flags == TCW_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  TCW_CUDA(c, cudaMemcpyAsync(feat_out, c->tri_feat.p, (size_t)P * kTriageBins * sizeof(float), kind, c->stream),
+           "copy out");
+  if (psi_out) {
+    std::vector<float> hp((size_t)P * c->Bpad), out((size_t)P * c->B);
+    TCW_CUDA(c, cudaMemcpyAsync(hp.data(), c->tri_psi.p, hp.size() * sizeof(float), cudaMemcpyDeviceToHost,
+                                c->stream), "copy out");
+    TCW_CUDA(c, cudaStreamSynchronize(c->stream), "coarse pass");
+    for (int p = 0; p < P; ++p)
+      for (int64_t b = 0; b < c->B; ++b) out[(size_t)p * c->B + c->h_bank_perm[b]] = hp[(size_t)p * c->Bpad + b];
+    TCW_CUDA(c, cudaMemcpyAsync(psi_out, out.data(), out.size() * sizeof(float),
+                                out_flags == TCW_HOST ? cudaMemcpyHostToHost : cudaMemcpyHostToDevice, c->stream),
+             "copy out");
+  }
+  TCW_CUDA(c, cudaStreamSynchronize(c->stream), "coarse pass");
+  return TCW_OK;
+}
+
+tcw_status tcw_search_triaged(tcw_ctx* c, const uint16_t* wbf, const float* theta, int patch_size, float psi_lo,
+                              float psi_hi, float frac, int k, float* psi_out, int64_t* idx_out,
+                              int32_t* searched_out, int out_flags) {
+  if (!c) return TCW_ERR_INVALID_ARGUMENT;
+  if (!wbf || !theta || !psi_out || !idx_out) return fail(c, TCW_ERR_INVALID_ARGUMENT, "null pointer");
+  if (patch_size < 1 || !(psi_hi > psi_lo) || !std::isfinite(psi_lo) || !std::isfinite(psi_hi))
+    return fail(c, TCW_ERR_INVALID_ARGUMENT, "bad patch size or histogram range");
+  if (!(frac > 0.f && frac <= 1.f)) return fail(c, TCW_ERR_INVALID_ARGUMENT, "frac must be in (0, 1]");
+  if (out_flags != TCW_HOST && out_flags != TCW_DEVICE) return fail(c, TCW_ERR_INVALID_ARGUMENT, "bad flags");
+  if (!c->have_bank) return fail(c, TCW_ERR_STATE, "no template bank defined");
+  if (k < 1 || k > 1024 || (int64_t)k > c->B)
+    return fail(c, TCW_ERR_INVALID_ARGUMENT, "k must be in [1, min(n_tmpl, 1024)]");
+  cudaSetDevice(c->device);
+  cudaEvent_t e0, e1, e2;
+  TCW_CUDA(c, cudaEventCreate(&e0), "event");
+  TCW_CUDA(c, cudaEventCreate(&e1), "event");
+  TCW_CUDA(c, cudaEventCreate(&e2), "event");
+  struct Ev {
+    cudaEvent_t a, b, d;
+    ~Ev() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+      cudaEventDestroy(d);
+    }
+  } guard{e0, e1, e2};
+  int P = 0;
+  TCW_CUDA(c, cudaEventRecord(e0, c->stream), "event");
+  tcw_status st = run_coarse(c, patch_size, psi_lo, psi_hi, false, &P);
+  if (st != TCW_OK) return st;
+  TCW_CUDA(c, cudaEventRecord(e1, c->stream), "event");
+  TCW_CUDA(c, c->tri_h1.ensure((size_t)P * kMlpH * sizeof(float)), "triage buffers");
+  TCW_CUDA(c, c->tri_h2.ensure((size_t)P * kMlpH * sizeof(float)), "triage buffers");
+  TCW_CUDA(c, c->tri_score.ensure((size_t)P * sizeof(float)), "triage buffers");
+  TCW_CUDA(c, c->tri_sel.ensure((size_t)P * sizeof(int)), "triage buffers");
+  TCW_CUDA(c, mlp_forward(reinterpret_cast<const __nv_bfloat16*>(wbf), theta, c->tri_feat.as<float>(), P,
+                          c->tri_h1.as<float>(), c->tri_h2.as<float>(), c->tri_score.as<float>(), c->stream),
+           "mlp forward");
+  const int m = std::max(1, std::min(P, (int)std::ceil((double)frac * P - 1e-9)));
+  TCW_CUDA(c, launch_rank(c->tri_score.as<float>(), P, m, c->tri_sel.as<int>(), c->stream), "rank");
+  TCW_CUDA(c, cudaEventRecord(e2, c->stream), "event");
+  std::vector<int> sel(P);
+  TCW_CUDA(c, cudaMemcpyAsync(sel.data(), c->tri_sel.p, P * sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+           "selection");
+  TCW_CUDA(c, cudaStreamSynchronize(c->stream), "selection");
+  float coarse_ms = 0, mlp_ms = 0;
+  cudaEventElapsedTime(&coarse_ms, e0, e1);
+  cudaEventElapsedTime(&mlp_ms, e1, e2);
+  // skies of the selected patches, in caller order of the full sky list
+  std::vector<int32_t> sub;
+  for (int p = 0; p < P; ++p) {
+    if (!sel[p]) continue;
+    for (int64_t i = (int64_t)p * patch_size; i < std::min<int64_t>(c->S, (int64_t)(p + 1) * patch_size); ++i)
+      sub.push_back(c->h_sky_perm[i]);
+  }
+  std::sort(sub.begin(), sub.end());
+  const int64_t S_full = c->S;
+  std::vector<double> full_nhat = c->h_nhat, sub_nhat(sub.size() * 3);
+  for (size_t i = 0; i < sub.size(); ++i)
+    for (int a = 0; a < 3; ++a) sub_nhat[i * 3 + a] = full_nhat[(size_t)sub[i] * 3 + a];
+  c->h_nhat = std::move(sub_nhat);
+  c->S = (int64_t)sub.size();
+  c->sky_dirty = true;
+  std::vector<float> sp(sub.size() * k);
+  std::vector<int64_t> si(sub.size() * k);
+  st = tcw_search(c, k, sp.data(), si.data(), TCW_HOST);
+  c->h_nhat = std::move(full_nhat);
+  c->S = S_full;
+  c->sky_dirty = true;
+  c->have_result = false;
+  if (st != TCW_OK) return st;
+  std::vector<float> fp((size_t)S_full * k, -INFINITY);
+  std::vector<int64_t> fi((size_t)S_full * k, -1);
+  std::vector<int32_t> searched(S_full, 0);
+  for (size_t i = 0; i < sub.size(); ++i) {
+    std::copy(sp.begin() + i * k, sp.begin() + (i + 1) * k, fp.begin() + (size_t)sub[i] * k);
+    std::copy(si.begin() + i * k, si.begin() + (i + 1) * k, fi.begin() + (size_t)sub[i] * k);
+    searched[sub[i]] = 1;
+  }
+  const cudaMemcpyKind kind = out_flags == TCW_HOST ? cudaMemcpyHostToHost : cudaMemcpyHostToDevice;
+  TCW_CUDA(c, cudaMemcpy(psi_out, fp.data(), fp.size() * sizeof(float), kind), "copy out");
+  TCW_CUDA(c, cudaMemcpy(idx_out, fi.data(), fi.size() * sizeof(int64_t), kind), "copy out");
+  if (searched_out)
+    TCW_CUDA(c, cudaMemcpy(searched_out, searched.data(), searched.size() * sizeof(int32_t), kind), "copy out");
+  c->tri_info.n_selected = m;
+  c->tri_info.skies_searched = (int64_t)sub.size();
+  c->tri_info.lookups_searched = (int64_t)sub.size() * c->B * c->D * c->Nseg;
+  c->tri_info.coarse_ms = coarse_ms;
+  c->tri_info.mlp_ms = mlp_ms;
+  c->tri_info.search_ms = c->info.search_ms;
+  return TCW_OK;
+}
+
+tcw_status tcw_get_triage_info(tcw_ctx* c, tcw_triage_info* info) {
+  if (!c || !info) return TCW_ERR_INVALID_ARGUMENT;
+  *info = c->tri_info;
+  return TCW_OK;
+}
+
+tcw_status tcw_sky_order(tcw_ctx* c, int32_t* order_out) {
+  if (!c) return TCW_ERR_INVALID_ARGUMENT;
+  if (!order_out) return fail(c, TCW_ERR_INVALID_ARGUMENT, "null output");
+  if (!c->have_sky || !c->have_vel) return fail(c, TCW_ERR_STATE, "sky or velocities not loaded");
+  cudaSetDevice(c->device);
+  tcw_status st = prepare_sky(c);
+  if (st != TCW_OK) return st;
+  std::copy(c->h_sky_perm.begin(), c->h_sky_perm.begin() + c->S, order_out);
   return TCW_OK;
 }
 

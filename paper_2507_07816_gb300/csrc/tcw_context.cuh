@@ -83,6 +83,10 @@ struct tcw_ctx {
   tcw_info info{};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   tcw::BatchState* batch = nullptr;  // owned; freed by tcw::batch_free
+  // learned triage
+  std::vector<int32_t> h_sky_perm, h_bank_perm;  // sorted -> caller (host copies)
+  tcw::DevBuf tri_dop, tri_hist, tri_feat, tri_psi, tri_anchor, tri_h1, tri_h2, tri_score, tri_sel;
+  tcw_triage_info tri_info{};
 };
 
 namespace tcw {

@@ -16,6 +16,7 @@
 // picks q so that F*q/2 stays below 0.75 * 2^-30 bins.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -169,6 +170,68 @@ size_t group_smem_bytes(int n_det);
 cudaError_t launch_anchors(const AnchorParams& p, cudaStream_t st);
 // per-CTA scratch of the group kernel, in float2 elements
 size_t group_dev_elems(int grid);
+
+// ---------------------------------------------------------------------------
+// Learned sky triage (tcw_triage.cu)
+// ---------------------------------------------------------------------------
+constexpr int kTriageBins = 128;  // histogram bins = MLP inputs
+constexpr int kMlpIn = 128, kMlpH = 256;
+// packed fp32 parameters: W1 [128][256] | b1 [256] | W2 [256][256] | b2 [256] | w3 [256] | b3
+constexpr int64_t kThW1 = 0, kThB1 = kThW1 + kMlpIn * kMlpH, kThW2 = kThB1 + kMlpH,
+                  kThB2 = kThW2 + kMlpH * kMlpH, kThW3 = kThB2 + kMlpH, kThB3 = kThW3 + kMlpH,
+                  kMlpParams = kThB3 + 1;
+// bfloat16 weights read by the forward pass: W1 | W2 | w3
+constexpr int64_t kWbfW1 = 0, kWbfW2 = kWbfW1 + kMlpIn * kMlpH, kWbfW3 = kWbfW2 + kMlpH * kMlpH,
+                  kMlpWeights = kWbfW3 + kMlpH;
+// position of packed parameter i in the bfloat16 weights, or -1 for a bias
+__host__ __device__ inline int64_t mlp_weight_index(int64_t i) {
+  if (i >= kThW1 && i < kThB1) return kWbfW1 + (i - kThW1);
+  if (i >= kThW2 && i < kThB2) return kWbfW2 + (i - kThW2);
+  if (i >= kThW3 && i < kThB3) return kWbfW3 + (i - kThW3);
+  return -1;
+}
+
+struct PatchDopplerParams {
+  const double* vel;        // [D][n_seg][3]
+  const double* nhat;       // sorted sky [S][3]
+  int n_det, n_seg, S, patch_size, P;
+  float* dop;               // [D][n_seg][P]
+};
+
+struct CoarseParams {
+  const void* rho;          // [D][n_seg][n_bin]
+  int64_t n_bin;
+  int n_det, n_seg;
+  const float* weights;     // [D][n_seg]
+  const double* t_mid;
+  double T0, f_min, df;
+  const float* dop;         // [D][n_seg][P]
+  int P;
+  const double* f0;         // sorted bank [Bpad]
+  const double* tau;
+  const double* nbr;
+  int B, Bpad;              // Bpad a multiple of 4
+  const double* anchors;    // [Bpad][n_tiles][2] at 64-segment tiles, or null when nterms == 0
+  int n_tiles, nterms;
+  float lo, hi;             // histogram range of Psi
+  float* psi;               // optional [P][Bpad]
+  unsigned* hist;           // [P][128], zero at launch
+  float* feat;              // [P][128] log(1 + count)
+};
+
+cudaError_t launch_patch_doppler(const PatchDopplerParams& p, cudaStream_t st);
+cudaError_t launch_coarse(const CoarseParams& p, bool half, cudaStream_t st);
+cudaError_t launch_rank(const float* score, int P, int m, int* selected, cudaStream_t st);
+cudaError_t mlp_forward(const __nv_bfloat16* wbf, const float* theta, const float* X, int64_t n, float* H1,
+                        float* H2, float* y, cudaStream_t st);
+// work: 2 * n * 256 floats
+cudaError_t mlp_backward(const __nv_bfloat16* wbf, const float* X, int64_t n, const float* H1, const float* H2,
+                         const float* dy, float* grad, float* work, cudaStream_t st);
+cudaError_t mlp_bce(const float* y, const float* label, int64_t n, float pw, float* loss, float* dy,
+                    cudaStream_t st);
+cudaError_t mlp_adam(float* theta, float* m, float* v, const float* grad, int64_t step, float lr, float b1,
+                     float b2, float eps, __nv_bfloat16* wbf, cudaStream_t st);
+cudaError_t mlp_pack(const float* theta, __nv_bfloat16* wbf, cudaStream_t st);
 
 // Host helpers of the group kernel (tcw_persist.cu).
 // CTAs of a group-kernel launch on the current device: one per SM.

@@ -1,0 +1,433 @@
+// tcw_triage.cu -- kernels of the learned sky triage.
+//
+// The paper searches every sky direction exhaustively (Sec. 2, Eq. 4).  The
+// triage ranks sky patches first and searches only the best-ranked ones:
+//
+//   patch_doppler_kernel  Eq. 2 factor v.nhat/c of each patch representative
+//   coarse_kernel         Psi (Eq. 4) of every template at every patch
+//                         representative, one thread per (template, patch),
+//                         and the 128-bin histogram of those Psi per patch
+//   features_kernel       log(1 + count) per histogram bin
+//   MLP 128 -> 256 -> 256 -> 1 (ReLU), bfloat16 weights, fp32 accumulation:
+//     gemm_kernel         tiled C = op(A) op(B) (+ bias, ReLU) for the forward
+//                         pass and every product of the backward pass
+//     relu_mask / colsum / bce / adam kernels
+//   rank_kernel           rank of each patch score (descending, ties by index)
+//
+// Patches are runs of consecutive skies in the Doppler-sorted order of the
+// search; the representative of a patch is its middle sky.  The coarse pass
+// takes the bin of every lookup from an FP64 track entry per (template,
+// segment) split into an integer base and an fp32 fraction, plus the fp32
+// Doppler term, so its bins equal the exact ones except within ~3e-7 bins of
+// a rounding tie.
+#include <cuda_bf16.h>
+
+#include <climits>
+#include <cmath>
+
+#include "tcw_internal.cuh"
+
+namespace tcw {
+namespace {
+
+constexpr int kCoarseLanes = 64;  // patches per block
+constexpr int kCoarseTmpl = 4;    // templates per block
+constexpr int kCoarseThreads = kCoarseLanes * kCoarseTmpl;
+constexpr int kCoarseTile = 64;   // segments per tile (= anchor tile of the coarse pass)
+constexpr int kCoarseMaxDet = 8;
+static_assert(kCoarseTile == kCoarseLanes, "one track entry per thread per tile");
+
+__device__ __forceinline__ float load_rho(const float* p, int64_t i) { return __ldg(p + i); }
+__device__ __forceinline__ float load_rho(const __half* p, int64_t i) { return __half2float(__ldg(p + i)); }
+
+__global__ void patch_doppler_kernel(PatchDopplerParams p) {
+  const int64_t total = (int64_t)p.n_det * p.n_seg * p.P;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int pi = (int)(i % p.P);
+    const int64_t dj = i / p.P;  // d * n_seg + j
+    const int r = min(pi * p.patch_size + (min(p.patch_size, p.S - pi * p.patch_size) - 1) / 2, p.S - 1);
+    const double* v = p.vel + dj * 3;
+    const double* n = p.nhat + (int64_t)r * 3;
+    p.dop[i] = (float)((v[0] * n[0] + v[1] * n[1] + v[2] * n[2]) / kLightSpeed);
+  }
+}
+
+template <typename RhoT>
+__global__ void __launch_bounds__(kCoarseThreads) coarse_kernel(CoarseParams p) {
+  __shared__ int s_base[kCoarseTmpl][kCoarseTile];
+  __shared__ float s_frac[kCoarseTmpl][kCoarseTile];
+  __shared__ float s_F[kCoarseTmpl][kCoarseTile];
+  __shared__ float s_w[kCoarseMaxDet][kCoarseTile];
+  __shared__ double s_coef[kCoarseTmpl][kMaxSeriesTerms];
+  const int tid = threadIdx.x;
+  const int pl = tid % kCoarseLanes, tl = tid / kCoarseLanes;
+  const int pi = blockIdx.x * kCoarseLanes + pl;
+  const int b = blockIdx.y * kCoarseTmpl + tl;
+  const bool active = pi < p.P;
+  const RhoT* rho = static_cast<const RhoT*>(p.rho);
+  if (pl < kCoarseTmpl && tl == 0) {
+    const int bb = blockIdx.y * kCoarseTmpl + pl;
+    const double r = 1.0 / (p.nbr[bb] - 1.0);
+    double c = 1.0;
+    for (int k = 0; k < p.nterms; ++k) {
+      s_coef[pl][k] = c;
+      c = c * (r - k) / (k + 1);
+    }
+  }
+  double S = 0.0, W1 = 0.0, W2 = 0.0;
+  const int n_tiles = (p.n_seg + kCoarseTile - 1) / kCoarseTile;
+  for (int ti = 0; ti < n_tiles; ++ti) {
+    const int j0 = ti * kCoarseTile;
+    const int jn = min(kCoarseTile, p.n_seg - j0);
+    __syncthreads();
+    {
+      // track entry of (template tl, segment j0 + pl) in FP64 (Eq. 1)
+      const int j = j0 + pl;
+      int base = INT_MIN;
+      float frac = 0.f, F = 0.f;
+      if (pl < jn && p.t_mid[j] >= p.T0) {
+        const double tj = p.t_mid[j];
+        double h;
+        if (p.nterms > 0) {
+          const double2 an = reinterpret_cast<const double2*>(p.anchors)[(int64_t)b * p.n_tiles + ti];
+          const double ta = fmax(p.t_mid[j0 + (jn - 1) / 2], p.T0);
+          const double delta = (tj - ta) * an.y;
+          double R = s_coef[tl][p.nterms - 1];
+          for (int k = p.nterms - 2; k >= 0; --k) R = fma(R, delta, s_coef[tl][k]);
+          h = an.x * R;
+        } else {
+          h = pow((tj - p.T0) / p.tau[b] + 1.0, 1.0 / (p.nbr[b] - 1.0)) / p.f0[b];
+        }
+        const double f = 1.0 / h;
+        const double x = (f - p.f_min) / p.df;
+        const double xr = rint(x);
+        if (fabs(xr) < 1.0e9) {
+          base = (int)xr;
+          frac = (float)(x - xr);
+          F = (float)(f / p.df);
+        }
+      }
+      s_base[tl][pl] = base;
+      s_frac[tl][pl] = frac;
+      s_F[tl][pl] = F;
+      for (int i = tid; i < p.n_det * kCoarseTile; i += kCoarseThreads) {
+        const int d = i / kCoarseTile, jj = i % kCoarseTile;
+        s_w[d][jj] = jj < jn ? p.weights[(int64_t)d * p.n_seg + j0 + jj] : 0.f;
+      }
+    }
+    __syncthreads();
+    if (!active) continue;
+    float st = 0.f, w1t = 0.f, w2t = 0.f;
+    for (int jj = 0; jj < jn; ++jj) {
+      const int base = s_base[tl][jj];
+      if (base == INT_MIN) continue;
+      const float frac = s_frac[tl][jj], F = s_F[tl][jj];
+      const int j = j0 + jj;
+      for (int d = 0; d < p.n_det; ++d) {
+        const float dop = __ldg(p.dop + ((int64_t)d * p.n_seg + j) * p.P + pi);
+        const int k = base + __float2int_rd(fmaf(F, dop, frac) + 0.5f);
+        if ((unsigned)k >= (unsigned)p.n_bin) continue;
+        const float w = s_w[d][jj];
+        st = fmaf(w, load_rho(rho, ((int64_t)d * p.n_seg + j) * p.n_bin + k), st);
+        w1t += w;
+        w2t = fmaf(w, w, w2t);
+      }
+    }
+    S += st;
+    W1 += w1t;
+    W2 += w2t;
+  }
+  if (!active || b >= p.B) return;
+  const float W2f = (float)W2;
+  const float psi = W2f > 0.f ? (float)(S - W1) * rsqrtf(W2f) : -INFINITY;
+  if (p.psi) p.psi[(int64_t)pi * p.Bpad + b] = psi;
+  int bin = 0;
+  if (psi > -INFINITY) {
+    const float u = floorf((psi - p.lo) / (p.hi - p.lo) * (float)kTriageBins);
+    bin = u < 0.f ? 0 : (u > (float)(kTriageBins - 1) ? kTriageBins - 1 : (int)u);
+  }
+  atomicAdd(p.hist + (int64_t)pi * kTriageBins + bin, 1u);
+}
+
+__global__ void features_kernel(const unsigned* hist, int64_t n, float* feat) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    feat[i] = log1pf((float)hist[i]);
+}
+
+// ---------------------------------------------------------------------------
+// MLP kernels
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float to_f32(float x) { return x; }
+__device__ __forceinline__ float to_f32(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+constexpr int kGemmTile = 64, kGemmK = 16, kGemmThreads = 256;
+
+// C[m][n] = sum_k A(m, k) B(k, n) (+ bias[n]) (ReLU), A(m, k) = A[m sa0 + k sa1],
+// B(k, n) = B[k sb0 + n sb1], C[m ldc + n]; fp32 accumulation.
+template <typename TB>
+__global__ void __launch_bounds__(kGemmThreads) gemm_kernel(const float* A, int64_t sa0, int64_t sa1,
+                                                            const TB* Bm, int64_t sb0, int64_t sb1, float* C,
+                                                            int64_t ldc, int M, int N, int K, const float* bias,
+                                                            int relu) {
+  __shared__ float sA[kGemmK][kGemmTile + 1];
+  __shared__ float sB[kGemmK][kGemmTile + 1];
+  const int tid = threadIdx.x;
+  const int tm = tid / 16, tn = tid % 16;
+  const int m0 = blockIdx.y * kGemmTile, n0 = blockIdx.x * kGemmTile;
+  float acc[4][4] = {};
+  for (int k0 = 0; k0 < K; k0 += kGemmK) {
+    for (int i = tid; i < kGemmK * kGemmTile; i += kGemmThreads) {
+      const int kk = i / kGemmTile, mm = i % kGemmTile;
+      const int m = m0 + mm, k = k0 + kk;
+      sA[kk][mm] = (m < M && k < K) ? A[(int64_t)m * sa0 + (int64_t)k * sa1] : 0.f;
+      const int n = n0 + mm;
+      sB[kk][mm] = (n < N && k < K) ? to_f32(Bm[(int64_t)k * sb0 + (int64_t)n * sb1]) : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kGemmK; ++kk) {
+      float a[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        a[i] = sA[kk][tm * 4 + i];
+        bv[i] = sB[kk][tn * 4 + i];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int jx = 0; jx < 4; ++jx) acc[i][jx] = fmaf(a[i], bv[jx], acc[i][jx]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int m = m0 + tm * 4 + i;
+    if (m >= M) continue;
+#pragma unroll
+    for (int jx = 0; jx < 4; ++jx) {
+      const int n = n0 + tn * 4 + jx;
+      if (n >= N) continue;
+      float v = acc[i][jx] + (bias ? bias[n] : 0.f);
+      if (relu) v = fmaxf(v, 0.f);
+      C[(int64_t)m * ldc + n] = v;
+    }
+  }
+}
+
+template <typename TB>
+cudaError_t gemm(const float* A, int64_t sa0, int64_t sa1, const TB* B, int64_t sb0, int64_t sb1, float* C,
+                 int64_t ldc, int M, int N, int K, const float* bias, bool relu, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return cudaSuccess;
+  dim3 grid((N + kGemmTile - 1) / kGemmTile, (M + kGemmTile - 1) / kGemmTile);
+  gemm_kernel<TB><<<grid, kGemmThreads, 0, st>>>(A, sa0, sa1, B, sb0, sb1, C, ldc, M, N, K, bias, relu ? 1 : 0);
+  return cudaGetLastError();
+}
+
+// dZ[i][j] = dY[i][j] (or dY[i] when ldy == 1) * scale[j] * (H[i][j] > 0)
+__global__ void relu_mask_kernel(const float* dY, int64_t ldy, const __nv_bfloat16* scale, const float* H,
+                                 int64_t n, int width, float* dZ) {
+  const int64_t total = n * width;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / width;
+    const int c = (int)(i % width);
+    const float g = dY[ldy == 1 ? r : r * ldy + c] * (scale ? __bfloat162float(scale[c]) : 1.f);
+    dZ[i] = H[i] > 0.f ? g : 0.f;
+  }
+}
+
+// out[j] = sum_i Z[i][j]
+__global__ void colsum_kernel(const float* Z, int64_t n, int width, float* out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= width) return;
+  float s = 0.f;
+  for (int64_t i = 0; i < n; ++i) s += Z[i * width + j];
+  out[j] = s;
+}
+
+__global__ void bce_kernel(const float* y, const float* label, int64_t n, float pw, float* loss, float* dy) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float v = y[i], l = label[i];
+    const float e = expf(-fabsf(v));
+    const float sp_pos = fmaxf(v, 0.f) + log1pf(e);   // softplus(v)
+    const float sp_neg = sp_pos - v;                  // softplus(-v)
+    const float sig = v >= 0.f ? 1.f / (1.f + e) : e / (1.f + e);
+    atomicAdd(loss, (pw * l * sp_neg + (1.f - l) * sp_pos) / (float)n);
+    dy[i] = (pw * l * (sig - 1.f) + (1.f - l) * sig) / (float)n;
+  }
+}
+
+__global__ void adam_kernel(float* theta, float* m, float* v, const float* g, int64_t n, float lr, float b1,
+                            float b2, float c1, float c2, float eps, __nv_bfloat16* wbf) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float th = theta[i] - lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    theta[i] = th;
+    const int64_t wi = mlp_weight_index(i);
+    if (wi >= 0) wbf[wi] = __float2bfloat16_rn(th);
+  }
+}
+
+__global__ void pack_kernel(const float* theta, __nv_bfloat16* wbf) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < kMlpParams; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t wi = mlp_weight_index(i);
+    if (wi >= 0) wbf[wi] = __float2bfloat16_rn(theta[i]);
+  }
+}
+
+__global__ void rank_kernel(const float* score, int P, int m, int* selected) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const float sp = isnan(score[p]) ? -INFINITY : score[p];
+  int rank = 0;
+  for (int q = 0; q < P; ++q) {
+    const float sq = isnan(score[q]) ? -INFINITY : score[q];
+    rank += (sq > sp || (sq == sp && q < p)) ? 1 : 0;
+  }
+  selected[p] = rank < m ? 1 : 0;
+}
+
+unsigned blocks_for(int64_t n, int threads) {
+  const int64_t b = (n + threads - 1) / threads;
+  return (unsigned)(b < 152 * 32 ? (b > 0 ? b : 1) : 152 * 32);
+}
+
+}  // namespace
+
+cudaError_t launch_patch_doppler(const PatchDopplerParams& p, cudaStream_t st) {
+  const int64_t total = (int64_t)p.n_det * p.n_seg * p.P;
+  patch_doppler_kernel<<<blocks_for(total, 256), 256, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarse(const CoarseParams& p, bool half, cudaStream_t st) {
+  if (p.n_det > kCoarseMaxDet) return cudaErrorInvalidValue;
+  dim3 grid((p.P + kCoarseLanes - 1) / kCoarseLanes, p.Bpad / kCoarseTmpl);
+  if (half)
+    coarse_kernel<__half><<<grid, kCoarseThreads, 0, st>>>(p);
+  else
+    coarse_kernel<float><<<grid, kCoarseThreads, 0, st>>>(p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int64_t n = (int64_t)p.P * kTriageBins;
+  features_kernel<<<blocks_for(n, 256), 256, 0, st>>>(p.hist, n, p.feat);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rank(const float* score, int P, int m, int* selected, cudaStream_t st) {
+  rank_kernel<<<(P + 255) / 256, 256, 0, st>>>(score, P, m, selected);
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_forward(const __nv_bfloat16* wbf, const float* theta, const float* X, int64_t n, float* H1,
+                        float* H2, float* y, cudaStream_t st) {
+  const int N = (int)n;
+  cudaError_t e = gemm(X, kMlpIn, 1, wbf + kWbfW1, kMlpH, 1, H1, kMlpH, N, kMlpH, kMlpIn, theta + kThB1, true, st);
+  if (e == cudaSuccess)
+    e = gemm(H1, kMlpH, 1, wbf + kWbfW2, kMlpH, 1, H2, kMlpH, N, kMlpH, kMlpH, theta + kThB2, true, st);
+  if (e == cudaSuccess) e = gemm(H2, kMlpH, 1, wbf + kWbfW3, 1, 0, y, 1, N, 1, kMlpH, theta + kThB3, false, st);
+  return e;
+}
+
+cudaError_t mlp_backward(const __nv_bfloat16* wbf, const float* X, int64_t n, const float* H1, const float* H2,
+                         const float* dy, float* grad, float* work, cudaStream_t st) {
+  const int N = (int)n;
+  float* dZ2 = work;
+  float* dZ1 = work + n * kMlpH;
+  const unsigned nb = blocks_for(n * kMlpH, 256);
+  // output layer: y = H2 w3 + b3
+  cudaError_t e = gemm(H2, 1, kMlpH, dy, 1, 0, grad + kThW3, 1, kMlpH, 1, N, nullptr, false, st);
+  if (e != cudaSuccess) return e;
+  colsum_kernel<<<1, 32, 0, st>>>(dy, n, 1, grad + kThB3);
+  relu_mask_kernel<<<nb, 256, 0, st>>>(dy, 1, wbf + kWbfW3, H2, n, kMlpH, dZ2);
+  // second hidden layer: H2 = relu(H1 W2 + b2)
+  e = gemm(H1, 1, kMlpH, dZ2, kMlpH, 1, grad + kThW2, kMlpH, kMlpH, kMlpH, N, nullptr, false, st);
+  if (e != cudaSuccess) return e;
+  colsum_kernel<<<1, kMlpH, 0, st>>>(dZ2, n, kMlpH, grad + kThB2);
+  e = gemm(dZ2, kMlpH, 1, wbf + kWbfW2, 1, kMlpH, dZ1, kMlpH, N, kMlpH, kMlpH, nullptr, false, st);
+  if (e != cudaSuccess) return e;
+  relu_mask_kernel<<<nb, 256, 0, st>>>(dZ1, kMlpH, nullptr, H1, n, kMlpH, dZ1);
+  // first hidden layer: H1 = relu(X W1 + b1)
+  e = gemm(X, 1, kMlpIn, dZ1, kMlpH, 1, grad + kThW1, kMlpH, kMlpIn, kMlpH, N, nullptr, false, st);
+  if (e != cudaSuccess) return e;
+  colsum_kernel<<<1, kMlpH, 0, st>>>(dZ1, n, kMlpH, grad + kThB1);
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_bce(const float* y, const float* label, int64_t n, float pw, float* loss, float* dy,
+                    cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(float), st);
+  if (e != cudaSuccess) return e;
+  bce_kernel<<<blocks_for(n, 256), 256, 0, st>>>(y, label, n, pw, loss, dy);
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_adam(float* theta, float* m, float* v, const float* grad, int64_t step, float lr, float b1,
+                     float b2, float eps, __nv_bfloat16* wbf, cudaStream_t st) {
+  const float c1 = (float)(1.0 / (1.0 - std::pow((double)b1, (double)step)));
+  const float c2 = (float)(1.0 / (1.0 - std::pow((double)b2, (double)step)));
+  adam_kernel<<<blocks_for(kMlpParams, 256), 256, 0, st>>>(theta, m, v, grad, kMlpParams, lr, b1, b2, c1, c2, eps,
+                                                           wbf);
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_pack(const float* theta, __nv_bfloat16* wbf, cudaStream_t st) {
+  pack_kernel<<<blocks_for(kMlpParams, 256), 256, 0, st>>>(theta, wbf);
+  return cudaGetLastError();
+}
+
+}  // namespace tcw
+
+using namespace tcw;
+
+extern "C" {
+
+tcw_status tcw_mlp_pack(const float* theta, uint16_t* wbf, void* stream) {
+  if (!theta || !wbf) return TCW_ERR_INVALID_ARGUMENT;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (mlp_pack(theta, reinterpret_cast<__nv_bfloat16*>(wbf), st) != cudaSuccess) return TCW_ERR_CUDA;
+  return TCW_OK;
+}
+
+tcw_status tcw_mlp_forward(const uint16_t* wbf, const float* theta, const float* X, int64_t n, float* H1,
+                           float* H2, float* y, void* stream) {
+  if (!wbf || !theta || !X || !H1 || !H2 || !y || n < 1 || n > INT32_MAX) return TCW_ERR_INVALID_ARGUMENT;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (mlp_forward(reinterpret_cast<const __nv_bfloat16*>(wbf), theta, X, n, H1, H2, y, st) != cudaSuccess)
+    return TCW_ERR_CUDA;
+  return TCW_OK;
+}
+
+tcw_status tcw_mlp_backward(const uint16_t* wbf, const float* X, int64_t n, const float* H1, const float* H2,
+                            const float* dy, float* grad, float* work, void* stream) {
+  if (!wbf || !X || !H1 || !H2 || !dy || !grad || !work || n < 1 || n > INT32_MAX) return TCW_ERR_INVALID_ARGUMENT;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (mlp_backward(reinterpret_cast<const __nv_bfloat16*>(wbf), X, n, H1, H2, dy, grad, work, st) != cudaSuccess)
+    return TCW_ERR_CUDA;
+  return TCW_OK;
+}
+
+tcw_status tcw_mlp_bce(const float* y, const float* label, int64_t n, float pos_weight, float* loss, float* dy,
+                       void* stream) {
+  if (!y || !label || !loss || !dy || n < 1 || !(pos_weight > 0)) return TCW_ERR_INVALID_ARGUMENT;
+  if (mlp_bce(y, label, n, pos_weight, loss, dy, static_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return TCW_ERR_CUDA;
+  return TCW_OK;
+}
+
+tcw_status tcw_mlp_adam(float* theta, float* m, float* v, const float* grad, int64_t step, float lr, float beta1,
+                        float beta2, float eps, uint16_t* wbf, void* stream) {
+  if (!theta || !m || !v || !grad || !wbf || step < 1 || !(lr > 0) || !(beta1 >= 0 && beta1 < 1) ||
+      !(beta2 >= 0 && beta2 < 1) || !(eps > 0))
+    return TCW_ERR_INVALID_ARGUMENT;
+  if (mlp_adam(theta, m, v, grad, step, lr, beta1, beta2, eps, reinterpret_cast<__nv_bfloat16*>(wbf),
+               static_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return TCW_ERR_CUDA;
+  return TCW_OK;
+}
+
+}  // extern "C"

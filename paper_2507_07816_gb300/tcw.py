@@ -56,6 +56,17 @@ class _BatchInfo(ctypes.Structure):
                 ("search_ms", ctypes.c_float)]
 
 
+class _TriageInfo(ctypes.Structure):
+    _fields_ = [("n_patch", ctypes.c_int), ("n_selected", ctypes.c_int),
+                ("skies_searched", ctypes.c_int64), ("lookups_full", ctypes.c_int64),
+                ("lookups_coarse", ctypes.c_int64), ("lookups_searched", ctypes.c_int64),
+                ("coarse_ms", ctypes.c_float), ("mlp_ms", ctypes.c_float),
+                ("search_ms", ctypes.c_float)]
+
+
+MLP_PARAMS, MLP_WEIGHTS = 99073, 98560
+
+
 def library_path() -> str:
     return _build.LIB
 
@@ -89,6 +100,17 @@ def load_library(build_if_missing: bool = True):
             "tcw_search_batched": [p, i, p, p, i],
             "tcw_get_batch_info": [p, ctypes.POINTER(_BatchInfo)],
             "tcw_get_tune_results": [p, i, p, p, p, p],
+            "tcw_mlp_pack": [p, p, p],
+            "tcw_mlp_forward": [p, p, p, i64, p, p, p, p],
+            "tcw_mlp_backward": [p, p, i64, p, p, p, p, p, p],
+            "tcw_mlp_bce": [p, p, i64, ctypes.c_float, p, p, p],
+            "tcw_mlp_adam": [p, p, p, p, i64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                             ctypes.c_float, p, p],
+            "tcw_triage_features": [p, i, ctypes.c_float, ctypes.c_float, p, p, i],
+            "tcw_search_triaged": [p, p, p, i, ctypes.c_float, ctypes.c_float, ctypes.c_float, i,
+                                   p, p, p, i],
+            "tcw_get_triage_info": [p, ctypes.POINTER(_TriageInfo)],
+            "tcw_sky_order": [p, p],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -329,3 +351,131 @@ class Search:
         rt = (ctypes.c_double * max(m, 1))()
         self._check(self._lib.tcw_get_tune_results(self._h, m, bc, ts, rt, ctypes.byref(n)))
         return [(bc[i], ts[i], rt[i]) for i in range(m)]
+
+    # ---------------------------------------------------------------- triage
+    def triage_features(self, patch_size, psi_lo, psi_hi, with_psi=False):
+        """Coarse-pass features [n_patch][128] (and Psi [n_patch][n_tmpl]) as numpy."""
+        P = -(-self.n_sky // int(patch_size))
+        feat = np.empty((P, 128), np.float32)
+        psi = np.empty((P, self.n_tmpl), np.float32) if with_psi else None
+        self._check(self._lib.tcw_triage_features(
+            self._h, int(patch_size), float(psi_lo), float(psi_hi),
+            feat.ctypes.data_as(ctypes.c_void_p),
+            None if psi is None else psi.ctypes.data_as(ctypes.c_void_p), HOST))
+        return (feat, psi) if with_psi else feat
+
+    def triage_features_device(self, patch_size, psi_lo, psi_hi, out):
+        """Coarse-pass features into a CUDA float32 tensor out [n_patch][128]."""
+        self._check(self._lib.tcw_triage_features(
+            self._h, int(patch_size), float(psi_lo), float(psi_hi), ctypes.c_void_p(out.data_ptr()),
+            None, DEVICE))
+        return out
+
+    def search_triaged(self, mlp, patch_size, psi_lo, psi_hi, frac, k):
+        """Triaged search: (psi [S][k], idx [S][k], searched [S]) as numpy."""
+        psi = np.empty((self.n_sky, k), np.float32)
+        idx = np.empty((self.n_sky, k), np.int64)
+        searched = np.empty(self.n_sky, np.int32)
+        self._check(self._lib.tcw_search_triaged(
+            self._h, ctypes.c_void_p(mlp.wbf.data_ptr()), ctypes.c_void_p(mlp.theta.data_ptr()),
+            int(patch_size), float(psi_lo), float(psi_hi), float(frac), int(k),
+            psi.ctypes.data_as(ctypes.c_void_p), idx.ctypes.data_as(ctypes.c_void_p),
+            searched.ctypes.data_as(ctypes.c_void_p), HOST))
+        return psi, idx, searched
+
+    def triage_info(self) -> dict:
+        i = _TriageInfo()
+        self._check(self._lib.tcw_get_triage_info(self._h, ctypes.byref(i)))
+        return {name: getattr(i, name) for name, _ in _TriageInfo._fields_}
+
+    def sky_order(self):
+        """Doppler-sorted order of the loaded sky (caller indices)."""
+        out = np.empty(self.n_sky, np.int32)
+        self._check(self._lib.tcw_sky_order(self._h, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+
+class Mlp:
+    """Parameters, bfloat16 weights and Adam moments of the triage network, as
+    CUDA tensors, driven through the tcw_mlp_* entry points."""
+
+    def __init__(self, theta=None, seed=0, device="cuda:0"):
+        import torch
+        self._lib = load_library()
+        self.device = torch.device(device)
+        if theta is None:
+            theta = self.initial(seed)
+        theta = np.ascontiguousarray(theta, np.float32)
+        if theta.shape != (MLP_PARAMS,):
+            raise ValueError(f"theta must have {MLP_PARAMS} entries")
+        self.theta = torch.as_tensor(theta, device=self.device).clone()
+        self.wbf = torch.empty(MLP_WEIGHTS, dtype=torch.int16, device=self.device)
+        self.m = torch.zeros_like(self.theta)
+        self.v = torch.zeros_like(self.theta)
+        self.step = 0
+        self._call("tcw_mlp_pack", self.theta, self.wbf)
+
+    @staticmethod
+    def initial(seed):
+        """He-normal weights, zero biases (packed layout of include/tcw.h)."""
+        r = np.random.default_rng(seed)
+        parts = [r.normal(0, np.sqrt(2.0 / 128), 128 * 256), np.zeros(256),
+                 r.normal(0, np.sqrt(2.0 / 256), 256 * 256), np.zeros(256),
+                 r.normal(0, np.sqrt(1.0 / 256), 256), np.zeros(1)]
+        return np.concatenate(parts).astype(np.float32)
+
+    def _stream(self):
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+
+    def _call(self, name, *args):
+        conv = []
+        for a in args:
+            if a is None:
+                conv.append(None)
+            elif _is_torch(a):
+                conv.append(ctypes.c_void_p(a.data_ptr()))
+            else:
+                conv.append(a)
+        st = getattr(self._lib, name)(*conv, self._stream())
+        if st != OK:
+            raise TcwError(st, f"{name}: " + self._lib.tcw_status_string(st).decode())
+
+    def forward(self, X):
+        import torch
+        n = X.shape[0]
+        H1 = torch.empty((n, 256), dtype=torch.float32, device=self.device)
+        H2 = torch.empty((n, 256), dtype=torch.float32, device=self.device)
+        y = torch.empty(n, dtype=torch.float32, device=self.device)
+        self._call("tcw_mlp_forward", self.wbf, self.theta, X.contiguous(), int(n), H1, H2, y)
+        return H1, H2, y
+
+    def backward(self, X, H1, H2, dy):
+        import torch
+        n = X.shape[0]
+        grad = torch.empty_like(self.theta)
+        work = torch.empty(2 * n * 256, dtype=torch.float32, device=self.device)
+        self._call("tcw_mlp_backward", self.wbf, X.contiguous(), int(n), H1, H2, dy, grad, work)
+        return grad
+
+    def bce(self, y, label, pos_weight=1.0):
+        import torch
+        loss = torch.empty(1, dtype=torch.float32, device=self.device)
+        dy = torch.empty_like(y)
+        self._call("tcw_mlp_bce", y, label.contiguous(), int(y.shape[0]), ctypes.c_float(pos_weight), loss, dy)
+        return loss, dy
+
+    def adam(self, grad, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        self.step += 1
+        self._call("tcw_mlp_adam", self.theta, self.m, self.v, grad, int(self.step), ctypes.c_float(lr),
+                   ctypes.c_float(beta1), ctypes.c_float(beta2), ctypes.c_float(eps), self.wbf)
+
+    def parameters(self):
+        return self.theta.detach().cpu().numpy()
+
+    def save(self, path):
+        np.savez(path, theta=self.parameters())
+
+    @classmethod
+    def load(cls, path, device="cuda:0"):
+        return cls(np.load(path)["theta"], device=device)

@@ -381,3 +381,100 @@ def config_batched(seed=20250714, n_events=64, n_seg_range=(2000, 20000), n_bin=
         events.append(Problem(rho, t, w, vel, f_min, df, T0, nhat, bank, [inj], dets,
                               name=f"event{i}-{n_det}det-{n_seg}x{n_bin}-sky{n_sky}"))
     return events, bank
+
+
+def spindown_frequency_many(f0, tau, n, T0, t, step=16.0):
+    """Source frequency of K sources at the times t: RK4 of the braking law
+    df/dt = -f^n/((n-1) tau f0^(n-1)) on a uniform grid of `step` seconds from
+    T0, then cubic Hermite interpolation (values and ODE slopes) to t.
+    Returns [K][len(t)], NaN before T0."""
+    f0, tau, n = (np.asarray(a, np.float64).reshape(-1, 1) for a in (f0, tau, n))
+    t = np.asarray(t, np.float64)
+    out = np.full((f0.shape[0], t.shape[0]), np.nan)
+    ok = t >= T0
+    if not ok.any():
+        return out
+    k = f0 ** (1.0 - n) / ((n - 1.0) * tau)
+    G = int(math.ceil((t[ok].max() - T0) / step)) + 1
+    fg = np.empty((f0.shape[0], G + 1))
+    f = f0[:, 0].copy()
+    kk, nn = k[:, 0], n[:, 0]
+    fg[:, 0] = f
+    for g in range(G):
+        k1 = -kk * f ** nn
+        k2 = -kk * (f + 0.5 * step * k1) ** nn
+        k3 = -kk * (f + 0.5 * step * k2) ** nn
+        k4 = -kk * (f + step * k3) ** nn
+        f = f + step * (k1 + 2.0 * k2 + 2.0 * k3 + k4) / 6.0
+        fg[:, g + 1] = f
+    dg = -k * fg ** n
+    u = (t[ok] - T0) / step
+    i = np.minimum(np.floor(u).astype(np.int64), G - 1)
+    s_ = u - i
+    h00 = (1 + 2 * s_) * (1 - s_) ** 2
+    h10 = s_ * (1 - s_) ** 2
+    h01 = s_ * s_ * (3 - 2 * s_)
+    h11 = s_ * s_ * (s_ - 1)
+    out[:, ok] = (h00 * fg[:, i] + h10 * step * dg[:, i] + h01 * fg[:, i + 1]
+                  + h11 * step * dg[:, i + 1])
+    return out
+
+
+def training_event(seed, bank, n_det=2, n_seg=10000, n_bin=10000, n_sky=1024, t_sft=4.0,
+                   f_min=500.0, n_inj=4, snr_range=(5.0, 12.0), device=None, dtype=np.float32):
+    """One event for the learned triage: exponential noise (drawn on `device`
+    by a seeded torch generator when given), `n_inj` injected tracks with
+    templates drawn from `bank`, skies drawn from the event's Fibonacci sky
+    and SNR uniform in snr_range.  Each injection records .template and .sky."""
+    r = rng(seed)
+    df = 1.0 / t_sft
+    t = segment_times(n_seg, t_sft, t_start=GPS_EPOCH0 + float(r.uniform(0.0, 3.0e7)))
+    T0 = float(t[0] - 0.5 * t_sft)
+    dets = random_detectors(r, n_det)
+    vel = np.stack([d.velocity(t) for d in dets])
+    nhat = fibonacci_sky(n_sky)
+    tb = r.integers(0, len(bank), n_inj)
+    sk = r.integers(0, n_sky, n_inj)
+    snr = r.uniform(snr_range[0], snr_range[1], n_inj)
+    fsrc = spindown_frequency_many(bank.f0[tb], bank.tau[tb], bank.n[tb], T0, t)
+    shape = (n_det, n_seg, n_bin)
+    injections, cells = [], []
+    for i in range(n_inj):
+        inj = Injection(float(bank.f0[tb[i]]), float(bank.tau[tb[i]]), float(bank.n[tb[i]]),
+                        nhat[sk[i]], float(snr[i]))
+        inj.template, inj.sky = int(tb[i]), int(sk[i])
+        bins = np.full((n_det, n_seg), -1, np.int64)
+        fdet = np.full((n_det, n_seg), np.nan)
+        for d, det in enumerate(dets):
+            fd = detector_frame_frequency(fsrc[i], det, inj.nhat, t)
+            fdet[d] = fd
+            bins[d] = signal_bins(fd, f_min, df, n_bin)
+        inj.bins = bins
+        ok = bins >= 0
+        if ok.any():
+            lam_shape = np.where(ok, (fdet / inj.f0) ** 4, 0.0)
+            lam_unit = lam_shape.sum() / math.sqrt(ok.sum())
+            mu = np.sqrt(2.0 * (inj.snr / lam_unit) * lam_shape)
+            dd, jj = np.nonzero(ok)
+            x = r.normal(size=dd.shape[0])
+            y = r.normal(size=dd.shape[0])
+            cells.append((dd, jj, bins[dd, jj], ((x + mu[dd, jj]) ** 2 + y ** 2) / 2.0))
+        injections.append(inj)
+    if device is None:
+        rho = exponential_noise(r, shape)
+        for dd, jj, kk, val in cells:
+            rho[dd, jj, kk] = val.astype(np.float32)
+        if dtype != np.float32:
+            rho = rho.astype(dtype)
+    else:
+        import torch
+        g = torch.Generator(device=device)
+        g.manual_seed(int(seed) % (2 ** 62))
+        rho = torch.empty(shape, dtype=torch.float32, device=device).exponential_(generator=g)
+        for dd, jj, kk, val in cells:
+            idx = tuple(torch.as_tensor(a, device=device) for a in (dd, jj, kk))
+            rho[idx] = torch.as_tensor(val, dtype=torch.float32, device=device)
+        if dtype == np.float16:
+            rho = rho.half()
+    return Problem(rho, t, None, vel, f_min, df, T0, nhat, bank, injections, dets,
+                   name=f"training-{n_det}det-{n_seg}x{n_bin}-sky{n_sky}")

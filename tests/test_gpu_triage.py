@@ -1,0 +1,153 @@
+"""GPU parity of the learned sky triage against the FP64 oracle
+(oracle/triage.py), through the C ABI: the coarse pass and its histogram
+features, the bf16 MLP forward and backward passes, BCE and Adam; then a
+short training run on method-generated injections that must beat the
+untrained network, and the triaged search whose searched rows must equal
+the exhaustive search's rows."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import triage as OT
+import paper_2507_07816_gb300 as tcw
+from paper_2507_07816_gb300 import triage as TR
+import tcw_synth as syn
+from _parity import REL
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+DEV = "cuda:0"
+COARSE_TIE = 1e-6   # bins: the coarse pass decides bins in fp32 around an FP64 split
+
+
+def small_event(seed, n_det=2, n_seg=150, n_bin=1200, n_sky=120, n_tmpl=96, n_inj=3, snr=(12.0, 16.0)):
+    r = syn.rng(seed)
+    f_min, t_sft = 500.0, 4.0
+    bank = syn.random_bank(r, n_tmpl, f0_range=(f_min - 3, f_min + n_bin / t_sft + 3),
+                           tau_range=(3500.0, 35000.0))
+    ev = syn.training_event(seed, bank, n_det=n_det, n_seg=n_seg, n_bin=n_bin, n_sky=n_sky,
+                            n_inj=n_inj, snr_range=snr)
+    return ev, bank
+
+
+def test_coarse_features_match_oracle():
+    ev, bank = small_event(81, n_inj=2)
+    P_SIZE, LO, HI = 8, -4.0, 12.0
+    s = tcw.Search(0)
+    TR.load_event(s, ev, bank)
+    feat, psi = s.triage_features(P_SIZE, LO, HI, with_psi=True)
+    ora = OT.coarse_psi(ev.rho, ev.f_min, ev.df, ev.t_mid, ev.weights, ev.velocity, ev.nhat,
+                        bank.f0, bank.tau, bank.n, ev.T0, P_SIZE)
+    # pairs with a lookup within COARSE_TIE of a rounding tie may differ
+    order = OT.sky_order(ev.velocity, ev.nhat)
+    reps = [order[r] for _, _, r in OT.patches(len(order), P_SIZE)]
+    pairs = np.array([(pi, b) for pi in range(len(reps)) for b in range(len(bank))])
+    x = oracle.track_coordinates(ev.rho.shape[0], ev.f_min, ev.df, ev.t_mid, ev.velocity,
+                                 ev.nhat[reps], bank.f0, bank.tau, bank.n, ev.T0, pairs)
+    fr = x - np.floor(x)
+    near = (np.isfinite(x) & (np.abs(fr - 0.5) <= COARSE_TIE)).any(axis=(1, 2)).reshape(len(reps), len(bank))
+    assert near.mean() < 0.05
+    S_, _, W2, _ = oracle.search_stats(ev.rho, ev.f_min, ev.df, ev.t_mid, ev.weights, ev.velocity,
+                                       ev.nhat[reps], bank.f0, bank.tau, bank.n, ev.T0)
+    fin = np.isfinite(ora)
+    np.testing.assert_array_equal(np.isfinite(psi), fin)
+    tol = REL * np.abs(S_) / np.sqrt(np.maximum(W2, 1e-30)) + 1e-5
+    ok = fin & ~near
+    err = np.abs(psi.astype(np.float64) - ora)
+    assert np.all(err[ok] <= tol[ok]), err[ok].max()
+    # histogram counts: equal to the oracle's up to pairs near a tie or a bin edge
+    counts_o, _ = OT.histogram_features(ora, LO, HI)
+    counts_g = np.rint(np.expm1(feat.astype(np.float64))).astype(np.int64)
+    scale = (ora - LO) / (HI - LO) * 128
+    edge = fin & (np.abs(scale - np.rint(scale)) < 1e-3)
+    slack = (near | edge).sum(axis=1)
+    assert np.all(np.abs(counts_g - counts_o).sum(axis=1) <= 2 * slack)
+    assert np.all(counts_g.sum(axis=1) == len(bank))
+    s.close()
+
+
+def test_mlp_forward_backward_bce_adam_match_oracle():
+    r = np.random.default_rng(82)
+    theta = (r.normal(size=OT.N_PARAMS) * 0.1).astype(np.float32)
+    X = np.abs(r.normal(size=(300, 128))).astype(np.float32)
+    lab = (r.random(300) < 0.2).astype(np.float32)
+    mlp = tcw.Mlp(theta, device=DEV)
+    Xt = torch.as_tensor(X, device=DEV)
+    H1, H2, y = mlp.forward(Xt)
+    oH1, oH2, oy = OT.mlp_forward(theta.astype(np.float64), X)
+    np.testing.assert_allclose(y.cpu().numpy(), oy, rtol=1e-4, atol=1e-4 * np.abs(oy).max())
+    np.testing.assert_allclose(H2.cpu().numpy(), oH2, rtol=1e-4, atol=1e-4 * np.abs(oH2).max())
+    loss, dy = mlp.bce(y, torch.as_tensor(lab, device=DEV), 3.0)
+    oloss, ody = OT.bce_with_logits(oy, lab, pw=3.0)
+    assert abs(loss.item() - oloss) <= 1e-4 * abs(oloss)
+    np.testing.assert_allclose(dy.cpu().numpy(), ody, rtol=1e-3, atol=1e-7)
+    grad = mlp.backward(Xt, H1, H2, dy).cpu().numpy().astype(np.float64)
+    ograd = OT.mlp_backward(theta.astype(np.float64), X, oH1, oH2, ody)
+    for name, sl in _slices().items():
+        g, o = grad[sl], ograd[sl]
+        assert np.max(np.abs(g - o)) <= 1e-3 * np.abs(o).max() + 1e-9, name
+    # one Adam step from zero moments, then the bf16 weights follow theta
+    mlp.adam(torch.as_tensor(ograd.astype(np.float32), device=DEV), lr=1e-3)
+    oth, _, _ = OT.adam_step(theta.astype(np.float64), 0.0, 0.0, ograd.astype(np.float32).astype(np.float64),
+                             1, lr=1e-3)
+    th = mlp.parameters().astype(np.float64)
+    np.testing.assert_allclose(th, oth, rtol=0, atol=2e-6)
+    wb = mlp.wbf.cpu().numpy().view(np.uint16).astype(np.uint32) << 16
+    w_gpu = wb.view(np.float32).astype(np.float64)
+    w_ora = np.concatenate([OT.bf16_round(th[sl]) for sl in
+                            (_slices()["W1"], _slices()["W2"], _slices()["w3"])])
+    np.testing.assert_array_equal(w_gpu, w_ora)
+
+
+def _slices():
+    out, off = {}, 0
+    for name, shape in OT.SIZES:
+        n = int(np.prod(shape))
+        out[name] = slice(off, off + n)
+        off += n
+    return out
+
+
+def test_training_beats_the_untrained_network():
+    r = syn.rng(83)
+    bank = syn.random_bank(r, 64, f0_range=(497.0, 803.0), tau_range=(3500.0, 35000.0))
+
+    def make(i):
+        return syn.training_event(1000 + i, bank, n_det=1, n_seg=120, n_bin=1200, n_sky=256,
+                                  n_inj=3, snr_range=(9.0, 14.0))
+
+    X, y = TR.collect(make, 24, bank, patch_size=16)
+    Xv, yv = TR.collect(lambda i: make(500 + i), 12, bank, patch_size=16)
+    assert y.sum().item() > 20
+    untrained = tcw.Mlp(seed=3, device=DEV)
+    mlp, losses = TR.train(X, y, steps=400, batch=256, lr=2e-3, seed=3, log_every=50)
+    assert losses[-1][1] < 0.5 * losses[0][1]
+    r_tr = TR.recall_at(mlp, Xv, yv, 0.15)
+    r_un = TR.recall_at(untrained, Xv, yv, 0.15)
+    assert r_tr >= 0.8 and r_tr > r_un + 0.3, (r_tr, r_un)
+
+
+def test_triaged_search_rows_equal_exhaustive_rows():
+    ev, bank = small_event(84, n_sky=200, n_inj=2, snr=(14.0, 16.0))
+    # hand-set network: score = sum of the log-counts of the 28 highest histogram bins
+    theta = np.zeros(OT.N_PARAMS, np.float32)
+    p = OT.unpack(theta)
+    p["W1"][100:, 0] = 1.0
+    p["W2"][0, 0] = 1.0
+    p["w3"][0] = 1.0
+    mlp = tcw.Mlp(theta, device=DEV)
+    s = tcw.Search(0)
+    TR.load_event(s, ev, bank)
+    k = 8
+    pf, xf = s.search(k)
+    pt, xt, searched = s.search_triaged(mlp, 16, -4.0, 12.0, 0.25, k)
+    info = s.triage_info()
+    assert info["n_selected"] == int(np.ceil(0.25 * info["n_patch"]))
+    assert searched.sum() == info["skies_searched"] > 0
+    rows = searched.astype(bool)
+    np.testing.assert_array_equal(xt[rows], xf[rows])
+    np.testing.assert_array_equal(pt[rows], pf[rows])
+    assert np.all(xt[~rows] == -1) and np.all(np.isneginf(pt[~rows]))
+    for inj in ev.injections:
+        assert searched[inj.sky] == 1
+    s.close()
