@@ -78,14 +78,18 @@ enum {
     TCW_OPT_TILE_SEGMENTS = 3, /* segments per tile of the group kernel: the spacing of
                                   the FP64 track anchors and of the fp32 partial sums;
                                   a power of two in [8, 128], default 32 */
-    TCW_OPT_BANK_CHUNK = 4,    /* groups of 8 sorted templates per work item of the
-                                  group kernel, in [1, 4096], default 1 */
+    TCW_OPT_BANK_CHUNK = 4,    /* template groups of one pass (512/lanes sorted
+                                  templates) per work item of the group kernel,
+                                  in [1, 4096], default 1 */
     TCW_OPT_AUTOTUNE = 5,      /* batched search: 1 (default) = choose the bank chunk
                                   and tile length by timing candidates on a sample of
                                   the batch; 0 = use TCW_OPT_BANK_CHUNK and
                                   TCW_OPT_TILE_SEGMENTS */
-    TCW_OPT_BATCH_MEMORY = 6   /* batched search: bytes of Psi and anchor buffers per
+    TCW_OPT_BATCH_MEMORY = 6,  /* batched search: bytes of Psi and anchor buffers per
                                   wave of events (default 48 GiB, minimum 1 MiB) */
+    TCW_OPT_SKY_LANES = 7      /* sky groups of 16 per chunk of the group kernel: 16,
+                                  32 or 64 (a pass covers 16*lanes skies x 512/lanes
+                                  templates); 0 (default) = the fewest padded skies */
 };
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
@@ -323,7 +327,8 @@ tcw_status tcw_mlp_adam(float *theta, float *m, float *v, const float *grad, int
 /* Coarse pass of the loaded search: feat_out [n_patch][128] float32,
  * n_patch = ceil(n_sky / patch_size); psi_out [n_patch][n_tmpl] (caller
  * template order) may be NULL.  Errors: STATE, INVALID_ARGUMENT (patch_size
- * < 1, psi_hi <= psi_lo), UNSUPPORTED (more than 8 detectors), CUDA. */
+ * < 1, psi_hi <= psi_lo), UNSUPPORTED (more than 2 detectors, or a Doppler
+ * shift above 2.9 bins), CUDA. */
 tcw_status tcw_triage_features(tcw_ctx *ctx, int patch_size, float psi_lo, float psi_hi,
                                float *feat_out, float *psi_out, int out_flags);
 

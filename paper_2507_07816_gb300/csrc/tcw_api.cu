@@ -98,8 +98,9 @@ tcw_status prepare_sky(tcw_ctx* c) {
   std::vector<int32_t> perm(S);
   std::iota(perm.begin(), perm.end(), 0);
   std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
+  c->lanes = c->opt_lanes ? c->opt_lanes : choose_lanes(S);
   c->NG = (int)((S + kGroupSkies - 1) / kGroupSkies);
-  c->Spad = (int)(((int64_t)c->NG + kGroupLanes - 1) / kGroupLanes) * kSkyPad;
+  c->Spad = padded_skies(S, c->lanes);
   c->NGpad = c->Spad / kGroupSkies;
   std::vector<double> ns((size_t)c->Spad * 3);
   std::vector<int32_t> pos(S);
@@ -142,7 +143,7 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
   int launches = 0;
 
   if (kernel == TCW_KERNEL_GROUP) {
-    const size_t blkn = (size_t)(c->Spad / kSkyPad) * c->Nseg * c->D * kBlockWords;
+    const size_t blkn = (size_t)(c->Spad / chunk_skies(c->lanes)) * c->Nseg * c->D * block_words(c->lanes);
     TCW_CUDA(c, c->dq.ensure(blkn * sizeof(int32_t)), "doppler table");
     DopplerParams dp{};
     dp.vel = c->vel.as<double>();
@@ -152,6 +153,7 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
     dp.Spad = c->Spad;
     dp.NG = c->NG;
     dp.group = kGroupSkies;
+    dp.lanes = c->lanes;
     dp.inv_q = pl.inv_q;
     dp.blk = c->dq.as<int32_t>();
     dp.spread_max = reinterpret_cast<unsigned*>(c->flags.as<char>() + 16);
@@ -172,18 +174,19 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
   if (kernel == TCW_KERNEL_GROUP) {
     const int tile_shift = ilog2(c->tile_segments);
     const int n_tiles = (int)((c->Nseg + c->tile_segments - 1) / c->tile_segments);
-    const int n_chunks = c->Spad / kSkyPad;
+    const int n_chunks = c->Spad / chunk_skies(c->lanes);
+    const int ptmpl = pass_templates(c->lanes);
     if (c->grid == 0) TCW_CUDA(c, group_grid(&c->grid), "device query");
-    const int64_t key[4] = {n_chunks, c->Bpad, c->bank_chunk, c->grid};
-    if (!std::equal(key, key + 4, c->items_key)) {
-      // bank chunks of bank_chunk groups of 8 templates x sky chunks, spread evenly over the CTAs
+    const int64_t key[5] = {n_chunks, c->Bpad, c->bank_chunk, c->grid, c->lanes};
+    if (!std::equal(key, key + 5, c->items_key)) {
+      // bank chunks of bank_chunk template groups x sky chunks, spread evenly over the CTAs
       std::vector<int4> items;
       std::vector<int64_t> cost;
-      const int groups = c->Bpad / kGroupTmplPerCta;
+      const int groups = c->Bpad / ptmpl;
       for (int g0 = 0; g0 < groups; g0 += c->bank_chunk)
         for (int ch = 0; ch < n_chunks; ++ch) {
           const int ng = std::min(c->bank_chunk, groups - g0);
-          items.push_back(make_int4(0, ch, g0 * kGroupTmplPerCta, ng));
+          items.push_back(make_int4(0, ch, g0 * ptmpl, ng));
           cost.push_back((int64_t)ng * c->Nseg);
         }
       std::vector<int4> order;
@@ -195,7 +198,7 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
       TCW_CUDA(c, cudaMemcpyAsync(c->items.as<char>() + ib, cta.data(), cb, cudaMemcpyHostToDevice, c->stream),
                "schedule");
       TCW_CUDA(c, cudaStreamSynchronize(c->stream), "schedule");
-      std::copy(key, key + 4, c->items_key);
+      std::copy(key, key + 5, c->items_key);
       c->n_items = (int)order.size();
     }
     TCW_CUDA(c, c->dev.ensure(group_dev_elems(c->grid) * sizeof(float2)), "scratch");
@@ -249,6 +252,7 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
     gp.tile_shift = tile_shift;
     gp.B = (int)c->B;
     gp.Bpad = c->Bpad;
+    gp.lanes = c->lanes;
     gp.dev = c->dev.as<float2>();
     gp.rec = rec_dev;
     gp.bank_perm = c->bank_perm.as<int32_t>();
@@ -327,11 +331,13 @@ tcw_status finish(tcw_ctx* c) {
 tcw_status run_coarse(tcw_ctx* c, int patch_size, float lo, float hi, bool keep_psi, int* P_out) {
   if (!c->have_spec || !c->have_vel || !c->have_bank || !c->have_sky)
     return fail(c, TCW_ERR_STATE, "inputs not loaded");
-  if (c->D > 8) return fail(c, TCW_ERR_UNSUPPORTED, "coarse pass handles at most 8 detectors");
+  if (c->D > 2) return fail(c, TCW_ERR_UNSUPPORTED, "coarse pass handles at most 2 detectors");
   tcw_status st = prepare_sky(c);
   if (st != TCW_OK) return st;
+  const Plan pl = make_plan(c);
+  if (pl.doppler_bins > 2.9) return fail(c, TCW_ERR_UNSUPPORTED, "coarse pass: Doppler shift exceeds 2.9 bins");
   const int P = (int)((c->S + patch_size - 1) / patch_size);
-  const int tile = 64;
+  const int tile = 32;
   const int n_tiles = (int)((c->Nseg + tile - 1) / tile);
   double tau_min = INFINITY, r_max = 0;
   for (size_t b = 0; b < c->h_tau.size(); ++b) {
@@ -364,7 +370,7 @@ tcw_status run_coarse(tcw_ctx* c, int patch_size, float lo, float hi, bool keep_
     ap.T0 = c->T0;
     ap.n_seg = (int)c->Nseg;
     ap.n_tiles = n_tiles;
-    ap.tile_shift = 6;
+    ap.tile_shift = 5;
     ap.Bpad = c->Bpad;
     ap.anchors = c->tri_anchor.as<double>();
     TCW_CUDA(c, launch_anchors(ap, c->stream), "anchor_kernel launch");
@@ -491,6 +497,12 @@ tcw_status tcw_set_option(tcw_ctx* c, int option, int64_t value) {
       if (value < 1 || value > 4096) return fail(c, TCW_ERR_INVALID_ARGUMENT, "bank_chunk must be in [1, 4096]");
       c->bank_chunk = (int)value;
       return TCW_OK;
+    case TCW_OPT_SKY_LANES:
+      if (value != 0 && value != 16 && value != 32 && value != 64)
+        return fail(c, TCW_ERR_INVALID_ARGUMENT, "sky lanes must be 0, 16, 32 or 64");
+      c->opt_lanes = (int)value;
+      c->sky_dirty = true;
+      return TCW_OK;
     case TCW_OPT_AUTOTUNE:
       c->autotune = value ? 1 : 0;
       return TCW_OK;
@@ -595,7 +607,7 @@ tcw_status tcw_define_bank(tcw_ctx* c, int64_t n_tmpl, const double* f0, const d
   std::vector<int32_t> perm(n_tmpl);
   std::iota(perm.begin(), perm.end(), 0);
   std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) { return hf[a] < hf[b]; });
-  const int Bpad = (int)((n_tmpl + kGroupTmplPerCta - 1) / kGroupTmplPerCta) * kGroupTmplPerCta;
+  const int Bpad = (int)((n_tmpl + kBankAlign - 1) / kBankAlign) * kBankAlign;
   std::vector<double> sf(Bpad), st(Bpad), sn(Bpad);
   std::vector<int32_t> pos(n_tmpl), permp(Bpad);
   for (int i = 0; i < Bpad; ++i) {

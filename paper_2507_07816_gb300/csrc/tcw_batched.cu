@@ -62,6 +62,7 @@ struct BatchState {
   bool planned = false;
   double q = 0, inv_q = 0, doppler_bins = 0;
   int nterms = 0, tile = 32, bank_chunk = 1, grid = 0, waves = 1;
+  int lanes = 64;                  // sky groups per chunk of the group kernel
   std::vector<int> wave_items;     // item offset of each wave in `items`, plus the end
   std::vector<int> wave_cta;       // offset (in ints) of each wave's CTA table
   int64_t lookups = 0;
@@ -140,6 +141,7 @@ tcw_status plan_batch(tcw_ctx* c, BatchState* b) {
     dp.Spad = e.Spad;
     dp.NG = e.NG;
     dp.group = kGroupSkies;
+    dp.lanes = b->lanes;
     dp.inv_q = b->inv_q;
     dp.blk = at<int32_t>(b->blk, e.o_blk);
     dp.spread_max = at<unsigned>(b->flags, 64 + 4 * i);
@@ -230,7 +232,8 @@ void wave_items(const tcw_ctx* c, const BatchState* b, int w, int bank_chunk, in
                 std::vector<int4>& order, std::vector<int>& cta, int64_t* sums) {
   std::vector<int4> items;
   std::vector<int64_t> cost;
-  const int groups = std::min(groups_limit, c->Bpad / kGroupTmplPerCta);
+  const int ptmpl = pass_templates(b->lanes), chunk = chunk_skies(b->lanes);
+  const int groups = std::min(groups_limit, c->Bpad / ptmpl);
   *sums = 0;
   for (size_t i = 0; i < b->ev.size(); ++i) {
     const EventHost& e = b->ev[i];
@@ -238,10 +241,10 @@ void wave_items(const tcw_ctx* c, const BatchState* b, int w, int bank_chunk, in
     for (int g0 = 0; g0 < groups; g0 += bank_chunk)
       for (int ch = 0; ch < e.n_chunks; ++ch) {
         const int ng = std::min(bank_chunk, groups - g0);
-        items.push_back(make_int4((int)i, ch, g0 * kGroupTmplPerCta, ng));
+        items.push_back(make_int4((int)i, ch, g0 * ptmpl, ng));
         cost.push_back((int64_t)ng * e.n_seg);
-        const int64_t skies = std::min<int64_t>(kSkyPad, e.n_sky - (int64_t)ch * kSkyPad);
-        *sums += (int64_t)ng * kGroupTmplPerCta * skies * b->D * e.n_seg;
+        const int64_t skies = std::min<int64_t>(chunk, e.n_sky - (int64_t)ch * chunk);
+        *sums += (int64_t)ng * ptmpl * skies * b->D * e.n_seg;
       }
   }
   schedule_items(items, cost, b->grid, order, cta);
@@ -263,6 +266,7 @@ GroupParams base_params(const tcw_ctx* c, BatchState* b, int tile, int nterms) {
   gp.tile_shift = ilog2(tile);
   gp.B = (int)c->B;
   gp.Bpad = c->Bpad;
+  gp.lanes = b->lanes;
   gp.dev = b->dev.as<float2>();
   gp.bank_perm = c->bank_perm.as<int32_t>();
   gp.n_general = at<unsigned long long>(b->flags, 8);
@@ -346,7 +350,7 @@ GroupParams wave_params(const tcw_ctx* c, BatchState* b, int w, int tile, int nt
 // candidate with the highest sums/s wins, ties going to the earlier one.
 tcw_status autotune(tcw_ctx* c, BatchState* b) {
   const auto t0 = std::chrono::steady_clock::now();
-  const int groups = c->Bpad / kGroupTmplPerCta;
+  const int groups = c->Bpad / pass_templates(b->lanes);
   const int probe_groups = std::min(groups, std::max(64, groups / 32));
   const int chunks[] = {1, 8, 64};
   const int tiles[] = {32, 16, 64};
@@ -423,7 +427,7 @@ tcw_status capture(tcw_ctx* c, BatchState* b, int k) {
   if ((st = upload_items(c, b, b->bank_chunk, INT32_MAX, &sums)) != TCW_OK) return st;
   TCW_CUDA(c, b->out_psi.ensure((size_t)b->total_sky * k * sizeof(float)), "output");
   TCW_CUDA(c, b->out_idx.ensure((size_t)b->total_sky * k * sizeof(int64_t)), "output");
-  TCW_CUDA(c, group_prepare(b->D, b->dtype == TCW_F16, !b->unit_weights), "group_kernel attributes");
+  TCW_CUDA(c, group_prepare(b->D, b->lanes, b->dtype == TCW_F16, !b->unit_weights), "group_kernel attributes");
   TCW_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "graph capture");
   cudaError_t err = cudaMemsetAsync(b->flags.p, 0, 64, c->stream);
   int nodes = 0;
@@ -437,6 +441,7 @@ tcw_status capture(tcw_ctx* c, BatchState* b, int k) {
     dp.Spad = e.Spad;
     dp.NG = e.NG;
     dp.group = kGroupSkies;
+    dp.lanes = b->lanes;
     dp.inv_q = b->inv_q;
     dp.blk = at<int32_t>(b->blk, e.o_blk);
     dp.spread_max = at<unsigned>(b->flags, 64 + 4 * i);
@@ -504,6 +509,21 @@ tcw_status tcw_load_events(tcw_ctx* c, int n_det, int64_t n_bin, int dtype, doub
   b->df = df;
   const size_t esz = dtype == TCW_F16 ? 2 : 4;
   size_t rho_bytes = 0, small_bytes = 0, blk_bytes = 0;
+  // chunk width: the option, else the fewest padded sky-segment lookups over the batch
+  b->lanes = c->opt_lanes;
+  if (!b->lanes) {
+    double best = -1;
+    for (int l : {64, 32, 16}) {
+      double cost = 0;
+      for (int i = 0; i < n_events; ++i)
+        cost += (double)padded_skies(std::max<int64_t>(events[i].n_sky, 1), l) *
+                (double)std::max<int64_t>(events[i].n_seg, 1) * lanes_cost(l);
+      if (best < 0 || cost < best) {
+        best = cost;
+        b->lanes = l;
+      }
+    }
+  }
   std::vector<std::vector<double>> nhat_sorted(n_events);
   std::vector<std::vector<int32_t>> perms(n_events);
   std::vector<std::vector<float>> wts(n_events);
@@ -563,8 +583,8 @@ tcw_status tcw_load_events(tcw_ctx* c, int n_det, int64_t n_bin, int dtype, doub
     std::iota(perm.begin(), perm.end(), 0);
     std::stable_sort(perm.begin(), perm.end(), [&](int32_t x, int32_t y) { return key[x] < key[y]; });
     e.NG = (int)((in.n_sky + kGroupSkies - 1) / kGroupSkies);
-    e.Spad = (int)(((int64_t)e.NG + kGroupLanes - 1) / kGroupLanes) * kSkyPad;
-    e.n_chunks = e.Spad / kSkyPad;
+    e.Spad = padded_skies(in.n_sky, b->lanes);
+    e.n_chunks = e.Spad / chunk_skies(b->lanes);
     std::vector<double> ns((size_t)e.Spad * 3);
     for (int s = 0; s < e.Spad; ++s) {
       const int32_t src = perm[std::min<int64_t>(s, in.n_sky - 1)];
@@ -589,7 +609,7 @@ tcw_status tcw_load_events(tcw_ctx* c, int n_det, int64_t n_bin, int dtype, doub
     e.o_perm = small_bytes;
     small_bytes += align256((size_t)e.Spad * 4);
     e.o_blk = blk_bytes;
-    blk_bytes += align256((size_t)e.n_chunks * in.n_seg * n_det * kBlockWords * 4);
+    blk_bytes += align256((size_t)e.n_chunks * in.n_seg * n_det * block_words(b->lanes) * 4);
     b->ev.push_back(std::move(e));
   }
   if (b->D > kMaxStageDet) {

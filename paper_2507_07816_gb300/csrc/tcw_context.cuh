@@ -44,7 +44,8 @@ struct tcw_ctx {
   int opt_kernel = TCW_KERNEL_AUTO;
   int keep_stats = 0;
   int tile_segments = 32;
-  int bank_chunk = 1;      // groups of 8 templates per work item
+  int bank_chunk = 1;      // template groups (of one pass each) per work item
+  int opt_lanes = 0;       // sky groups per chunk: 0 = the fewest padded skies, else 16/32/64
   int autotune = 1;        // batched search: pick bank_chunk and tile_segments by timing
   int64_t batch_memory = (int64_t)48 << 30;  // batched search: Psi + anchor bytes per wave
   unsigned bank_epoch = 0; // bumped by every tcw_define_bank
@@ -71,13 +72,13 @@ struct tcw_ctx {
   // sky
   bool have_sky = false;
   int64_t S = 0;
-  int Spad = 0, NG = 0, NGpad = 0;
+  int Spad = 0, NG = 0, NGpad = 0, lanes = 64;
   std::vector<double> h_nhat;
   bool sky_dirty = true;
   tcw::DevBuf nhat_sorted, sky_perm, sky_pos;
   // derived and outputs
   tcw::DevBuf dq, anchors, psi, st_S, st_W1, st_W2, dev, flags, stage_f, stage_i, evtab, items;
-  int64_t items_key[4] = {-1, -1, -1, -1};  // (n_chunks, Bpad, bank_chunk, grid) of the uploaded schedule
+  int64_t items_key[5] = {-1, -1, -1, -1, -1};  // (n_chunks, Bpad, bank_chunk, grid, lanes) of the schedule
   int grid = 0, n_items = 0;
   bool have_result = false, stats_kept = false;
   tcw_info info{};

@@ -74,7 +74,7 @@ struct EventDesc {
   const void* rho;         // [D][n_seg][pitch] float or half, 16-byte aligned base
   const float* weights;    // [D][n_seg]
   const double* t_mid;     // [n_seg]
-  const int32_t* blk;      // Doppler blocks [Spad/1024][n_seg][D][kBlockWords], see kBlockWords
+  const int32_t* blk;      // Doppler blocks [Spad / (16 lanes)][n_seg][D][block_words(lanes)]
   const double* anchors;   // [Bpad][n_tiles][2]: 1/f and 1/(tau + t_a - T0) at each tile's
                            // anchor t_a; read only when nterms > 0
   float* psi;              // [Spad][Bpad]
@@ -86,8 +86,8 @@ struct EventDesc {
   int n_seg, n_tiles, S, Spad, NG, pad_;
 };
 
-// Work item of the group kernel: one sky chunk of 1024 sorted directions of
-// one event x `groups` consecutive groups of 8 sorted templates.
+// Work item of the group kernel: one sky chunk of 16 lanes sorted directions
+// of one event x `groups` consecutive groups of 512 / lanes sorted templates.
 //   x = event, y = sky chunk, z = first sorted template, w = groups
 // CTA i runs items [cta_items[i], cta_items[i + 1]) in order.
 struct GroupParams {
@@ -104,7 +104,8 @@ struct GroupParams {
   int nterms;              // binomial-series length for the track; 0 = pow per entry
   int tile_shift;          // tiles of 2^tile_shift segments: anchors and fp32 partial sums
   int B, Bpad;
-  float2* dev;             // scratch [gridDim.x][8][1024]: per-sky weight sums at band edges
+  int lanes;               // sky groups per chunk: 16, 32 or 64
+  float2* dev;             // scratch [gridDim.x][8192]: per-sky weight sums at band edges
   int32_t* rec;            // optional [S][B][D][Nseg], caller order (single-event searches)
   const int32_t* bank_perm;  // sorted -> caller template index
   const int32_t* sky_perm;   // sorted -> caller sky index (event 0)
@@ -146,18 +147,20 @@ struct LookupParams {
   const int32_t* sky_perm;
 };
 
-// One Doppler block per (sky chunk of 1024 sorted skies, segment, detector):
-//   words [0, 1024): floor(v.nhat/c / q) of sky 16 g + 4 v + k at (v * 64 + g) * 4 + k
-//   words [1024, 1088): fp32 mid-range of v.nhat/c over sky group g (bits)
+// One Doppler block per (sky chunk of 16 L sorted skies, segment, detector),
+// L = lanes (sky groups) per chunk:
+//   words [0, 16 L): floor(v.nhat/c / q) of sky 16 g + 4 v + k at (v L + g) * 4 + k
+//   words [16 L, 17 L): fp32 mid-range of v.nhat/c over sky group g (bits)
 // so that one bulk copy moves a chunk's segment for every detector.
-constexpr int kBlockWords = 1088;
+__host__ __device__ constexpr int block_words(int lanes) { return 17 * lanes; }
 
 struct DopplerParams {
   const double* vel;       // [D][Nseg][3]
   const double* nhat;      // [Spad][3] sorted
   int n_det, n_seg, Spad, NG, group;
+  int lanes;               // sky groups per chunk (16, 32 or 64)
   double inv_q;
-  int32_t* blk;            // [Spad/1024][Nseg][D][kBlockWords]
+  int32_t* blk;            // [Spad / (16 lanes)][Nseg][D][block_words(lanes)]
   unsigned* spread_max;    // float bits of max (hi - lo) of v.nhat/c over the groups
 };
 
@@ -166,7 +169,7 @@ constexpr int kMaxStageDet = 2;          // detectors the group kernel stages in
 constexpr int kTileShift = 5;           // default tile: 32 segments
 
 // dynamic shared memory of the group kernel for D detectors
-size_t group_smem_bytes(int n_det);
+size_t group_smem_bytes(int n_det, int lanes);
 cudaError_t launch_anchors(const AnchorParams& p, cudaStream_t st);
 // per-CTA scratch of the group kernel, in float2 elements
 size_t group_dev_elems(int grid);
@@ -211,7 +214,7 @@ struct CoarseParams {
   const double* tau;
   const double* nbr;
   int B, Bpad;              // Bpad a multiple of 4
-  const double* anchors;    // [Bpad][n_tiles][2] at 64-segment tiles, or null when nterms == 0
+  const double* anchors;    // [Bpad][n_tiles][2] at 32-segment tiles, or null when nterms == 0
   int n_tiles, nterms;
   float lo, hi;             // histogram range of Psi
   float* psi;               // optional [P][Bpad]
@@ -257,7 +260,7 @@ inline int ilog2(int v) {
 cudaError_t launch_doppler(const DopplerParams& p, cudaStream_t st);
 // Set the shared-memory attribute of the group-kernel variant (also done by
 // launch_group on first use); call before capturing a launch into a graph.
-cudaError_t group_prepare(int n_det, bool half, bool weighted);
+cudaError_t group_prepare(int n_det, int lanes, bool half, bool weighted);
 // grid = number of CTAs (the length of p.cta_items minus one); one CTA per SM at most
 cudaError_t launch_group(const GroupParams& p, int grid, bool half, bool record, bool weighted,
                          cudaStream_t st);
@@ -269,13 +272,27 @@ cudaError_t launch_unpermute(const float* src, int Spad, int Bpad, int S, int B,
                              const int32_t* sky_pos, const int32_t* bank_pos, float* dst,
                              cudaStream_t st);
 
-// group-kernel geometry (shared by the host planner and the kernel)
+// group-kernel geometry (shared by the host planner and the kernels): a sky
+// chunk is `lanes` groups of kGroupSkies sorted skies (lanes = 16, 32 or 64),
+// and one pass of the kernel covers one chunk x 512 / lanes templates.
 constexpr int kGroupSkies = 16;     // skies per thread
-constexpr int kGroupTmpl = 2;       // templates per thread
-constexpr int kGroupUnits = 4;      // template pairs per work item
-constexpr int kGroupWarps = 2;      // warps per unit
-constexpr int kGroupLanes = 32 * kGroupWarps;             // sky groups per CTA
-constexpr int kGroupTmplPerCta = kGroupUnits * kGroupTmpl;  // 8 templates per work item
-constexpr int kSkyPad = kGroupSkies * kGroupLanes;        // 1024
+constexpr int kBankAlign = 32;      // Bpad is a multiple of every pass's template count
+__host__ __device__ constexpr int chunk_skies(int lanes) { return kGroupSkies * lanes; }
+__host__ __device__ constexpr int pass_templates(int lanes) { return 512 / lanes; }
+inline int padded_skies(int64_t S, int lanes) {
+  const int64_t ng = (S + kGroupSkies - 1) / kGroupSkies;
+  return (int)((ng + lanes - 1) / lanes) * chunk_skies(lanes);
+}
+// Relative cost of one padded (template, sky, segment) at each chunk width:
+// a narrow chunk computes the track entries of 4x (2x) more templates per
+// stage for the same number of lookups (measured on GB300 at 1e4 segments).
+inline double lanes_cost(int lanes) { return lanes == 16 ? 1.6 : (lanes == 32 ? 1.25 : 1.0); }
+// The chunk width with the lowest padded cost (ties: the widest chunk).
+inline int choose_lanes(int64_t S) {
+  int best = 64;
+  for (int l : {32, 16})
+    if (padded_skies(S, l) * lanes_cost(l) < padded_skies(S, best) * lanes_cost(best)) best = l;
+  return best;
+}
 
 }  // namespace tcw

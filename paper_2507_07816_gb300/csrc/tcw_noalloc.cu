@@ -124,9 +124,11 @@ extern "C" tcw_status tcw_search_noalloc(int n_det, int64_t n_seg, int64_t n_bin
 
   // Scratch layout (every region 256-byte aligned).
   const int B = (int)n_tmpl, S = (int)n_sky, D = n_det, Nseg = (int)n_seg;
-  const int Bpad = (B + kGroupTmplPerCta - 1) / kGroupTmplPerCta * kGroupTmplPerCta;
+  constexpr int kLanes = 64;   // sky groups per chunk of the group kernel
+  const int ptmpl = pass_templates(kLanes);
+  const int Bpad = (B + ptmpl - 1) / ptmpl * ptmpl;
   const int NG = (S + kGroupSkies - 1) / kGroupSkies;
-  const int NGpad = (NG + kGroupLanes - 1) / kGroupLanes * kGroupLanes;
+  const int NGpad = (NG + kLanes - 1) / kLanes * kLanes;
   const int Spad = NGpad * kGroupSkies;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -139,11 +141,11 @@ extern "C" tcw_status tcw_search_noalloc(int n_det, int64_t n_seg, int64_t n_bin
   const size_t o_bperm = take((size_t)Bpad * 4), o_sperm = take((size_t)Spad * 4);
   const size_t o_nhat = take((size_t)Spad * 24);
   const size_t o_ones = take(weights ? 0 : (size_t)D * Nseg * 4);
-  const size_t o_dq = take((size_t)(Spad / kSkyPad) * Nseg * D * kBlockWords * 4);
+  const size_t o_dq = take((size_t)(Spad / chunk_skies(kLanes)) * Nseg * D * block_words(kLanes) * 4);
   const size_t o_psi = take((size_t)Spad * Bpad * 4);
   int grid = 0;
   if (group_grid(&grid) != cudaSuccess) return TCW_ERR_CUDA;
-  const int n_chunks = Spad / kSkyPad, n_groups = Bpad / kGroupTmplPerCta;
+  const int n_chunks = Spad / chunk_skies(kLanes), n_groups = Bpad / ptmpl;
   const int64_t n_items = (int64_t)n_chunks * n_groups;
   const size_t o_dev = take(group_dev_elems(grid) * 8);
   const size_t o_ev = take(sizeof(EventDesc));
@@ -222,6 +224,7 @@ extern "C" tcw_status tcw_search_noalloc(int n_det, int64_t n_seg, int64_t n_bin
   dp.Spad = Spad;
   dp.NG = NG;
   dp.group = kGroupSkies;
+  dp.lanes = kLanes;
   dp.inv_q = std::ldexp(1.0, -e);
   dp.blk = reinterpret_cast<int32_t*>(base + o_dq);
   dp.spread_max = reinterpret_cast<unsigned*>(base + o_flags + 32);
@@ -257,7 +260,7 @@ extern "C" tcw_status tcw_search_noalloc(int n_det, int64_t n_seg, int64_t n_bin
     items.reserve(n_items);
     for (int g = 0; g < n_groups; ++g)
       for (int ch = 0; ch < n_chunks; ++ch) {
-        items.push_back(make_int4(0, ch, g * kGroupTmplPerCta, 1));
+        items.push_back(make_int4(0, ch, g * ptmpl, 1));
         cost.push_back(Nseg);
       }
     std::vector<int4> order;
@@ -288,6 +291,7 @@ extern "C" tcw_status tcw_search_noalloc(int n_det, int64_t n_seg, int64_t n_bin
     gp.tile_shift = kTileShift;
     gp.B = B;
     gp.Bpad = Bpad;
+    gp.lanes = kLanes;
     gp.dev = reinterpret_cast<float2*>(base + o_dev);
     gp.bank_perm = pp.bank_perm;
     gp.sky_perm = pp.sky_perm;

@@ -1,17 +1,19 @@
 // tcw_persist.cu -- the hot loop: a persistent, warp-specialised group kernel.
 //
 // One CTA per SM runs its list of work items in order; an item is one chunk
-// of 1024 sorted sky directions of one event x a run of groups of 8 sorted
-// templates, and each group of 8 templates (a "pass") streams every segment
-// and detector of the event through shared memory:
+// of 16 L sorted sky directions of one event (L = 16, 32 or 64 sky groups of
+// 16) x a run of template groups, and each group of 512 / L sorted templates
+// (a "pass") streams every segment and detector of the event through shared
+// memory:
 //
-//   producer warps (3)   warp w owns every third batch of 4 segments of the
-//                        CTA's pass sequence: the 8 x 4 track entries in FP64
-//                        (Eq. 1, one lane per entry, from the tile anchors of
-//                        anchor_kernel), their 64-byte power windows (16-byte
-//                        async copies), the segment weights, and one bulk copy
-//                        of the chunk's Doppler blocks per segment (Eq. 2
-//                        factor on the fixed-point grid) into a 16-stage ring
+//   producer warps (3-4) warp w owns every third (fourth) batch of the CTA's
+//                        pass sequence, one lane per (template, segment) of
+//                        the batch: the track entry in FP64 (Eq. 1, from the
+//                        tile anchors of anchor_kernel), its 64-byte power
+//                        windows (16-byte async copies), the segment weights,
+//                        and one bulk copy of the chunk's Doppler blocks per
+//                        segment (Eq. 2 factor on the fixed-point grid) into
+//                        a 16-stage ring
 //   consumer warps (8)   per segment: for each detector and each of two
 //                        templates, the candidate bin pair of the lane's
 //                        16-sky group, two window reads, and per sky one int32
@@ -35,26 +37,38 @@
 namespace tcw {
 namespace {
 
-constexpr int kPT = kGroupTmplPerCta;             // templates per work item
 constexpr int kConsumerWarps = 8;
-constexpr int kConsumers = kConsumerWarps * 32;   // 4 template pairs x 64 sky groups
-constexpr int kProducerWarps = 3;
-constexpr int kThreads = kConsumers + kProducerWarps * 32;
-constexpr int kBatch = 32 / kPT;                  // segments per producer batch (one lane per entry)
+constexpr int kConsumers = kConsumerWarps * 32;   // template pairs x sky groups of one pass
 constexpr int kRing = 16;                         // ring stages
-static_assert(kPT == 8 && kBatch == 4, "geometry");
-static_assert(kConsumers == (kPT / 2) * kGroupLanes, "two templates per consumer thread");
-static_assert(kRing >= (kProducerWarps + 1) * kBatch, "every producer's batch fits the ring");
+// producer warps: narrow chunks compute more track entries per stage
+__host__ __device__ constexpr int producer_warps(int lanes) { return lanes == 64 ? 3 : 4; }
+
+// Geometry of a pass for LN sky groups per chunk (LN = 16, 32 or 64): the
+// consumers are kConsumers / LN units (template pairs) x LN lanes (sky groups
+// of 16), so a pass covers 512 / LN templates x 16 LN skies; a producer batch
+// is one lane per (template, segment).
+template <int LN>
+struct Geo {
+  static constexpr int kPT = 2 * kConsumers / LN;          // templates per pass
+  static constexpr int kBatch = 32 / kPT;                  // segments per producer batch
+  static constexpr int kChunk = kGroupSkies * LN;          // skies per chunk
+  static constexpr int kDetBytes = 4 * block_words(LN);    // one Doppler block per detector
+  static constexpr int kProd = producer_warps(LN);
+  static constexpr int kThreads = kConsumers + 32 * kProd;
+  static_assert(kPT >= 8 && kPT <= 32 && kBatch * kPT == 32, "geometry");
+  static_assert(kRing >= (kProd + 1) * kBatch, "every producer's batch fits the ring");
+};
 
 struct PersistLayout {
   size_t ent, win, hdr, stage, coef, bar, total;
-  __host__ __device__ explicit PersistLayout(int D) {
-    ent = (size_t)D * kStageDetBytes;                 // Doppler blocks first (bulk-copy target)
-    win = ent + (size_t)kPT * sizeof(TrackEntry);
-    hdr = win + (size_t)kPT * D * kWinBytes;          // segment weight of each detector
+  __host__ __device__ PersistLayout(int D, int lanes) {
+    const int pt = 2 * kConsumers / lanes;
+    ent = (size_t)D * 4 * block_words(lanes);         // Doppler blocks first (bulk-copy target)
+    win = ent + (size_t)pt * sizeof(TrackEntry);
+    hdr = win + (size_t)pt * D * kWinBytes;           // segment weight of each detector
     stage = (hdr + 16 + 127) & ~(size_t)127;
     coef = stage * kRing;
-    bar = coef + (size_t)kProducerWarps * kPT * kMaxSeriesTerms * 8;
+    bar = coef + (size_t)producer_warps(lanes) * pt * kMaxSeriesTerms * 8;
     total = bar + (size_t)2 * kRing * 8;
   }
 };
@@ -152,13 +166,16 @@ __device__ __forceinline__ void compute_entry(const GroupParams& p, const EventD
   }
 }
 
-template <typename RhoT, bool RECORD, bool WEIGHTED, int DT>
-__global__ void __launch_bounds__(kThreads, 1) group_kernel(GroupParams p) {
+template <typename RhoT, bool RECORD, bool WEIGHTED, int DT, int LN>
+__global__ void __launch_bounds__(Geo<LN>::kThreads, 1) group_kernel(GroupParams p) {
   constexpr int G = kGroupSkies;
   constexpr uint32_t ESZ = sizeof(RhoT);
+  constexpr int kPT = Geo<LN>::kPT, kBatch = Geo<LN>::kBatch, kChunk = Geo<LN>::kChunk;
+  constexpr int kStageDetBytes = Geo<LN>::kDetBytes, kBlockWords = block_words(LN);
+  constexpr int kProducerWarps = Geo<LN>::kProd;
   extern __shared__ __align__(128) unsigned char smem[];
   const int D = DT > 0 ? DT : p.n_det;
-  const PersistLayout L(D);
+  const PersistLayout L(D, LN);
   const uint32_t smem0 = smem_addr(smem);
   const uint32_t bar_full = smem0 + (uint32_t)L.bar;
   const uint32_t bar_empty = bar_full + kRing * 8;
@@ -255,8 +272,8 @@ __global__ void __launch_bounds__(kThreads, 1) group_kernel(GroupParams p) {
   }
 
   // ======================= consumer warps =======================
-  const int u = tid / kGroupLanes, l = tid % kGroupLanes;  // template pair, sky group in the chunk
-  float2* const dev_cta = p.dev + (int64_t)blockIdx.x * kPT * kSkyPad;
+  const int u = tid / LN, l = tid % LN;  // template pair, sky group in the chunk
+  float2* const dev_cta = p.dev + (int64_t)blockIdx.x * kPT * kChunk;
   unsigned long long ngen = 0;
   long long q = 0;
   bool ok = true;
@@ -264,7 +281,7 @@ __global__ void __launch_bounds__(kThreads, 1) group_kernel(GroupParams p) {
     const int4 item = p.items[it];
     const EventDesc ev = p.events[item.x];
     const int n_seg = ev.n_seg;
-    const int g = item.y * kGroupLanes + l;
+    const int g = item.y * LN + l;
     const bool gval = g < ev.NG;
     const int s0 = g * G;
     for (int tg = 0; tg < item.w && ok; ++tg) {
@@ -298,7 +315,7 @@ __global__ void __launch_bounds__(kThreads, 1) group_kernel(GroupParams p) {
           for (int d = 0; d < D; ++d) {
             const float wd = WEIGHTED ? (d == 0 ? wseg.x : wseg.y) : 1.0f;
             const uint32_t sd = stage + d * kStageDetBytes;
-            const float gm = lds_f32(sd - l * 16 + 4 * kGroupLanes * 16 + l * 4);
+            const float gm = lds_f32(sd - l * 16 + 4 * LN * 16 + l * 4);
             int th0 = INT_MAX, th1 = INT_MAX;
             float dw0 = 0.f, dw1 = 0.f;
             const int zb0 = __float_as_int(fmaf(h0.x, gm, h0.y) + kMagic);
@@ -325,7 +342,7 @@ __global__ void __launch_bounds__(kThreads, 1) group_kernel(GroupParams p) {
             }
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
-              const int4 qv = lds_v4(sd + v * kGroupLanes * 16);
+              const int4 qv = lds_v4(sd + v * LN * 16);
               pred_add(acc[0][4 * v + 0], qv.x, th0, dw0);
               pred_add(acc[1][4 * v + 0], qv.x, th1, dw1);
               pred_add(acc[0][4 * v + 1], qv.y, th0, dw0);
@@ -359,7 +376,7 @@ __global__ void __launch_bounds__(kThreads, 1) group_kernel(GroupParams p) {
                 if (c == kEntryInside) {
                   if (RECORD && rp)
                     for (int k = 0; k < G; ++k) {
-                      const int qk = (int)lds_u32(sd + (k >> 2) * kGroupLanes * 16 + (k & 3) * 4);
+                      const int qk = (int)lds_u32(sd + (k >> 2) * LN * 16 + (k & 3) * 4);
                       if (s0 + k < ev.S) rp[(int64_t)p.sky_perm[s0 + k] * rstride] = K0 + (qk >= th ? 1 : 0);
                     }
                   continue;
@@ -370,14 +387,14 @@ __global__ void __launch_bounds__(kThreads, 1) group_kernel(GroupParams p) {
                 const float rlo = vlo ? lds_pow(a, RhoT()) : 0.f;
                 const float rhi = vhi ? lds_pow(a + ESZ, RhoT()) : 0.f;
                 ++ngen;
-                float2* dvp = dev_cta + (2 * u + t) * kSkyPad + l * G;
+                float2* dvp = dev_cta + (2 * u + t) * kChunk + l * G;
                 if (!(touched & (1u << t))) {
                   touched |= 1u << t;
                   for (int k = 0; k < G; ++k) dvp[k] = make_float2(0.f, 0.f);
                 }
 #pragma unroll
                 for (int k = 0; k < G; ++k) {
-                  const int qk = (int)lds_u32(sd + (k >> 2) * kGroupLanes * 16 + (k & 3) * 4);
+                  const int qk = (int)lds_u32(sd + (k >> 2) * LN * 16 + (k & 3) * 4);
                   const bool up = qk >= th;
                   const bool okb = up ? vhi : vlo;
                   if (RECORD && rp && s0 + k < ev.S)
@@ -416,7 +433,7 @@ __global__ void __launch_bounds__(kThreads, 1) group_kernel(GroupParams p) {
       for (int t = 0; t < 2; ++t) {
         const int b = b0 + 2 * u + t;
         const double base_num = gw[t] - w1[t];
-        const float2* dvp = dev_cta + (2 * u + t) * kSkyPad + l * G;
+        const float2* dvp = dev_cta + (2 * u + t) * kChunk + l * G;
 #pragma unroll
         for (int k = 0; k < G; ++k) {
           const int sk = s0 + k;
@@ -445,7 +462,8 @@ __global__ void __launch_bounds__(kThreads, 1) group_kernel(GroupParams p) {
 
 }  // namespace
 
-size_t group_smem_bytes(int n_det) { return PersistLayout(n_det).total; }
+size_t group_smem_bytes(int n_det, int lanes) { return PersistLayout(n_det, lanes).total; }
+size_t group_dev_elems(int grid) { return (size_t)grid * 2 * kConsumers * kGroupSkies; }
 
 cudaError_t group_grid(int* grid) {
   int dev = 0, sms = 0;
@@ -503,7 +521,6 @@ int series_terms_for(const double* t_mid, int64_t n_seg, double T0, int tile, do
   }
   return 0;
 }
-size_t group_dev_elems(int grid) { return (size_t)grid * kPT * kSkyPad; }
 
 cudaError_t launch_anchors(const AnchorParams& p, cudaStream_t st) {
   const int64_t total = (int64_t)p.Bpad * p.n_tiles;
@@ -515,7 +532,7 @@ cudaError_t launch_anchors(const AnchorParams& p, cudaStream_t st) {
 
 // The dynamic shared-memory limit of each variant is raised once per device
 // (again when a variant shared by several detector counts needs more).
-template <typename R, bool REC, bool WT, int DT>
+template <typename R, bool REC, bool WT, int DT, int LN>
 cudaError_t set_smem_t(size_t smem) {
   constexpr int kDevices = 64;
   static size_t done[kDevices] = {};
@@ -523,52 +540,73 @@ cudaError_t set_smem_t(size_t smem) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev >= 0 && dev < kDevices && done[dev] >= smem) return cudaSuccess;
-  e = cudaFuncSetAttribute(group_kernel<R, REC, WT, DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(group_kernel<R, REC, WT, DT, LN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem);
   if (e == cudaSuccess && dev >= 0 && dev < kDevices) done[dev] = smem;
   return e;
 }
 
-template <typename R, bool REC, bool WT, int DT>
-cudaError_t launch_group_t(const GroupParams& p, int grid, size_t smem, cudaStream_t st) {
-  cudaError_t e = set_smem_t<R, REC, WT, DT>(smem);
+template <typename R, bool REC, bool WT, int DT, int LN>
+cudaError_t launch_group_t(const GroupParams& p, int grid, cudaStream_t st) {
+  const size_t smem = PersistLayout(p.n_det, LN).total;
+  cudaError_t e = set_smem_t<R, REC, WT, DT, LN>(smem);
   if (e != cudaSuccess) return e;
-  group_kernel<R, REC, WT, DT><<<grid, kThreads, smem, st>>>(p);
+  group_kernel<R, REC, WT, DT, LN><<<grid, Geo<LN>::kThreads, smem, st>>>(p);
   return cudaGetLastError();
 }
 
-template <typename R>
-cudaError_t launch_group_r(const GroupParams& p, bool record, bool weighted, int grid, size_t smem,
-                           cudaStream_t st) {
-  if (record) return launch_group_t<R, true, true, 0>(p, grid, smem, st);
+template <typename R, int LN>
+cudaError_t launch_group_l(const GroupParams& p, bool record, bool weighted, int grid, cudaStream_t st) {
+  if (record) return launch_group_t<R, true, true, 0, LN>(p, grid, st);
   if (weighted) {
-    if (p.n_det == 1) return launch_group_t<R, false, true, 1>(p, grid, smem, st);
-    return launch_group_t<R, false, true, 2>(p, grid, smem, st);
+    if (p.n_det == 1) return launch_group_t<R, false, true, 1, LN>(p, grid, st);
+    return launch_group_t<R, false, true, 2, LN>(p, grid, st);
   }
-  if (p.n_det == 1) return launch_group_t<R, false, false, 1>(p, grid, smem, st);
-  return launch_group_t<R, false, false, 2>(p, grid, smem, st);
+  if (p.n_det == 1) return launch_group_t<R, false, false, 1, LN>(p, grid, st);
+  return launch_group_t<R, false, false, 2, LN>(p, grid, st);
 }
 
 template <typename R>
-cudaError_t prepare_r(int n_det, bool weighted) {
-  const size_t smem = PersistLayout(n_det).total;
-  if (weighted) return n_det == 1 ? set_smem_t<R, false, true, 1>(smem) : set_smem_t<R, false, true, 2>(smem);
-  return n_det == 1 ? set_smem_t<R, false, false, 1>(smem) : set_smem_t<R, false, false, 2>(smem);
+cudaError_t launch_group_r(const GroupParams& p, bool record, bool weighted, int grid, cudaStream_t st) {
+  switch (p.lanes) {
+    case 16: return launch_group_l<R, 16>(p, record, weighted, grid, st);
+    case 32: return launch_group_l<R, 32>(p, record, weighted, grid, st);
+    case 64: return launch_group_l<R, 64>(p, record, weighted, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
-cudaError_t group_prepare(int n_det, bool half, bool weighted) {
+template <typename R, int LN>
+cudaError_t prepare_l(int n_det, bool weighted) {
+  const size_t smem = PersistLayout(n_det, LN).total;
+  if (weighted)
+    return n_det == 1 ? set_smem_t<R, false, true, 1, LN>(smem) : set_smem_t<R, false, true, 2, LN>(smem);
+  return n_det == 1 ? set_smem_t<R, false, false, 1, LN>(smem) : set_smem_t<R, false, false, 2, LN>(smem);
+}
+
+template <typename R>
+cudaError_t prepare_r(int n_det, int lanes, bool weighted) {
+  switch (lanes) {
+    case 16: return prepare_l<R, 16>(n_det, weighted);
+    case 32: return prepare_l<R, 32>(n_det, weighted);
+    case 64: return prepare_l<R, 64>(n_det, weighted);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t group_prepare(int n_det, int lanes, bool half, bool weighted) {
   if (n_det < 1 || n_det > kMaxStageDet) return cudaErrorInvalidValue;
-  return half ? prepare_r<__half>(n_det, weighted) : prepare_r<float>(n_det, weighted);
+  return half ? prepare_r<__half>(n_det, lanes, weighted) : prepare_r<float>(n_det, lanes, weighted);
 }
 
-// Needs 1 <= p.n_det <= kMaxStageDet, and the anchors of launch_anchors when p.nterms > 0.
+// Needs 1 <= p.n_det <= kMaxStageDet, p.lanes in {16, 32, 64}, and the
+// anchors of launch_anchors when p.nterms > 0.
 cudaError_t launch_group(const GroupParams& p, int grid, bool half, bool record, bool weighted,
                          cudaStream_t st) {
   if (p.n_det < 1 || p.n_det > kMaxStageDet) return cudaErrorInvalidValue;
   if (grid <= 0) return cudaSuccess;
-  const size_t smem = PersistLayout(p.n_det).total;
-  return half ? launch_group_r<__half>(p, record, weighted, grid, smem, st)
-              : launch_group_r<float>(p, record, weighted, grid, smem, st);
+  return half ? launch_group_r<__half>(p, record, weighted, grid, st)
+              : launch_group_r<float>(p, record, weighted, grid, st);
 }
 
 }  // namespace tcw

@@ -12,7 +12,6 @@ namespace tcw {
 // Shared-memory staging: mbarriers and bulk asynchronous copies (PTX).
 // ---------------------------------------------------------------------------
 constexpr int kMaxSpin = 1 << 26;              // bound on every mbarrier wait
-constexpr int kStageDetBytes = kBlockWords * 4;  // one Doppler block per detector
 constexpr int kWinBytes = 64;                  // staged power window per (entry, detector)
 
 __device__ __forceinline__ uint32_t smem_addr(const void* ptr) {

@@ -38,16 +38,17 @@ __global__ void doppler_kernel(DopplerParams p) {
     const double* n = p.nhat + (int64_t)s * 3;
     const double dD = (v[0] * n[0] + v[1] * n[1] + v[2] * n[2]) / kLightSpeed;
     const double qd = floor(dD * p.inv_q);
-    const int c = s >> 10, gl = (s >> 4) & 63, sv = (s >> 2) & 3, sk = s & 3;
-    int32_t* blk = p.blk + (((int64_t)c * p.n_seg + j) * p.n_det + d) * kBlockWords;
-    blk[(sv * 64 + gl) * 4 + sk] = (int32_t)fmax(fmin(qd, 2147483647.0), -2147483648.0);
+    const int L = p.lanes;
+    const int c = s / chunk_skies(L), gl = (s >> 4) & (L - 1), sv = (s >> 2) & 3, sk = s & 3;
+    int32_t* blk = p.blk + (((int64_t)c * p.n_seg + j) * p.n_det + d) * block_words(L);
+    blk[(sv * L + gl) * 4 + sk] = (int32_t)fmax(fmin(qd, 2147483647.0), -2147483648.0);
     float lo = (float)dD, hi = lo;
     for (int off = 1; off < p.group; off <<= 1) {
       lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, off));
       hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, off));
     }
     if (s % p.group == 0) {
-      blk[1024 + gl] = __float_as_int(0.5f * (lo + hi));
+      blk[16 * L + gl] = __float_as_int(0.5f * (lo + hi));
       if (s / p.group < p.NG) spread = fmaxf(spread, hi - lo);
     }
   }

@@ -19,7 +19,9 @@
 // takes the bin of every lookup from an FP64 track entry per (template,
 // segment) split into an integer base and an fp32 fraction, plus the fp32
 // Doppler term, so its bins equal the exact ones except within ~3e-7 bins of
-// a rounding tie.
+// a rounding tie.  The Doppler term must stay within 2.9 bins, so every bin a
+// patch can pick lies in an 8-bin window around the base that the block
+// stages in shared memory once per (template, segment, detector).
 #include <cuda_bf16.h>
 
 #include <climits>
@@ -33,9 +35,10 @@ namespace {
 constexpr int kCoarseLanes = 64;  // patches per block
 constexpr int kCoarseTmpl = 4;    // templates per block
 constexpr int kCoarseThreads = kCoarseLanes * kCoarseTmpl;
-constexpr int kCoarseTile = 64;   // segments per tile (= anchor tile of the coarse pass)
-constexpr int kCoarseMaxDet = 8;
-static_assert(kCoarseTile == kCoarseLanes, "one track entry per thread per tile");
+constexpr int kCoarseTile = 32;   // segments per tile (= anchor tile of the coarse pass)
+constexpr int kCoarseMaxDet = 2;  // detectors staged in shared memory
+constexpr int kCoarseWin = 8;     // staged bins per (template, segment, detector): base - 3 .. base + 4
+static_assert(kCoarseTile <= kCoarseLanes, "at most one track entry per thread per tile");
 
 __device__ __forceinline__ float load_rho(const float* p, int64_t i) { return __ldg(p + i); }
 __device__ __forceinline__ float load_rho(const __half* p, int64_t i) { return __half2float(__ldg(p + i)); }
@@ -53,12 +56,15 @@ __global__ void patch_doppler_kernel(PatchDopplerParams p) {
   }
 }
 
-template <typename RhoT>
+template <typename RhoT, int D>
 __global__ void __launch_bounds__(kCoarseThreads) coarse_kernel(CoarseParams p) {
-  __shared__ int s_base[kCoarseTmpl][kCoarseTile];
-  __shared__ float s_frac[kCoarseTmpl][kCoarseTile];
-  __shared__ float s_F[kCoarseTmpl][kCoarseTile];
-  __shared__ float s_w[kCoarseMaxDet][kCoarseTile];
+  // per (template, segment) of the tile: {base, frac bits, F bits, window inside the band}
+  __shared__ int4 s_ent[kCoarseTmpl][kCoarseTile];
+  // power window rho[d][j][base - 3 .. base + 4] per (template, segment, detector)
+  __shared__ float s_win[kCoarseTmpl][kCoarseTile][D][kCoarseWin];
+  __shared__ float s_w[D][kCoarseTile];
+  __shared__ float s_dop[D][kCoarseTile][kCoarseLanes];  // Doppler factor per patch
+  __shared__ float s_wsum[kCoarseTmpl][2];
   __shared__ double s_coef[kCoarseTmpl][kMaxSeriesTerms];
   const int tid = threadIdx.x;
   const int pl = tid % kCoarseLanes, tl = tid / kCoarseLanes;
@@ -66,6 +72,8 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_kernel(CoarseParams p) 
   const int b = blockIdx.y * kCoarseTmpl + tl;
   const bool active = pi < p.P;
   const RhoT* rho = static_cast<const RhoT*>(p.rho);
+  const double inv_df = 1.0 / p.df;
+  const double x0 = -p.f_min * inv_df;
   if (pl < kCoarseTmpl && tl == 0) {
     const int bb = blockIdx.y * kCoarseTmpl + pl;
     const double r = 1.0 / (p.nbr[bb] - 1.0);
@@ -81,12 +89,25 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_kernel(CoarseParams p) 
     const int j0 = ti * kCoarseTile;
     const int jn = min(kCoarseTile, p.n_seg - j0);
     __syncthreads();
+    if (tid < kCoarseTmpl * 2) s_wsum[tid / 2][tid % 2] = 0.f;
+    for (int i = tid; i < D * kCoarseTile; i += kCoarseThreads) {
+      const int d = i / kCoarseTile, jj = i % kCoarseTile;
+      s_w[d][jj] = jj < jn ? p.weights[(int64_t)d * p.n_seg + j0 + jj] : 0.f;
+    }
+#pragma unroll
+    for (int r = 0; r < D * kCoarseTile * kCoarseLanes / kCoarseThreads; ++r) {
+      const int i = tid + r * kCoarseThreads;
+      const int q = i % kCoarseLanes, jj = (i / kCoarseLanes) % kCoarseTile, d = i / (kCoarseLanes * kCoarseTile);
+      const int pq = blockIdx.x * kCoarseLanes + q;
+      s_dop[d][jj][q] = (jj < jn && pq < p.P) ? p.dop[((int64_t)d * p.n_seg + j0 + jj) * p.P + pq] : 0.f;
+    }
     {
-      // track entry of (template tl, segment j0 + pl) in FP64 (Eq. 1)
+      // track entry of (template tl, segment j0 + pl) in FP64 (Eq. 1):
+      // x = (f - f_min)/df = base + frac, F = f/df
       const int j = j0 + pl;
-      int base = INT_MIN;
+      int base = INT_MIN, inside = 0;
       float frac = 0.f, F = 0.f;
-      if (pl < jn && p.t_mid[j] >= p.T0) {
+      if (pl < kCoarseTile && pl < jn && p.t_mid[j] >= p.T0) {
         const double tj = p.t_mid[j];
         double h;
         if (p.nterms > 0) {
@@ -99,44 +120,74 @@ __global__ void __launch_bounds__(kCoarseThreads) coarse_kernel(CoarseParams p) 
         } else {
           h = pow((tj - p.T0) / p.tau[b] + 1.0, 1.0 / (p.nbr[b] - 1.0)) / p.f0[b];
         }
-        const double f = 1.0 / h;
-        const double x = (f - p.f_min) / p.df;
+        // f = 1/h: fp32 seed and two Newton steps in FP64
+        double f = (double)__frcp_rn((float)h);
+        f = f * fma(-h, f, 2.0);
+        f = f * fma(-h, f, 2.0);
+        const double x = fma(f, inv_df, x0);
         const double xr = rint(x);
         if (fabs(xr) < 1.0e9) {
           base = (int)xr;
           frac = (float)(x - xr);
-          F = (float)(f / p.df);
+          F = (float)(f * inv_df);
+          inside = (base - 3 >= 0 && (int64_t)base + 4 < p.n_bin) ? 1 : 0;
         }
       }
-      s_base[tl][pl] = base;
-      s_frac[tl][pl] = frac;
-      s_F[tl][pl] = F;
-      for (int i = tid; i < p.n_det * kCoarseTile; i += kCoarseThreads) {
-        const int d = i / kCoarseTile, jj = i % kCoarseTile;
-        s_w[d][jj] = jj < jn ? p.weights[(int64_t)d * p.n_seg + j0 + jj] : 0.f;
+      if (pl < kCoarseTile) s_ent[tl][pl] = make_int4(base, __float_as_int(frac), __float_as_int(F), inside);
+    }
+    __syncthreads();
+    // stage the windows; add the weights of in-band entries once per template
+#pragma unroll
+    for (int r = 0; r < kCoarseTmpl * kCoarseTile * D * kCoarseWin / kCoarseThreads; ++r) {
+      const int i = tid + r * kCoarseThreads;
+      const int o = i % kCoarseWin;
+      const int d = (i / kCoarseWin) % D;
+      const int jj = (i / (kCoarseWin * D)) % kCoarseTile;
+      const int t = i / (kCoarseWin * D * kCoarseTile);
+      const int base = s_ent[t][jj].x;
+      float v = 0.f;
+      const int64_t k = (int64_t)base - 3 + o;
+      if (base != INT_MIN && k >= 0 && k < p.n_bin) v = load_rho(rho, ((int64_t)d * p.n_seg + j0 + jj) * p.n_bin + k);
+      s_win[t][jj][d][o] = v;
+    }
+    if (pl < kCoarseTile && pl < jn && s_ent[tl][pl].w && s_ent[tl][pl].x != INT_MIN) {
+      float a = 0.f, a2 = 0.f;
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        const float w = s_w[d][pl];
+        a += w;
+        a2 = fmaf(w, w, a2);
       }
+      atomicAdd(&s_wsum[tl][0], a);
+      atomicAdd(&s_wsum[tl][1], a2);
     }
     __syncthreads();
     if (!active) continue;
     float st = 0.f, w1t = 0.f, w2t = 0.f;
+#pragma unroll 4
     for (int jj = 0; jj < jn; ++jj) {
-      const int base = s_base[tl][jj];
-      if (base == INT_MIN) continue;
-      const float frac = s_frac[tl][jj], F = s_F[tl][jj];
-      const int j = j0 + jj;
-      for (int d = 0; d < p.n_det; ++d) {
-        const float dop = __ldg(p.dop + ((int64_t)d * p.n_seg + j) * p.P + pi);
-        const int k = base + __float2int_rd(fmaf(F, dop, frac) + 0.5f);
-        if ((unsigned)k >= (unsigned)p.n_bin) continue;
+      const int4 e = s_ent[tl][jj];
+      if (e.x == INT_MIN) continue;
+      const float frac5 = __int_as_float(e.y) + 0.5f, F = __int_as_float(e.z);
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        const float dop = s_dop[d][jj][pl];
+        int off = __float2int_rd(fmaf(F, dop, frac5));
+        off = min(max(off, -3), kCoarseWin - 4);
         const float w = s_w[d][jj];
-        st = fmaf(w, load_rho(rho, ((int64_t)d * p.n_seg + j) * p.n_bin + k), st);
-        w1t += w;
-        w2t = fmaf(w, w, w2t);
+        const float v = s_win[tl][jj][d][off + 3];
+        if (e.w) {
+          st = fmaf(w, v, st);
+        } else if ((unsigned)(e.x + off) < (unsigned)p.n_bin) {
+          st = fmaf(w, v, st);
+          w1t += w;
+          w2t = fmaf(w, w, w2t);
+        }
       }
     }
     S += st;
-    W1 += w1t;
-    W2 += w2t;
+    W1 += (double)w1t + (double)s_wsum[tl][0];
+    W2 += (double)w2t + (double)s_wsum[tl][1];
   }
   if (!active || b >= p.B) return;
   const float W2f = (float)W2;
@@ -305,12 +356,19 @@ cudaError_t launch_patch_doppler(const PatchDopplerParams& p, cudaStream_t st) {
 }
 
 cudaError_t launch_coarse(const CoarseParams& p, bool half, cudaStream_t st) {
-  if (p.n_det > kCoarseMaxDet) return cudaErrorInvalidValue;
+  if (p.n_det < 1 || p.n_det > kCoarseMaxDet) return cudaErrorInvalidValue;
   dim3 grid((p.P + kCoarseLanes - 1) / kCoarseLanes, p.Bpad / kCoarseTmpl);
-  if (half)
-    coarse_kernel<__half><<<grid, kCoarseThreads, 0, st>>>(p);
-  else
-    coarse_kernel<float><<<grid, kCoarseThreads, 0, st>>>(p);
+  if (half) {
+    if (p.n_det == 1)
+      coarse_kernel<__half, 1><<<grid, kCoarseThreads, 0, st>>>(p);
+    else
+      coarse_kernel<__half, 2><<<grid, kCoarseThreads, 0, st>>>(p);
+  } else {
+    if (p.n_det == 1)
+      coarse_kernel<float, 1><<<grid, kCoarseThreads, 0, st>>>(p);
+    else
+      coarse_kernel<float, 2><<<grid, kCoarseThreads, 0, st>>>(p);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t n = (int64_t)p.P * kTriageBins;

@@ -47,10 +47,11 @@ def patch_labels(search, ev, patch_size=PATCH_SIZE):
 
 
 def collect(make_event, n_events, bank, patch_size=PATCH_SIZE, lo=PSI_LO, hi=PSI_HI, device="cuda:0"):
-    """Features [N][128] and labels [N] (CUDA tensors) of n_events events."""
+    """Features [N][128] and labels [N] (CUDA tensors) of n_events events, and
+    the number of patches of each event."""
     import torch
     s = Search(0)
-    feats, labs = [], []
+    feats, labs, sizes = [], [], []
     for i in range(n_events):
         ev = make_event(i)
         load_event(s, ev, bank)
@@ -59,8 +60,9 @@ def collect(make_event, n_events, bank, patch_size=PATCH_SIZE, lo=PSI_LO, hi=PSI
         s.triage_features_device(patch_size, lo, hi, out)
         feats.append(out)
         labs.append(torch.as_tensor(lab, device=device))
+        sizes.append(lab.shape[0])
     s.close()
-    return torch.cat(feats), torch.cat(labs)
+    return torch.cat(feats), torch.cat(labs), sizes
 
 
 def train(X, y, steps=2000, batch=4096, lr=1e-3, seed=0, pos_weight=None, mlp=None, log_every=0):
@@ -85,17 +87,22 @@ def train(X, y, steps=2000, batch=4096, lr=1e-3, seed=0, pos_weight=None, mlp=No
     return mlp, losses
 
 
-def recall_at(mlp, X, y, frac):
-    """Fraction of positive examples ranked within the top `frac` of their
-    score list (the whole set ranked at once)."""
+def recall_at(mlp, X, y, sizes, frac):
+    """Fraction of positive patches that rank within the top ceil(frac * P)
+    patches of their own event (ties by patch index, as the search ranks)."""
     _, _, s = mlp.forward(X)
     s = s.detach().cpu().numpy()
     lab = y.detach().cpu().numpy() > 0.5
-    m = max(1, int(np.ceil(frac * s.shape[0])))
-    top = np.argsort(-s, kind="stable")[:m]
-    sel = np.zeros(s.shape[0], bool)
-    sel[top] = True
-    return float((sel & lab).sum() / max(lab.sum(), 1))
+    hit = tot = 0
+    off = 0
+    for P in sizes:
+        sc, lb = s[off:off + P], lab[off:off + P]
+        m = max(1, int(np.ceil(frac * P - 1e-9)))
+        top = np.argsort(-sc, kind="stable")[:m]
+        hit += int(lb[top].sum())
+        tot += int(lb.sum())
+        off += P
+    return hit / max(tot, 1)
 
 
 def judge(ev, psi, idx, k_det=10, psi_det=6.5):

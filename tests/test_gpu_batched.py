@@ -106,7 +106,7 @@ def test_batched_f32_two_detectors_weighted_fixed_shape():
 def test_batched_replay_waves_and_shapes_agree():
     events, bank = make_batch(73, 1, np.float32, False, [200, 45, 1030])
     k = 9
-    s, val, idx = run_batched(events, bank, k, options=[(tcw.OPT_AUTOTUNE, 0)])
+    s, val, idx = run_batched(events, bank, k, options=[(tcw.OPT_AUTOTUNE, 0), (tcw.OPT_SKY_LANES, 64)])
     # a replay of the recorded graph is bit-identical
     val2, idx2 = s.search_batched(k)
     np.testing.assert_array_equal(val, val2)

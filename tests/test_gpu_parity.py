@@ -93,6 +93,23 @@ def test_random_bank_two_detectors_many_skies(kernel):
         assert info.general_path_lanes > 0      # band edges were exercised
 
 
+@pytest.mark.parametrize("lanes", [16, 32, 64])
+def test_sky_chunk_widths(lanes):
+    # 300 skies: two chunks at 16 lanes (256 skies each), one at 32 and at 64
+    p = multi_problem(seed=35, n_sky=300, n_tmpl=200, n_seg=70)
+    s = tcw.Search(0)
+    s.set_option(tcw.OPT_SKY_LANES, lanes)
+    s.set_option(tcw.OPT_KEEP_STATS, 1)
+    s.load_problem(p)
+    val, idx = s.search(10)
+    st = s.statistics()
+    assert s.info().kernel == tcw.KERNEL_GROUP
+    ora = oracle_stats(p)
+    assert_stats_close((st["S"], st["W1"], st["W2"], st["psi"]), ora, where=f"lanes {lanes}")
+    assert_topk_matches_oracle(idx, val, ora[3], ora[0], ora[2], 10)
+    s.close()
+
+
 def test_T0_inside_the_data():
     p = multi_problem(seed=32, t0_shift=40)
     _check_all(p, tcw.KERNEL_GROUP)
