@@ -360,6 +360,14 @@ tcw_status tcw_get_triage_info(tcw_ctx *ctx, tcw_triage_info *info);
  * i-th sky (host memory, n_sky entries).  Errors: STATE, INVALID_ARGUMENT. */
 tcw_status tcw_sky_order(tcw_ctx *ctx, int32_t *order_out);
 
+/* Measurement helper (not part of the method): best-of-`reps` read
+ * bandwidth in GB/s of a kernel streaming 16-byte L2-cached loads over a
+ * `bytes` device buffer `passes` times per launch, on the current device.
+ * A buffer that fits in L2 (e.g. 64 MiB) measures L2, a larger one DRAM.
+ * Errors: INVALID_ARGUMENT (bytes outside [1 MiB, 64 GiB], passes or reps
+ * < 1, NULL), CUDA. */
+tcw_status tcw_probe_read_bandwidth(int64_t bytes, int passes, int reps, double *gbps_out);
+
 /* Information about the last search. */
 typedef struct {
     int kernel;                 /* TCW_KERNEL_GROUP or TCW_KERNEL_LOOKUP */

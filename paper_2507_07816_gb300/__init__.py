@@ -5,4 +5,5 @@ The compute path is the CUDA library built from ``csrc/`` (C ABI in
 """
 from .tcw import (DEVICE, F16, F32, HOST, KERNEL_AUTO, KERNEL_GROUP, KERNEL_LOOKUP,  # noqa: F401
                   OPT_AUTOTUNE, OPT_BANK_CHUNK, OPT_BATCH_MEMORY, OPT_KEEP_STATS, OPT_SKY_LANES, OPT_KERNEL, OPT_TILE_SEGMENTS, Info, Search, TcwError,
-                  library_path, load_library, Mlp, MLP_PARAMS, MLP_WEIGHTS)
+                  library_path, load_library, Mlp, MLP_PARAMS, MLP_WEIGHTS,
+                  probe_read_bandwidth)

@@ -111,6 +111,7 @@ def load_library(build_if_missing: bool = True):
                                    p, p, p, i],
             "tcw_get_triage_info": [p, ctypes.POINTER(_TriageInfo)],
             "tcw_sky_order": [p, p],
+            "tcw_probe_read_bandwidth": [i64, i, i, ctypes.POINTER(d)],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -122,6 +123,16 @@ def load_library(build_if_missing: bool = True):
         lib.tcw_last_error.restype = ctypes.c_char_p
         _lib = lib
         return lib
+
+
+def probe_read_bandwidth(nbytes, passes=50, reps=5):
+    """Read bandwidth (GB/s) of a streaming kernel over an nbytes device buffer."""
+    lib = load_library()
+    out = ctypes.c_double()
+    st = lib.tcw_probe_read_bandwidth(int(nbytes), int(passes), int(reps), ctypes.byref(out))
+    if st != OK:
+        raise TcwError(st, "tcw_probe_read_bandwidth: " + lib.tcw_status_string(st).decode())
+    return out.value
 
 
 def _is_torch(a):

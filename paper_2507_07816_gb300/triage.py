@@ -22,8 +22,15 @@ import numpy as np
 
 from .tcw import Mlp, Search
 
-PATCH_SIZE = 16
+PATCH_SIZE = 32
 PSI_LO, PSI_HI = -4.0, 12.0
+# Sky resolution of the statistic: skies whose Doppler factors differ by a
+# small fraction of a bin see the same track bins for most segments, so a
+# signal is found at every sky of its Doppler neighbourhood.  Labels mark the
+# patches within LABEL_RADIUS patches of an injected sky; the judge accepts
+# the injected template at any sky within JUDGE_RADIUS Doppler-sorted skies.
+LABEL_RADIUS = 1
+JUDGE_RADIUS = 64
 
 
 def load_event(search, ev, bank, define_bank=True):
@@ -34,15 +41,22 @@ def load_event(search, ev, bank, define_bank=True):
     search.define_sky(ev.nhat)
 
 
-def patch_labels(search, ev, patch_size=PATCH_SIZE):
-    """1 for every patch that holds an injected sky, else 0."""
+def sorted_positions(search):
+    """Position of every sky in the search's Doppler-sorted order."""
     order = search.sky_order()
     pos = np.empty_like(order)
     pos[order] = np.arange(order.shape[0])
-    P = -(-order.shape[0] // patch_size)
+    return pos
+
+
+def patch_labels(search, ev, patch_size=PATCH_SIZE, radius=LABEL_RADIUS):
+    """1 for the patches within `radius` patches of an injected sky, else 0."""
+    pos = sorted_positions(search)
+    P = -(-pos.shape[0] // patch_size)
     lab = np.zeros(P, np.float32)
     for inj in ev.injections:
-        lab[pos[inj.sky] // patch_size] = 1.0
+        p = pos[inj.sky] // patch_size
+        lab[max(0, p - radius):min(P, p + radius + 1)] = 1.0
     return lab
 
 
@@ -105,14 +119,16 @@ def recall_at(mlp, X, y, sizes, frac):
     return hit / max(tot, 1)
 
 
-def judge(ev, psi, idx, k_det=10, psi_det=6.5):
-    """Injections found: the injected template within the first k_det entries
-    of its sky with Psi >= psi_det."""
+def judge(ev, psi, idx, pos, k_det=10, psi_det=6.5, radius=JUDGE_RADIUS):
+    """Injections found: the injected template within the first k_det entries,
+    with Psi >= psi_det, of some sky within `radius` Doppler-sorted positions
+    (pos) of the injected sky."""
     found = []
     for inj in ev.injections:
-        row_i, row_p = idx[inj.sky, :k_det], psi[inj.sky, :k_det]
-        hit = np.nonzero(row_i == inj.template)[0]
-        found.append(bool(hit.size and row_p[hit[0]] >= psi_det))
+        near = np.nonzero(np.abs(pos - pos[inj.sky]) <= radius)[0]
+        rows_i, rows_p = idx[near, :k_det], psi[near, :k_det]
+        hit = (rows_i == inj.template) & (rows_p >= psi_det)
+        found.append(bool(hit.any()))
     return found
 
 
@@ -133,12 +149,13 @@ def evaluate(mlp, make_event, n_events, bank, frac=0.1, k=100, patch_size=PATCH_
         pt, xt, searched = s.search_triaged(mlp, patch_size, lo, hi, frac, k)
         t2 = time.perf_counter()
         info = s.triage_info()
+        pos = sorted_positions(s)
         t_full += t1 - t0
         t_tri += t2 - t1
         sums_full += info["lookups_full"]
         sums_tri += info["lookups_coarse"] + info["lookups_searched"]
-        ff = judge(ev, pf, xf, k_det, psi_det)
-        tf = judge(ev, pt, xt, k_det, psi_det)
+        ff = judge(ev, pf, xf, pos, k_det, psi_det)
+        tf = judge(ev, pt, xt, pos, k_det, psi_det)
         full_found += sum(ff)
         tri_found += sum(tf)
         missed += sum(a and not b for a, b in zip(ff, tf))

@@ -226,7 +226,7 @@ def injection_values(r: np.random.Generator, shape, injection: Injection, detect
     """The (detector, segment, bin) cells of one injected signal and their new
     powers ((x + mu)^2 + y^2)/2, x, y ~ N(0, 1); sets injection.bins."""
     D, n_seg, n_bin = shape
-    f_src = spindown_frequency(injection.f0, injection.tau, injection.n, T0, t)
+    f_src = spindown_frequency_many([injection.f0], [injection.tau], [injection.n], T0, t)[0]
     bins = np.full((D, n_seg), -1, np.int64)
     fdet = np.full((D, n_seg), np.nan)
     for d, det in enumerate(detectors):
