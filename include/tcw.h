@@ -87,9 +87,12 @@ enum {
                                   TCW_OPT_TILE_SEGMENTS */
     TCW_OPT_BATCH_MEMORY = 6,  /* batched search: bytes of Psi and anchor buffers per
                                   wave of events (default 48 GiB, minimum 1 MiB) */
-    TCW_OPT_SKY_LANES = 7      /* sky groups of 16 per chunk of the group kernel: 16,
+    TCW_OPT_SKY_LANES = 7,     /* sky groups of 16 per chunk of the group kernel: 16,
                                   32 or 64 (a pass covers 16*lanes skies x 512/lanes
-                                  templates); 0 (default) = the fewest padded skies */
+                                  templates); 0 (default) = the lowest padded cost */
+    TCW_OPT_TRIAGE_SPREAD = 8  /* triaged search: a chosen patch suppresses the patches
+                                  within this many positions (default 2; 0 = plain
+                                  ranking); best suppressed ones fill up if needed */
 };
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
@@ -333,7 +336,8 @@ tcw_status tcw_triage_features(tcw_ctx *ctx, int patch_size, float psi_lo, float
                                float *feat_out, float *psi_out, int out_flags);
 
 /* Triaged search: coarse pass, network score per patch, the ceil(frac *
- * n_patch) best patches searched exhaustively as tcw_search does.
+ * n_patch) best patches (spread apart by TCW_OPT_TRIAGE_SPREAD) searched
+ * exhaustively as tcw_search does.
  * psi_out/idx_out [n_sky][k] as tcw_search for searched skies; rows of
  * skipped skies hold -inf and -1.  searched_out [n_sky] (may be NULL): 1 for
  * searched skies.  wbf and theta are device pointers.

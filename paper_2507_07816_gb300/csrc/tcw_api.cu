@@ -503,6 +503,10 @@ tcw_status tcw_set_option(tcw_ctx* c, int option, int64_t value) {
       c->opt_lanes = (int)value;
       c->sky_dirty = true;
       return TCW_OK;
+    case TCW_OPT_TRIAGE_SPREAD:
+      if (value < 0 || value > 1024) return fail(c, TCW_ERR_INVALID_ARGUMENT, "triage spread must be in [0, 1024]");
+      c->triage_spread = (int)value;
+      return TCW_OK;
     case TCW_OPT_AUTOTUNE:
       c->autotune = value ? 1 : 0;
       return TCW_OK;
@@ -815,7 +819,8 @@ tcw_status tcw_search_triaged(tcw_ctx* c, const uint16_t* wbf, const float* thet
                           c->tri_h1.as<float>(), c->tri_h2.as<float>(), c->tri_score.as<float>(), c->stream),
            "mlp forward");
   const int m = std::max(1, std::min(P, (int)std::ceil((double)frac * P - 1e-9)));
-  TCW_CUDA(c, launch_rank(c->tri_score.as<float>(), P, m, c->tri_sel.as<int>(), c->stream), "rank");
+  TCW_CUDA(c, launch_rank(c->tri_score.as<float>(), P, m, c->triage_spread, c->tri_sel.as<int>(), c->stream),
+           "rank");
   TCW_CUDA(c, cudaEventRecord(e2, c->stream), "event");
   std::vector<int> sel(P);
   TCW_CUDA(c, cudaMemcpyAsync(sel.data(), c->tri_sel.p, P * sizeof(int), cudaMemcpyDeviceToHost, c->stream),

@@ -224,7 +224,9 @@ struct CoarseParams {
 
 cudaError_t launch_patch_doppler(const PatchDopplerParams& p, cudaStream_t st);
 cudaError_t launch_coarse(const CoarseParams& p, bool half, cudaStream_t st);
-cudaError_t launch_rank(const float* score, int P, int m, int* selected, cudaStream_t st);
+// selected[p] = 1 for the m best patches; a chosen patch suppresses the
+// patches within `radius` of it (0 = plain ranking)
+cudaError_t launch_rank(const float* score, int P, int m, int radius, int* selected, cudaStream_t st);
 cudaError_t mlp_forward(const __nv_bfloat16* wbf, const float* theta, const float* X, int64_t n, float* H1,
                         float* H2, float* y, cudaStream_t st);
 // work: 2 * n * 256 floats

@@ -12,7 +12,8 @@
 //     gemm_kernel         tiled C = op(A) op(B) (+ bias, ReLU) for the forward
 //                         pass and every product of the backward pass
 //     relu_mask / colsum / bce / adam kernels
-//   rank_kernel           rank of each patch score (descending, ties by index)
+//   select_kernel         best patches by score with suppression of their
+//                         neighbours (rank_kernel: plain ranking)
 //
 // Patches are runs of consecutive skies in the Doppler-sorted order of the
 // search; the representative of a patch is its middle sky.  The coarse pass
@@ -342,6 +343,47 @@ __global__ void rank_kernel(const float* score, int P, int m, int* selected) {
   selected[p] = rank < m ? 1 : 0;
 }
 
+// Greedy selection with suppression: patches in descending score order
+// (ties by index); a chosen patch suppresses the patches within `radius`; when
+// fewer than m survive, the best suppressed ones fill up.  One block.
+constexpr int kSelectMax = 8192;
+__global__ void __launch_bounds__(256) select_kernel(const float* score, int P, int m, int radius,
+                                                     int* selected) {
+  __shared__ int order[kSelectMax];
+  __shared__ unsigned char state[kSelectMax];   // 0 free, 1 chosen, 2 suppressed
+  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    const float sp = isnan(score[p]) ? -INFINITY : score[p];
+    int rank = 0;
+    for (int q = 0; q < P; ++q) {
+      const float sq = isnan(score[q]) ? -INFINITY : score[q];
+      rank += (sq > sp || (sq == sp && q < p)) ? 1 : 0;
+    }
+    order[rank] = p;
+    state[p] = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int n = 0;
+    for (int r = 0; r < P && n < m; ++r) {
+      const int p = order[r];
+      if (state[p] != 0) continue;
+      state[p] = 1;
+      ++n;
+      for (int q = max(0, p - radius); q <= min(P - 1, p + radius); ++q)
+        if (state[q] == 0) state[q] = 2;
+    }
+    for (int r = 0; r < P && n < m; ++r) {
+      const int p = order[r];
+      if (state[p] == 2) {
+        state[p] = 1;
+        ++n;
+      }
+    }
+  }
+  __syncthreads();
+  for (int p = threadIdx.x; p < P; p += blockDim.x) selected[p] = state[p] == 1 ? 1 : 0;
+}
+
 unsigned blocks_for(int64_t n, int threads) {
   const int64_t b = (n + threads - 1) / threads;
   return (unsigned)(b < 152 * 32 ? (b > 0 ? b : 1) : 152 * 32);
@@ -376,8 +418,11 @@ cudaError_t launch_coarse(const CoarseParams& p, bool half, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_rank(const float* score, int P, int m, int* selected, cudaStream_t st) {
-  rank_kernel<<<(P + 255) / 256, 256, 0, st>>>(score, P, m, selected);
+cudaError_t launch_rank(const float* score, int P, int m, int radius, int* selected, cudaStream_t st) {
+  if (radius > 0 && P <= kSelectMax)
+    select_kernel<<<1, 256, 0, st>>>(score, P, m, radius, selected);
+  else
+    rank_kernel<<<(P + 255) / 256, 256, 0, st>>>(score, P, m, selected);
   return cudaGetLastError();
 }
 

@@ -140,6 +140,7 @@ def test_triaged_search_rows_equal_exhaustive_rows():
     p["w3"][0] = 1.0
     mlp = tcw.Mlp(theta, device=DEV)
     s = tcw.Search(0)
+    s.set_option(tcw.OPT_TRIAGE_SPREAD, 0)
     TR.load_event(s, ev, bank)
     k = 8
     pf, xf = s.search(k)
@@ -153,4 +154,11 @@ def test_triaged_search_rows_equal_exhaustive_rows():
     assert np.all(xt[~rows] == -1) and np.all(np.isneginf(pt[~rows]))
     for inj in ev.injections:
         assert searched[inj.sky] == 1
+    # with suppression the chosen patches are more than `spread` positions apart
+    s.set_option(tcw.OPT_TRIAGE_SPREAD, 2)
+    _, _, searched = s.search_triaged(mlp, 16, -4.0, 12.0, 0.2, k)   # 3 of 13 patches always fit
+    pos = TR.sorted_positions(s)
+    chosen = sorted({int(pos[i]) // 16 for i in np.nonzero(searched)[0]})
+    assert len(chosen) == s.triage_info()["n_selected"] == 3
+    assert all(b - a > 2 for a, b in zip(chosen, chosen[1:])), chosen
     s.close()
