@@ -271,7 +271,7 @@ def bench_learned(args, dev):
     seed0 = int(meta["valid_seed"]) + 10_000
 
     def make(i):
-        return syn.training_event(seed0 + i, bank, n_inj=4, snr_range=(6.0, 12.0),
+        return syn.training_event(seed0 + i, bank, n_inj=int(meta["injections"]), snr_range=(6.0, 12.0),
                                   device=torch.device(f"cuda:{dev}"))
 
     make(0)

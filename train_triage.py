@@ -3,8 +3,8 @@
 
 Training set: method-generated events at the shapes of the plain 2-detector
 workload (10^4 segments x 10^4 bins, T_SFT = 4 s, 500-3000 Hz, 1024
-Fibonacci-sphere skies), each with 4 injected tracks of SNR uniform in
-[6, 12] whose templates come from a 2e4-template uniform-random bank; one
+Fibonacci-sphere skies), each with one injected track of SNR uniform in
+[6, 12] whose template comes from a 2e4-template uniform-random bank; one
 example per sky patch (32 Doppler-sorted skies), label 1 for the patches
 within one patch of an injected sky.  The features come from the library's coarse pass and
 the network is trained by the library's own forward/backward/Adam kernels.
@@ -43,6 +43,7 @@ def main():
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--frac", type=float, default=0.1)
     ap.add_argument("--patch-size", type=int, default=32)
+    ap.add_argument("--injections", type=int, default=1)
     ap.add_argument("--out", default=os.path.join(ROOT, "paper_2507_07816_gb300", "triage_weights.npz"))
     ap.add_argument("--report", default=None)
     args = ap.parse_args()
@@ -57,7 +58,8 @@ def main():
     bank = syn.random_bank(syn.rng(bank_seed), args.n_tmpl, f0_range=(500.0, 3000.0))
 
     def make(seed0):
-        return lambda i: syn.training_event(seed0 + i, bank, n_inj=4, snr_range=(6.0, 12.0), device=dev)
+        return lambda i: syn.training_event(seed0 + i, bank, n_inj=args.injections, snr_range=(6.0, 12.0),
+                                            device=dev)
 
     t0 = time.perf_counter()
     X, y, sizes = TR.collect(make(train_seed), args.train_events, bank, patch_size=args.patch_size)
@@ -76,7 +78,8 @@ def main():
           f"patch recall trained {rec} untrained {rec_un}", flush=True)
     np.savez(args.out, theta=mlp.parameters(), bank_seed=bank_seed, n_tmpl=args.n_tmpl,
              patch_size=args.patch_size, frac=args.frac, psi_lo=TR.PSI_LO, psi_hi=TR.PSI_HI,
-             valid_seed=valid_seed, train_events=args.train_events, train_examples=int(X.shape[0]))
+             valid_seed=valid_seed, train_events=args.train_events, train_examples=int(X.shape[0]),
+             injections=args.injections)
     t0 = time.perf_counter()
     judged = TR.evaluate(mlp, make(valid_seed + 1000), args.valid_events, bank, frac=args.frac,
                          patch_size=args.patch_size)
