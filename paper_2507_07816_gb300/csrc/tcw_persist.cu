@@ -11,9 +11,9 @@
 //                        the batch: the track entry in FP64 (Eq. 1, from the
 //                        tile anchors of anchor_kernel), its 64-byte power
 //                        windows (16-byte async copies), the segment weights,
-//                        and one bulk copy of the chunk's Doppler blocks per
-//                        segment (Eq. 2 factor on the fixed-point grid) into
-//                        a 16-stage ring
+//                        and one bulk copy of the chunk's Doppler blocks of
+//                        the batch's segments (Eq. 2 factor on the fixed-point
+//                        grid) into one stage of a ring holding 16 segments
 //   consumer warps (8)   per segment: for each detector and each of two
 //                        templates, the candidate bin pair of the lane's
 //                        16-sky group, two window reads, and per sky one int32
@@ -21,7 +21,8 @@
 //                        plus the weight sums W1, W2; Psi of Eq. 4 at the end
 //                        of the pass
 //
-// Ring position q counts the segments of all passes of the CTA so far, so
+// A ring stage holds one producer batch (4, 2 or 1 segments for L = 64, 32,
+// 16); ring position q counts the batches of all passes of the CTA so far, so
 // both sides derive every index from their walk over the item list.  The ring
 // is driven by mbarriers (full: one producer arrival + the bulk-copy bytes;
 // empty: one arrival per consumer warp); every wait is bounded.
@@ -39,9 +40,13 @@ namespace {
 
 constexpr int kConsumerWarps = 8;
 constexpr int kConsumers = kConsumerWarps * 32;   // template pairs x sky groups of one pass
-constexpr int kRing = 16;                         // ring stages
+constexpr int kRingSegments = 16;                 // segments buffered by the ring
 // producer warps: narrow chunks compute more track entries per stage
 __host__ __device__ constexpr int producer_warps(int lanes) { return lanes == 64 ? 3 : 4; }
+__host__ __device__ constexpr int pass_tmpl(int lanes) { return 2 * kConsumers / lanes; }
+// a stage holds one producer batch: 32 lanes = templates x segments
+__host__ __device__ constexpr int batch_segments(int lanes) { return 32 / pass_tmpl(lanes); }
+__host__ __device__ constexpr int ring_stages(int lanes) { return kRingSegments / batch_segments(lanes); }
 
 // Geometry of a pass for LN sky groups per chunk (LN = 16, 32 or 64): the
 // consumers are kConsumers / LN units (template pairs) x LN lanes (sky groups
@@ -49,27 +54,35 @@ __host__ __device__ constexpr int producer_warps(int lanes) { return lanes == 64
 // is one lane per (template, segment).
 template <int LN>
 struct Geo {
-  static constexpr int kPT = 2 * kConsumers / LN;          // templates per pass
-  static constexpr int kBatch = 32 / kPT;                  // segments per producer batch
+  static constexpr int kPT = pass_tmpl(LN);                // templates per pass
+  static constexpr int kBatch = batch_segments(LN);        // segments per stage (producer batch)
+  static constexpr int kRing = ring_stages(LN);            // ring stages
   static constexpr int kChunk = kGroupSkies * LN;          // skies per chunk
   static constexpr int kDetBytes = 4 * block_words(LN);    // one Doppler block per detector
   static constexpr int kProd = producer_warps(LN);
   static constexpr int kThreads = kConsumers + 32 * kProd;
   static_assert(kPT >= 8 && kPT <= 32 && kBatch * kPT == 32, "geometry");
-  static_assert(kRing >= (kProd + 1) * kBatch, "every producer's batch fits the ring");
+  static_assert(kRing >= kProd + 1, "every producer's stage fits the ring, plus the one being consumed");
 };
 
+// One ring stage = one producer batch of kBatch segments:
+//   Doppler blocks [kBatch][D][block_words]   (one bulk copy; contiguous in HBM)
+//   track entries  [kBatch][kPT]
+//   power windows  [kBatch][kPT][D][64 B]
+//   weights        [kBatch][4 floats]
 struct PersistLayout {
   size_t ent, win, hdr, stage, coef, bar, total;
+  int ring;
   __host__ __device__ PersistLayout(int D, int lanes) {
-    const int pt = 2 * kConsumers / lanes;
-    ent = (size_t)D * 4 * block_words(lanes);         // Doppler blocks first (bulk-copy target)
-    win = ent + (size_t)pt * sizeof(TrackEntry);
-    hdr = win + (size_t)pt * D * kWinBytes;           // segment weight of each detector
-    stage = (hdr + 16 + 127) & ~(size_t)127;
-    coef = stage * kRing;
+    const int pt = pass_tmpl(lanes), nb = batch_segments(lanes);
+    ring = ring_stages(lanes);
+    ent = (size_t)nb * D * 4 * block_words(lanes);
+    win = ent + (size_t)nb * pt * sizeof(TrackEntry);
+    hdr = win + (size_t)nb * pt * D * kWinBytes;
+    stage = (hdr + (size_t)nb * 16 + 127) & ~(size_t)127;
+    coef = stage * ring;
     bar = coef + (size_t)producer_warps(lanes) * pt * kMaxSeriesTerms * 8;
-    total = bar + (size_t)2 * kRing * 8;
+    total = bar + (size_t)2 * ring * 8;
   }
 };
 
@@ -172,7 +185,7 @@ __global__ void __launch_bounds__(Geo<LN>::kThreads, 1) group_kernel(GroupParams
   constexpr uint32_t ESZ = sizeof(RhoT);
   constexpr int kPT = Geo<LN>::kPT, kBatch = Geo<LN>::kBatch, kChunk = Geo<LN>::kChunk;
   constexpr int kStageDetBytes = Geo<LN>::kDetBytes, kBlockWords = block_words(LN);
-  constexpr int kProducerWarps = Geo<LN>::kProd;
+  constexpr int kProducerWarps = Geo<LN>::kProd, kRing = Geo<LN>::kRing;
   extern __shared__ __align__(128) unsigned char smem[];
   const int D = DT > 0 ? DT : p.n_det;
   const PersistLayout L(D, LN);
@@ -180,7 +193,7 @@ __global__ void __launch_bounds__(Geo<LN>::kThreads, 1) group_kernel(GroupParams
   const uint32_t bar_full = smem0 + (uint32_t)L.bar;
   const uint32_t bar_empty = bar_full + kRing * 8;
   const int tid = threadIdx.x, lane = tid & 31;
-  const uint32_t dq_bytes = (uint32_t)(D * kStageDetBytes);
+  const uint32_t dq_seg = (uint32_t)(D * kStageDetBytes);   // Doppler bytes of one segment
   const int it0 = p.cta_items[blockIdx.x], it1 = p.cta_items[blockIdx.x + 1];
   const int tmask = (1 << p.tile_shift) - 1;
 
@@ -195,16 +208,16 @@ __global__ void __launch_bounds__(Geo<LN>::kThreads, 1) group_kernel(GroupParams
 
   if (tid >= kConsumers) {
     // ======================= producer warps =======================
-    // Batches of 4 segments are numbered along the CTA's pass sequence; warp
-    // pw takes those with number = pw (mod 3).  Each warp fills its batches
-    // in increasing order, so a stage it waits for was last used by an
-    // earlier batch and the waits cannot deadlock.
+    // Batches (= stages) are numbered along the CTA's pass sequence; warp pw
+    // takes those with number = pw (mod kProducerWarps).  Each warp fills its
+    // batches in increasing order, so a stage it waits for was last used by
+    // an earlier batch and the waits cannot deadlock.
     const int pw = (tid - kConsumers) >> 5;
     const int lt = lane % kPT, lk = lane / kPT;   // template and segment slot of this lane
     double* coef = reinterpret_cast<double*>(smem + L.coef) + pw * kPT * kMaxSeriesTerms;
     const float fmin_f = (float)p.f_min, inv_df_f = (float)(1.0 / p.df);
-    long long qbase = 0;   // ring position of the pass's first segment
-    int nmod = 0;          // number of the pass's first batch, mod 3
+    long long nbase = 0;   // number of the pass's first batch
+    int nmod = 0;          // nbase mod kProducerWarps
     bool ok = true;
     for (int it = it0; it < it1 && ok; ++it) {
       const int4 item = p.items[it];
@@ -229,42 +242,33 @@ __global__ void __launch_bounds__(Geo<LN>::kThreads, 1) group_kernel(GroupParams
         for (int jbi = (pw - nmod + kProducerWarps) % kProducerWarps; jbi < bpi; jbi += kProducerWarps) {
           const int jb = jbi * kBatch;
           const int nb = min(kBatch, n_seg - jb);
-          const long long q0 = qbase + jb;
+          const long long q = nbase + jbi;             // ring position of this batch
+          const unsigned s = (unsigned)(q % kRing);
           int okw = 1;
-          if (lane == 0) {
-            for (int k = 0; k < nb && okw; ++k) {
-              const long long q = q0 + k;
-              okw = mbar_wait(bar_empty + 8 * (unsigned)(q % kRing), (unsigned)(((q / kRing) & 1) ^ 1), p.err);
-            }
-          }
+          if (lane == 0) okw = mbar_wait(bar_empty + 8 * s, (unsigned)(((q / kRing) & 1) ^ 1), p.err);
           okw = __shfl_sync(0xffffffffu, okw, 0);
           if (!okw) {
             ok = false;
             break;
           }
           fence_proxy_async();
+          unsigned char* st = smem + s * L.stage;
           if (lk < nb) {
-            const int j = jb + lk;
-            const unsigned s = (unsigned)((q0 + lk) % kRing);
-            unsigned char* st = smem + s * L.stage;
-            TrackEntry& e = *reinterpret_cast<TrackEntry*>(st + L.ent + lt * sizeof(TrackEntry));
+            const int j = jb + lk, slot = lk * kPT + lt;
+            TrackEntry& e = *reinterpret_cast<TrackEntry*>(st + L.ent + slot * sizeof(TrackEntry));
             compute_entry<RhoT>(p, ev, coef + lt * kMaxSeriesTerms, b0 + lt, j, fmin_f, inv_df_f, e,
-                                smem0 + s * (uint32_t)L.stage + (uint32_t)L.win + lt * D * kWinBytes);
-            if (lt < D) reinterpret_cast<float*>(st + L.hdr)[lt] = ev.weights[(int64_t)lt * n_seg + j];
+                                smem0 + s * (uint32_t)L.stage + (uint32_t)L.win + slot * D * kWinBytes);
+            if (lt < D) reinterpret_cast<float*>(st + L.hdr + lk * 16)[lt] = ev.weights[(int64_t)lt * n_seg + j];
           }
           cp_async_wait_all();
           __syncwarp();
           if (lane == 0) {
-            for (int k = 0; k < nb; ++k) {
-              const unsigned s = (unsigned)((q0 + k) % kRing);
-              const uint32_t full = bar_full + 8 * s;
-              mbar_arrive_expect_tx(full, dq_bytes);
-              bulk_g2s(smem0 + s * (uint32_t)L.stage, blk + (int64_t)(jb + k) * D * kBlockWords, dq_bytes,
-                       full);
-            }
+            const uint32_t full = bar_full + 8 * s;
+            mbar_arrive_expect_tx(full, dq_seg * nb);
+            bulk_g2s(smem0 + s * (uint32_t)L.stage, blk + (int64_t)jb * D * kBlockWords, dq_seg * nb, full);
           }
         }
-        qbase += n_seg;
+        nbase += bpi;
         nmod = (nmod + bpi) % kProducerWarps;
       }
     }
@@ -296,21 +300,25 @@ __global__ void __launch_bounds__(Geo<LN>::kThreads, 1) group_kernel(GroupParams
 #pragma unroll
         for (int k = 0; k < G; ++k) acc[t][k] = tot[t][k] = 0.f;
       }
-      for (int j = 0; j < n_seg; ++j, ++q) {
+      for (int jb = 0; jb < n_seg && ok; jb += kBatch, ++q) {
         const unsigned s = (unsigned)(q % kRing);
         if (!mbar_wait(bar_full + 8 * s, (unsigned)((q / kRing) & 1), p.err)) {
           ok = false;
           break;
         }
-        const uint32_t sb = smem0 + s * (uint32_t)L.stage;
+        const int nb = min(kBatch, n_seg - jb);
+        const uint32_t sbase = smem0 + s * (uint32_t)L.stage;
+        for (int kseg = 0; kseg < nb; ++kseg) {
+        const int j = jb + kseg;
+        const uint32_t sb = sbase + (uint32_t)(kseg * D * kStageDetBytes);   // this segment's Doppler blocks
         if (gval) {
           const uint32_t stage = sb + l * 16;
-          const uint32_t e0 = sb + (uint32_t)L.ent + (uint32_t)(2 * u * (int)sizeof(TrackEntry));
+          const uint32_t e0 = sbase + (uint32_t)L.ent + (uint32_t)((kseg * kPT + 2 * u) * (int)sizeof(TrackEntry));
           const uint32_t e1 = e0 + (uint32_t)sizeof(TrackEntry);
           const float4 h0 = lds_f4(e0), h1 = lds_f4(e1);
           const int4 wa0 = lds_v4(e0 + 16), wa1 = lds_v4(e1 + 16);
           const int c0 = __float_as_int(h0.w), c1 = __float_as_int(h1.w);
-          const float4 wseg = lds_f4(sb + (uint32_t)L.hdr);
+          const float4 wseg = lds_f4(sbase + (uint32_t)L.hdr + (uint32_t)(kseg * 16));
 #pragma unroll
           for (int d = 0; d < D; ++d) {
             const float wd = WEIGHTED ? (d == 0 ? wseg.x : wseg.y) : 1.0f;
@@ -411,8 +419,6 @@ __global__ void __launch_bounds__(Geo<LN>::kThreads, 1) group_kernel(GroupParams
             }
           }
         }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(bar_empty + 8 * s);
         if ((j & tmask) == tmask || j == n_seg - 1) {
 #pragma unroll
           for (int t = 0; t < 2; ++t) {
@@ -427,6 +433,9 @@ __global__ void __launch_bounds__(Geo<LN>::kThreads, 1) group_kernel(GroupParams
             }
           }
         }
+        }  // segments of the stage
+        __syncwarp();
+        if (lane == 0) mbar_arrive(bar_empty + 8 * s);
       }
       if (!ok || !gval) continue;
 #pragma unroll
