@@ -6,14 +6,14 @@
 // (a "pass") streams every segment and detector of the event through shared
 // memory:
 //
-//   producer warps (3-4) warp w owns every third (fourth) batch of the CTA's
-//                        pass sequence, one lane per (template, segment) of
-//                        the batch: the track entry in FP64 (Eq. 1, from the
+//   producer warps (3-4) warp w owns every third (fourth) batch of 4 segments
+//                        of the CTA's pass sequence, one lane per (template,
+//                        segment) of the batch per round: the track entry in FP64 (Eq. 1, from the
 //                        tile anchors of anchor_kernel), its 64-byte power
 //                        windows (16-byte async copies), the segment weights,
 //                        and one bulk copy of the chunk's Doppler blocks of
 //                        the batch's segments (Eq. 2 factor on the fixed-point
-//                        grid) into one stage of a ring holding 16 segments
+//                        grid) into one stage of a 5-stage ring
 //   consumer warps (8)   per segment: for each detector and each of two
 //                        templates, the candidate bin pair of the lane's
 //                        16-sky group, two window reads, and per sky one int32
@@ -21,9 +21,9 @@
 //                        plus the weight sums W1, W2; Psi of Eq. 4 at the end
 //                        of the pass
 //
-// A ring stage holds one producer batch (4, 2 or 1 segments for L = 64, 32,
-// 16); ring position q counts the batches of all passes of the CTA so far, so
-// both sides derive every index from their walk over the item list.  The ring
+// A ring stage holds one producer batch of 4 segments (5 stages); ring
+// position q counts the batches of all passes of the CTA so far, so both
+// sides derive every index from their walk over the item list.  The ring
 // is driven by mbarriers (full: one producer arrival + the bulk-copy bytes;
 // empty: one arrival per consumer warp); every wait is bounded.
 #include <algorithm>
@@ -40,13 +40,13 @@ namespace {
 
 constexpr int kConsumerWarps = 8;
 constexpr int kConsumers = kConsumerWarps * 32;   // template pairs x sky groups of one pass
-constexpr int kRingSegments = 16;                 // segments buffered by the ring
 // producer warps: narrow chunks compute more track entries per stage
 __host__ __device__ constexpr int producer_warps(int lanes) { return lanes == 64 ? 3 : 4; }
 __host__ __device__ constexpr int pass_tmpl(int lanes) { return 2 * kConsumers / lanes; }
-// a stage holds one producer batch: 32 lanes = templates x segments
-__host__ __device__ constexpr int batch_segments(int lanes) { return 32 / pass_tmpl(lanes); }
-__host__ __device__ constexpr int ring_stages(int lanes) { return kRingSegments / batch_segments(lanes); }
+// a stage holds 4 segments of one pass; its producer warp fills it in
+// 4 * pass_tmpl / 32 rounds of one lane per (template, segment)
+__host__ __device__ constexpr int batch_segments(int) { return 4; }
+__host__ __device__ constexpr int ring_stages(int) { return 5; }
 
 // Geometry of a pass for LN sky groups per chunk (LN = 16, 32 or 64): the
 // consumers are kConsumers / LN units (template pairs) x LN lanes (sky groups
@@ -56,12 +56,13 @@ template <int LN>
 struct Geo {
   static constexpr int kPT = pass_tmpl(LN);                // templates per pass
   static constexpr int kBatch = batch_segments(LN);        // segments per stage (producer batch)
+  static constexpr int kRounds = kBatch * pass_tmpl(LN) / 32;  // producer rounds per stage
   static constexpr int kRing = ring_stages(LN);            // ring stages
   static constexpr int kChunk = kGroupSkies * LN;          // skies per chunk
   static constexpr int kDetBytes = 4 * block_words(LN);    // one Doppler block per detector
   static constexpr int kProd = producer_warps(LN);
   static constexpr int kThreads = kConsumers + 32 * kProd;
-  static_assert(kPT >= 8 && kPT <= 32 && kBatch * kPT == 32, "geometry");
+  static_assert(kPT >= 8 && kPT <= 32 && kRounds * 32 == kBatch * kPT, "geometry");
   static_assert(kRing >= kProd + 1, "every producer's stage fits the ring, plus the one being consumed");
 };
 
@@ -213,7 +214,6 @@ __global__ void __launch_bounds__(Geo<LN>::kThreads, 1) group_kernel(GroupParams
     // batches in increasing order, so a stage it waits for was last used by
     // an earlier batch and the waits cannot deadlock.
     const int pw = (tid - kConsumers) >> 5;
-    const int lt = lane % kPT, lk = lane / kPT;   // template and segment slot of this lane
     double* coef = reinterpret_cast<double*>(smem + L.coef) + pw * kPT * kMaxSeriesTerms;
     const float fmin_f = (float)p.f_min, inv_df_f = (float)(1.0 / p.df);
     long long nbase = 0;   // number of the pass's first batch
@@ -253,12 +253,17 @@ __global__ void __launch_bounds__(Geo<LN>::kThreads, 1) group_kernel(GroupParams
           }
           fence_proxy_async();
           unsigned char* st = smem + s * L.stage;
-          if (lk < nb) {
-            const int j = jb + lk, slot = lk * kPT + lt;
-            TrackEntry& e = *reinterpret_cast<TrackEntry*>(st + L.ent + slot * sizeof(TrackEntry));
-            compute_entry<RhoT>(p, ev, coef + lt * kMaxSeriesTerms, b0 + lt, j, fmin_f, inv_df_f, e,
-                                smem0 + s * (uint32_t)L.stage + (uint32_t)L.win + slot * D * kWinBytes);
-            if (lt < D) reinterpret_cast<float*>(st + L.hdr + lk * 16)[lt] = ev.weights[(int64_t)lt * n_seg + j];
+#pragma unroll 1
+          for (int r = 0; r < Geo<LN>::kRounds; ++r) {
+            const int slot = r * 32 + lane;
+            const int lt = slot % kPT, lk = slot / kPT;   // template and segment of this lane's entry
+            if (lk < nb) {
+              const int j = jb + lk;
+              TrackEntry& e = *reinterpret_cast<TrackEntry*>(st + L.ent + slot * sizeof(TrackEntry));
+              compute_entry<RhoT>(p, ev, coef + lt * kMaxSeriesTerms, b0 + lt, j, fmin_f, inv_df_f, e,
+                                  smem0 + s * (uint32_t)L.stage + (uint32_t)L.win + slot * D * kWinBytes);
+              if (lt < D) reinterpret_cast<float*>(st + L.hdr + lk * 16)[lt] = ev.weights[(int64_t)lt * n_seg + j];
+            }
           }
           cp_async_wait_all();
           __syncwarp();
