@@ -120,13 +120,26 @@ __global__ void anchor_kernel(AnchorParams p) {
 // chain with 8 extra bits.  Issues the 16-byte asynchronous copies of the
 // 64-byte power windows around the track.
 // ---------------------------------------------------------------------------
+// An entry with no lookup.  Its fields still point inside the entry and its
+// power window (candidate pair at offset 0, threshold th[-kMLo]), so the
+// consumers can read them unconditionally and discard the values.
+template <typename RhoT>
+__device__ __forceinline__ void set_none(TrackEntry& e, uint32_t win_dst, int n_det) {
+  e.cls = kEntryNone;
+  e.F = 0.f;
+  e.Cm = 0.f;
+  e.tha = smem_addr(&e.th[0]) - 4u * (uint32_t)(kMagicBits + kMLo);
+  for (int d = 0; d < n_det; ++d)
+    e.wa[d] = win_dst + d * kWinBytes - (uint32_t)sizeof(RhoT) * (uint32_t)(kMagicBits + kMLo);
+}
+
 template <typename RhoT>
 __device__ __forceinline__ void compute_entry(const GroupParams& p, const EventDesc& ev,
                                               const double* coef, int b, int j, float fmin_f,
                                               float inv_df_f, TrackEntry& e, uint32_t win_dst) {
   const double tj = ev.t_mid[j];
   if (!(tj >= ev.T0)) {
-    e.cls = kEntryNone;
+    set_none<RhoT>(e, win_dst, p.n_det);
     return;
   }
   double h;
@@ -144,7 +157,7 @@ __device__ __forceinline__ void compute_entry(const GroupParams& p, const EventD
   const float x = (f - fmin_f) * inv_df_f;
   const int base = __float2int_rn(x);
   if (!(base >= -kMHi && (int64_t)base < p.n_bin - kMLo)) {
-    e.cls = kEntryNone;
+    set_none<RhoT>(e, win_dst, p.n_det);
     return;
   }
   e.cls = (base + kMLo >= 0 && (int64_t)base + kMHi <= p.n_bin - 1) ? kEntryInside : kEntryEdge;
@@ -335,23 +348,26 @@ __global__ void __launch_bounds__(Geo<LN>::kThreads, 1) group_kernel(GroupParams
             const int zb1 = __float_as_int(fmaf(h1.x, gm, h1.y) + kMagic);
             const uint32_t wd0 = (uint32_t)(d == 0 ? wa0.x : wa0.y);
             const uint32_t wd1 = (uint32_t)(d == 0 ? wa1.x : wa1.y);
-            if (c0 == kEntryInside) {
-              th0 = (int)lds_u32(__float_as_uint(h0.z) + 4u * (uint32_t)zb0);
-              const uint32_t a = wd0 + ESZ * (uint32_t)zb0;
-              const float rlo = lds_pow(a, RhoT()), rhi = lds_pow(a + ESZ, RhoT());
-              gt[0] = fmaf(wd, rlo, gt[0]);
-              dw0 = wd * (rhi - rlo);
-              w1t[0] += wd;
-              w2t[0] = fmaf(wd, wd, w2t[0]);
-            }
-            if (c1 == kEntryInside) {
-              th1 = (int)lds_u32(__float_as_uint(h1.z) + 4u * (uint32_t)zb1);
-              const uint32_t a = wd1 + ESZ * (uint32_t)zb1;
-              const float rlo = lds_pow(a, RhoT()), rhi = lds_pow(a + ESZ, RhoT());
-              gt[1] = fmaf(wd, rlo, gt[1]);
-              dw1 = wd * (rhi - rlo);
-              w1t[1] += wd;
-              w2t[1] = fmaf(wd, wd, w2t[1]);
+            {
+              // branch-free: every entry points at valid shared memory (set_none),
+              // and the values of entries that are not wholly in band are discarded
+              const bool in0 = c0 == kEntryInside, in1 = c1 == kEntryInside;
+              const int t0 = (int)lds_u32(__float_as_uint(h0.z) + 4u * (uint32_t)zb0);
+              const int t1 = (int)lds_u32(__float_as_uint(h1.z) + 4u * (uint32_t)zb1);
+              const uint32_t a0 = wd0 + ESZ * (uint32_t)zb0, a1 = wd1 + ESZ * (uint32_t)zb1;
+              const float rlo0 = lds_pow(a0, RhoT()), rhi0 = lds_pow(a0 + ESZ, RhoT());
+              const float rlo1 = lds_pow(a1, RhoT()), rhi1 = lds_pow(a1 + ESZ, RhoT());
+              const float we0 = in0 ? wd : 0.f, we1 = in1 ? wd : 0.f;
+              th0 = in0 ? t0 : INT_MAX;
+              th1 = in1 ? t1 : INT_MAX;
+              gt[0] = fmaf(we0, in0 ? rlo0 : 0.f, gt[0]);
+              gt[1] = fmaf(we1, in1 ? rlo1 : 0.f, gt[1]);
+              dw0 = in0 ? wd * (rhi0 - rlo0) : 0.f;
+              dw1 = in1 ? wd * (rhi1 - rlo1) : 0.f;
+              w1t[0] += we0;
+              w1t[1] += we1;
+              w2t[0] = fmaf(we0, we0, w2t[0]);
+              w2t[1] = fmaf(we1, we1, w2t[1]);
             }
 #pragma unroll
             for (int v = 0; v < 4; ++v) {

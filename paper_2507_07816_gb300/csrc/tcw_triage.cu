@@ -5,7 +5,8 @@
 //
 //   patch_doppler_kernel  Eq. 2 factor v.nhat/c of each patch representative
 //   coarse_kernel         Psi (Eq. 4) of every template at every patch
-//                         representative, one thread per (template, patch),
+//                         representative, one thread per (template, patch)
+//                         (blocks of 32 or 64 patches x 8 or 4 templates),
 //                         and the 128-bin histogram of those Psi per patch
 //   features_kernel       log(1 + count) per histogram bin
 //   MLP 128 -> 256 -> 256 -> 1 (ReLU), bfloat16 weights, fp32 accumulation:
@@ -33,13 +34,10 @@
 namespace tcw {
 namespace {
 
-constexpr int kCoarseLanes = 64;  // patches per block
-constexpr int kCoarseTmpl = 4;    // templates per block
-constexpr int kCoarseThreads = kCoarseLanes * kCoarseTmpl;
+constexpr int kCoarseThreads = 256;  // one thread per (template, patch): 256 / PL templates x PL patches
 constexpr int kCoarseTile = 32;   // segments per tile (= anchor tile of the coarse pass)
 constexpr int kCoarseMaxDet = 2;  // detectors staged in shared memory
 constexpr int kCoarseWin = 8;     // staged bins per (template, segment, detector): base - 3 .. base + 4
-static_assert(kCoarseTile <= kCoarseLanes, "at most one track entry per thread per tile");
 
 __device__ __forceinline__ float load_rho(const float* p, int64_t i) { return __ldg(p + i); }
 __device__ __forceinline__ float load_rho(const __half* p, int64_t i) { return __half2float(__ldg(p + i)); }
@@ -57,8 +55,10 @@ __global__ void patch_doppler_kernel(PatchDopplerParams p) {
   }
 }
 
-template <typename RhoT, int D>
+template <typename RhoT, int D, int kCoarseLanes>
 __global__ void __launch_bounds__(kCoarseThreads) coarse_kernel(CoarseParams p) {
+  constexpr int kCoarseTmpl = kCoarseThreads / kCoarseLanes;   // templates per block
+  static_assert(kCoarseTile <= kCoarseLanes, "at most one track entry per thread per tile");
   // per (template, segment) of the tile: {base, frac bits, F bits, window inside the band}
   __shared__ int4 s_ent[kCoarseTmpl][kCoarseTile];
   // power window rho[d][j][base - 3 .. base + 4] per (template, segment, detector)
@@ -397,20 +397,28 @@ cudaError_t launch_patch_doppler(const PatchDopplerParams& p, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_coarse(const CoarseParams& p, bool half, cudaStream_t st) {
-  if (p.n_det < 1 || p.n_det > kCoarseMaxDet) return cudaErrorInvalidValue;
-  dim3 grid((p.P + kCoarseLanes - 1) / kCoarseLanes, p.Bpad / kCoarseTmpl);
+template <int PL>
+void launch_coarse_l(const CoarseParams& p, bool half, cudaStream_t st) {
+  dim3 grid((p.P + PL - 1) / PL, p.Bpad / (kCoarseThreads / PL));
   if (half) {
     if (p.n_det == 1)
-      coarse_kernel<__half, 1><<<grid, kCoarseThreads, 0, st>>>(p);
+      coarse_kernel<__half, 1, PL><<<grid, kCoarseThreads, 0, st>>>(p);
     else
-      coarse_kernel<__half, 2><<<grid, kCoarseThreads, 0, st>>>(p);
+      coarse_kernel<__half, 2, PL><<<grid, kCoarseThreads, 0, st>>>(p);
   } else {
     if (p.n_det == 1)
-      coarse_kernel<float, 1><<<grid, kCoarseThreads, 0, st>>>(p);
+      coarse_kernel<float, 1, PL><<<grid, kCoarseThreads, 0, st>>>(p);
     else
-      coarse_kernel<float, 2><<<grid, kCoarseThreads, 0, st>>>(p);
+      coarse_kernel<float, 2, PL><<<grid, kCoarseThreads, 0, st>>>(p);
   }
+}
+
+cudaError_t launch_coarse(const CoarseParams& p, bool half, cudaStream_t st) {
+  if (p.n_det < 1 || p.n_det > kCoarseMaxDet) return cudaErrorInvalidValue;
+  if (p.P <= 32)
+    launch_coarse_l<32>(p, half, st);
+  else
+    launch_coarse_l<64>(p, half, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t n = (int64_t)p.P * kTriageBins;

@@ -31,9 +31,10 @@ def small_event(seed, n_det=2, n_seg=150, n_bin=1200, n_sky=120, n_tmpl=96, n_in
     return ev, bank
 
 
-def test_coarse_features_match_oracle():
+@pytest.mark.parametrize("P_SIZE", [8, 1])     # 15 patches (32-patch blocks) and 120 (64-patch blocks)
+def test_coarse_features_match_oracle(P_SIZE):
     ev, bank = small_event(81, n_inj=2)
-    P_SIZE, LO, HI = 8, -4.0, 12.0
+    LO, HI = -4.0, 12.0
     s = tcw.Search(0)
     TR.load_event(s, ev, bank)
     feat, psi = s.triage_features(P_SIZE, LO, HI, with_psi=True)
