@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(Geo<LN>::kThreads, 1) group_kernel(GroupParams
 
   if (tid == 0) {
     for (int i = 0; i < kRing; ++i) {
-      mbar_init(bar_full + 8 * i, 1);
+      mbar_init(bar_full + 8 * i, 1 + 32);   // lane 0's expect_tx + one cp.async arrival per producer lane
       mbar_init(bar_empty + 8 * i, kConsumerWarps);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -278,10 +278,12 @@ __global__ void __launch_bounds__(Geo<LN>::kThreads, 1) group_kernel(GroupParams
               if (lt < D) reinterpret_cast<float*>(st + L.hdr + lk * 16)[lt] = ev.weights[(int64_t)lt * n_seg + j];
             }
           }
-          cp_async_wait_all();
+          // the power windows land asynchronously: each lane's copies arrive on
+          // the stage's full barrier when they complete, so the warp moves on
+          const uint32_t full = bar_full + 8 * s;
+          cp_async_mbar_arrive_noinc(full);
           __syncwarp();
           if (lane == 0) {
-            const uint32_t full = bar_full + 8 * s;
             mbar_arrive_expect_tx(full, dq_seg * nb);
             bulk_g2s(smem0 + s * (uint32_t)L.stage, blk + (int64_t)jb * D * kBlockWords, dq_seg * nb, full);
           }
