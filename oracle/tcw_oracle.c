@@ -89,7 +89,7 @@ static void oracle_pair_stats(const float *rho, int D, int Nseg, int Nbin,
                               double f_min, double df, const double *t_mid,
                               const float *w, const double *v,
                               const double *nhat, double f0, double tau,
-                              double n, double T0, double out[3])
+                              double n, double T0, int amp_power, double out[3])
 {
     double S = 0.0, W1 = 0.0, W2 = 0.0;
     for (int d = 0; d < D; ++d) {
@@ -101,6 +101,10 @@ static void oracle_pair_stats(const float *rho, int D, int Nseg, int Nbin,
             int64_t k = oracle_bin_index(fh, f_min, df);
             if (k < 0 || k >= Nbin) continue;
             double wj = w ? (double)w[(size_t)d * Nseg + j] : 1.0;
+            /* optional amplitude weight: the signal power follows h0^2 and
+             * h0 grows as f^2 (Eq. 3), so a template's expected excess in
+             * segment j scales as (f(t_j)/f0)^4 (amp_power = 4) */
+            if (amp_power > 0) wj *= pow(f / f0, (double)amp_power);
             double r = (double)rho[((size_t)d * Nseg + j) * (size_t)Nbin + (size_t)k];
             S += wj * r;
             W1 += wj;
@@ -118,6 +122,16 @@ static void oracle_pair_stats(const float *rho, int D, int Nseg, int Nbin,
  * Outputs S_out, W1_out, W2_out, Psi_out (any may be NULL).
  * nthreads <= 0 uses the OpenMP default.
  */
+void oracle_search_stats_amp(const float *rho, int D, int Nseg, int Nbin,
+                             double f_min, double df, const double *t_mid,
+                             const float *w, const double *v,
+                             const double *nhat, int n_sky,
+                             const double *f0, const double *tau, const double *n,
+                             int n_tmpl, double T0, int amp_power,
+                             const int64_t *pairs, int64_t P,
+                             double *S_out, double *W1_out, double *W2_out,
+                             double *Psi_out, int nthreads);
+
 void oracle_search_stats(const float *rho, int D, int Nseg, int Nbin,
                          double f_min, double df, const double *t_mid,
                          const float *w, const double *v,
@@ -127,6 +141,22 @@ void oracle_search_stats(const float *rho, int D, int Nseg, int Nbin,
                          const int64_t *pairs, int64_t P,
                          double *S_out, double *W1_out, double *W2_out,
                          double *Psi_out, int nthreads)
+{
+    oracle_search_stats_amp(rho, D, Nseg, Nbin, f_min, df, t_mid, w, v, nhat, n_sky, f0, tau, n,
+                            n_tmpl, T0, 0, pairs, P, S_out, W1_out, W2_out, Psi_out, nthreads);
+}
+
+/* As oracle_search_stats, with every weight multiplied by (f(t_j)/f0)^amp_power
+ * (amp_power = 0: none). */
+void oracle_search_stats_amp(const float *rho, int D, int Nseg, int Nbin,
+                             double f_min, double df, const double *t_mid,
+                             const float *w, const double *v,
+                             const double *nhat, int n_sky,
+                             const double *f0, const double *tau, const double *n,
+                             int n_tmpl, double T0, int amp_power,
+                             const int64_t *pairs, int64_t P,
+                             double *S_out, double *W1_out, double *W2_out,
+                             double *Psi_out, int nthreads)
 {
     int64_t total = pairs ? P : (int64_t)n_sky * n_tmpl;
 #ifdef _OPENMP
@@ -144,7 +174,7 @@ void oracle_search_stats(const float *rho, int D, int Nseg, int Nbin,
         }
         double st[3];
         oracle_pair_stats(rho, D, Nseg, Nbin, f_min, df, t_mid, w, v,
-                          nhat + 3 * s, f0[b], tau[b], n[b], T0, st);
+                          nhat + 3 * s, f0[b], tau[b], n[b], T0, amp_power, st);
         if (S_out) S_out[i] = st[0];
         if (W1_out) W1_out[i] = st[1];
         if (W2_out) W2_out[i] = st[2];

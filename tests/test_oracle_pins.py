@@ -152,6 +152,59 @@ def test_out_of_band_and_pre_T0_fixture():
     assert bins == list(map(int, kv["bins"]))
 
 
+def test_amplitude_weight_fixture():
+    """Eq. 3 amplitude weight (f/f0)^4 on the hand-computed band-edge case:
+    exact rational S, W1, W2 derived by hand from (1 + dt/tau)^-2 for n = 3."""
+    kv = {row[0]: row[1:] for row in _read_rows("out_of_band_case.txt")}
+    amp = {row[0]: row[1:] for row in _read_rows("amplitude_weight_case.txt")}
+    t = np.array(list(map(float, kv["t_mid"])))
+    w = np.array([list(map(float, kv["weights"]))], np.float32)
+    n_bin = int(kv["n_bin"][0])
+    rho = np.zeros((1, t.size, n_bin), np.float32)
+    for j in range(t.size):
+        rho[0, j] = 1 + j + np.arange(n_bin) / 100.0
+    S, W1, W2, Psi = oracle.search_stats(
+        rho, float(kv["f_min"][0]), float(kv["df"][0]), t, w, np.zeros((1, t.size, 3)),
+        np.array([[0.0, 0.0, 1.0]]), [float(kv["f0"][0])], [float(kv["tau"][0])],
+        [float(kv["n"][0])], float(kv["T0"][0]), amp_power=int(amp["amp_power"][0]))
+    ex = {k: int(amp[k + "_num"][0]) / int(amp[k + "_den"][0]) for k in ("S", "W1", "W2")}
+    assert S[0, 0] == pytest.approx(ex["S"], rel=1e-6)       # rho is float32
+    assert W1[0, 0] == pytest.approx(ex["W1"], rel=1e-12)
+    assert W2[0, 0] == pytest.approx(ex["W2"], rel=1e-12)
+    assert Psi[0, 0] == pytest.approx((ex["S"] - ex["W1"]) / math.sqrt(ex["W2"]), rel=1e-6)
+
+
+def test_amplitude_weight_closed_form_n5():
+    """For n = 5, (f/f0)^4 = tau / (tau + t - T0) exactly (Eq. 1 and Eq. 3), so
+    with unit power in every bin S = W1 = sum_j w_j tau/(tau + dt_j) and
+    W2 = sum_j (w_j tau/(tau + dt_j))^2.  amp_power = 0 recovers the plain sums."""
+    r = syn.rng(21)
+    n_seg, n_bin = 40, 4096
+    t = syn.segment_times(n_seg, 600.0)
+    T0 = t[0] - 10.0
+    rho = np.ones((2, n_seg, n_bin), np.float32)
+    w = syn.uniform_weights(r, 2, n_seg, 0.2, 2.0)
+    vel = np.zeros((2, n_seg, 3))
+    f0 = r.uniform(900.0, 1000.0, 6)
+    tau = r.uniform(3500.0, 35000.0, 6)
+    n = np.full(6, 5.0)
+    S, W1, W2, Psi = oracle.search_stats(rho, 500.0, 0.125, t, w, vel, np.array([[0, 0, 1.0]]),
+                                         f0, tau, n, T0, amp_power=4)
+    S0, W10, W20, _ = oracle.search_stats(rho, 500.0, 0.125, t, w, vel, np.array([[0, 0, 1.0]]),
+                                          f0, tau, n, T0)
+    wd = w.astype(np.float64)
+    for b in range(6):
+        a = tau[b] / (tau[b] + (t - T0))
+        assert W1[0, b] == pytest.approx((wd * a).sum(), rel=1e-13)
+        assert W2[0, b] == pytest.approx(((wd * a) ** 2).sum(), rel=1e-13)
+        assert S[0, b] == pytest.approx(W1[0, b], rel=1e-13)
+        assert Psi[0, b] == pytest.approx(0.0, abs=1e-12)
+        assert W10[0, b] == pytest.approx(wd.sum(), rel=1e-13)
+        assert W20[0, b] == pytest.approx((wd ** 2).sum(), rel=1e-13)
+    # the weight decays: the template's own later segments count for less
+    assert (W1 < W10).all()
+
+
 def test_pre_T0_segments_are_dropped():
     """Statistic with T0 mid-way equals the statistic of the map cut at T0."""
     p = syn.config_small(seed=11, n_seg=64, n_bin=1024, n_f0=4, n_tau=4, snr=0, weights=True)
