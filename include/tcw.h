@@ -90,9 +90,19 @@ enum {
     TCW_OPT_SKY_LANES = 7,     /* sky groups of 16 per chunk of the group kernel: 16,
                                   32 or 64 (a pass covers 16*lanes skies x 512/lanes
                                   templates); 0 (default) = the lowest padded cost */
-    TCW_OPT_TRIAGE_SPREAD = 8  /* triaged search: a chosen patch suppresses the patches
+    TCW_OPT_TRIAGE_SPREAD = 8, /* triaged search: a chosen patch suppresses the patches
                                   within this many positions (default 2; 0 = plain
                                   ranking); best suppressed ones fill up if needed */
+    TCW_OPT_AMPLITUDE_POWER = 9 /* p in [0, 8]: every lookup's weight w_{d,j} is
+                                  multiplied by the template's own amplitude
+                                  weight (f(t_j)/f0)^p, so S, W1 = sum w and
+                                  W2 = sum w^2 of Eq. 4 use w_{d,j} (f(t_j)/f0)^p.
+                                  The signal power grows as h0^2 and h0 as f^2
+                                  (Eq. 3 of arXiv:2507.07816), so p = 4 weights
+                                  each segment by the expected signal power of
+                                  the template; default 0 (the weights as given).
+                                  Applies to tcw_search, tcw_search_batched and
+                                  the exhaustive part of tcw_search_triaged */
 };
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t

@@ -250,6 +250,7 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
     gp.inv_q = pl.inv_q;
     gp.nterms = pl.nterms;
     gp.tile_shift = tile_shift;
+    gp.amp_power = c->amp_power;
     gp.B = (int)c->B;
     gp.Bpad = c->Bpad;
     gp.lanes = c->lanes;
@@ -264,7 +265,8 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
       TCW_CUDA(c, launch_anchors(ap, c->stream), "anchor_kernel launch");
       ++launches;
     }
-    TCW_CUDA(c, launch_group(gp, c->grid, c->dtype == TCW_F16, record, !c->unit_weights, c->stream),
+    const int wt = c->amp_power > 0 ? kAmplitudeWeights : (c->unit_weights ? kUnitWeights : kSegmentWeights);
+    TCW_CUDA(c, launch_group(gp, c->grid, c->dtype == TCW_F16, record, wt, c->stream),
              "group_kernel launch");
     TCW_CUDA(c, cudaEventRecord(c->ev1, c->stream), "event");
     ++launches;
@@ -284,6 +286,7 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
     lp.T0 = c->T0;
     lp.f_min = c->f_min;
     lp.df = c->df;
+    lp.amp_power = c->amp_power;
     lp.B = (int)c->B;
     lp.Bpad = c->Bpad;
     lp.S = (int)c->S;
@@ -502,6 +505,10 @@ tcw_status tcw_set_option(tcw_ctx* c, int option, int64_t value) {
         return fail(c, TCW_ERR_INVALID_ARGUMENT, "sky lanes must be 0, 16, 32 or 64");
       c->opt_lanes = (int)value;
       c->sky_dirty = true;
+      return TCW_OK;
+    case TCW_OPT_AMPLITUDE_POWER:
+      if (value < 0 || value > 8) return fail(c, TCW_ERR_INVALID_ARGUMENT, "amplitude power must be in [0, 8]");
+      c->amp_power = (int)value;
       return TCW_OK;
     case TCW_OPT_TRIAGE_SPREAD:
       if (value < 0 || value > 1024) return fail(c, TCW_ERR_INVALID_ARGUMENT, "triage spread must be in [0, 1024]");

@@ -75,6 +75,7 @@ struct BatchState {
   cudaGraphExec_t exec = nullptr;
   int graph_k = 0, graph_nodes = 0;
   int64_t graph_mem = 0;           // wave budget the graph was recorded with
+  int graph_amp = 0;               // amplitude power the graph was recorded with
   // last search
   bool have_result = false;
   int last_k = 0;
@@ -250,6 +251,10 @@ void wave_items(const tcw_ctx* c, const BatchState* b, int w, int bank_chunk, in
   schedule_items(items, cost, b->grid, order, cta);
 }
 
+int weighting(const tcw_ctx* c, const BatchState* b) {
+  return c->amp_power > 0 ? kAmplitudeWeights : (b->unit_weights ? kUnitWeights : kSegmentWeights);
+}
+
 GroupParams base_params(const tcw_ctx* c, BatchState* b, int tile, int nterms) {
   GroupParams gp{};
   gp.events = b->evtab.as<EventDesc>();
@@ -264,6 +269,7 @@ GroupParams base_params(const tcw_ctx* c, BatchState* b, int tile, int nterms) {
   gp.inv_q = b->inv_q;
   gp.nterms = nterms;
   gp.tile_shift = ilog2(tile);
+  gp.amp_power = c->amp_power;
   gp.B = (int)c->B;
   gp.Bpad = c->Bpad;
   gp.lanes = b->lanes;
@@ -379,7 +385,7 @@ tcw_status autotune(tcw_ctx* c, BatchState* b) {
         cudaEventRecord(e0, c->stream);
         for (int w = 0; w < b->waves; ++w) {
           const GroupParams gp = wave_params(c, b, w, tile, nterms);
-          cudaError_t err = launch_group(gp, b->grid, b->dtype == TCW_F16, false, !b->unit_weights, c->stream);
+          cudaError_t err = launch_group(gp, b->grid, b->dtype == TCW_F16, false, weighting(c, b), c->stream);
           if (err != cudaSuccess) {
             st = cuda_fail(c, err, "group_kernel launch");
             break;
@@ -427,7 +433,7 @@ tcw_status capture(tcw_ctx* c, BatchState* b, int k) {
   if ((st = upload_items(c, b, b->bank_chunk, INT32_MAX, &sums)) != TCW_OK) return st;
   TCW_CUDA(c, b->out_psi.ensure((size_t)b->total_sky * k * sizeof(float)), "output");
   TCW_CUDA(c, b->out_idx.ensure((size_t)b->total_sky * k * sizeof(int64_t)), "output");
-  TCW_CUDA(c, group_prepare(b->D, b->lanes, b->dtype == TCW_F16, !b->unit_weights), "group_kernel attributes");
+  TCW_CUDA(c, group_prepare(b->D, b->lanes, b->dtype == TCW_F16, weighting(c, b)), "group_kernel attributes");
   TCW_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "graph capture");
   cudaError_t err = cudaMemsetAsync(b->flags.p, 0, 64, c->stream);
   int nodes = 0;
@@ -455,7 +461,7 @@ tcw_status capture(tcw_ctx* c, BatchState* b, int k) {
     }
     if (err != cudaSuccess) break;
     const GroupParams gp = wave_params(c, b, w, b->tile, nterms);
-    err = launch_group(gp, b->grid, b->dtype == TCW_F16, false, !b->unit_weights, c->stream);
+    err = launch_group(gp, b->grid, b->dtype == TCW_F16, false, weighting(c, b), c->stream);
     ++nodes;
     for (const EventHost& e : b->ev) {
       if (e.wave != w || err != cudaSuccess) continue;
@@ -477,6 +483,7 @@ tcw_status capture(tcw_ctx* c, BatchState* b, int k) {
   }
   b->graph_k = k;
   b->graph_mem = c->batch_memory;
+  b->graph_amp = c->amp_power;
   b->graph_nodes = nodes;
   return TCW_OK;
 }
@@ -689,7 +696,7 @@ tcw_status tcw_search_batched(tcw_ctx* c, int k, float* psi_out, int64_t* idx_ou
     }
     drop_graph(b);
   }
-  if (!b->exec || b->graph_k != k || b->graph_mem != c->batch_memory) {
+  if (!b->exec || b->graph_k != k || b->graph_mem != c->batch_memory || b->graph_amp != c->amp_power) {
     if ((st = capture(c, b, k)) != TCW_OK) return st;
   }
   TCW_CUDA(c, cudaEventRecord(c->ev0, c->stream), "event");

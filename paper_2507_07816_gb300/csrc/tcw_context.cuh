@@ -47,6 +47,7 @@ struct tcw_ctx {
   int bank_chunk = 1;      // template groups (of one pass each) per work item
   int opt_lanes = 0;       // sky groups per chunk: 0 = the fewest padded skies, else 16/32/64
   int autotune = 1;        // batched search: pick bank_chunk and tile_segments by timing
+  int amp_power = 0;       // weights times (f(t_j)/f0)^amp_power (Eq. 3)
   int triage_spread = 2;   // triage: patches within this distance of a chosen one are suppressed
   int64_t batch_memory = (int64_t)48 << 30;  // batched search: Psi + anchor bytes per wave
   unsigned bank_epoch = 0; // bumped by every tcw_define_bank

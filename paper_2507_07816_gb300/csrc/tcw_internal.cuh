@@ -49,6 +49,8 @@ constexpr int kNThr = kMHi - kMLo;  // 8 thresholds
 //   cls    kEntryNone / kEntryInside / kEntryEdge
 //   wa[d]  shared address of detector d's staged power window minus
 //          elem*(kMagicBits + woff_d): power of bin base + n0 is at wa[d] + elem*zb
+//          (d < kMaxStageDet = 2); wa[kAmpSlot] holds the fp32 bits of the
+//          template's amplitude weight (f(t_j)/f0)^p of Eq. 3 (1 when p = 0)
 //   kb     base - kMagicBits, so that base + n0 = kb + zb
 //   th[i]  round((c_K/f - 1)/q) with c_K = f_min + (K + 1/2) df, K = base + kMLo + i
 struct __align__(16) TrackEntry {
@@ -61,6 +63,8 @@ struct __align__(16) TrackEntry {
   int pad[3];
   int th[kNThr];
 };
+
+constexpr int kAmpSlot = 2;      // wa[] word of the amplitude weight
 
 constexpr int kEntryNone = 0;    // segment before T0, or every candidate bin outside the band
 constexpr int kEntryInside = 1;  // every candidate bin inside the band
@@ -103,6 +107,7 @@ struct GroupParams {
   double f_min, df, inv_q;
   int nterms;              // binomial-series length for the track; 0 = pow per entry
   int tile_shift;          // tiles of 2^tile_shift segments: anchors and fp32 partial sums
+  int amp_power;           // weights times (f(t_j)/f0)^amp_power (Eq. 3); 0 = none
   int B, Bpad;
   int lanes;               // sky groups per chunk: 16, 32 or 64
   float2* dev;             // scratch [gridDim.x][8192]: per-sky weight sums at band edges
@@ -137,6 +142,7 @@ struct LookupParams {
   const double* tau;
   const double* nbr;
   double T0, f_min, df;
+  int amp_power;           // weights times (f(t_j)/f0)^amp_power (Eq. 3); 0 = none
   int B, Bpad, S, Spad;
   float* psi;
   float* S_out;
@@ -166,6 +172,7 @@ struct DopplerParams {
 
 constexpr int kMaxSeriesTerms = 24;
 constexpr int kMaxStageDet = 2;          // detectors the group kernel stages in shared memory
+static_assert(kAmpSlot >= kMaxStageDet && kAmpSlot < 4, "the amplitude word is a free wa[] slot");
 constexpr int kTileShift = 5;           // default tile: 32 segments
 
 // dynamic shared memory of the group kernel for D detectors
@@ -262,9 +269,12 @@ inline int ilog2(int v) {
 cudaError_t launch_doppler(const DopplerParams& p, cudaStream_t st);
 // Set the shared-memory attribute of the group-kernel variant (also done by
 // launch_group on first use); call before capturing a launch into a graph.
-cudaError_t group_prepare(int n_det, int lanes, bool half, bool weighted);
+// Weighting of the group kernel's lookups: unit weights, the per-segment
+// weights, or the weights times the template's amplitude weight.
+enum Weighting { kUnitWeights = 0, kSegmentWeights = 1, kAmplitudeWeights = 2 };
+cudaError_t group_prepare(int n_det, int lanes, bool half, int weighting);
 // grid = number of CTAs (the length of p.cta_items minus one); one CTA per SM at most
-cudaError_t launch_group(const GroupParams& p, int grid, bool half, bool record, bool weighted,
+cudaError_t launch_group(const GroupParams& p, int grid, bool half, bool record, int weighting,
                          cudaStream_t st);
 cudaError_t launch_lookup(const LookupParams& p, bool half, bool record, cudaStream_t st);
 cudaError_t launch_topk(const float* psi, int Bpad, int B, int S, int k, const int32_t* bank_perm,

@@ -154,6 +154,15 @@ __device__ __forceinline__ void compute_entry(const GroupParams& p, const EventD
     h = pow((tj - ev.T0) / p.tau[b] + 1.0, 1.0 / (p.nbr[b] - 1.0)) / p.f0[b];
   }
   const float f = __frcp_rn((float)h);
+  if (p.amp_power > 0) {
+    // amplitude weight (f/f0)^p = (f0 h)^-p (Eq. 3: power grows as h0^2 ~ f^4)
+    const float r = (float)(h * p.f0[b]);
+    float rp = r;
+    for (int k = 1; k < p.amp_power; ++k) rp *= r;
+    e.wa[kAmpSlot] = __float_as_uint(__frcp_rn(rp));
+  } else {
+    e.wa[kAmpSlot] = __float_as_uint(1.0f);
+  }
   const float x = (f - fmin_f) * inv_df_f;
   const int base = __float2int_rn(x);
   if (!(base >= -kMHi && (int64_t)base < p.n_bin - kMLo)) {
@@ -193,7 +202,9 @@ __device__ __forceinline__ void compute_entry(const GroupParams& p, const EventD
   }
 }
 
-template <typename RhoT, bool RECORD, bool WEIGHTED, int DT, int LN>
+// WT: kUnitWeights, kSegmentWeights or kAmplitudeWeights (segment weight
+// times the entry's amplitude weight, per template).
+template <typename RhoT, bool RECORD, int WT, int DT, int LN>
 __global__ void __launch_bounds__(Geo<LN>::kThreads, 1) group_kernel(GroupParams p) {
   constexpr int G = kGroupSkies;
   constexpr uint32_t ESZ = sizeof(RhoT);
@@ -340,8 +351,14 @@ __global__ void __launch_bounds__(Geo<LN>::kThreads, 1) group_kernel(GroupParams
           const int c0 = __float_as_int(h0.w), c1 = __float_as_int(h1.w);
           const float4 wseg = lds_f4(sbase + (uint32_t)L.hdr + (uint32_t)(kseg * 16));
 #pragma unroll
+          const float am0 = WT == kAmplitudeWeights ? __int_as_float(wa0.z) : 1.0f;
+          const float am1 = WT == kAmplitudeWeights ? __int_as_float(wa1.z) : 1.0f;
+          static_assert(kAmpSlot == 2, "wa[kAmpSlot] is the .z word of the entry's second vector");
+#pragma unroll
           for (int d = 0; d < D; ++d) {
-            const float wd = WEIGHTED ? (d == 0 ? wseg.x : wseg.y) : 1.0f;
+            const float wd = WT != kUnitWeights ? (d == 0 ? wseg.x : wseg.y) : 1.0f;
+            const float ww0 = WT == kAmplitudeWeights ? wd * am0 : wd;
+            const float ww1 = WT == kAmplitudeWeights ? wd * am1 : wd;
             const uint32_t sd = stage + d * kStageDetBytes;
             const float gm = lds_f32(sd - l * 16 + 4 * LN * 16 + l * 4);
             int th0 = INT_MAX, th1 = INT_MAX;
@@ -359,13 +376,13 @@ __global__ void __launch_bounds__(Geo<LN>::kThreads, 1) group_kernel(GroupParams
               const uint32_t a0 = wd0 + ESZ * (uint32_t)zb0, a1 = wd1 + ESZ * (uint32_t)zb1;
               const float rlo0 = lds_pow(a0, RhoT()), rhi0 = lds_pow(a0 + ESZ, RhoT());
               const float rlo1 = lds_pow(a1, RhoT()), rhi1 = lds_pow(a1 + ESZ, RhoT());
-              const float we0 = in0 ? wd : 0.f, we1 = in1 ? wd : 0.f;
+              const float we0 = in0 ? ww0 : 0.f, we1 = in1 ? ww1 : 0.f;
               th0 = in0 ? t0 : INT_MAX;
               th1 = in1 ? t1 : INT_MAX;
               gt[0] = fmaf(we0, in0 ? rlo0 : 0.f, gt[0]);
               gt[1] = fmaf(we1, in1 ? rlo1 : 0.f, gt[1]);
-              dw0 = in0 ? wd * (rhi0 - rlo0) : 0.f;
-              dw1 = in1 ? wd * (rhi1 - rlo1) : 0.f;
+              dw0 = in0 ? ww0 * (rhi0 - rlo0) : 0.f;
+              dw1 = in1 ? ww1 * (rhi1 - rlo1) : 0.f;
               w1t[0] += we0;
               w1t[1] += we1;
               w2t[0] = fmaf(we0, we0, w2t[0]);
@@ -389,6 +406,7 @@ __global__ void __launch_bounds__(Geo<LN>::kThreads, 1) group_kernel(GroupParams
               for (int t = 0; t < 2; ++t) {
                 const int c = t ? c1 : c0;
                 const int zb = t ? zb1 : zb0;
+                const float wt = t ? ww1 : ww0;
                 const uint32_t tha = __float_as_uint(t ? h1.z : h0.z);
                 const uint32_t wdt = t ? wd1 : wd0;
                 const uint32_t ea = t ? e1 : e0;
@@ -431,10 +449,10 @@ __global__ void __launch_bounds__(Geo<LN>::kThreads, 1) group_kernel(GroupParams
                   if (RECORD && rp && s0 + k < ev.S)
                     rp[(int64_t)p.sky_perm[s0 + k] * rstride] = okb ? K0 + (up ? 1 : 0) : -1;
                   if (okb) {
-                    acc[t][k] = fmaf(wd, up ? rhi : rlo, acc[t][k]);
+                    acc[t][k] = fmaf(wt, up ? rhi : rlo, acc[t][k]);
                     float2 dv = dvp[k];
-                    dv.x += wd;
-                    dv.y = fmaf(wd, wd, dv.y);
+                    dv.x += wt;
+                    dv.y = fmaf(wt, wt, dv.y);
                     dvp[k] = dv;
                   }
                 }
@@ -564,7 +582,7 @@ cudaError_t launch_anchors(const AnchorParams& p, cudaStream_t st) {
 
 // The dynamic shared-memory limit of each variant is raised once per device
 // (again when a variant shared by several detector counts needs more).
-template <typename R, bool REC, bool WT, int DT, int LN>
+template <typename R, bool REC, int WT, int DT, int LN>
 cudaError_t set_smem_t(size_t smem) {
   constexpr int kDevices = 64;
   static size_t done[kDevices] = {};
@@ -578,7 +596,7 @@ cudaError_t set_smem_t(size_t smem) {
   return e;
 }
 
-template <typename R, bool REC, bool WT, int DT, int LN>
+template <typename R, bool REC, int WT, int DT, int LN>
 cudaError_t launch_group_t(const GroupParams& p, int grid, cudaStream_t st) {
   const size_t smem = PersistLayout(p.n_det, LN).total;
   cudaError_t e = set_smem_t<R, REC, WT, DT, LN>(smem);
@@ -588,57 +606,74 @@ cudaError_t launch_group_t(const GroupParams& p, int grid, cudaStream_t st) {
 }
 
 template <typename R, int LN>
-cudaError_t launch_group_l(const GroupParams& p, bool record, bool weighted, int grid, cudaStream_t st) {
-  if (record) return launch_group_t<R, true, true, 0, LN>(p, grid, st);
-  if (weighted) {
-    if (p.n_det == 1) return launch_group_t<R, false, true, 1, LN>(p, grid, st);
-    return launch_group_t<R, false, true, 2, LN>(p, grid, st);
+cudaError_t launch_group_l(const GroupParams& p, bool record, int wt, int grid, cudaStream_t st) {
+  // recording reads the amplitude word, which holds 1 when p.amp_power == 0
+  if (record) return launch_group_t<R, true, kAmplitudeWeights, 0, LN>(p, grid, st);
+  switch (wt) {
+    case kAmplitudeWeights:
+      if (p.n_det == 1) return launch_group_t<R, false, kAmplitudeWeights, 1, LN>(p, grid, st);
+      return launch_group_t<R, false, kAmplitudeWeights, 2, LN>(p, grid, st);
+    case kSegmentWeights:
+      if (p.n_det == 1) return launch_group_t<R, false, kSegmentWeights, 1, LN>(p, grid, st);
+      return launch_group_t<R, false, kSegmentWeights, 2, LN>(p, grid, st);
+    case kUnitWeights:
+      if (p.n_det == 1) return launch_group_t<R, false, kUnitWeights, 1, LN>(p, grid, st);
+      return launch_group_t<R, false, kUnitWeights, 2, LN>(p, grid, st);
+    default:
+      return cudaErrorInvalidValue;
   }
-  if (p.n_det == 1) return launch_group_t<R, false, false, 1, LN>(p, grid, st);
-  return launch_group_t<R, false, false, 2, LN>(p, grid, st);
 }
 
 template <typename R>
-cudaError_t launch_group_r(const GroupParams& p, bool record, bool weighted, int grid, cudaStream_t st) {
+cudaError_t launch_group_r(const GroupParams& p, bool record, int wt, int grid, cudaStream_t st) {
   switch (p.lanes) {
-    case 16: return launch_group_l<R, 16>(p, record, weighted, grid, st);
-    case 32: return launch_group_l<R, 32>(p, record, weighted, grid, st);
-    case 64: return launch_group_l<R, 64>(p, record, weighted, grid, st);
+    case 16: return launch_group_l<R, 16>(p, record, wt, grid, st);
+    case 32: return launch_group_l<R, 32>(p, record, wt, grid, st);
+    case 64: return launch_group_l<R, 64>(p, record, wt, grid, st);
     default: return cudaErrorInvalidValue;
   }
+}
+
+template <typename R, int LN, int WT>
+cudaError_t prepare_w(int n_det, size_t smem) {
+  return n_det == 1 ? set_smem_t<R, false, WT, 1, LN>(smem) : set_smem_t<R, false, WT, 2, LN>(smem);
 }
 
 template <typename R, int LN>
-cudaError_t prepare_l(int n_det, bool weighted) {
+cudaError_t prepare_l(int n_det, int wt) {
   const size_t smem = PersistLayout(n_det, LN).total;
-  if (weighted)
-    return n_det == 1 ? set_smem_t<R, false, true, 1, LN>(smem) : set_smem_t<R, false, true, 2, LN>(smem);
-  return n_det == 1 ? set_smem_t<R, false, false, 1, LN>(smem) : set_smem_t<R, false, false, 2, LN>(smem);
-}
-
-template <typename R>
-cudaError_t prepare_r(int n_det, int lanes, bool weighted) {
-  switch (lanes) {
-    case 16: return prepare_l<R, 16>(n_det, weighted);
-    case 32: return prepare_l<R, 32>(n_det, weighted);
-    case 64: return prepare_l<R, 64>(n_det, weighted);
+  switch (wt) {
+    case kAmplitudeWeights: return prepare_w<R, LN, kAmplitudeWeights>(n_det, smem);
+    case kSegmentWeights: return prepare_w<R, LN, kSegmentWeights>(n_det, smem);
+    case kUnitWeights: return prepare_w<R, LN, kUnitWeights>(n_det, smem);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t group_prepare(int n_det, int lanes, bool half, bool weighted) {
+template <typename R>
+cudaError_t prepare_r(int n_det, int lanes, int wt) {
+  switch (lanes) {
+    case 16: return prepare_l<R, 16>(n_det, wt);
+    case 32: return prepare_l<R, 32>(n_det, wt);
+    case 64: return prepare_l<R, 64>(n_det, wt);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t group_prepare(int n_det, int lanes, bool half, int weighting) {
   if (n_det < 1 || n_det > kMaxStageDet) return cudaErrorInvalidValue;
-  return half ? prepare_r<__half>(n_det, lanes, weighted) : prepare_r<float>(n_det, lanes, weighted);
+  return half ? prepare_r<__half>(n_det, lanes, weighting) : prepare_r<float>(n_det, lanes, weighting);
 }
 
 // Needs 1 <= p.n_det <= kMaxStageDet, p.lanes in {16, 32, 64}, and the
 // anchors of launch_anchors when p.nterms > 0.
-cudaError_t launch_group(const GroupParams& p, int grid, bool half, bool record, bool weighted,
+cudaError_t launch_group(const GroupParams& p, int grid, bool half, bool record, int weighting,
                          cudaStream_t st) {
   if (p.n_det < 1 || p.n_det > kMaxStageDet) return cudaErrorInvalidValue;
+  if (p.amp_power > 0 && weighting != kAmplitudeWeights && !record) return cudaErrorInvalidValue;
   if (grid <= 0) return cudaSuccess;
-  return half ? launch_group_r<__half>(p, record, weighted, grid, st)
-              : launch_group_r<float>(p, record, weighted, grid, st);
+  return half ? launch_group_r<__half>(p, record, weighting, grid, st)
+              : launch_group_r<float>(p, record, weighting, grid, st);
 }
 
 }  // namespace tcw

@@ -64,7 +64,8 @@ __global__ void doppler_kernel(DopplerParams p) {
 
 // ---------------------------------------------------------------------------
 // Per-lookup kernel: one thread per (sorted sky, sorted template), FP64
-// throughout (Eq. 1, Eq. 2, nearest bin, weighted sum, Eq. 4).
+// throughout (Eq. 1, Eq. 2, nearest bin, weighted sum with the optional
+// amplitude weight (f/f0)^p of Eq. 3, Eq. 4).
 // ---------------------------------------------------------------------------
 template <typename RhoT, bool RECORD>
 __global__ void lookup_kernel(LookupParams p) {
@@ -80,9 +81,11 @@ __global__ void lookup_kernel(LookupParams p) {
     for (int j = 0; j < p.n_seg; ++j) {
       const int64_t dj = (int64_t)d * p.n_seg + j;
       int64_t k = -1;
+      double amp = 1.0;
       const double t = p.t_mid[j];
       if (t >= p.T0) {
         const double f = f0 * pow((t - p.T0) / tau + 1.0, ex);
+        for (int e = 0; e < p.amp_power; ++e) amp *= f / f0;   // (f/f0)^p, Eq. 3
         const double* v = p.vel + dj * 3;
         const double fh = f * (1.0 + (v[0] * n[0] + v[1] * n[1] + v[2] * n[2]) / kLightSpeed);
         const double kk = floor((fh - p.f_min) / p.df + 0.5);
@@ -92,7 +95,7 @@ __global__ void lookup_kernel(LookupParams p) {
         p.rec[(((int64_t)p.sky_perm[s] * p.B + p.bank_perm[b]) * p.n_det + d) * p.n_seg + j] =
             (int32_t)k;
       if (k < 0) continue;
-      const double w = (double)p.weights[dj];
+      const double w = (double)p.weights[dj] * amp;
       S += w * (double)load_rho(rho + dj * p.n_bin, k);
       W1 += w;
       W2 += w * w;

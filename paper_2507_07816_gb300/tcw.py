@@ -22,6 +22,7 @@ F32, F16 = 0, 1
 KERNEL_AUTO, KERNEL_GROUP, KERNEL_LOOKUP = 0, 1, 2
 OPT_KERNEL, OPT_KEEP_STATS, OPT_TILE_SEGMENTS, OPT_BANK_CHUNK = 1, 2, 3, 4
 OPT_AUTOTUNE, OPT_BATCH_MEMORY, OPT_SKY_LANES, OPT_TRIAGE_SPREAD = 5, 6, 7, 8
+OPT_AMPLITUDE_POWER = 9
 
 _lock = threading.Lock()
 _lib = None

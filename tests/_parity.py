@@ -15,10 +15,10 @@ REL = 1e-5
 TIE = 2.0 ** -30
 
 
-def oracle_stats(p, pairs=None, rho=None, nthreads=0):
+def oracle_stats(p, pairs=None, rho=None, nthreads=0, amp_power=0):
     return oracle.search_stats(p.rho if rho is None else rho, p.f_min, p.df, p.t_mid, p.weights,
                                p.velocity, p.nhat, p.bank.f0, p.bank.tau, p.bank.n, p.T0,
-                               pairs=pairs, nthreads=nthreads)
+                               pairs=pairs, nthreads=nthreads, amp_power=amp_power)
 
 
 def assert_stats_close(gpu, ora, where=""):

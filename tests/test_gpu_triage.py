@@ -131,7 +131,8 @@ def test_training_beats_the_untrained_network():
     assert r_tr >= 0.5 and r_tr > r_un + 0.2, (r_tr, r_un)
 
 
-def test_triaged_search_rows_equal_exhaustive_rows():
+@pytest.mark.parametrize("amp", [0, 4])
+def test_triaged_search_rows_equal_exhaustive_rows(amp):
     ev, bank = small_event(84, n_sky=200, n_inj=2, snr=(14.0, 16.0), n_bin=9600, t_sft=32.0)
     # hand-set network: score = sum of the log-counts of the 28 highest histogram bins
     theta = np.zeros(OT.N_PARAMS, np.float32)
@@ -142,6 +143,7 @@ def test_triaged_search_rows_equal_exhaustive_rows():
     mlp = tcw.Mlp(theta, device=DEV)
     s = tcw.Search(0)
     s.set_option(tcw.OPT_TRIAGE_SPREAD, 0)
+    s.set_option(tcw.OPT_AMPLITUDE_POWER, amp)     # the exhaustive part takes the weighting too
     TR.load_event(s, ev, bank)
     k = 8
     pf, xf = s.search(k)
