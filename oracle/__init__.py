@@ -70,9 +70,9 @@ def _load():
             lib.oracle_search_stats.argtypes = [
                 p, i, i, i, d, d, p, p, p, p, i, p, p, p, i, d, p, i64,
                 p, p, p, p, i]
-            lib.oracle_search_stats_amp.restype = None
-            lib.oracle_search_stats_amp.argtypes = [
-                p, i, i, i, d, d, p, p, p, p, i, p, p, p, i, d, i, p, i64,
+            lib.oracle_search_stats_ext.restype = None
+            lib.oracle_search_stats_ext.argtypes = [
+                p, i, i, i, d, d, p, p, p, p, i, p, p, p, i, d, i, i, d, p, i64,
                 p, p, p, p, i]
             lib.oracle_track_coordinates.restype = None
             lib.oracle_track_coordinates.argtypes = [
@@ -122,7 +122,7 @@ def critical_ratio(S, W1, W2) -> float:
 
 
 def search_stats(rho, f_min, df, t_mid, weights, velocity, nhat, f0, tau, n, T0,
-                 pairs=None, nthreads=0, amp_power=0):
+                 pairs=None, nthreads=0, amp_power=0, rho_th=None):
     """S, W1, W2, Psi for every (sky, template) pair.
 
     rho [D][Nseg][Nbin] float32 (float16 input is widened exactly);
@@ -130,7 +130,10 @@ def search_stats(rho, f_min, df, t_mid, weights, velocity, nhat, f0, tau, n, T0,
     nhat [S][3]; f0/tau/n [B]; pairs [P][2] of (sky, template) or None for the
     full [S][B] grid.  amp_power > 0 multiplies every weight by
     (f(t_j)/f0)^amp_power, the template's own amplitude evolution (Eq. 3 gives
-    4 for a power statistic).  Returns four float64 arrays shaped [P] or [S][B].
+    4 for a power statistic).  rho_th (a float > 0) selects the number count
+    instead of the power: nu = 1 where rho > rho_th, Psi with mean q*W1 and
+    variance q(1-q)*W2, q = exp(-rho_th).  Returns four float64 arrays shaped
+    [P] or [S][B].
     """
     rho = _c(np.asarray(rho).astype(np.float32, copy=False), np.float32)
     D, Nseg, Nbin = rho.shape
@@ -152,10 +155,12 @@ def search_stats(rho, f_min, df, t_mid, weights, velocity, nhat, f0, tau, n, T0,
         shape, P = (pp.shape[0],), pp.shape[0]
     outs = [np.empty(shape, np.float64) for _ in range(4)]
     assert int(amp_power) >= 0
-    _load().oracle_search_stats_amp(
+    assert rho_th is None or float(rho_th) > 0
+    _load().oracle_search_stats_ext(
         _ptr(rho), D, Nseg, Nbin, float(f_min), float(df), _ptr(t_mid),
         _ptr(weights), _ptr(velocity), _ptr(nhat), S_, _ptr(f0), _ptr(tau),
-        _ptr(n), B, float(T0), int(amp_power), _ptr(pp), P, *(_ptr(o) for o in outs),
+        _ptr(n), B, float(T0), int(amp_power), 0 if rho_th is None else 1,
+        0.0 if rho_th is None else float(rho_th), _ptr(pp), P, *(_ptr(o) for o in outs),
         int(nthreads))
     return tuple(outs)
 

@@ -30,6 +30,12 @@
  *   - detectors are combined inside one sum;
  *   - Psi = -inf when no lookup is valid (W2 == 0);
  *   - top-k orders by (Psi descending, template index ascending).
+ *
+ * Number count (Sec. 2, the second statistic of the paper): each lookup
+ * contributes nu = 1 when the bin's normalized power exceeds rho_th strictly
+ * (compared in double), else 0, so s = sum w*nu.  Under noise rho is Exp(1),
+ * so nu is Bernoulli(q) with q = exp(-rho_th): <s> = q*W1 and
+ * sigma_s^2 = q(1-q)*W2.  rho_th is a caller parameter.
  */
 #include <math.h>
 #include <stdint.h>
@@ -74,6 +80,14 @@ double oracle_critical_ratio(double S, double W1, double W2)
     return (S - W1) / sqrt(W2);
 }
 
+/* Eq. 4 for the number count: <s> = q*W1, sigma_s = sqrt(q(1-q)*W2), q = exp(-rho_th). */
+double oracle_critical_ratio_count(double S, double W1, double W2, double rho_th)
+{
+    double q = exp(-rho_th);
+    if (W2 <= 0.0) return -INFINITY;
+    return (S - q * W1) / sqrt(q * (1.0 - q) * W2);
+}
+
 /*
  * Statistic of one (sky, template) pair: S = sum w*rho, W1 = sum w,
  * W2 = sum w^2 over every detector d and segment j whose track bin lies in
@@ -89,7 +103,8 @@ static void oracle_pair_stats(const float *rho, int D, int Nseg, int Nbin,
                               double f_min, double df, const double *t_mid,
                               const float *w, const double *v,
                               const double *nhat, double f0, double tau,
-                              double n, double T0, int amp_power, double out[3])
+                              double n, double T0, int amp_power,
+                              int number_count, double rho_th, double out[3])
 {
     double S = 0.0, W1 = 0.0, W2 = 0.0;
     for (int d = 0; d < D; ++d) {
@@ -106,6 +121,7 @@ static void oracle_pair_stats(const float *rho, int D, int Nseg, int Nbin,
              * segment j scales as (f(t_j)/f0)^4 (amp_power = 4) */
             if (amp_power > 0) wj *= pow(f / f0, (double)amp_power);
             double r = (double)rho[((size_t)d * Nseg + j) * (size_t)Nbin + (size_t)k];
+            if (number_count) r = r > rho_th ? 1.0 : 0.0;
             S += wj * r;
             W1 += wj;
             W2 += wj * wj;
@@ -122,12 +138,13 @@ static void oracle_pair_stats(const float *rho, int D, int Nseg, int Nbin,
  * Outputs S_out, W1_out, W2_out, Psi_out (any may be NULL).
  * nthreads <= 0 uses the OpenMP default.
  */
-void oracle_search_stats_amp(const float *rho, int D, int Nseg, int Nbin,
+void oracle_search_stats_ext(const float *rho, int D, int Nseg, int Nbin,
                              double f_min, double df, const double *t_mid,
                              const float *w, const double *v,
                              const double *nhat, int n_sky,
                              const double *f0, const double *tau, const double *n,
                              int n_tmpl, double T0, int amp_power,
+                             int number_count, double rho_th,
                              const int64_t *pairs, int64_t P,
                              double *S_out, double *W1_out, double *W2_out,
                              double *Psi_out, int nthreads);
@@ -142,18 +159,21 @@ void oracle_search_stats(const float *rho, int D, int Nseg, int Nbin,
                          double *S_out, double *W1_out, double *W2_out,
                          double *Psi_out, int nthreads)
 {
-    oracle_search_stats_amp(rho, D, Nseg, Nbin, f_min, df, t_mid, w, v, nhat, n_sky, f0, tau, n,
-                            n_tmpl, T0, 0, pairs, P, S_out, W1_out, W2_out, Psi_out, nthreads);
+    oracle_search_stats_ext(rho, D, Nseg, Nbin, f_min, df, t_mid, w, v, nhat, n_sky, f0, tau, n,
+                            n_tmpl, T0, 0, 0, 0.0, pairs, P, S_out, W1_out, W2_out, Psi_out,
+                            nthreads);
 }
 
 /* As oracle_search_stats, with every weight multiplied by (f(t_j)/f0)^amp_power
- * (amp_power = 0: none). */
-void oracle_search_stats_amp(const float *rho, int D, int Nseg, int Nbin,
+ * (amp_power = 0: none), and with the number count of threshold rho_th in
+ * place of the power when number_count != 0. */
+void oracle_search_stats_ext(const float *rho, int D, int Nseg, int Nbin,
                              double f_min, double df, const double *t_mid,
                              const float *w, const double *v,
                              const double *nhat, int n_sky,
                              const double *f0, const double *tau, const double *n,
                              int n_tmpl, double T0, int amp_power,
+                             int number_count, double rho_th,
                              const int64_t *pairs, int64_t P,
                              double *S_out, double *W1_out, double *W2_out,
                              double *Psi_out, int nthreads)
@@ -174,11 +194,14 @@ void oracle_search_stats_amp(const float *rho, int D, int Nseg, int Nbin,
         }
         double st[3];
         oracle_pair_stats(rho, D, Nseg, Nbin, f_min, df, t_mid, w, v,
-                          nhat + 3 * s, f0[b], tau[b], n[b], T0, amp_power, st);
+                          nhat + 3 * s, f0[b], tau[b], n[b], T0, amp_power,
+                          number_count, rho_th, st);
         if (S_out) S_out[i] = st[0];
         if (W1_out) W1_out[i] = st[1];
         if (W2_out) W2_out[i] = st[2];
-        if (Psi_out) Psi_out[i] = oracle_critical_ratio(st[0], st[1], st[2]);
+        if (Psi_out)
+            Psi_out[i] = number_count ? oracle_critical_ratio_count(st[0], st[1], st[2], rho_th)
+                                      : oracle_critical_ratio(st[0], st[1], st[2]);
     }
 }
 

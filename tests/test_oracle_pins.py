@@ -205,6 +205,87 @@ def test_amplitude_weight_closed_form_n5():
     assert (W1 < W10).all()
 
 
+def _band_edge_case(**kw):
+    kv = {row[0]: row[1:] for row in _read_rows("out_of_band_case.txt")}
+    t = np.array(list(map(float, kv["t_mid"])))
+    w = np.array([list(map(float, kv["weights"]))], np.float32)
+    n_bin = int(kv["n_bin"][0])
+    rho = np.zeros((1, t.size, n_bin), np.float32)
+    for j in range(t.size):
+        rho[0, j] = 1 + j + np.arange(n_bin) / 100.0
+    out = oracle.search_stats(
+        rho, float(kv["f_min"][0]), float(kv["df"][0]), t, w, np.zeros((1, t.size, 3)),
+        np.array([[0.0, 0.0, 1.0]]), [float(kv["f0"][0])], [float(kv["tau"][0])],
+        [float(kv["n"][0])], float(kv["T0"][0]), **kw)
+    return tuple(float(x[0, 0]) for x in out)
+
+
+def test_number_count_fixture():
+    """Number count on the hand-computed band-edge case: nu = [rho > rho_th],
+    S = sum w nu, Psi with the Bernoulli(exp(-rho_th)) mean and variance."""
+    kv = {row[0]: row[1:] for row in _read_rows("number_count_case.txt")}
+    th = float(kv["rho_th"][0])
+    S, W1, W2, Psi = _band_edge_case(rho_th=th)
+    assert S == float(kv["S"][0])
+    assert W1 == pytest.approx(float(kv["W1"][0]), rel=1e-12)
+    assert W2 == pytest.approx(float(kv["W2"][0]), rel=1e-12)
+    q = math.exp(-th)
+    assert Psi == pytest.approx((0.75 - q * 2.75) / math.sqrt(q * (1 - q) * 4.3125), rel=1e-12)
+
+
+def test_number_count_threshold_is_strict_in_double():
+    """rho equal to rho_th counts 0 and the compare is made in double: a
+    threshold one double ulp below the float power 3.01f counts it."""
+    r301 = float(np.float32(3.01))
+    assert _band_edge_case(rho_th=r301)[0] == 0.25               # 3.01f == rho_th: not counted
+    assert _band_edge_case(rho_th=math.nextafter(r301, 0.0))[0] == 0.75
+    r61 = float(np.float32(6.1))                                  # 6.0999999046..., below 6.1
+    assert _band_edge_case(rho_th=6.1)[0] == 0.0
+    assert _band_edge_case(rho_th=r61)[0] == 0.0
+    assert _band_edge_case(rho_th=math.nextafter(r61, 0.0))[0] == 0.25
+
+
+def test_number_count_noise_mean_zero_variance_one():
+    """Under Exp(1) noise nu is Bernoulli(exp(-rho_th)): the weighted count's
+    Psi has mean 0 and variance 1 over disjoint tracks (binomial moments)."""
+    vals = []
+    r = syn.rng(23)
+    n_seg, n_bin = 48, 2048
+    t = syn.segment_times(n_seg, 32.0)
+    T0 = t[0] - 16.0
+    vel = np.zeros((1, n_seg, 3))
+    f0 = 510.0 + 1.25 * np.arange(48)
+    tau = np.full(f0.shape, 35000.0)
+    n = np.full(f0.shape, 5.0)
+    for _ in range(300):
+        rho = syn.exponential_noise(r, (1, n_seg, n_bin))
+        w = syn.uniform_weights(r, 1, n_seg, 0.2, 2.0)
+        vals.append(oracle.search_stats(rho, 500.0, 1 / 32, t, w, vel, np.array([[0, 0, 1.0]]),
+                                        f0, tau, n, T0, rho_th=1.6)[3].ravel())
+    v = np.concatenate(vals)
+    N = v.size
+    assert abs(v.mean()) < 4.0 / math.sqrt(N)
+    assert abs(v.var() - 1.0) < 4.0 * math.sqrt(3.0 / N)
+
+
+def test_number_count_is_the_power_sum_of_the_thresholded_map():
+    """S and W of the count equal the power statistic of the 0/1 map [rho > rho_th]
+    (brute-force threshold in numpy), with and without the amplitude weight."""
+    p = syn.config_small(seed=24, n_seg=40, n_bin=1024, n_f0=6, n_tau=3, snr=8, weights=True)
+    nu = (p.rho.astype(np.float64) > 1.6).astype(np.float32)
+    for amp in (0, 4):
+        a = oracle.search_stats(p.rho, p.f_min, p.df, p.t_mid, p.weights, p.velocity, p.nhat,
+                                p.bank.f0, p.bank.tau, p.bank.n, p.T0, amp_power=amp, rho_th=1.6)
+        b = oracle.search_stats(nu, p.f_min, p.df, p.t_mid, p.weights, p.velocity, p.nhat,
+                                p.bank.f0, p.bank.tau, p.bank.n, p.T0, amp_power=amp)
+        for x, y in zip(a[:3], b[:3]):
+            np.testing.assert_array_equal(x, y)
+        q = math.exp(-1.6)
+        fin = b[2] > 0
+        np.testing.assert_allclose(a[3][fin], (b[0][fin] - q * b[1][fin]) / np.sqrt(q * (1 - q) * b[2][fin]),
+                                   rtol=1e-13, atol=1e-13)
+
+
 def test_pre_T0_segments_are_dropped():
     """Statistic with T0 mid-way equals the statistic of the map cut at T0."""
     p = syn.config_small(seed=11, n_seg=64, n_bin=1024, n_f0=4, n_tau=4, snr=0, weights=True)
