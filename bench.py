@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--no-amplitude", action="store_true", help="skip the amplitude and count variants")
     ap.add_argument("--batched-events", type=int, default=64)
     ap.add_argument("--batched-templates", type=int, default=20000)
     ap.add_argument("--learned-events", type=int, default=6)
@@ -414,6 +415,37 @@ def bench_ours(args):
                        "probe over a 64 MiB L2-resident buffer, measured in this run"}
 
     extras = {}
+    if rank == 0 and world == 1 and args.workload == "full" and not args.no_amplitude:
+        # the same search with the Eq. 3 amplitude weight (f(t_j)/f0)^4 on every
+        # lookup, and with the number count (rho > 1.6) in place of the power
+        def variant(name, on, off, meta):
+            try:
+                on()
+                s.search(k, psi_out, idx_out)      # warm-up (builds the count bit map)
+                torch.cuda.synchronize()
+                v_ms = []
+                a0 = torch.cuda.Event(enable_timing=True)
+                a1 = torch.cuda.Event(enable_timing=True)
+                n_v = max(1, min(3, args.steps))
+                a0.record(stream)
+                for _ in range(n_v):
+                    s.search(k, psi_out, idx_out)
+                    v_ms.append(s.info().search_ms)
+                a1.record(stream)
+                torch.cuda.synchronize()
+                ms = a0.elapsed_time(a1) / n_v
+                extras[name] = dict(meta, value=U / (ms / 1000.0), unit=UNIT, ms_per_step=ms,
+                                    kernel_ms=statistics.mean(v_ms), steps=n_v,
+                                    vs_plain=(U / (ms / 1000.0)) / value)
+            except Exception as exc:
+                extras[name] = {"error": f"{type(exc).__name__}: {exc}"}
+            finally:
+                off()
+
+        variant("amplitude", lambda: s.set_option(tcw.OPT_AMPLITUDE_POWER, 4),
+                lambda: s.set_option(tcw.OPT_AMPLITUDE_POWER, 0), {"amp_power": 4})
+        variant("number_count", lambda: s.set_statistic(tcw.STAT_NUMBER_COUNT, 1.6),
+                lambda: s.set_statistic(tcw.STAT_POWER), {"rho_th": 1.6})
     if rank == 0 and world == 1 and args.workload == "full":
         for name, fn, skip in (("batched", bench_batched, args.no_batched),
                                ("learned", bench_learned, args.no_learned)):

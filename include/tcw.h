@@ -116,6 +116,23 @@ tcw_status tcw_destroy(tcw_ctx *ctx);
 /* Set an option (TCW_OPT_*).  Errors: INVALID_ARGUMENT. */
 tcw_status tcw_set_option(tcw_ctx *ctx, int option, int64_t value);
 
+/* Statistic summed along the tracks (Sec. 2 of arXiv:2507.07816 names two):
+ *   TCW_STAT_POWER          s = sum w rho; Eq. 4 with <s> = W1, sigma^2 = W2
+ *                           (default; rho_th ignored)
+ *   TCW_STAT_NUMBER_COUNT   s = sum w nu with nu = 1 where the bin's power
+ *                           exceeds rho_th strictly (compared in double),
+ *                           else 0; under noise rho ~ Exp(1), so nu is
+ *                           Bernoulli(q), q = exp(-rho_th), and Eq. 4 uses
+ *                           <s> = q W1, sigma^2 = q (1 - q) W2.
+ * The spectrogram stays loaded as power; the count is taken from it on the
+ * device (a bit map of n_det x n_seg x (n_bin/32 + 2) words, rebuilt after
+ * each load or threshold change).  Applies to tcw_search, tcw_search_batched,
+ * tcw_search_triaged (its exhaustive part; the coarse ranking stays on power)
+ * and tcw_statistics (S = sum w nu).  Not available in tcw_search_noalloc.
+ * Errors: INVALID_ARGUMENT (unknown statistic; rho_th not finite and > 0). */
+enum { TCW_STAT_POWER = 0, TCW_STAT_NUMBER_COUNT = 1 };
+tcw_status tcw_set_statistic(tcw_ctx *ctx, int statistic, double rho_th);
+
 /*
  * Load the normalized-power spectrogram (Sec. 2: SFT data processed into
  * normalized power rho_j) of n_det detectors that share segment times.

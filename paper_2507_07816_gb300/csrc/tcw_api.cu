@@ -117,6 +117,22 @@ tcw_status prepare_sky(tcw_ctx* c) {
   return TCW_OK;
 }
 
+// Number-count bit map of the loaded spectrogram, rebuilt after a new load or
+// a threshold change.  Adds its launch to *launches.
+tcw_status ensure_bits(tcw_ctx* c, int* launches) {
+  if (c->bits_epoch == c->spec_epoch && c->bits_th == c->rho_th) return TCW_OK;
+  const int bp = bit_pitch_for(c->Nbin);
+  const int64_t rows = (int64_t)c->D * c->Nseg;
+  TCW_CUDA(c, c->bits.ensure((size_t)rows * bp * sizeof(uint32_t)), "count bit map");
+  TCW_CUDA(c, launch_count_bits(c->rho.p, c->dtype == TCW_F16, rows, c->Nbin, bp, c->rho_th,
+                                c->bits.as<uint32_t>(), c->stream),
+           "count_bits_kernel launch");
+  ++*launches;
+  c->bits_epoch = c->spec_epoch;
+  c->bits_th = c->rho_th;
+  return TCW_OK;
+}
+
 tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
   if (!c->have_spec) return fail(c, TCW_ERR_STATE, "no spectrogram loaded");
   if (!c->have_vel) return fail(c, TCW_ERR_STATE, "no velocities loaded");
@@ -171,7 +187,9 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
       kernel = TCW_KERNEL_LOOKUP;
     }
   }
+  const bool count = c->statistic == TCW_STAT_NUMBER_COUNT;
   if (kernel == TCW_KERNEL_GROUP) {
+    if (count && (st = ensure_bits(c, &launches)) != TCW_OK) return st;
     const int tile_shift = ilog2(c->tile_segments);
     const int n_tiles = (int)((c->Nseg + c->tile_segments - 1) / c->tile_segments);
     const int n_chunks = c->Spad / chunk_skies(c->lanes);
@@ -218,6 +236,8 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
     ev.S = (int)c->S;
     ev.Spad = c->Spad;
     ev.NG = c->NG;
+    ev.bits = count ? c->bits.as<uint32_t>() : nullptr;
+    ev.bit_pitch = count ? bit_pitch_for(c->Nbin) : 0;
     AnchorParams ap{};
     if (pl.nterms > 0) {
       TCW_CUDA(c, c->anchors.ensure((size_t)c->Bpad * n_tiles * 2 * sizeof(double)), "anchors");
@@ -251,6 +271,7 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
     gp.nterms = pl.nterms;
     gp.tile_shift = tile_shift;
     gp.amp_power = c->amp_power;
+    gp.nc_q = count ? std::exp(-c->rho_th) : 0.0;
     gp.B = (int)c->B;
     gp.Bpad = c->Bpad;
     gp.lanes = c->lanes;
@@ -266,7 +287,8 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
       ++launches;
     }
     const int wt = c->amp_power > 0 ? kAmplitudeWeights : (c->unit_weights ? kUnitWeights : kSegmentWeights);
-    TCW_CUDA(c, launch_group(gp, c->grid, c->dtype == TCW_F16, record, wt, c->stream),
+    // counts are staged as fp32 windows whatever the map's type
+    TCW_CUDA(c, launch_group(gp, c->grid, c->dtype == TCW_F16 && !count, record, wt, c->stream),
              "group_kernel launch");
     TCW_CUDA(c, cudaEventRecord(c->ev1, c->stream), "event");
     ++launches;
@@ -287,6 +309,8 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
     lp.f_min = c->f_min;
     lp.df = c->df;
     lp.amp_power = c->amp_power;
+    lp.number_count = count ? 1 : 0;
+    lp.rho_th = c->rho_th;
     lp.B = (int)c->B;
     lp.Bpad = c->Bpad;
     lp.S = (int)c->S;
@@ -570,6 +594,21 @@ tcw_status tcw_load_spectrogram(tcw_ctx* c, int n_det, int64_t n_seg, int64_t n_
   c->have_spec = true;
   c->have_result = false;
   c->sky_dirty = true;
+  ++c->spec_epoch;
+  return TCW_OK;
+}
+
+tcw_status tcw_set_statistic(tcw_ctx* c, int statistic, double rho_th) {
+  if (!c) return TCW_ERR_INVALID_ARGUMENT;
+  if (statistic == TCW_STAT_POWER) {
+    c->statistic = statistic;
+    return TCW_OK;
+  }
+  if (statistic != TCW_STAT_NUMBER_COUNT) return fail(c, TCW_ERR_INVALID_ARGUMENT, "unknown statistic");
+  if (!std::isfinite(rho_th) || !(rho_th > 0))
+    return fail(c, TCW_ERR_INVALID_ARGUMENT, "rho_th must be finite and > 0");
+  c->statistic = statistic;
+  c->rho_th = rho_th;
   return TCW_OK;
 }
 

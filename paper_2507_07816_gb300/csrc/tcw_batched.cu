@@ -35,6 +35,7 @@ struct EventHost {
   bool unit_w = true;
   int Spad = 0, NG = 0, n_chunks = 0;
   size_t o_rho = 0, o_t = 0, o_w = 0, o_v = 0, o_nhat = 0, o_perm = 0, o_blk = 0;  // byte offsets
+  size_t o_bits = 0;               // byte offset of the number-count bit map
   size_t o_anchor = 0, o_psi = 0;  // byte offsets in the wave buffers
   int64_t out_row = 0;             // first output row (sum of earlier events' n_sky)
   int wave = 0;
@@ -58,6 +59,8 @@ struct BatchState {
   bool unit_weights = true;
   int64_t total_sky = 0;
   DevBuf rho, small, blk, anchors, psi, out_psi, out_idx, evtab, items, dev, flags;
+  DevBuf bits;                     // number-count bit maps of every event
+  double bits_th = -1;             // threshold the bit maps were made with
   // plan
   bool planned = false;
   double q = 0, inv_q = 0, doppler_bins = 0;
@@ -76,6 +79,7 @@ struct BatchState {
   int graph_k = 0, graph_nodes = 0;
   int64_t graph_mem = 0;           // wave budget the graph was recorded with
   int graph_amp = 0;               // amplitude power the graph was recorded with
+  double graph_nc = 0;             // number-count q the graph was recorded with (0 = power)
   // last search
   bool have_result = false;
   int last_k = 0;
@@ -88,7 +92,7 @@ void batch_free(tcw_ctx* c) {
   BatchState* b = c->batch;
   if (b->exec) cudaGraphExecDestroy(b->exec);
   DevBuf* bufs[] = {&b->rho, &b->small, &b->blk, &b->anchors, &b->psi, &b->out_psi,
-                    &b->out_idx, &b->evtab, &b->items, &b->dev, &b->flags};
+                    &b->out_idx, &b->evtab, &b->items, &b->dev, &b->flags, &b->bits};
   for (DevBuf* d : bufs) d->release();
   delete b;
   c->batch = nullptr;
@@ -223,8 +227,38 @@ EventDesc make_desc(const tcw_ctx* c, BatchState* b, const EventHost& e, int til
   d.S = (int)e.n_sky;
   d.Spad = e.Spad;
   d.NG = e.NG;
-  (void)c;
+  if (c->statistic == TCW_STAT_NUMBER_COUNT) {
+    d.bits = at<uint32_t>(b->bits, e.o_bits);
+    d.bit_pitch = bit_pitch_for(b->n_bin);
+  }
   return d;
+}
+
+// q of the number count (0 for the power statistic).
+double count_q(const tcw_ctx* c) { return c->statistic == TCW_STAT_NUMBER_COUNT ? std::exp(-c->rho_th) : 0.0; }
+
+// Counts are staged as fp32 windows whatever the map's type.
+bool half_windows(const tcw_ctx* c, const BatchState* b) {
+  return b->dtype == TCW_F16 && c->statistic != TCW_STAT_NUMBER_COUNT;
+}
+
+// Number-count bit maps of every event for the current threshold.
+tcw_status ensure_batch_bits(tcw_ctx* c, BatchState* b) {
+  if (c->statistic != TCW_STAT_NUMBER_COUNT || b->bits_th == c->rho_th) return TCW_OK;
+  const int bp = bit_pitch_for(b->n_bin);
+  size_t total = 0;
+  for (EventHost& e : b->ev) {
+    e.o_bits = total;
+    total += align256((size_t)b->D * e.n_seg * bp * sizeof(uint32_t));
+  }
+  TCW_CUDA(c, b->bits.ensure(total), "count bit maps");
+  for (const EventHost& e : b->ev)
+    TCW_CUDA(c, launch_count_bits(at<char>(b->rho, e.o_rho), b->dtype == TCW_F16, (int64_t)b->D * e.n_seg,
+                                  b->n_bin, bp, c->rho_th, at<uint32_t>(b->bits, e.o_bits), c->stream),
+             "count_bits_kernel launch");
+  TCW_CUDA(c, cudaStreamSynchronize(c->stream), "count bit maps");
+  b->bits_th = c->rho_th;
+  return TCW_OK;
 }
 
 // Work items of the events of wave w over `groups_limit` groups of 8
@@ -270,6 +304,7 @@ GroupParams base_params(const tcw_ctx* c, BatchState* b, int tile, int nterms) {
   gp.nterms = nterms;
   gp.tile_shift = ilog2(tile);
   gp.amp_power = c->amp_power;
+  gp.nc_q = count_q(c);
   gp.B = (int)c->B;
   gp.Bpad = c->Bpad;
   gp.lanes = b->lanes;
@@ -385,7 +420,7 @@ tcw_status autotune(tcw_ctx* c, BatchState* b) {
         cudaEventRecord(e0, c->stream);
         for (int w = 0; w < b->waves; ++w) {
           const GroupParams gp = wave_params(c, b, w, tile, nterms);
-          cudaError_t err = launch_group(gp, b->grid, b->dtype == TCW_F16, false, weighting(c, b), c->stream);
+          cudaError_t err = launch_group(gp, b->grid, half_windows(c, b), false, weighting(c, b), c->stream);
           if (err != cudaSuccess) {
             st = cuda_fail(c, err, "group_kernel launch");
             break;
@@ -433,7 +468,7 @@ tcw_status capture(tcw_ctx* c, BatchState* b, int k) {
   if ((st = upload_items(c, b, b->bank_chunk, INT32_MAX, &sums)) != TCW_OK) return st;
   TCW_CUDA(c, b->out_psi.ensure((size_t)b->total_sky * k * sizeof(float)), "output");
   TCW_CUDA(c, b->out_idx.ensure((size_t)b->total_sky * k * sizeof(int64_t)), "output");
-  TCW_CUDA(c, group_prepare(b->D, b->lanes, b->dtype == TCW_F16, weighting(c, b)), "group_kernel attributes");
+  TCW_CUDA(c, group_prepare(b->D, b->lanes, half_windows(c, b), weighting(c, b)), "group_kernel attributes");
   TCW_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "graph capture");
   cudaError_t err = cudaMemsetAsync(b->flags.p, 0, 64, c->stream);
   int nodes = 0;
@@ -461,7 +496,7 @@ tcw_status capture(tcw_ctx* c, BatchState* b, int k) {
     }
     if (err != cudaSuccess) break;
     const GroupParams gp = wave_params(c, b, w, b->tile, nterms);
-    err = launch_group(gp, b->grid, b->dtype == TCW_F16, false, weighting(c, b), c->stream);
+    err = launch_group(gp, b->grid, half_windows(c, b), false, weighting(c, b), c->stream);
     ++nodes;
     for (const EventHost& e : b->ev) {
       if (e.wave != w || err != cudaSuccess) continue;
@@ -484,6 +519,7 @@ tcw_status capture(tcw_ctx* c, BatchState* b, int k) {
   b->graph_k = k;
   b->graph_mem = c->batch_memory;
   b->graph_amp = c->amp_power;
+  b->graph_nc = count_q(c);
   b->graph_nodes = nodes;
   return TCW_OK;
 }
@@ -684,6 +720,7 @@ tcw_status tcw_search_batched(tcw_ctx* c, int k, float* psi_out, int64_t* idx_ou
   }
   tcw_status st = TCW_OK;
   if (!b->planned && (st = plan_batch(c, b)) != TCW_OK) return st;
+  if ((st = ensure_batch_bits(c, b)) != TCW_OK) return st;
   if (!b->tuned) {
     if (c->autotune) {
       if ((st = autotune(c, b)) != TCW_OK) return st;
@@ -696,7 +733,8 @@ tcw_status tcw_search_batched(tcw_ctx* c, int k, float* psi_out, int64_t* idx_ou
     }
     drop_graph(b);
   }
-  if (!b->exec || b->graph_k != k || b->graph_mem != c->batch_memory || b->graph_amp != c->amp_power) {
+  if (!b->exec || b->graph_k != k || b->graph_mem != c->batch_memory || b->graph_amp != c->amp_power ||
+      b->graph_nc != count_q(c)) {
     if ((st = capture(c, b, k)) != TCW_OK) return st;
   }
   TCW_CUDA(c, cudaEventRecord(c->ev0, c->stream), "event");

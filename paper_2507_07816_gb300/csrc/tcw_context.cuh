@@ -51,6 +51,9 @@ struct tcw_ctx {
   int triage_spread = 2;   // triage: patches within this distance of a chosen one are suppressed
   int64_t batch_memory = (int64_t)48 << 30;  // batched search: Psi + anchor bytes per wave
   unsigned bank_epoch = 0; // bumped by every tcw_define_bank
+  int statistic = TCW_STAT_POWER;
+  double rho_th = 0;       // number-count threshold
+  unsigned spec_epoch = 0; // bumped by every tcw_load_spectrogram
   // spectrogram
   bool have_spec = false;
   int D = 0;
@@ -60,6 +63,9 @@ struct tcw_ctx {
   std::vector<double> h_t;
   bool unit_weights = true;
   tcw::DevBuf rho, t_mid, weights;
+  tcw::DevBuf bits;        // number-count bit map of rho (see tcw_set_statistic)
+  unsigned bits_epoch = ~0u;
+  double bits_th = -1;
   // velocity
   bool have_vel = false;
   std::vector<double> h_v;

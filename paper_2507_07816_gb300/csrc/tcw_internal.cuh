@@ -87,7 +87,10 @@ struct EventDesc {
   float* W2_out;
   int64_t total_elems;     // D * n_seg * pitch
   double T0;
-  int n_seg, n_tiles, S, Spad, NG, pad_;
+  int n_seg, n_tiles, S, Spad, NG;
+  int bit_pitch;           // words per row of `bits`
+  const uint32_t* bits;    // number count: [D][n_seg][bit_pitch] bit k of a row = [rho_k > rho_th];
+                           // null for the power statistic
 };
 
 // Work item of the group kernel: one sky chunk of 16 lanes sorted directions
@@ -108,6 +111,8 @@ struct GroupParams {
   int nterms;              // binomial-series length for the track; 0 = pow per entry
   int tile_shift;          // tiles of 2^tile_shift segments: anchors and fp32 partial sums
   int amp_power;           // weights times (f(t_j)/f0)^amp_power (Eq. 3); 0 = none
+  double nc_q;             // number count: q = exp(-rho_th), <s> = q W1, sigma^2 = q(1-q) W2;
+                           // 0 = power (<s> = W1, sigma^2 = W2).  Needs every event's bits.
   int B, Bpad;
   int lanes;               // sky groups per chunk: 16, 32 or 64
   float2* dev;             // scratch [gridDim.x][8192]: per-sky weight sums at band edges
@@ -143,6 +148,8 @@ struct LookupParams {
   const double* nbr;
   double T0, f_min, df;
   int amp_power;           // weights times (f(t_j)/f0)^amp_power (Eq. 3); 0 = none
+  int number_count;        // 1: nu = [rho > rho_th] in place of rho, Psi with q = exp(-rho_th)
+  double rho_th;
   int B, Bpad, S, Spad;
   float* psi;
   float* S_out;
@@ -277,6 +284,11 @@ cudaError_t group_prepare(int n_det, int lanes, bool half, int weighting);
 cudaError_t launch_group(const GroupParams& p, int grid, bool half, bool record, int weighting,
                          cudaStream_t st);
 cudaError_t launch_lookup(const LookupParams& p, bool half, bool record, cudaStream_t st);
+// Number-count bit map: bits[r][w] bit i = [rho[r][32 w + i] > rho_th] (compared
+// in double; 0 past n_bin) for rows r < rows, words w < bit_pitch.
+int bit_pitch_for(int64_t n_bin);
+cudaError_t launch_count_bits(const void* rho, bool half, int64_t rows, int64_t n_bin, int bit_pitch,
+                              double rho_th, uint32_t* bits, cudaStream_t st);
 cudaError_t launch_topk(const float* psi, int Bpad, int B, int S, int k, const int32_t* bank_perm,
                         const int32_t* sky_perm, float* psi_out, int64_t* idx_out,
                         cudaStream_t st);

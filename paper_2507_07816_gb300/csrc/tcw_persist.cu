@@ -184,6 +184,28 @@ __device__ __forceinline__ void compute_entry(const GroupParams& p, const EventD
     v = v > 2147483647LL ? 2147483647LL : (v < -2147483647LL ? -2147483647LL : v);
     e.th[i] = (int)v;
   }
+  if constexpr (sizeof(RhoT) == 4) {
+    if (ev.bits) {
+      // number count: the window holds nu = [rho > rho_th] of bins base + kMLo
+      // .. base + kMLo + 15 as fp32 0/1, unpacked from the bit map (0 outside
+      // the band), so the consumers run unchanged
+      const int g0 = base + kMLo;
+      const int wi = g0 >> 5, sh = g0 & 31;   // floor division: g0 may be negative at the low edge
+      for (int d = 0; d < p.n_det; ++d) {
+        const uint32_t* row = ev.bits + ((int64_t)d * ev.n_seg + j) * ev.bit_pitch;
+        const uint32_t lo = (unsigned)wi < (unsigned)ev.bit_pitch ? __ldg(row + wi) : 0u;
+        const uint32_t hi = (unsigned)(wi + 1) < (unsigned)ev.bit_pitch ? __ldg(row + wi + 1) : 0u;
+        const uint32_t m = __funnelshift_r(lo, hi, sh);
+        const uint32_t dst = win_dst + d * kWinBytes;
+        e.wa[d] = dst - 4u * (uint32_t)(kMagicBits + kMLo);
+#pragma unroll
+        for (int c = 0; c < kWinBytes / 16; ++c)
+          sts_f4(dst + 16 * c, (float)((m >> (4 * c)) & 1u), (float)((m >> (4 * c + 1)) & 1u),
+                 (float)((m >> (4 * c + 2)) & 1u), (float)((m >> (4 * c + 3)) & 1u));
+      }
+      return;
+    }
+  }
   // power windows: 64 bytes from a 16-byte boundary at or below bin base + kMLo,
   // clamped into the array (the valid candidates stay inside the window)
   constexpr int64_t E = 16 / sizeof(RhoT), W = kWinBytes / sizeof(RhoT);
@@ -479,10 +501,12 @@ __global__ void __launch_bounds__(Geo<LN>::kThreads, 1) group_kernel(GroupParams
         if (lane == 0) mbar_arrive(bar_empty + 8 * s);
       }
       if (!ok || !gval) continue;
+      // Eq. 4: <s> = mq W1, sigma^2 = vq W2 (power: 1, 1; number count: q, q(1-q))
+      const double mq = p.nc_q > 0.0 ? p.nc_q : 1.0;
+      const float vq = p.nc_q > 0.0 ? (float)(p.nc_q * (1.0 - p.nc_q)) : 1.0f;
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
         const int b = b0 + 2 * u + t;
-        const double base_num = gw[t] - w1[t];
         const float2* dvp = dev_cta + (2 * u + t) * kChunk + l * G;
 #pragma unroll
         for (int k = 0; k < G; ++k) {
@@ -495,9 +519,9 @@ __global__ void __launch_bounds__(Geo<LN>::kThreads, 1) group_kernel(GroupParams
           }
           const float W1 = (float)(w1[t] + (double)dv1);
           const float W2 = (float)(w2[t] + (double)dv2);
-          const float num = (float)(base_num - (double)dv1) + tot[t][k];
+          const float num = (float)(gw[t] - mq * (w1[t] + (double)dv1)) + tot[t][k];
           const int64_t o = (int64_t)sk * p.Bpad + b;
-          ev.psi[o] = W2 > 0.f ? num * rsqrtf(W2) : -INFINITY;
+          ev.psi[o] = W2 > 0.f ? num * rsqrtf(vq * W2) : -INFINITY;
           if (ev.S_out) {
             ev.S_out[o] = (float)gw[t] + tot[t][k];
             ev.W1_out[o] = W1;
@@ -670,6 +694,7 @@ cudaError_t group_prepare(int n_det, int lanes, bool half, int weighting) {
 cudaError_t launch_group(const GroupParams& p, int grid, bool half, bool record, int weighting,
                          cudaStream_t st) {
   if (p.n_det < 1 || p.n_det > kMaxStageDet) return cudaErrorInvalidValue;
+  if (p.nc_q > 0.0 && half) return cudaErrorInvalidValue;   // counts are staged as fp32 windows
   if (p.amp_power > 0 && weighting != kAmplitudeWeights && !record) return cudaErrorInvalidValue;
   if (grid <= 0) return cudaSuccess;
   return half ? launch_group_r<__half>(p, record, weighting, grid, st)

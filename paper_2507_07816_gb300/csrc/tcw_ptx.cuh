@@ -67,6 +67,10 @@ __device__ __forceinline__ float lds_pow(uint32_t a, __half) {
   asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(a));
   return __half2float(__ushort_as_half(v));
 }
+__device__ __forceinline__ void sts_f4(uint32_t a, float x, float y, float z, float w) {
+  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(x), "f"(y), "f"(z), "f"(w)
+               : "memory");
+}
 __device__ __forceinline__ int4 lds_v4(uint32_t a) {
   int4 v;
   asm volatile("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];"

@@ -5,6 +5,7 @@
 //   (the hot loop, group_kernel, is in tcw_persist.cu)
 //   lookup_kernel   one thread per (sky, template), FP64 per lookup; used when
 //                   the group kernel's exactness conditions do not hold
+//   count_bits_kernel number-count bit map [rho > rho_th]
 //   unpermute_kernel  sorted -> caller order for the statistics getter
 #include <climits>
 
@@ -96,17 +97,41 @@ __global__ void lookup_kernel(LookupParams p) {
             (int32_t)k;
       if (k < 0) continue;
       const double w = (double)p.weights[dj] * amp;
-      S += w * (double)load_rho(rho + dj * p.n_bin, k);
+      double r = (double)load_rho(rho + dj * p.n_bin, k);
+      if (p.number_count) r = r > p.rho_th ? 1.0 : 0.0;
+      S += w * r;
       W1 += w;
       W2 += w * w;
     }
   }
   const int64_t o = (int64_t)s * p.Bpad + b;
-  p.psi[o] = W2 > 0.0 ? (float)((S - W1) / sqrt(W2)) : -INFINITY;
+  const double q = p.number_count ? exp(-p.rho_th) : 1.0;        // <s> = q W1
+  const double var = p.number_count ? q * (1.0 - q) : 1.0;        // sigma^2 = var W2
+  p.psi[o] = W2 > 0.0 ? (float)((S - q * W1) / sqrt(var * W2)) : -INFINITY;
   if (p.S_out) {
     p.S_out[o] = (float)S;
     p.W1_out[o] = (float)W1;
     p.W2_out[o] = (float)W2;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Number-count bit map (Sec. 2): one warp per 32-bin word, a coalesced read of
+// 32 powers and one ballot.  The compare is made in double so that it agrees
+// with a double threshold exactly.
+// ---------------------------------------------------------------------------
+template <typename RhoT>
+__global__ void count_bits_kernel(const RhoT* rho, int64_t rows, int64_t n_bin, int bit_pitch,
+                                  double rho_th, uint32_t* bits) {
+  const int lane = threadIdx.x & 31;
+  const int64_t words = rows * bit_pitch;
+  const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < words; w += wstride) {
+    const int64_t r = w / bit_pitch, k = (w % bit_pitch) * 32 + lane;
+    bool on = false;
+    if (k < n_bin) on = (double)load_rho(rho + r * n_bin, k) > rho_th;
+    const uint32_t m = __ballot_sync(0xffffffffu, on);
+    if (lane == 0) bits[w] = m;
   }
 }
 
@@ -139,6 +164,23 @@ cudaError_t launch_lookup(const LookupParams& p, bool half, bool record, cudaStr
     if (record) lookup_kernel<float, true><<<blocks, threads, 0, st>>>(p);
     else lookup_kernel<float, false><<<blocks, threads, 0, st>>>(p);
   }
+  return cudaGetLastError();
+}
+
+int bit_pitch_for(int64_t n_bin) { return (int)((n_bin + 31) / 32) + 1; }   // + one zero word
+
+cudaError_t launch_count_bits(const void* rho, bool half, int64_t rows, int64_t n_bin, int bit_pitch,
+                              double rho_th, uint32_t* bits, cudaStream_t st) {
+  const int64_t words = rows * bit_pitch;
+  if (words == 0) return cudaSuccess;
+  const int threads = 256;
+  const int64_t blocks = std::min<int64_t>((words * 32 + threads - 1) / threads, 152LL * 32);
+  if (half)
+    count_bits_kernel<__half><<<(unsigned)blocks, threads, 0, st>>>(static_cast<const __half*>(rho), rows,
+                                                                    n_bin, bit_pitch, rho_th, bits);
+  else
+    count_bits_kernel<float><<<(unsigned)blocks, threads, 0, st>>>(static_cast<const float*>(rho), rows,
+                                                                   n_bin, bit_pitch, rho_th, bits);
   return cudaGetLastError();
 }
 

@@ -23,6 +23,7 @@ KERNEL_AUTO, KERNEL_GROUP, KERNEL_LOOKUP = 0, 1, 2
 OPT_KERNEL, OPT_KEEP_STATS, OPT_TILE_SEGMENTS, OPT_BANK_CHUNK = 1, 2, 3, 4
 OPT_AUTOTUNE, OPT_BATCH_MEMORY, OPT_SKY_LANES, OPT_TRIAGE_SPREAD = 5, 6, 7, 8
 OPT_AMPLITUDE_POWER = 9
+STAT_POWER, STAT_NUMBER_COUNT = 0, 1
 
 _lock = threading.Lock()
 _lib = None
@@ -89,6 +90,7 @@ def load_library(build_if_missing: bool = True):
             "tcw_create": [ctypes.POINTER(p), i, p],
             "tcw_destroy": [p],
             "tcw_set_option": [p, i, i64],
+            "tcw_set_statistic": [p, i, d],
             "tcw_load_spectrogram": [p, i, i64, i64, i, p, i, d, d, p, p],
             "tcw_load_velocity": [p, p, i],
             "tcw_define_bank": [p, i64, p, p, p, d, i],
@@ -206,6 +208,10 @@ class Search:
 
     def set_option(self, option: int, value: int):
         self._check(self._lib.tcw_set_option(self._h, option, int(value)))
+
+    def set_statistic(self, statistic: int, rho_th: float = 0.0):
+        """STAT_POWER (default) or STAT_NUMBER_COUNT with threshold rho_th > 0."""
+        self._check(self._lib.tcw_set_statistic(self._h, int(statistic), float(rho_th)))
 
     def load_spectrogram(self, rho, f_min, df, t_mid, weights=None):
         dt = np.float16 if str(getattr(rho, "dtype", "")).endswith("float16") else np.float32

@@ -131,8 +131,8 @@ def test_training_beats_the_untrained_network():
     assert r_tr >= 0.5 and r_tr > r_un + 0.2, (r_tr, r_un)
 
 
-@pytest.mark.parametrize("amp", [0, 4])
-def test_triaged_search_rows_equal_exhaustive_rows(amp):
+@pytest.mark.parametrize("amp,count", [(0, False), (4, False), (0, True)])
+def test_triaged_search_rows_equal_exhaustive_rows(amp, count):
     ev, bank = small_event(84, n_sky=200, n_inj=2, snr=(14.0, 16.0), n_bin=9600, t_sft=32.0)
     # hand-set network: score = sum of the log-counts of the 28 highest histogram bins
     theta = np.zeros(OT.N_PARAMS, np.float32)
@@ -143,7 +143,9 @@ def test_triaged_search_rows_equal_exhaustive_rows(amp):
     mlp = tcw.Mlp(theta, device=DEV)
     s = tcw.Search(0)
     s.set_option(tcw.OPT_TRIAGE_SPREAD, 0)
-    s.set_option(tcw.OPT_AMPLITUDE_POWER, amp)     # the exhaustive part takes the weighting too
+    s.set_option(tcw.OPT_AMPLITUDE_POWER, amp)     # the exhaustive part takes the weighting
+    if count:                                      # and the statistic too
+        s.set_statistic(tcw.STAT_NUMBER_COUNT, 1.6)
     TR.load_event(s, ev, bank)
     k = 8
     pf, xf = s.search(k)
