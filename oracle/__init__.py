@@ -79,6 +79,11 @@ def _load():
                 i, i, d, d, p, p, p, p, p, p, d, p, i64, p]
             lib.oracle_topk.restype = None
             lib.oracle_topk.argtypes = [p, i64, i64, i64, p, p]
+            lib.oracle_philox4x64_10.restype = None
+            lib.oracle_philox4x64_10.argtypes = [p, p, p]
+            lib.oracle_bank_templates.restype = None
+            lib.oracle_bank_templates.argtypes = [i, i64, i64, i64, p, p, ctypes.c_uint64, i64, i64,
+                                                  p, p, p]
             lib.oracle_max_threads.restype = i
             lib.oracle_max_threads.argtypes = []
             _lib = lib
@@ -194,3 +199,23 @@ def topk(psi, k):
     val = np.empty((rows, k), np.float64)
     _load().oracle_topk(_ptr(psi), rows, B, k, _ptr(idx), _ptr(val))
     return idx, val
+
+
+def philox4x64_10(counter, key):
+    """Philox4x64-10 block (Salmon et al., SC 2011): four uint64 outputs."""
+    c = np.ascontiguousarray(np.asarray(counter, np.uint64).reshape(4))
+    k = np.ascontiguousarray(np.asarray(key, np.uint64).reshape(2))
+    out = np.empty(4, np.uint64)
+    _load().oracle_philox4x64_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def bank_templates(kind, first, count, lo, hi, n_f0=1, n_tau=1, n_n=1, seed=0):
+    """Templates [first, first + count) of a lattice (kind 0) or uniform random
+    (kind 1) bank over the box lo..hi = (f0, tau, n); three float64 arrays."""
+    lo = np.ascontiguousarray(np.asarray(lo, np.float64).reshape(3))
+    hi = np.ascontiguousarray(np.asarray(hi, np.float64).reshape(3))
+    outs = [np.empty(int(count), np.float64) for _ in range(3)]
+    _load().oracle_bank_templates(int(kind), int(n_f0), int(n_tau), int(n_n), _ptr(lo), _ptr(hi),
+                                  int(seed), int(first), int(count), *(_ptr(o) for o in outs))
+    return tuple(outs)

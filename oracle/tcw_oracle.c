@@ -275,3 +275,86 @@ int oracle_max_threads(void)
     return 1;
 #endif
 }
+
+/*
+ * Template banks (Sec. 2: a cubic lattice with equal spacing per axis, or
+ * templates drawn uniformly over the parameter box), written out template by
+ * template so that any range [first, first + count) of a bank of 1e8-1e9
+ * templates can be produced on its own.
+ *
+ * Lattice of n_f0 x n_tau x n_n points, f0 fastest:
+ *   t -> (i0, i1, i2) = (t mod n_f0, (t / n_f0) mod n_tau, t / (n_f0 n_tau));
+ *   axis value at i of m points: lo for i = 0 (or m = 1), hi for i = m - 1,
+ *   else fma(hi - lo, i / (m - 1), lo).
+ * Uniform random: the 4 x 64-bit output of Philox4x64-10 (Salmon, Moraes, Dror
+ * and Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC 2011) at counter
+ * (t, 0, 0, 0) and key (seed, 0); u_a = (x_a >> 11) 2^-53 for a = 0, 1, 2 and
+ * value = fma(hi - lo, u, lo) for f0, tau, n in that order.
+ */
+static void oracle_mulhilo64(uint64_t a, uint64_t b, uint64_t *hi, uint64_t *lo)
+{
+    unsigned __int128 p = (unsigned __int128)a * (unsigned __int128)b;
+    *hi = (uint64_t)(p >> 64);
+    *lo = (uint64_t)p;
+}
+
+/* Philox4x64 with 10 rounds: the multipliers and Weyl key increments are the
+ * ones the SC 2011 paper gives for the 4 x 64 variant. */
+void oracle_philox4x64_10(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4])
+{
+    const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+    uint64_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint64_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        uint64_t hi0, lo0, hi1, lo1;
+        oracle_mulhilo64(M0, x0, &hi0, &lo0);
+        oracle_mulhilo64(M1, x2, &hi1, &lo1);
+        uint64_t y0 = hi1 ^ x1 ^ k0, y1 = lo1, y2 = hi0 ^ x3 ^ k1, y3 = lo0;
+        x0 = y0;
+        x1 = y1;
+        x2 = y2;
+        x3 = y3;
+        k0 += W0;
+        k1 += W1;
+    }
+    out[0] = x0;
+    out[1] = x1;
+    out[2] = x2;
+    out[3] = x3;
+}
+
+static double oracle_lattice_axis(double lo, double hi, int64_t m, int64_t i)
+{
+    if (m == 1 || i == 0) return lo;
+    if (i == m - 1) return hi;
+    return fma(hi - lo, (double)i / (double)(m - 1), lo);
+}
+
+/* kind 0 = lattice (n_f0, n_tau, n_n), 1 = uniform random (seed);
+ * lo/hi = {f0, tau, n} bounds.  Writes templates first .. first + count - 1. */
+void oracle_bank_templates(int kind, int64_t n_f0, int64_t n_tau, int64_t n_n,
+                           const double lo[3], const double hi[3], uint64_t seed,
+                           int64_t first, int64_t count,
+                           double *f0, double *tau, double *n)
+{
+    for (int64_t i = 0; i < count; ++i) {
+        int64_t t = first + i;
+        double v[3];
+        if (kind == 0) {
+            int64_t idx[3] = {t % n_f0, (t / n_f0) % n_tau, t / (n_f0 * n_tau)};
+            int64_t m[3] = {n_f0, n_tau, n_n};
+            for (int a = 0; a < 3; ++a) v[a] = oracle_lattice_axis(lo[a], hi[a], m[a], idx[a]);
+        } else {
+            uint64_t ctr[4] = {(uint64_t)t, 0, 0, 0}, key[2] = {seed, 0}, x[4];
+            oracle_philox4x64_10(ctr, key, x);
+            for (int a = 0; a < 3; ++a) {
+                double u = (double)(x[a] >> 11) * 0x1p-53;
+                v[a] = fma(hi[a] - lo[a], u, lo[a]);
+            }
+        }
+        f0[i] = v[0];
+        tau[i] = v[1];
+        n[i] = v[2];
+    }
+}
