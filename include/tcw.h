@@ -93,7 +93,7 @@ enum {
     TCW_OPT_TRIAGE_SPREAD = 8, /* triaged search: a chosen patch suppresses the patches
                                   within this many positions (default 2; 0 = plain
                                   ranking); best suppressed ones fill up if needed */
-    TCW_OPT_AMPLITUDE_POWER = 9 /* p in [0, 8]: every lookup's weight w_{d,j} is
+    TCW_OPT_AMPLITUDE_POWER = 9, /* p in [0, 8]: every lookup's weight w_{d,j} is
                                   multiplied by the template's own amplitude
                                   weight (f(t_j)/f0)^p, so S, W1 = sum w and
                                   W2 = sum w^2 of Eq. 4 use w_{d,j} (f(t_j)/f0)^p.
@@ -103,6 +103,8 @@ enum {
                                   the template; default 0 (the weights as given).
                                   Applies to tcw_search, tcw_search_batched and
                                   the exhaustive part of tcw_search_triaged */
+    TCW_OPT_GEN_CHUNK = 10     /* tcw_search_generated: templates per chunk, a multiple
+                                  of 32 in [32, 2^24] (default 2^18) */
 };
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
@@ -400,6 +402,72 @@ tcw_status tcw_sky_order(tcw_ctx *ctx, int32_t *order_out);
 tcw_status tcw_probe_read_bandwidth(int64_t bytes, int passes, int reps, double *gbps_out);
 
 /* Information about the last search. */
+/* ---------------------------------------------------------------------------
+ * Template banks generated on the device (Sec. 2 of arXiv:2507.07816 uses a
+ * cubic lattice with equal spacing per axis and a uniform random bank over
+ * (f0, tau, n)).  A bank is a pure function of its spec and the template
+ * index t, so any range of a bank of 1e8-1e9 templates is produced alone:
+ *   TCW_BANK_LATTICE  n_f0 x n_tau x n_n points, f0 fastest:
+ *                     t -> (t mod n_f0, (t / n_f0) mod n_tau, t / (n_f0 n_tau));
+ *                     the i-th of m points is lo (i = 0 or m = 1), hi
+ *                     (i = m - 1), else fma(hi - lo, i / (m - 1), lo)
+ *   TCW_BANK_RANDOM   n_tmpl templates; template t takes the 4 x 64-bit block
+ *                     of Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC 2011)
+ *                     at counter (t, 0, 0, 0) and key (seed, 0); its first
+ *                     three words x give u = (x >> 11) 2^-53 in [0, 1) and
+ *                     f0, tau, n = fma(hi - lo, u, lo)
+ * Bounds: finite, lo <= hi, f0_lo > 0, tau_lo > 0, n_lo > 1.
+ * ------------------------------------------------------------------------- */
+enum { TCW_BANK_LATTICE = 0, TCW_BANK_RANDOM = 1 };
+typedef struct {
+    int kind;                          /* TCW_BANK_LATTICE or TCW_BANK_RANDOM */
+    int reserved;                      /* 0 */
+    int64_t n_f0, n_tau, n_n;          /* lattice points per axis, each >= 1 */
+    int64_t n_tmpl;                    /* random: number of templates >= 1 */
+    double f0_lo, f0_hi;               /* Hz */
+    double tau_lo, tau_hi;             /* s */
+    double n_lo, n_hi;                 /* braking index */
+    uint64_t seed;                     /* random: Philox key word 0 */
+} tcw_bank_spec;
+
+/* Number of templates of a spec (n_f0 n_tau n_n, or n_tmpl; at most 2^62).
+ * Errors: INVALID_ARGUMENT (bad spec). */
+tcw_status tcw_bank_size(const tcw_bank_spec *spec, int64_t *n_out);
+
+/* Templates [first, first + count) of the bank, generated on the device, into
+ * f0, tau, n (float64, count entries each; out_flags TCW_HOST or TCW_DEVICE).
+ * Errors: INVALID_ARGUMENT (bad spec or range), OUT_OF_MEMORY, CUDA. */
+tcw_status tcw_generate_bank(tcw_ctx *ctx, const tcw_bank_spec *spec, int64_t first, int64_t count,
+                             double *f0, double *tau, double *n, int out_flags);
+
+/* Search a generated bank with the loaded spectrogram, velocities and sky,
+ * like tcw_search: psi_out/idx_out [n_sky][k] with idx the generated template
+ * index t (int64).  The bank is produced chunk by chunk on the device
+ * (TCW_OPT_GEN_CHUNK templates), each chunk searched and its per-sky top-k
+ * merged into a running top-k by (Psi desc, t asc), so the full Psi array is
+ * never held: memory is one chunk's Psi (n_sky x chunk floats), whatever the
+ * bank size.  Honours the statistic, amplitude, lanes and kernel options.
+ * Replaces any bank defined with tcw_define_bank (define it again before
+ * tcw_search); tcw_get_statistics is not available afterwards.
+ * 1 <= k <= min(bank size, 1024).  Errors: as tcw_search, plus
+ * INVALID_ARGUMENT for a bad spec. */
+tcw_status tcw_search_generated(tcw_ctx *ctx, const tcw_bank_spec *spec, double T0, int k,
+                                float *psi_out, int64_t *idx_out, int out_flags);
+
+typedef struct {
+    int64_t n_tmpl;             /* templates searched */
+    int64_t chunks;             /* chunks (kernel passes over the data) */
+    int64_t chunk_templates;    /* templates per chunk */
+    int64_t lookups;            /* n_sky * n_tmpl * n_det * n_seg */
+    int kernel;                 /* TCW_KERNEL_GROUP or TCW_KERNEL_LOOKUP (last chunk) */
+    int launches;               /* kernels launched */
+    float search_ms;            /* device time of the search kernels, summed over chunks */
+    float total_ms;             /* device time from the first generation to the last merge */
+} tcw_generated_info;
+
+/* Information about the last tcw_search_generated.  Errors: STATE. */
+tcw_status tcw_get_generated_info(tcw_ctx *ctx, tcw_generated_info *info);
+
 typedef struct {
     int kernel;                 /* TCW_KERNEL_GROUP or TCW_KERNEL_LOOKUP */
     int launches;               /* kernels launched by the search */

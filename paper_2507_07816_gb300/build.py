@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libtcw.so")
 SOURCES = ["tcw_api.cu", "tcw_batched.cu", "tcw_search.cu", "tcw_persist.cu", "tcw_topk.cu", "tcw_triage.cu",
-           "tcw_noalloc.cu", "tcw_probe.cu"]
+           "tcw_noalloc.cu", "tcw_probe.cu", "tcw_bank.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]

@@ -30,12 +30,7 @@ struct Plan {
 };
 
 int series_terms(const tcw_ctx* c) {
-  double tau_min = INFINITY, r_max = 0;
-  for (size_t b = 0; b < c->h_tau.size(); ++b) {
-    tau_min = std::min(tau_min, c->h_tau[b]);
-    r_max = std::max(r_max, 1.0 / (c->h_n[b] - 1.0));
-  }
-  return series_terms_for(c->h_t.data(), c->Nseg, c->T0, c->tile_segments, tau_min, r_max);
+  return series_terms_for(c->h_t.data(), c->Nseg, c->T0, c->tile_segments, c->bank_tau_min, c->bank_r_max);
 }
 
 // Fixed-point step and the exactness conditions of the group kernel.
@@ -53,10 +48,8 @@ Plan make_plan(const tcw_ctx* c) {
   pl.inv_q = std::ldexp(1.0, -e);
   // tracks only fall (Eq. 1), and lookups outside the band are never made, so
   // the largest f/df that reaches the bin decision is bounded by both
-  double f0max = 0;
-  for (double f : c->h_f0) f0max = std::max(f0max, f);
   const double fband = c->f_min + ((double)c->Nbin + 5.0) * c->df;
-  pl.fmax_bins = std::min(f0max, fband) * (1.0 + pl.dmax) / c->df;
+  pl.fmax_bins = std::min(c->bank_f0max, fband) * (1.0 + pl.dmax) / c->df;
   pl.doppler_bins = pl.fmax_bins * pl.dmax;
   const double tie_budget = 0.75 * std::ldexp(1.0, -30);
   pl.group_ok = true;
@@ -366,11 +359,7 @@ tcw_status run_coarse(tcw_ctx* c, int patch_size, float lo, float hi, bool keep_
   const int P = (int)((c->S + patch_size - 1) / patch_size);
   const int tile = 32;
   const int n_tiles = (int)((c->Nseg + tile - 1) / tile);
-  double tau_min = INFINITY, r_max = 0;
-  for (size_t b = 0; b < c->h_tau.size(); ++b) {
-    tau_min = std::min(tau_min, c->h_tau[b]);
-    r_max = std::max(r_max, 1.0 / (c->h_n[b] - 1.0));
-  }
+  const double tau_min = c->bank_tau_min, r_max = c->bank_r_max;
   const int nterms = series_terms_for(c->h_t.data(), c->Nseg, c->T0, tile, tau_min, r_max);
   TCW_CUDA(c, c->tri_dop.ensure((size_t)c->D * c->Nseg * P * sizeof(float)), "triage buffers");
   TCW_CUDA(c, c->tri_hist.ensure((size_t)P * kTriageBins * sizeof(unsigned)), "triage buffers");
@@ -494,11 +483,14 @@ tcw_status tcw_destroy(tcw_ctx* c) {
                     &c->dq, &c->anchors, &c->psi, &c->st_S, &c->st_W1, &c->st_W2, &c->dev,
                     &c->flags, &c->stage_f, &c->stage_i, &c->evtab, &c->items, &c->tri_dop,
                     &c->tri_hist, &c->tri_feat, &c->tri_psi, &c->tri_anchor, &c->tri_h1, &c->tri_h2,
-                    &c->tri_score, &c->tri_sel};
+                    &c->tri_score, &c->tri_sel, &c->bits, &c->gen_psi[0], &c->gen_psi[1],
+                    &c->gen_idx[0], &c->gen_idx[1], &c->gen_cpsi, &c->gen_cidx};
   for (DevBuf* b : bufs) b->release();
   batch_free(c);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->gen_ev0) cudaEventDestroy(c->gen_ev0);
+  if (c->gen_ev1) cudaEventDestroy(c->gen_ev1);
   if (c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
   return TCW_OK;
@@ -529,6 +521,11 @@ tcw_status tcw_set_option(tcw_ctx* c, int option, int64_t value) {
         return fail(c, TCW_ERR_INVALID_ARGUMENT, "sky lanes must be 0, 16, 32 or 64");
       c->opt_lanes = (int)value;
       c->sky_dirty = true;
+      return TCW_OK;
+    case TCW_OPT_GEN_CHUNK:
+      if (value < 32 || value > ((int64_t)1 << 24) || value % kBankAlign)
+        return fail(c, TCW_ERR_INVALID_ARGUMENT, "gen_chunk must be a multiple of 32 in [32, 2^24]");
+      c->gen_chunk = (int)value;
       return TCW_OK;
     case TCW_OPT_AMPLITUDE_POWER:
       if (value < 0 || value > 8) return fail(c, TCW_ERR_INVALID_ARGUMENT, "amplitude power must be in [0, 8]");
@@ -678,9 +675,14 @@ tcw_status tcw_define_bank(tcw_ctx* c, int64_t n_tmpl, const double* f0, const d
   c->Bpad = Bpad;
   ++c->bank_epoch;
   c->T0 = T0;
-  c->h_f0 = std::move(hf);
-  c->h_tau = std::move(ht);
-  c->h_n = std::move(hn);
+  c->bank_f0max = 0;
+  c->bank_tau_min = INFINITY;
+  c->bank_r_max = 0;
+  for (int64_t b = 0; b < n_tmpl; ++b) {
+    c->bank_f0max = std::max(c->bank_f0max, hf[b]);
+    c->bank_tau_min = std::min(c->bank_tau_min, ht[b]);
+    c->bank_r_max = std::max(c->bank_r_max, 1.0 / (hn[b] - 1.0));
+  }
   c->have_bank = true;
   c->have_result = false;
   return TCW_OK;
@@ -737,6 +739,194 @@ tcw_status tcw_search(tcw_ctx* c, int k, float* psi_out, int64_t* idx_out, int o
     TCW_CUDA(c, cudaMemcpyAsync(idx_out, didx, n * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream), "copy out");
   }
   return finish(c);
+}
+
+// ---------------------------------------------------------------------------
+// Generated banks
+// ---------------------------------------------------------------------------
+namespace {
+
+tcw_status check_spec(tcw_ctx* c, const tcw_bank_spec* sp, int64_t* n_out) {
+  if (!sp) return fail(c, TCW_ERR_INVALID_ARGUMENT, "null bank spec");
+  const double lo[3] = {sp->f0_lo, sp->tau_lo, sp->n_lo}, hi[3] = {sp->f0_hi, sp->tau_hi, sp->n_hi};
+  for (int a = 0; a < 3; ++a)
+    if (!std::isfinite(lo[a]) || !std::isfinite(hi[a]) || !(lo[a] <= hi[a]))
+      return fail(c, TCW_ERR_INVALID_ARGUMENT, "bank bounds must be finite with lo <= hi");
+  if (!(sp->f0_lo > 0) || !(sp->tau_lo > 0) || !(sp->n_lo > 1))
+    return fail(c, TCW_ERR_INVALID_ARGUMENT, "bank bounds need f0 > 0, tau > 0, n > 1");
+  const int64_t cap = (int64_t)1 << 62;
+  if (sp->kind == TCW_BANK_LATTICE) {
+    if (sp->n_f0 < 1 || sp->n_tau < 1 || sp->n_n < 1)
+      return fail(c, TCW_ERR_INVALID_ARGUMENT, "lattice axes need >= 1 point");
+    if (sp->n_f0 > cap / sp->n_tau || sp->n_f0 * sp->n_tau > cap / sp->n_n)
+      return fail(c, TCW_ERR_INVALID_ARGUMENT, "lattice larger than 2^62 templates");
+    *n_out = sp->n_f0 * sp->n_tau * sp->n_n;
+  } else if (sp->kind == TCW_BANK_RANDOM) {
+    if (sp->n_tmpl < 1 || sp->n_tmpl > cap) return fail(c, TCW_ERR_INVALID_ARGUMENT, "n_tmpl out of range");
+    *n_out = sp->n_tmpl;
+  } else {
+    return fail(c, TCW_ERR_INVALID_ARGUMENT, "unknown bank kind");
+  }
+  return TCW_OK;
+}
+
+BankGenParams gen_params(const tcw_bank_spec* sp) {
+  BankGenParams g{};
+  g.kind = sp->kind;
+  g.n_f0 = sp->kind == TCW_BANK_LATTICE ? sp->n_f0 : 1;
+  g.n_tau = sp->kind == TCW_BANK_LATTICE ? sp->n_tau : 1;
+  g.n_n = sp->kind == TCW_BANK_LATTICE ? sp->n_n : 1;
+  g.lo[0] = sp->f0_lo;
+  g.lo[1] = sp->tau_lo;
+  g.lo[2] = sp->n_lo;
+  g.hi[0] = sp->f0_hi;
+  g.hi[1] = sp->tau_hi;
+  g.hi[2] = sp->n_hi;
+  g.seed = sp->seed;
+  return g;
+}
+
+}  // namespace
+
+tcw_status tcw_bank_size(const tcw_bank_spec* spec, int64_t* n_out) {
+  if (!n_out) return TCW_ERR_INVALID_ARGUMENT;
+  return check_spec(nullptr, spec, n_out);
+}
+
+tcw_status tcw_generate_bank(tcw_ctx* c, const tcw_bank_spec* spec, int64_t first, int64_t count, double* f0,
+                             double* tau, double* n, int out_flags) {
+  if (!c) return TCW_ERR_INVALID_ARGUMENT;
+  int64_t N = 0;
+  tcw_status st = check_spec(c, spec, &N);
+  if (st != TCW_OK) return st;
+  if (!f0 || !tau || !n) return fail(c, TCW_ERR_INVALID_ARGUMENT, "null output");
+  if (out_flags != TCW_HOST && out_flags != TCW_DEVICE) return fail(c, TCW_ERR_INVALID_ARGUMENT, "bad flags");
+  if (first < 0 || count < 0 || first > N - count) return fail(c, TCW_ERR_INVALID_ARGUMENT, "range outside the bank");
+  if (count == 0) return TCW_OK;
+  cudaSetDevice(c->device);
+  const BankGenParams g = gen_params(spec);
+  if (out_flags == TCW_DEVICE) {
+    TCW_CUDA(c, launch_gen_bank(g, first, count, count, f0, tau, n, nullptr, c->stream), "gen_bank_kernel launch");
+    TCW_CUDA(c, cudaStreamSynchronize(c->stream), "bank generation");
+    return TCW_OK;
+  }
+  // host outputs: generate in device slices of up to 2^24 templates
+  const int64_t slice = std::min<int64_t>(count, (int64_t)1 << 24);
+  TCW_CUDA(c, c->stage_f.ensure((size_t)slice * 3 * sizeof(double)), "staging");
+  double* d = reinterpret_cast<double*>(c->stage_f.p);
+  for (int64_t o = 0; o < count; o += slice) {
+    const int64_t m = std::min(slice, count - o);
+    TCW_CUDA(c, launch_gen_bank(g, first + o, m, m, d, d + slice, d + 2 * slice, nullptr, c->stream),
+             "gen_bank_kernel launch");
+    TCW_CUDA(c, cudaMemcpyAsync(f0 + o, d, m * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy out");
+    TCW_CUDA(c, cudaMemcpyAsync(tau + o, d + slice, m * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+             "copy out");
+    TCW_CUDA(c, cudaMemcpyAsync(n + o, d + 2 * slice, m * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+             "copy out");
+    TCW_CUDA(c, cudaStreamSynchronize(c->stream), "bank generation");
+  }
+  return TCW_OK;
+}
+
+tcw_status tcw_search_generated(tcw_ctx* c, const tcw_bank_spec* spec, double T0, int k, float* psi_out,
+                                int64_t* idx_out, int out_flags) {
+  if (!c) return TCW_ERR_INVALID_ARGUMENT;
+  int64_t N = 0;
+  tcw_status st = check_spec(c, spec, &N);
+  if (st != TCW_OK) return st;
+  if (!psi_out || !idx_out) return fail(c, TCW_ERR_INVALID_ARGUMENT, "null output");
+  if (out_flags != TCW_HOST && out_flags != TCW_DEVICE) return fail(c, TCW_ERR_INVALID_ARGUMENT, "bad flags");
+  if (!std::isfinite(T0)) return fail(c, TCW_ERR_INVALID_ARGUMENT, "non-finite T0");
+  if (k < 1 || k > 1024 || (int64_t)k > N) return fail(c, TCW_ERR_INVALID_ARGUMENT, "k must be in [1, min(bank size, 1024)]");
+  if (!c->have_spec || !c->have_vel || !c->have_sky) return fail(c, TCW_ERR_STATE, "inputs not loaded");
+  cudaSetDevice(c->device);
+  c->have_gen = false;
+  if (!c->gen_ev0) TCW_CUDA(c, cudaEventCreate(&c->gen_ev0), "event");
+  if (!c->gen_ev1) TCW_CUDA(c, cudaEventCreate(&c->gen_ev1), "event");
+  const int64_t C = std::min<int64_t>(c->gen_chunk, (N + kBankAlign - 1) / kBankAlign * kBankAlign);
+  const int64_t S = c->S;
+  const BankGenParams g = gen_params(spec);
+  // the plan's bounds come from the spec: every template lies inside them
+  c->bank_f0max = spec->f0_hi;
+  c->bank_tau_min = spec->tau_lo;
+  c->bank_r_max = 1.0 / (spec->n_lo - 1.0);
+  c->T0 = T0;
+  c->have_bank = true;
+  c->have_result = false;
+  ++c->bank_epoch;
+  TCW_CUDA(c, c->f0.ensure((size_t)C * sizeof(double)), "bank buffer");
+  TCW_CUDA(c, c->tau.ensure((size_t)C * sizeof(double)), "bank buffer");
+  TCW_CUDA(c, c->nbr.ensure((size_t)C * sizeof(double)), "bank buffer");
+  TCW_CUDA(c, c->bank_perm.ensure((size_t)C * sizeof(int32_t)), "bank buffer");
+  for (int i = 0; i < 2; ++i) {
+    TCW_CUDA(c, c->gen_psi[i].ensure((size_t)S * k * sizeof(float)), "top-k buffer");
+    TCW_CUDA(c, c->gen_idx[i].ensure((size_t)S * k * sizeof(int64_t)), "top-k buffer");
+  }
+  TCW_CUDA(c, c->gen_cpsi.ensure((size_t)S * k * sizeof(float)), "top-k buffer");
+  TCW_CUDA(c, c->gen_cidx.ensure((size_t)S * k * sizeof(int64_t)), "top-k buffer");
+  tcw_generated_info gi{};
+  gi.n_tmpl = N;
+  gi.chunk_templates = C;
+  int cur = 0, have = 0;
+  double search_ms = 0;
+  TCW_CUDA(c, cudaEventRecord(c->gen_ev0, c->stream), "event");
+  for (int64_t base = 0; base < N; base += C) {
+    const int64_t cnt = std::min(C, N - base);
+    const int Bpad = (int)((cnt + kBankAlign - 1) / kBankAlign * kBankAlign);
+    TCW_CUDA(c, launch_gen_bank(g, base, cnt, Bpad, c->f0.as<double>(), c->tau.as<double>(), c->nbr.as<double>(),
+                                c->bank_perm.as<int32_t>(), c->stream),
+             "gen_bank_kernel launch");
+    c->B = cnt;
+    c->Bpad = Bpad;
+    if ((st = run_search(c, false, nullptr)) != TCW_OK) {
+      c->have_bank = false;
+      return st;
+    }
+    const int kc = (int)std::min<int64_t>(k, cnt);
+    TCW_CUDA(c, launch_topk(c->psi.as<float>(), Bpad, (int)cnt, (int)S, kc, c->bank_perm.as<int32_t>(),
+                            c->sky_perm.as<int32_t>(), c->gen_cpsi.as<float>(), c->gen_cidx.as<int64_t>(),
+                            c->stream),
+             "topk_kernel launch");
+    TCW_CUDA(c, launch_merge_topk(c->gen_psi[cur].as<float>(), c->gen_idx[cur].as<int64_t>(), have,
+                                  c->gen_cpsi.as<float>(), c->gen_cidx.as<int64_t>(), kc, base, k, S,
+                                  c->gen_psi[cur ^ 1].as<float>(), c->gen_idx[cur ^ 1].as<int64_t>(), c->stream),
+             "merge_topk_kernel launch");
+    cur ^= 1;
+    have = (int)std::min<int64_t>(k, have + kc);
+    // per chunk: device-side error flags and the search kernel's time
+    if ((st = finish(c)) != TCW_OK) {
+      c->have_bank = false;
+      return st;
+    }
+    search_ms += c->info.search_ms;
+    gi.launches += c->info.launches + 3;
+    gi.kernel = c->info.kernel;
+    ++gi.chunks;
+  }
+  TCW_CUDA(c, cudaEventRecord(c->gen_ev1, c->stream), "event");
+  const size_t nn = (size_t)S * k;
+  const cudaMemcpyKind kind = out_flags == TCW_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  TCW_CUDA(c, cudaMemcpyAsync(psi_out, c->gen_psi[cur].p, nn * sizeof(float), kind, c->stream), "copy out");
+  TCW_CUDA(c, cudaMemcpyAsync(idx_out, c->gen_idx[cur].p, nn * sizeof(int64_t), kind, c->stream), "copy out");
+  TCW_CUDA(c, cudaStreamSynchronize(c->stream), "generated search");
+  float total = 0;
+  cudaEventElapsedTime(&total, c->gen_ev0, c->gen_ev1);
+  gi.search_ms = (float)search_ms;
+  gi.total_ms = total;
+  gi.lookups = S * N * c->D * c->Nseg;
+  c->gen_info = gi;
+  c->have_gen = true;
+  // the context's bank buffers now hold the last chunk only
+  c->have_bank = false;
+  c->have_result = false;
+  return TCW_OK;
+}
+
+tcw_status tcw_get_generated_info(tcw_ctx* c, tcw_generated_info* info) {
+  if (!c || !info) return TCW_ERR_INVALID_ARGUMENT;
+  if (!c->have_gen) return fail(c, TCW_ERR_STATE, "no completed generated-bank search");
+  *info = c->gen_info;
+  return TCW_OK;
 }
 
 tcw_status tcw_get_statistics(tcw_ctx* c, float* S_out, float* W1_out, float* W2_out, float* psi_out,

@@ -124,10 +124,8 @@ tcw_status plan_batch(tcw_ctx* c, BatchState* b) {
   ex = std::max(ex, -80);
   b->q = std::ldexp(1.0, ex);
   b->inv_q = std::ldexp(1.0, -ex);
-  double f0max = 0;
-  for (double f : c->h_f0) f0max = std::max(f0max, f);
   const double fband = b->f_min + ((double)b->n_bin + 5.0) * b->df;
-  const double fmax_bins = std::min(f0max, fband) * (1.0 + dmax) / b->df;
+  const double fmax_bins = std::min(c->bank_f0max, fband) * (1.0 + dmax) / b->df;
   b->doppler_bins = fmax_bins * dmax;
   if (fmax_bins * b->q * 0.5 > 0.75 * std::ldexp(1.0, -30))
     return fail(c, TCW_ERR_UNSUPPORTED, "batched search: fixed-point Doppler step too coarse for the bin width");
@@ -169,11 +167,7 @@ tcw_status plan_batch(tcw_ctx* c, BatchState* b) {
 }
 
 int batch_series_terms(const tcw_ctx* c, const BatchState* b, int tile) {
-  double tau_min = INFINITY, r_max = 0;
-  for (size_t i = 0; i < c->h_tau.size(); ++i) {
-    tau_min = std::min(tau_min, c->h_tau[i]);
-    r_max = std::max(r_max, 1.0 / (c->h_n[i] - 1.0));
-  }
+  const double tau_min = c->bank_tau_min, r_max = c->bank_r_max;
   int nt = 1;
   for (const EventHost& e : b->ev) {
     const int n = series_terms_for(e.t.data(), e.n_seg, e.T0, tile, tau_min, r_max);

@@ -48,6 +48,7 @@ struct tcw_ctx {
   int opt_lanes = 0;       // sky groups per chunk: 0 = the fewest padded skies, else 16/32/64
   int autotune = 1;        // batched search: pick bank_chunk and tile_segments by timing
   int amp_power = 0;       // weights times (f(t_j)/f0)^amp_power (Eq. 3)
+  int gen_chunk = 1 << 18; // generated-bank search: templates per chunk
   int triage_spread = 2;   // triage: patches within this distance of a chosen one are suppressed
   int64_t batch_memory = (int64_t)48 << 30;  // batched search: Psi + anchor bytes per wave
   unsigned bank_epoch = 0; // bumped by every tcw_define_bank
@@ -75,7 +76,7 @@ struct tcw_ctx {
   int64_t B = 0;
   int Bpad = 0;
   double T0 = 0;
-  std::vector<double> h_f0, h_tau, h_n;
+  double bank_f0max = 0, bank_tau_min = 0, bank_r_max = 0;  // bounds the plan is made for
   tcw::DevBuf f0, tau, nbr, bank_perm, bank_pos;
   // sky
   bool have_sky = false;
@@ -92,6 +93,11 @@ struct tcw_ctx {
   tcw_info info{};
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   tcw::BatchState* batch = nullptr;  // owned; freed by tcw::batch_free
+  // generated-bank search: running and chunk top-k, timing
+  tcw::DevBuf gen_psi[2], gen_idx[2], gen_cpsi, gen_cidx;
+  cudaEvent_t gen_ev0 = nullptr, gen_ev1 = nullptr;
+  bool have_gen = false;
+  tcw_generated_info gen_info{};
   // learned triage
   std::vector<int32_t> h_sky_perm, h_bank_perm;  // sorted -> caller (host copies)
   tcw::DevBuf tri_dop, tri_hist, tri_feat, tri_psi, tri_anchor, tri_h1, tri_h2, tri_score, tri_sel;

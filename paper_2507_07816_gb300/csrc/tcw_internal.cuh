@@ -284,6 +284,20 @@ cudaError_t group_prepare(int n_det, int lanes, bool half, int weighting);
 cudaError_t launch_group(const GroupParams& p, int grid, bool half, bool record, int weighting,
                          cudaStream_t st);
 cudaError_t launch_lookup(const LookupParams& p, bool half, bool record, cudaStream_t st);
+// A generated template bank (tcw_bank_spec on the device).
+struct BankGenParams {
+  int kind;                // TCW_BANK_LATTICE or TCW_BANK_RANDOM
+  int64_t n_f0, n_tau, n_n;
+  double lo[3], hi[3];     // (f0, tau, n) bounds
+  uint64_t seed;
+};
+cudaError_t launch_gen_bank(const BankGenParams& p, int64_t first, int64_t count, int64_t pad_to, double* f0,
+                            double* tau, double* nbr, int32_t* perm, cudaStream_t st);
+// Per sky: the first k of the merge of a (ra entries) and b (rb entries, local
+// indices + b_base) by (Psi desc, index asc) into o; rows of a and o hold k.
+cudaError_t launch_merge_topk(const float* a_psi, const int64_t* a_idx, int ra, const float* b_psi,
+                              const int64_t* b_idx, int rb, int64_t b_base, int k, int64_t S, float* o_psi,
+                              int64_t* o_idx, cudaStream_t st);
 // Number-count bit map: bits[r][w] bit i = [rho[r][32 w + i] > rho_th] (compared
 // in double; 0 past n_bin) for rows r < rows, words w < bit_pitch.
 int bit_pitch_for(int64_t n_bin);

@@ -22,7 +22,7 @@ F32, F16 = 0, 1
 KERNEL_AUTO, KERNEL_GROUP, KERNEL_LOOKUP = 0, 1, 2
 OPT_KERNEL, OPT_KEEP_STATS, OPT_TILE_SEGMENTS, OPT_BANK_CHUNK = 1, 2, 3, 4
 OPT_AUTOTUNE, OPT_BATCH_MEMORY, OPT_SKY_LANES, OPT_TRIAGE_SPREAD = 5, 6, 7, 8
-OPT_AMPLITUDE_POWER = 9
+OPT_AMPLITUDE_POWER, OPT_GEN_CHUNK = 9, 10
 STAT_POWER, STAT_NUMBER_COUNT = 0, 1
 
 _lock = threading.Lock()
@@ -45,6 +45,30 @@ class _Event(ctypes.Structure):
     _fields_ = [("rho", ctypes.c_void_p), ("t_mid", ctypes.c_void_p), ("weights", ctypes.c_void_p),
                 ("velocity", ctypes.c_void_p), ("nhat", ctypes.c_void_p), ("n_seg", ctypes.c_int64),
                 ("n_sky", ctypes.c_int64), ("T0", ctypes.c_double)]
+
+
+class _BankSpec(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("reserved", ctypes.c_int), ("n_f0", ctypes.c_int64),
+                ("n_tau", ctypes.c_int64), ("n_n", ctypes.c_int64), ("n_tmpl", ctypes.c_int64),
+                ("f0_lo", ctypes.c_double), ("f0_hi", ctypes.c_double), ("tau_lo", ctypes.c_double),
+                ("tau_hi", ctypes.c_double), ("n_lo", ctypes.c_double), ("n_hi", ctypes.c_double),
+                ("seed", ctypes.c_uint64)]
+
+
+class _GenInfo(ctypes.Structure):
+    _fields_ = [("n_tmpl", ctypes.c_int64), ("chunks", ctypes.c_int64), ("chunk_templates", ctypes.c_int64),
+                ("lookups", ctypes.c_int64), ("kernel", ctypes.c_int), ("launches", ctypes.c_int),
+                ("search_ms", ctypes.c_float), ("total_ms", ctypes.c_float)]
+
+
+BANK_LATTICE, BANK_RANDOM = 0, 1
+
+
+def bank_spec(kind, lo, hi, n_f0=1, n_tau=1, n_n=1, n_tmpl=0, seed=0):
+    """A tcw_bank_spec: lattice (n_f0 x n_tau x n_n points) or uniform random
+    (n_tmpl templates, Philox key `seed`) over lo..hi = (f0, tau, n)."""
+    return _BankSpec(int(kind), 0, int(n_f0), int(n_tau), int(n_n), int(n_tmpl), float(lo[0]), float(hi[0]),
+                     float(lo[1]), float(hi[1]), float(lo[2]), float(hi[2]), int(seed))
 
 
 class _BatchInfo(ctypes.Structure):
@@ -114,6 +138,10 @@ def load_library(build_if_missing: bool = True):
                                    p, p, p, i],
             "tcw_get_triage_info": [p, ctypes.POINTER(_TriageInfo)],
             "tcw_sky_order": [p, p],
+            "tcw_bank_size": [ctypes.POINTER(_BankSpec), ctypes.POINTER(i64)],
+            "tcw_generate_bank": [p, ctypes.POINTER(_BankSpec), i64, i64, p, p, p, i],
+            "tcw_search_generated": [p, ctypes.POINTER(_BankSpec), d, i, p, p, i],
+            "tcw_get_generated_info": [p, ctypes.POINTER(_GenInfo)],
             "tcw_probe_read_bandwidth": [i64, i, i, ctypes.POINTER(d)],
         }
         for name, args in sig.items():
@@ -400,6 +428,48 @@ class Search:
             psi.ctypes.data_as(ctypes.c_void_p), idx.ctypes.data_as(ctypes.c_void_p),
             searched.ctypes.data_as(ctypes.c_void_p), HOST))
         return psi, idx, searched
+
+    # -------------------------------------------------------- generated banks
+    def bank_size(self, spec) -> int:
+        n = ctypes.c_int64()
+        self._check(self._lib.tcw_bank_size(ctypes.byref(spec), ctypes.byref(n)))
+        return n.value
+
+    def generate_bank(self, spec, first=0, count=None, out=None):
+        """Templates [first, first + count) of `spec`: (f0, tau, n) float64.
+        ``out``: three torch CUDA tensors to fill on the device, else numpy."""
+        if count is None:
+            count = self.bank_size(spec) - first
+        if out is None:
+            out = tuple(np.empty(int(count), np.float64) for _ in range(3))
+        ptrs, flags = [], set()
+        for a in out:
+            pa, fa, _ = _arg(a, np.float64)
+            ptrs.append(pa)
+            flags.add(fa)
+        if len(flags) != 1:
+            raise ValueError("outputs must all be host or all device")
+        self._check(self._lib.tcw_generate_bank(self._h, ctypes.byref(spec), int(first), int(count), *ptrs,
+                                                flags.pop()))
+        return out
+
+    def search_generated(self, spec, T0, k, psi_out=None, idx_out=None):
+        """Top-k per sky over a generated bank: (psi [S][k], idx [S][k] int64 =
+        generated template index)."""
+        if psi_out is None:
+            psi_out = np.empty((self.n_sky, k), np.float32)
+            idx_out = np.empty((self.n_sky, k), np.int64)
+        pp, pf, _ = _arg(psi_out, np.float32)
+        ip, iff, _ = _arg(idx_out, np.int64)
+        if pf != iff:
+            raise ValueError("outputs must both be host or both device")
+        self._check(self._lib.tcw_search_generated(self._h, ctypes.byref(spec), float(T0), int(k), pp, ip, pf))
+        return psi_out, idx_out
+
+    def generated_info(self) -> dict:
+        i = _GenInfo()
+        self._check(self._lib.tcw_get_generated_info(self._h, ctypes.byref(i)))
+        return {name: getattr(i, name) for name, _ in _GenInfo._fields_}
 
     def triage_info(self) -> dict:
         i = _TriageInfo()

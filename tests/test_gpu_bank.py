@@ -1,0 +1,190 @@
+"""GPU parity of the device-generated template banks and of the streamed
+search over them (Sec. 2: cubic-lattice and uniform random banks), against
+the oracle's generators and FP64 statistic.
+
+Generated templates are compared bit for bit (both sides make the same
+correctly rounded operations from the same integers).  The streamed search is
+compared with the oracle's top-k over the whole bank, across several chunks
+with a ragged last one, k larger than a chunk, the number-count statistic and
+the amplitude weight, and on a 1e7-template bank through sampled entries.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2507_07816_gb300 as tcw
+import tcw_synth as syn
+from _parity import REL, assert_topk_matches_oracle
+from test_gpu_parity import multi_problem
+
+pytestmark = pytest.mark.gpu
+
+LO = (500.0, 3500.0, 3.0)
+HI = (3000.0, 35000.0, 7.0)
+
+
+def spec_pair(kind, **kw):
+    """(library spec, oracle kwargs) of one bank."""
+    lo, hi = kw.pop("lo", LO), kw.pop("hi", HI)
+    sp = tcw.bank_spec(kind, lo, hi, **kw)
+    okw = dict(lo=lo, hi=hi, n_f0=kw.get("n_f0", 1), n_tau=kw.get("n_tau", 1), n_n=kw.get("n_n", 1),
+               seed=kw.get("seed", 0))
+    return sp, okw
+
+
+@pytest.mark.parametrize("kind,kw,first,count", [
+    (tcw.BANK_RANDOM, dict(n_tmpl=10**9, seed=20250715), 0, 5000),
+    (tcw.BANK_RANDOM, dict(n_tmpl=10**9, seed=20250715), 10**9 - 3000, 3000),
+    (tcw.BANK_LATTICE, dict(n_f0=10**4, n_tau=10**3, n_n=100), 0, 4096),
+    (tcw.BANK_LATTICE, dict(n_f0=10**4, n_tau=10**3, n_n=100), 10**9 - 12345, 12345),
+    (tcw.BANK_LATTICE, dict(n_f0=7, n_tau=1, n_n=3), 0, 21),
+])
+def test_generated_templates_bit_exact(kind, kw, first, count):
+    sp, okw = spec_pair(kind, **kw)
+    s = tcw.Search(0)
+    assert s.bank_size(sp) == (kw.get("n_tmpl") or kw["n_f0"] * kw["n_tau"] * kw["n_n"])
+    got = s.generate_bank(sp, first, count)
+    ref = oracle.bank_templates(kind, first, count, okw["lo"], okw["hi"], okw["n_f0"], okw["n_tau"],
+                                okw["n_n"], okw["seed"])
+    for g, r in zip(got, ref):
+        np.testing.assert_array_equal(g, r)
+    # into device memory
+    import torch
+    dev = tuple(torch.empty(count, dtype=torch.float64, device="cuda:0") for _ in range(3))
+    s.generate_bank(sp, first, count, out=dev)
+    for g, r in zip(dev, ref):
+        np.testing.assert_array_equal(g.cpu().numpy(), r)
+    s.close()
+
+
+def test_invalid_specs_and_ranges():
+    s = tcw.Search(0)
+    bad = [tcw.bank_spec(tcw.BANK_RANDOM, LO, HI, n_tmpl=0),
+           tcw.bank_spec(tcw.BANK_LATTICE, LO, HI, n_f0=0),
+           tcw.bank_spec(tcw.BANK_RANDOM, (0.0, 3500.0, 3.0), HI, n_tmpl=5),
+           tcw.bank_spec(tcw.BANK_RANDOM, (500.0, 3500.0, 1.0), HI, n_tmpl=5),
+           tcw.bank_spec(tcw.BANK_RANDOM, (3001.0, 3500.0, 3.0), HI, n_tmpl=5),
+           tcw.bank_spec(tcw.BANK_LATTICE, LO, HI, n_f0=2**31, n_tau=2**31, n_n=2),
+           tcw.bank_spec(7, LO, HI, n_tmpl=5)]
+    for sp in bad:
+        with pytest.raises(tcw.TcwError):
+            s.bank_size(sp)
+    sp = tcw.bank_spec(tcw.BANK_RANDOM, LO, HI, n_tmpl=100)
+    with pytest.raises(tcw.TcwError):
+        s.generate_bank(sp, 50, 51)
+    with pytest.raises(tcw.TcwError):
+        s.set_option(tcw.OPT_GEN_CHUNK, 100)      # not a multiple of 32
+    s.close()
+
+
+def load(s, p):
+    s.load_spectrogram(p.rho, p.f_min, p.df, p.t_mid, p.weights)
+    s.load_velocity(p.velocity)
+    s.define_sky(p.nhat)
+
+
+def oracle_generated(p, kind, okw, N, **stat):
+    f0, tau, n = oracle.bank_templates(kind, 0, N, okw["lo"], okw["hi"], okw["n_f0"], okw["n_tau"],
+                                       okw["n_n"], okw["seed"])
+    return oracle.search_stats(p.rho, p.f_min, p.df, p.t_mid, p.weights, p.velocity, p.nhat, f0, tau, n,
+                               p.T0, **stat)
+
+
+@pytest.mark.parametrize("chunk,k", [(1024, 25), (64, 100), (1 << 18, 10)])
+def test_streamed_random_bank_search(chunk, k):
+    p = multi_problem(seed=121, n_sky=40, n_seg=90, n_tmpl=8)
+    band = (p.f_min - 5, p.f_min + p.rho.shape[2] * p.df + 5)
+    N = 3000
+    sp, okw = spec_pair(tcw.BANK_RANDOM, n_tmpl=N, seed=99, lo=(band[0], 3500.0, 3.0),
+                        hi=(band[1], 35000.0, 7.0))
+    s = tcw.Search(0)
+    s.set_option(tcw.OPT_GEN_CHUNK, chunk)
+    load(s, p)
+    val, idx = s.search_generated(sp, p.T0, k)
+    info = s.generated_info()
+    assert info["n_tmpl"] == N and info["chunks"] == -(-N // min(chunk, 3008))
+    oS, oW1, oW2, oP = oracle_generated(p, tcw.BANK_RANDOM, okw, N)
+    assert_topk_matches_oracle(idx, val, oP, oS, oW2, k)
+    # the bank buffers now hold one chunk: a plain search needs define_bank again
+    with pytest.raises(tcw.TcwError):
+        s.search(5)
+    s.close()
+
+
+def test_streamed_lattice_count_and_amplitude():
+    p = multi_problem(seed=122, n_sky=20, n_seg=70, n_tmpl=8)
+    band = (p.f_min - 2, p.f_min + p.rho.shape[2] * p.df + 2)
+    sp, okw = spec_pair(tcw.BANK_LATTICE, n_f0=150, n_tau=4, n_n=3, lo=(band[0], 3500.0, 3.0),
+                        hi=(band[1], 35000.0, 7.0))
+    N = 150 * 4 * 3
+    s = tcw.Search(0)
+    s.set_option(tcw.OPT_GEN_CHUNK, 512)
+    load(s, p)
+    val, idx = s.search_generated(sp, p.T0, 12)
+    oS, oW1, oW2, oP = oracle_generated(p, tcw.BANK_LATTICE, okw, N)
+    assert_topk_matches_oracle(idx, val, oP, oS, oW2, 12)
+    s.set_option(tcw.OPT_AMPLITUDE_POWER, 4)
+    val, idx = s.search_generated(sp, p.T0, 12)
+    oS, oW1, oW2, oP = oracle_generated(p, tcw.BANK_LATTICE, okw, N, amp_power=4)
+    assert_topk_matches_oracle(idx, val, oP, oS, oW2, 12)
+    s.set_option(tcw.OPT_AMPLITUDE_POWER, 0)
+    s.set_statistic(tcw.STAT_NUMBER_COUNT, 1.6)
+    val, idx = s.search_generated(sp, p.T0, 12)
+    o = oracle_generated(p, tcw.BANK_LATTICE, okw, N, rho_th=1.6)
+    # count ties are common (S is a sum of a few weights): compare values by rank
+    o_idx, o_val = oracle.topk(o[3], 12)
+    q = np.exp(-1.6)
+    tol = REL * (o[0].max() + q * o[1].max()) / np.sqrt(q * (1 - q) * o[2][o[2] > 0].min()) + 1e-4
+    assert np.all(np.abs(val - o_val) <= tol)
+    rows = np.arange(idx.shape[0])[:, None]
+    assert np.all(np.abs(val - o[3][rows, idx]) <= tol)
+    s.close()
+
+
+def test_ten_million_template_bank():
+    """1e7 random templates streamed in 2^20-template chunks over 64 skies;
+    the returned entries match the oracle at their own (sky, template)."""
+    r = syn.rng(123)
+    n_seg, n_bin = 64, 4096
+    t = syn.segment_times(n_seg, 8.0)
+    T0 = t[0] - 4.0
+    f_min, df = 1000.0, 1 / 8
+    dets = syn.random_detectors(r, 1)
+    vel = np.stack([d.velocity(t) for d in dets])
+    rho = syn.exponential_noise(r, (1, n_seg, n_bin))
+    nhat = syn.random_sky(r, 64)
+    N = 10**7
+    lo, hi = (1000.0, 3500.0, 3.0), (1500.0, 35000.0, 7.0)
+    sp = tcw.bank_spec(tcw.BANK_RANDOM, lo, hi, n_tmpl=N, seed=5)
+    s = tcw.Search(0)
+    s.set_option(tcw.OPT_GEN_CHUNK, 1 << 20)
+    s.load_spectrogram(rho, f_min, df, t, None)
+    s.load_velocity(vel)
+    s.define_sky(nhat)
+    k = 20
+    val, idx = s.search_generated(sp, T0, k)
+    info = s.generated_info()
+    assert info["chunks"] == 10 and info["n_tmpl"] == N and info["kernel"] == tcw.KERNEL_GROUP
+    assert idx.min() >= 0 and idx.max() < N
+    assert np.all(np.diff(val, axis=1) <= 0)
+    rows = r.integers(0, 64, 6)
+
+    def templates_at(ts):
+        cols = [oracle.bank_templates(1, int(b), 1, lo, hi, seed=5) for b in ts]
+        return tuple(np.array([c[a][0] for c in cols]) for a in range(3))
+
+    # returned entries against the oracle at their own (sky, template)
+    tb = np.unique(idx[rows])
+    pos = {int(b): i for i, b in enumerate(tb)}
+    pp = np.array([(sk, pos[int(idx[sk, j])]) for sk in rows for j in range(k)])
+    o = oracle.search_stats(rho, f_min, df, t, None, vel, nhat, *templates_at(tb), T0, pairs=pp)
+    got = np.array([val[sk, j] for sk in rows for j in range(k)])
+    tol = REL * o[0] / np.sqrt(o[2]) + 1e-5
+    assert np.all(np.abs(got - o[3]) <= tol)
+    # a random sample of the bank: every template outside the top-k lies at or below the k-th value
+    sample = r.integers(0, N, 2000)
+    osamp = oracle.search_stats(rho, f_min, df, t, None, vel, nhat[rows], *templates_at(sample), T0)[3]
+    for a, sk in enumerate(rows):
+        outside = ~np.isin(sample, idx[sk])
+        assert np.all(osamp[a][outside] <= val[sk, k - 1] + 1e-4)
+    s.close()
