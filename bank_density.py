@@ -1,0 +1,230 @@
+#!/usr/bin/env python
+"""Template-bank density study on the GPU: detection efficiency against the
+number of templates N, the study of Sec. 3 of arXiv:2507.07816 (which runs
+N = 1e4 .. 1e7 and argues that 1e8 - 1e9 reach the best sensitivity).
+
+Data (synthetic, shaped like the paper's): one detector, 24 h of 8 s
+segments (10800), band 550 - 1210 Hz at 1/8 Hz (5280 bins), exponential
+noise.  Every data set carries M = 256 signals, each at its own sky
+direction, with f0 uniform in [1000, 1200] Hz, n = 5, tau = 1e4 s, all
+starting at the data start T0, at a common SNR (the expected Psi of the exact
+track with the power statistic); SNR plays the role of the paper's distance
+(d ~ SNR^-1/2 at fixed noise).  Banks cover f0 in [1000, 1200] Hz, tau in
+[3500, 35000] s and n in [3, 7]: a cubic lattice (equal points per axis) or
+uniform random (Philox), generated on the device and streamed through
+tcw_search_generated at the M injection skies with the injections' T0.
+
+Detection, as in the paper: the threshold Psi_noise_max(N) comes from a
+noise-only data set searched with the same bank (the 99th percentile over the
+M skies of each sky's largest Psi); an injection counts as found when a
+template close to it has Psi above the threshold among the k best of its sky.
+"Close" is read two ways (the paper only says that templates far from the
+injection are excluded): "near", the template's source frequency within 2 Hz
+(16 bins) of the injection's at 16 times over the day, and "track", within
+4 bins.  The SNR at 90 % efficiency comes from a logistic fit of efficiency
+against SNR.  The exact-track row searches each injection's own template.
+
+  python bank_density.py [--n-list 1e4,1e5,1e6,1e7] [--n-big 1e8]
+                         [--snr 6,10,15,20,30] [--report gpurun_out/bank_density.json]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+LO = (1000.0, 3500.0, 3.0)
+HI = (1200.0, 35000.0, 7.0)
+VARIANTS = [  # name, bank kind, statistic, amplitude power
+    ("random/power", "random", "power", 0),
+    ("lattice/power", "lattice", "power", 0),
+    ("random/count", "random", "count", 0),
+    ("random/power+amp4", "random", "power", 4),
+]
+
+
+def source_frequency(f0, tau, n, T0, t):
+    """Eq. 1 at the times t (broadcast)."""
+    return f0 * ((t - T0) / tau + 1.0) ** (1.0 / (1.0 - n))
+
+
+def snr90(levels, eff):
+    """SNR at 90 % efficiency: logistic fit, else linear interpolation."""
+    levels, eff = np.asarray(levels, float), np.asarray(eff, float)
+    try:
+        from scipy.optimize import curve_fit
+        p, _ = curve_fit(lambda x, a, b: 1.0 / (1.0 + np.exp(-(x - a) / b)), levels, eff,
+                         p0=(float(np.median(levels)), 1.0), bounds=((0.0, 0.05), (50.0, 20.0)), maxfev=10000)
+        return float(p[0] + p[1] * math.log(9.0))
+    except Exception:
+        above = np.nonzero(eff >= 0.9)[0]
+        if not above.size:
+            return None
+        i = above[0]
+        if i == 0:
+            return float(levels[0])
+        x0, x1, y0, y1 = levels[i - 1], levels[i], eff[i - 1], eff[i]
+        return float(x0 + (0.9 - y0) * (x1 - x0) / max(y1 - y0, 1e-12))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n-list", default="1e4,1e5,1e6,1e7")
+    ap.add_argument("--n-big", default="1e8", help="random/power only; empty to skip")
+    ap.add_argument("--big-snr", default="10,20", help="SNR levels searched with the big bank")
+    ap.add_argument("--snr", default="6,10,15,20,30")
+    ap.add_argument("--skies", type=int, default=256)
+    ap.add_argument("--segments", type=int, default=10800)
+    ap.add_argument("--t-sft", type=float, default=8.0)
+    ap.add_argument("--k", type=int, default=64)
+    ap.add_argument("--seed", type=int, default=20250801)
+    ap.add_argument("--report", default=None)
+    args = ap.parse_args()
+
+    import paper_2507_07816_gb300 as tcw
+    import tcw_synth as syn
+
+    r = syn.rng(args.seed)
+    n_seg, t_sft = args.segments, args.t_sft
+    df = 1.0 / t_sft
+    f_min = 550.0
+    n_bin = int(round((1210.0 - f_min) / df))
+    t = syn.segment_times(n_seg, t_sft)
+    T0 = float(t[0] - 0.5 * t_sft)
+    dets = syn.random_detectors(r, 1)
+    vel = np.stack([d.velocity(t) for d in dets])
+    M = args.skies
+    sky = syn.random_sky(r, M)
+    levels = [float(x) for x in args.snr.split(",")]
+    n_list = [int(float(x)) for x in args.n_list.split(",") if x]
+    n_big = int(float(args.n_big)) if args.n_big else 0
+    big_levels = [float(x) for x in args.big_snr.split(",") if x]
+    t_check = T0 + np.linspace(0.0, t[-1] - T0, 16)
+
+    def dataset(level, seed):
+        rr = syn.rng(seed)
+        rho = syn.exponential_noise(rr, (1, n_seg, n_bin))
+        injs = []
+        if level > 0:
+            f0s = rr.uniform(LO[0], HI[0], M)
+            injs = [syn.Injection(float(f0s[m]), 1e4, 5.0, sky[m], level) for m in range(M)]
+            syn.inject_many(rr, rho, injs, dets, t, T0, f_min, df)
+        return rho, injs
+
+    def spec(kind, N):
+        if kind == "lattice":
+            m = max(1, int(round(N ** (1.0 / 3.0))))
+            return tcw.bank_spec(tcw.BANK_LATTICE, LO, HI, n_f0=m, n_tau=m, n_n=m)
+        return tcw.bank_spec(tcw.BANK_RANDOM, LO, HI, n_tmpl=N, seed=args.seed + N)
+
+    s = tcw.Search(0)
+    s.define_sky(sky)
+    k = args.k
+
+    def search(rho, variant, N):
+        _, kind, stat, amp = variant
+        s.load_spectrogram(rho, f_min, df, t, None)
+        s.load_velocity(vel)
+        if stat == "count":
+            s.set_statistic(tcw.STAT_NUMBER_COUNT, 1.6)
+        else:
+            s.set_statistic(tcw.STAT_POWER)
+        s.set_option(tcw.OPT_AMPLITUDE_POWER, amp)
+        sp = spec(kind, N)
+        val, idx = s.search_generated(sp, T0, k)
+        return sp, val, idx, s.generated_info()
+
+    def found(sp, val, idx, thr, injs):
+        """Fractions of injections found under the "near" and "track" readings,
+        and with any template above the threshold."""
+        near = track = above = 0
+        for m, inj in enumerate(injs):
+            cand = idx[m][val[m] > thr]
+            if not cand.size:
+                continue
+            above += 1
+            f0, tau, n = s.generate_bank_at(sp, cand)
+            ft = source_frequency(f0[:, None], tau[:, None], n[:, None], T0, t_check[None, :])
+            fi = source_frequency(inj.f0, inj.tau, inj.n, T0, t_check)
+            dev = np.max(np.abs(ft - fi[None, :]), axis=1)
+            near += bool(np.any(dev <= 16 * df))
+            track += bool(np.any(dev <= 4 * df))
+        return near / len(injs), track / len(injs), above / len(injs)
+
+    runs = [(v, N) for N in n_list for v in VARIANTS]
+    if n_big:
+        runs.append((VARIANTS[0], n_big))
+    t0 = time.perf_counter()
+    noise, _ = dataset(0.0, args.seed + 1)
+    res = {}
+    gpu_s = 0.0
+    for v, N in runs:
+        sp, val, idx, info = search(noise, v, N)
+        gpu_s += info["total_ms"] / 1e3
+        res[(v[0], N)] = {"variant": v[0], "N": s.bank_size(sp), "threshold": float(np.quantile(val[:, 0], 0.99)),
+                          "noise_max_median": float(np.median(val[:, 0])), "eff": {}, "eff_track": {},
+                          "above": {},
+                          "ms_per_search": info["total_ms"], "lookups": info["lookups"]}
+        print(f"noise {v[0]:18s} N={res[(v[0], N)]['N']:>11d} thr={res[(v[0], N)]['threshold']:.2f} "
+              f"({info['total_ms']:.0f} ms)", flush=True)
+    exact = {}
+    for li, level in enumerate(levels):
+        rho, injs = dataset(level, args.seed + 100 + li)
+        for v, N in runs:
+            if N == n_big and level not in big_levels:
+                continue
+            sp, val, idx, info = search(rho, v, N)
+            gpu_s += info["total_ms"] / 1e3
+            e, et, ab = found(sp, val, idx, res[(v[0], N)]["threshold"], injs)
+            res[(v[0], N)]["eff"][level] = e
+            res[(v[0], N)]["eff_track"][level] = et
+            res[(v[0], N)]["above"][level] = ab
+            print(f"snr {level:5.1f} {v[0]:18s} N={res[(v[0], N)]['N']:>11d} efficiency near {e:.3f} "
+                  f"track {et:.3f} (any above threshold {ab:.3f})", flush=True)
+        # exact tracks: each sky searched with the M injected templates; its own template's Psi
+        s.set_statistic(tcw.STAT_POWER)
+        s.set_option(tcw.OPT_AMPLITUDE_POWER, 0)
+        s.set_option(tcw.OPT_KEEP_STATS, 1)
+        s.load_spectrogram(rho, f_min, df, t, None)
+        s.load_velocity(vel)
+        s.define_bank([i.f0 for i in injs], [i.tau for i in injs], [i.n for i in injs], T0)
+        s.search(1)
+        psi = s.statistics(("psi",))["psi"]
+        own = np.array([psi[m, m] for m in range(M)])
+        thr = res[(VARIANTS[0][0], max(n_list))]["threshold"]
+        exact[level] = {"efficiency": float(np.mean(own > thr)), "psi_median": float(np.median(own))}
+        s.set_option(tcw.OPT_KEEP_STATS, 0)
+        print(f"snr {level:5.1f} exact track efficiency {exact[level]['efficiency']:.3f} "
+              f"(median Psi {exact[level]['psi_median']:.2f})", flush=True)
+    s.close()
+    rows = []
+    for (name, N), d in res.items():
+        lv = sorted(d["eff"])
+        d["snr90"] = snr90(lv, [d["eff"][x] for x in lv]) if len(lv) >= 3 else None
+        d["snr90_track"] = snr90(lv, [d["eff_track"][x] for x in lv]) if len(lv) >= 3 else None
+        for key in ("eff", "eff_track", "above"):
+            d[key] = {str(x): d[key][x] for x in lv}
+        rows.append(d)
+    ex_lv = sorted(exact)
+    report = {"segments": n_seg, "t_sft": t_sft, "bins": n_bin, "skies": M, "k": k, "snr_levels": levels,
+              "rows": rows, "exact": {str(x): exact[x] for x in ex_lv},
+              "exact_snr90": snr90(ex_lv, [exact[x]["efficiency"] for x in ex_lv]),
+              "gpu_search_s": gpu_s, "wall_s": time.perf_counter() - t0}
+    print(json.dumps(report), flush=True)
+    if args.report:
+        os.makedirs(os.path.dirname(os.path.abspath(args.report)), exist_ok=True)
+        with open(args.report, "w") as f:
+            json.dump(report, f, indent=1)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -420,6 +420,36 @@ def spindown_frequency_many(f0, tau, n, T0, t, step=16.0):
     return out
 
 
+def inject_many(r: np.random.Generator, rho, injections, detectors, t, T0, f_min, df, weights=None):
+    """inject() for many signals at once: the braking-law frequencies of all
+    sources come from one vectorised integration; the cells of each signal
+    are then set as inject() does (later signals overwrite shared cells)."""
+    if not injections:
+        return
+    fsrc = spindown_frequency_many([i.f0 for i in injections], [i.tau for i in injections],
+                                   [i.n for i in injections], T0, t)
+    D, n_seg, n_bin = rho.shape
+    w = np.ones((D, n_seg)) if weights is None else np.asarray(weights, np.float64)
+    for i, inj in enumerate(injections):
+        bins = np.full((D, n_seg), -1, np.int64)
+        fdet = np.full((D, n_seg), np.nan)
+        for d, det in enumerate(detectors):
+            fd = detector_frame_frequency(fsrc[i], det, inj.nhat, t)
+            fdet[d] = fd
+            bins[d] = signal_bins(fd, f_min, df, n_bin)
+        inj.bins = bins
+        ok = bins >= 0
+        if not ok.any():
+            continue
+        lam_shape = np.where(ok, (fdet / inj.f0) ** 4, 0.0)
+        lam_unit = (w * lam_shape).sum() / math.sqrt((w * w * ok).sum())
+        mu = np.sqrt(2.0 * (inj.snr / lam_unit) * lam_shape)
+        dd, jj = np.nonzero(ok)
+        x = r.normal(size=dd.shape[0])
+        y = r.normal(size=dd.shape[0])
+        rho[dd, jj, bins[dd, jj]] = (((x + mu[dd, jj]) ** 2 + y ** 2) / 2.0).astype(rho.dtype)
+
+
 def training_event(seed, bank, n_det=2, n_seg=10000, n_bin=10000, n_sky=1024, t_sft=4.0,
                    f_min=500.0, n_inj=4, snr_range=(5.0, 12.0), device=None, dtype=np.float32):
     """One event for the learned triage: exponential noise (drawn on `device`
