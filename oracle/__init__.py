@@ -72,7 +72,7 @@ def _load():
                 p, p, p, p, i]
             lib.oracle_search_stats_ext.restype = None
             lib.oracle_search_stats_ext.argtypes = [
-                p, i, i, i, d, d, p, p, p, p, i, p, p, p, i, d, i, i, d, p, i64,
+                p, i, i, i, d, d, p, p, p, p, i, p, p, p, i, d, i, i, d, i, p, i64,
                 p, p, p, p, i]
             lib.oracle_track_coordinates.restype = None
             lib.oracle_track_coordinates.argtypes = [
@@ -127,7 +127,7 @@ def critical_ratio(S, W1, W2) -> float:
 
 
 def search_stats(rho, f_min, df, t_mid, weights, velocity, nhat, f0, tau, n, T0,
-                 pairs=None, nthreads=0, amp_power=0, rho_th=None):
+                 pairs=None, nthreads=0, amp_power=0, rho_th=None, track_bins=1):
     """S, W1, W2, Psi for every (sky, template) pair.
 
     rho [D][Nseg][Nbin] float32 (float16 input is widened exactly);
@@ -137,8 +137,10 @@ def search_stats(rho, f_min, df, t_mid, weights, velocity, nhat, f0, tau, n, T0,
     (f(t_j)/f0)^amp_power, the template's own amplitude evolution (Eq. 3 gives
     4 for a power statistic).  rho_th (a float > 0) selects the number count
     instead of the power: nu = 1 where rho > rho_th, Psi with mean q*W1 and
-    variance q(1-q)*W2, q = exp(-rho_th).  Returns four float64 arrays shaped
-    [P] or [S][B].
+    variance q(1-q)*W2, q = exp(-rho_th).  track_bins = 2 sums the two bins
+    whose centres bracket the track (floor(x), floor(x) + 1, both in band),
+    doubling the mean and variance of Eq. 4.  Returns four float64 arrays
+    shaped [P] or [S][B].
     """
     rho = _c(np.asarray(rho).astype(np.float32, copy=False), np.float32)
     D, Nseg, Nbin = rho.shape
@@ -161,11 +163,12 @@ def search_stats(rho, f_min, df, t_mid, weights, velocity, nhat, f0, tau, n, T0,
     outs = [np.empty(shape, np.float64) for _ in range(4)]
     assert int(amp_power) >= 0
     assert rho_th is None or float(rho_th) > 0
+    assert track_bins in (1, 2)
     _load().oracle_search_stats_ext(
         _ptr(rho), D, Nseg, Nbin, float(f_min), float(df), _ptr(t_mid),
         _ptr(weights), _ptr(velocity), _ptr(nhat), S_, _ptr(f0), _ptr(tau),
         _ptr(n), B, float(T0), int(amp_power), 0 if rho_th is None else 1,
-        0.0 if rho_th is None else float(rho_th), _ptr(pp), P, *(_ptr(o) for o in outs),
+        0.0 if rho_th is None else float(rho_th), int(track_bins), _ptr(pp), P, *(_ptr(o) for o in outs),
         int(nthreads))
     return tuple(outs)
 

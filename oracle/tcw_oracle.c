@@ -36,6 +36,13 @@
  * (compared in double), else 0, so s = sum w*nu.  Under noise rho is Exp(1),
  * so nu is Bernoulli(q) with q = exp(-rho_th): <s> = q*W1 and
  * sigma_s^2 = q(1-q)*W2.  rho_th is a caller parameter.
+ *
+ * Two-bin tracks (an extension for tracks that fall between bins or move by
+ * more than a bin within one SFT, where a signal's power leaks into the
+ * neighbouring bin): with track_bins = 2 each lookup takes the two bins whose
+ * centres bracket the track, k = floor(x) and k + 1 (x the bin coordinate),
+ * valid when both lie in the band; its value is the sum of their powers (or
+ * counts).  Bins are independent under noise, so <s> and sigma_s^2 double.
  */
 #include <math.h>
 #include <stdint.h>
@@ -88,6 +95,19 @@ double oracle_critical_ratio_count(double S, double W1, double W2, double rho_th
     return (S - q * W1) / sqrt(q * (1.0 - q) * W2);
 }
 
+/* Eq. 4 when each lookup sums m independent bins: mean and variance scale by m. */
+static double oracle_critical_ratio_bins(double S, double W1, double W2, int number_count,
+                                         double rho_th, int m)
+{
+    if (W2 <= 0.0) return -INFINITY;
+    double mean = 1.0, var = 1.0;
+    if (number_count) {
+        mean = exp(-rho_th);
+        var = mean * (1.0 - mean);
+    }
+    return (S - m * mean * W1) / sqrt(m * var * W2);
+}
+
 /*
  * Statistic of one (sky, template) pair: S = sum w*rho, W1 = sum w,
  * W2 = sum w^2 over every detector d and segment j whose track bin lies in
@@ -104,7 +124,8 @@ static void oracle_pair_stats(const float *rho, int D, int Nseg, int Nbin,
                               const float *w, const double *v,
                               const double *nhat, double f0, double tau,
                               double n, double T0, int amp_power,
-                              int number_count, double rho_th, double out[3])
+                              int number_count, double rho_th, int track_bins,
+                              double out[3])
 {
     double S = 0.0, W1 = 0.0, W2 = 0.0;
     for (int d = 0; d < D; ++d) {
@@ -113,15 +134,25 @@ static void oracle_pair_stats(const float *rho, int D, int Nseg, int Nbin,
             if (t < T0) continue;
             double f = oracle_track_frequency(f0, tau, n, T0, t);
             double fh = oracle_doppler_frequency(f, v + ((size_t)d * Nseg + j) * 3, nhat);
-            int64_t k = oracle_bin_index(fh, f_min, df);
-            if (k < 0 || k >= Nbin) continue;
+            int64_t k;
+            if (track_bins == 2) {
+                k = (int64_t)floor(oracle_bin_coordinate(fh, f_min, df));
+                if (k < 0 || k + 1 >= Nbin) continue;
+            } else {
+                k = oracle_bin_index(fh, f_min, df);
+                if (k < 0 || k >= Nbin) continue;
+            }
             double wj = w ? (double)w[(size_t)d * Nseg + j] : 1.0;
             /* optional amplitude weight: the signal power follows h0^2 and
              * h0 grows as f^2 (Eq. 3), so a template's expected excess in
              * segment j scales as (f(t_j)/f0)^4 (amp_power = 4) */
             if (amp_power > 0) wj *= pow(f / f0, (double)amp_power);
-            double r = (double)rho[((size_t)d * Nseg + j) * (size_t)Nbin + (size_t)k];
-            if (number_count) r = r > rho_th ? 1.0 : 0.0;
+            const float *row = rho + ((size_t)d * Nseg + j) * (size_t)Nbin;
+            double r = 0.0;
+            for (int64_t b = k; b < k + track_bins; ++b) {
+                double rb = (double)row[b];
+                r += number_count ? (rb > rho_th ? 1.0 : 0.0) : rb;
+            }
             S += wj * r;
             W1 += wj;
             W2 += wj * wj;
@@ -144,7 +175,7 @@ void oracle_search_stats_ext(const float *rho, int D, int Nseg, int Nbin,
                              const double *nhat, int n_sky,
                              const double *f0, const double *tau, const double *n,
                              int n_tmpl, double T0, int amp_power,
-                             int number_count, double rho_th,
+                             int number_count, double rho_th, int track_bins,
                              const int64_t *pairs, int64_t P,
                              double *S_out, double *W1_out, double *W2_out,
                              double *Psi_out, int nthreads);
@@ -160,20 +191,21 @@ void oracle_search_stats(const float *rho, int D, int Nseg, int Nbin,
                          double *Psi_out, int nthreads)
 {
     oracle_search_stats_ext(rho, D, Nseg, Nbin, f_min, df, t_mid, w, v, nhat, n_sky, f0, tau, n,
-                            n_tmpl, T0, 0, 0, 0.0, pairs, P, S_out, W1_out, W2_out, Psi_out,
+                            n_tmpl, T0, 0, 0, 0.0, 1, pairs, P, S_out, W1_out, W2_out, Psi_out,
                             nthreads);
 }
 
 /* As oracle_search_stats, with every weight multiplied by (f(t_j)/f0)^amp_power
- * (amp_power = 0: none), and with the number count of threshold rho_th in
- * place of the power when number_count != 0. */
+ * (amp_power = 0: none), with the number count of threshold rho_th in place of
+ * the power when number_count != 0, and with two-bin lookups when
+ * track_bins == 2 (1: the nearest bin). */
 void oracle_search_stats_ext(const float *rho, int D, int Nseg, int Nbin,
                              double f_min, double df, const double *t_mid,
                              const float *w, const double *v,
                              const double *nhat, int n_sky,
                              const double *f0, const double *tau, const double *n,
                              int n_tmpl, double T0, int amp_power,
-                             int number_count, double rho_th,
+                             int number_count, double rho_th, int track_bins,
                              const int64_t *pairs, int64_t P,
                              double *S_out, double *W1_out, double *W2_out,
                              double *Psi_out, int nthreads)
@@ -195,13 +227,17 @@ void oracle_search_stats_ext(const float *rho, int D, int Nseg, int Nbin,
         double st[3];
         oracle_pair_stats(rho, D, Nseg, Nbin, f_min, df, t_mid, w, v,
                           nhat + 3 * s, f0[b], tau[b], n[b], T0, amp_power,
-                          number_count, rho_th, st);
+                          number_count, rho_th, track_bins, st);
         if (S_out) S_out[i] = st[0];
         if (W1_out) W1_out[i] = st[1];
         if (W2_out) W2_out[i] = st[2];
-        if (Psi_out)
-            Psi_out[i] = number_count ? oracle_critical_ratio_count(st[0], st[1], st[2], rho_th)
-                                      : oracle_critical_ratio(st[0], st[1], st[2]);
+        if (Psi_out) {
+            if (track_bins == 2)
+                Psi_out[i] = oracle_critical_ratio_bins(st[0], st[1], st[2], number_count, rho_th, 2);
+            else
+                Psi_out[i] = number_count ? oracle_critical_ratio_count(st[0], st[1], st[2], rho_th)
+                                          : oracle_critical_ratio(st[0], st[1], st[2]);
+        }
     }
 }
 

@@ -286,6 +286,52 @@ def test_number_count_is_the_power_sum_of_the_thresholded_map():
                                    rtol=1e-13, atol=1e-13)
 
 
+def test_two_bin_fixture():
+    """Two-bin lookups on the hand-computed band-edge case: the pair floor(x),
+    floor(x) + 1 (not the nearest bin), both in band; Eq. 4 with 2 W1, 2 W2."""
+    kv = {row[0]: row[1:] for row in _read_rows("two_bin_case.txt")}
+    S, W1, W2, Psi = _band_edge_case(track_bins=2)
+    ex = float(kv["S"][0])
+    assert S == pytest.approx(ex, rel=1e-6)                        # float32 powers
+    assert W1 == pytest.approx(float(kv["W1"][0]), rel=1e-12)
+    assert W2 == pytest.approx(float(kv["W2"][0]), rel=1e-12)
+    assert Psi == pytest.approx((ex - 2 * 2.75) / math.sqrt(2 * 4.3125), rel=1e-6)
+    # the pair must lie in the band: x = 15.3 in a 16-bin band
+    f0 = float(kv["edge_f0"][0])
+    rho = np.zeros((1, 1, 16), np.float32)
+    rho[0, 0] = 1 + np.arange(16) / 100.0
+    args = (90.0, 1.0, np.array([5000.0]), None, np.zeros((1, 1, 3)), np.array([[0.0, 0.0, 1.0]]),
+            [f0], [1000.0], [3.0], 5000.0)
+    one = oracle.search_stats(rho, *args)
+    two = oracle.search_stats(rho, *args, track_bins=2)
+    assert one[0][0, 0] == pytest.approx(float(kv["edge_S1"][0]), rel=1e-6)
+    assert two[2][0, 0] == 0.0 and two[3][0, 0] == -math.inf
+
+
+def test_two_bin_noise_mean_zero_variance_one():
+    """Two independent Exp(1) bins per lookup: Psi with mean 2 W1 and variance
+    2 W2 has mean 0 and variance 1 under noise (power and count)."""
+    r = syn.rng(25)
+    n_seg, n_bin = 48, 2048
+    t = syn.segment_times(n_seg, 32.0)
+    T0 = t[0] - 16.0
+    vel = np.zeros((1, n_seg, 3))
+    f0 = 510.0 + 1.25 * np.arange(48)
+    tau = np.full(f0.shape, 35000.0)
+    n = np.full(f0.shape, 5.0)
+    for kw in ({}, {"rho_th": 1.6}):
+        vals = []
+        for _ in range(300):
+            rho = syn.exponential_noise(r, (1, n_seg, n_bin))
+            w = syn.uniform_weights(r, 1, n_seg, 0.2, 2.0)
+            vals.append(oracle.search_stats(rho, 500.0, 1 / 32, t, w, vel, np.array([[0, 0, 1.0]]),
+                                            f0, tau, n, T0, track_bins=2, **kw)[3].ravel())
+        v = np.concatenate(vals)
+        N = v.size
+        assert abs(v.mean()) < 4.0 / math.sqrt(N), kw
+        assert abs(v.var() - 1.0) < 4.0 * math.sqrt(3.0 / N), kw
+
+
 def test_pre_T0_segments_are_dropped():
     """Statistic with T0 mid-way equals the statistic of the map cut at T0."""
     p = syn.config_small(seed=11, n_seg=64, n_bin=1024, n_f0=4, n_tau=4, snr=0, weights=True)
