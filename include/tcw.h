@@ -103,8 +103,19 @@ enum {
                                   the template; default 0 (the weights as given).
                                   Applies to tcw_search, tcw_search_batched and
                                   the exhaustive part of tcw_search_triaged */
-    TCW_OPT_GEN_CHUNK = 10     /* tcw_search_generated: templates per chunk, a multiple
+    TCW_OPT_GEN_CHUNK = 10,    /* tcw_search_generated: templates per chunk, a multiple
                                   of 32 in [32, 2^24] (default 2^18) */
+    TCW_OPT_TRACK_BINS = 11    /* bins per lookup: 1 (default) = the nearest bin, as
+                                  in the paper; 2 = the two bins whose centres
+                                  bracket the track, k = floor((fhat - f_min)/df)
+                                  and k + 1, both required in the band, their
+                                  powers (or counts) summed; Eq. 4 then uses twice
+                                  the mean and variance (independent bins).  For
+                                  tracks between bins or moving more than a bin per
+                                  SFT, whose power leaks into the neighbour.
+                                  tcw_track_bins reports k.  Applies like
+                                  TCW_OPT_AMPLITUDE_POWER, and to
+                                  tcw_search_generated */
 };
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
@@ -439,6 +450,14 @@ tcw_status tcw_bank_size(const tcw_bank_spec *spec, int64_t *n_out);
  * Errors: INVALID_ARGUMENT (bad spec or range), OUT_OF_MEMORY, CUDA. */
 tcw_status tcw_generate_bank(tcw_ctx *ctx, const tcw_bank_spec *spec, int64_t first, int64_t count,
                              double *f0, double *tau, double *n, int out_flags);
+
+/* The templates of the bank at the indices idx[0 .. count) (host int64, each
+ * in [0, bank size)), e.g. the idx_out of tcw_search_generated, into f0, tau,
+ * n (float64, count entries; out_flags TCW_HOST or TCW_DEVICE).
+ * Errors: INVALID_ARGUMENT (bad spec, index outside the bank), OUT_OF_MEMORY,
+ * CUDA. */
+tcw_status tcw_generate_bank_at(tcw_ctx *ctx, const tcw_bank_spec *spec, const int64_t *idx, int64_t count,
+                                double *f0, double *tau, double *n, int out_flags);
 
 /* Search a generated bank with the loaded spectrogram, velocities and sky,
  * like tcw_search: psi_out/idx_out [n_sky][k] with idx the generated template

@@ -265,6 +265,8 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
     gp.tile_shift = tile_shift;
     gp.amp_power = c->amp_power;
     gp.nc_q = count ? std::exp(-c->rho_th) : 0.0;
+    gp.track_bins = c->track_bins;
+    gp.map_half = c->dtype == TCW_F16 ? 1 : 0;
     gp.B = (int)c->B;
     gp.Bpad = c->Bpad;
     gp.lanes = c->lanes;
@@ -280,8 +282,9 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
       ++launches;
     }
     const int wt = c->amp_power > 0 ? kAmplitudeWeights : (c->unit_weights ? kUnitWeights : kSegmentWeights);
-    // counts are staged as fp32 windows whatever the map's type
-    TCW_CUDA(c, launch_group(gp, c->grid, c->dtype == TCW_F16 && !count, record, wt, c->stream),
+    // counts and two-bin sums are staged as fp32 windows whatever the map's type
+    const bool half = c->dtype == TCW_F16 && !count && c->track_bins == 1;
+    TCW_CUDA(c, launch_group(gp, c->grid, half, record, wt, c->stream),
              "group_kernel launch");
     TCW_CUDA(c, cudaEventRecord(c->ev1, c->stream), "event");
     ++launches;
@@ -304,6 +307,7 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
     lp.amp_power = c->amp_power;
     lp.number_count = count ? 1 : 0;
     lp.rho_th = c->rho_th;
+    lp.track_bins = c->track_bins;
     lp.B = (int)c->B;
     lp.Bpad = c->Bpad;
     lp.S = (int)c->S;
@@ -521,6 +525,10 @@ tcw_status tcw_set_option(tcw_ctx* c, int option, int64_t value) {
         return fail(c, TCW_ERR_INVALID_ARGUMENT, "sky lanes must be 0, 16, 32 or 64");
       c->opt_lanes = (int)value;
       c->sky_dirty = true;
+      return TCW_OK;
+    case TCW_OPT_TRACK_BINS:
+      if (value != 1 && value != 2) return fail(c, TCW_ERR_INVALID_ARGUMENT, "track_bins must be 1 or 2");
+      c->track_bins = (int)value;
       return TCW_OK;
     case TCW_OPT_GEN_CHUNK:
       if (value < 32 || value > ((int64_t)1 << 24) || value % kBankAlign)
@@ -825,6 +833,35 @@ tcw_status tcw_generate_bank(tcw_ctx* c, const tcw_bank_spec* spec, int64_t firs
              "copy out");
     TCW_CUDA(c, cudaStreamSynchronize(c->stream), "bank generation");
   }
+  return TCW_OK;
+}
+
+tcw_status tcw_generate_bank_at(tcw_ctx* c, const tcw_bank_spec* spec, const int64_t* idx, int64_t count,
+                                double* f0, double* tau, double* n, int out_flags) {
+  if (!c) return TCW_ERR_INVALID_ARGUMENT;
+  int64_t N = 0;
+  tcw_status st = check_spec(c, spec, &N);
+  if (st != TCW_OK) return st;
+  if (count < 0 || (count > 0 && (!idx || !f0 || !tau || !n))) return fail(c, TCW_ERR_INVALID_ARGUMENT, "null pointer");
+  if (out_flags != TCW_HOST && out_flags != TCW_DEVICE) return fail(c, TCW_ERR_INVALID_ARGUMENT, "bad flags");
+  for (int64_t i = 0; i < count; ++i)
+    if (idx[i] < 0 || idx[i] >= N) return fail(c, TCW_ERR_INVALID_ARGUMENT, "index outside the bank");
+  if (count == 0) return TCW_OK;
+  cudaSetDevice(c->device);
+  const size_t b8 = (size_t)count * sizeof(double);
+  TCW_CUDA(c, c->stage_i.ensure((size_t)count * sizeof(int64_t)), "staging");
+  TCW_CUDA(c, c->stage_f.ensure(3 * b8), "staging");
+  double* d = reinterpret_cast<double*>(c->stage_f.p);
+  TCW_CUDA(c, cudaMemcpyAsync(c->stage_i.p, idx, (size_t)count * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream),
+           "index upload");
+  TCW_CUDA(c, launch_gen_bank_at(gen_params(spec), c->stage_i.as<int64_t>(), count, d, d + count, d + 2 * count,
+                                 c->stream),
+           "gen_bank_kernel launch");
+  const cudaMemcpyKind kind = out_flags == TCW_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  TCW_CUDA(c, cudaMemcpyAsync(f0, d, b8, kind, c->stream), "copy out");
+  TCW_CUDA(c, cudaMemcpyAsync(tau, d + count, b8, kind, c->stream), "copy out");
+  TCW_CUDA(c, cudaMemcpyAsync(n, d + 2 * count, b8, kind, c->stream), "copy out");
+  TCW_CUDA(c, cudaStreamSynchronize(c->stream), "bank generation");
   return TCW_OK;
 }
 

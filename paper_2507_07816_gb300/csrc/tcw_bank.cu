@@ -38,13 +38,15 @@ __device__ __forceinline__ double lattice_axis(double lo, double hi, int64_t m, 
   return fma(hi - lo, __ddiv_rn((double)i, (double)(m - 1)), lo);
 }
 
-// Templates first .. first + count - 1 into out[0 .. count); out[count .. pad_to)
-// repeat the last one.  perm (optional) gets the local index of each slot.
-__global__ void gen_bank_kernel(BankGenParams p, int64_t first, int64_t count, int64_t pad_to, double* f0,
-                                double* tau, double* nbr, int32_t* perm) {
+// Templates first .. first + count - 1 (or at[0 .. count) when at is given)
+// into out[0 .. count); out[count .. pad_to) repeat the last one.  perm
+// (optional) gets the local index of each slot.
+__global__ void gen_bank_kernel(BankGenParams p, int64_t first, const int64_t* at, int64_t count, int64_t pad_to,
+                                double* f0, double* tau, double* nbr, int32_t* perm) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < pad_to; i += stride) {
-    const int64_t t = first + (i < count ? i : count - 1);
+    const int64_t li = i < count ? i : count - 1;
+    const int64_t t = at ? at[li] : first + li;
     double v[3];
     if (p.kind == TCW_BANK_LATTICE) {
       const int64_t idx[3] = {t % p.n_f0, (t / p.n_f0) % p.n_tau, t / (p.n_f0 * p.n_tau)};
@@ -106,7 +108,16 @@ cudaError_t launch_gen_bank(const BankGenParams& p, int64_t first, int64_t count
   if (pad_to <= 0 || count <= 0) return cudaSuccess;
   const int threads = 256;
   const int64_t blocks = std::min<int64_t>((pad_to + threads - 1) / threads, 152LL * 64);
-  gen_bank_kernel<<<(unsigned)blocks, threads, 0, st>>>(p, first, count, pad_to, f0, tau, nbr, perm);
+  gen_bank_kernel<<<(unsigned)blocks, threads, 0, st>>>(p, first, nullptr, count, pad_to, f0, tau, nbr, perm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gen_bank_at(const BankGenParams& p, const int64_t* at, int64_t count, double* f0, double* tau,
+                               double* nbr, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  const int threads = 256;
+  const int64_t blocks = std::min<int64_t>((count + threads - 1) / threads, 152LL * 64);
+  gen_bank_kernel<<<(unsigned)blocks, threads, 0, st>>>(p, 0, at, count, count, f0, tau, nbr, nullptr);
   return cudaGetLastError();
 }
 

@@ -80,6 +80,7 @@ struct BatchState {
   int64_t graph_mem = 0;           // wave budget the graph was recorded with
   int graph_amp = 0;               // amplitude power the graph was recorded with
   double graph_nc = 0;             // number-count q the graph was recorded with (0 = power)
+  int graph_bins = 1;              // bins per lookup the graph was recorded with
   // last search
   bool have_result = false;
   int last_k = 0;
@@ -231,9 +232,9 @@ EventDesc make_desc(const tcw_ctx* c, BatchState* b, const EventHost& e, int til
 // q of the number count (0 for the power statistic).
 double count_q(const tcw_ctx* c) { return c->statistic == TCW_STAT_NUMBER_COUNT ? std::exp(-c->rho_th) : 0.0; }
 
-// Counts are staged as fp32 windows whatever the map's type.
+// Counts and two-bin sums are staged as fp32 windows whatever the map's type.
 bool half_windows(const tcw_ctx* c, const BatchState* b) {
-  return b->dtype == TCW_F16 && c->statistic != TCW_STAT_NUMBER_COUNT;
+  return b->dtype == TCW_F16 && c->statistic != TCW_STAT_NUMBER_COUNT && c->track_bins == 1;
 }
 
 // Number-count bit maps of every event for the current threshold.
@@ -299,6 +300,8 @@ GroupParams base_params(const tcw_ctx* c, BatchState* b, int tile, int nterms) {
   gp.tile_shift = ilog2(tile);
   gp.amp_power = c->amp_power;
   gp.nc_q = count_q(c);
+  gp.track_bins = c->track_bins;
+  gp.map_half = b->dtype == TCW_F16 ? 1 : 0;
   gp.B = (int)c->B;
   gp.Bpad = c->Bpad;
   gp.lanes = b->lanes;
@@ -514,6 +517,7 @@ tcw_status capture(tcw_ctx* c, BatchState* b, int k) {
   b->graph_mem = c->batch_memory;
   b->graph_amp = c->amp_power;
   b->graph_nc = count_q(c);
+  b->graph_bins = c->track_bins;
   b->graph_nodes = nodes;
   return TCW_OK;
 }
@@ -728,7 +732,7 @@ tcw_status tcw_search_batched(tcw_ctx* c, int k, float* psi_out, int64_t* idx_ou
     drop_graph(b);
   }
   if (!b->exec || b->graph_k != k || b->graph_mem != c->batch_memory || b->graph_amp != c->amp_power ||
-      b->graph_nc != count_q(c)) {
+      b->graph_nc != count_q(c) || b->graph_bins != c->track_bins) {
     if ((st = capture(c, b, k)) != TCW_OK) return st;
   }
   TCW_CUDA(c, cudaEventRecord(c->ev0, c->stream), "event");

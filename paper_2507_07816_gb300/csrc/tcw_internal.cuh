@@ -113,6 +113,9 @@ struct GroupParams {
   int amp_power;           // weights times (f(t_j)/f0)^amp_power (Eq. 3); 0 = none
   double nc_q;             // number count: q = exp(-rho_th), <s> = q W1, sigma^2 = q(1-q) W2;
                            // 0 = power (<s> = W1, sigma^2 = W2).  Needs every event's bits.
+  int track_bins;          // 2: each lookup sums the bins floor(x), floor(x) + 1 (staged as fp32
+                           // pair sums; <s> and sigma^2 doubled); otherwise the nearest bin
+  int map_half;            // the events' maps are fp16 (read by the two-bin producers)
   int B, Bpad;
   int lanes;               // sky groups per chunk: 16, 32 or 64
   float2* dev;             // scratch [gridDim.x][8192]: per-sky weight sums at band edges
@@ -150,6 +153,7 @@ struct LookupParams {
   int amp_power;           // weights times (f(t_j)/f0)^amp_power (Eq. 3); 0 = none
   int number_count;        // 1: nu = [rho > rho_th] in place of rho, Psi with q = exp(-rho_th)
   double rho_th;
+  int track_bins;          // 2: the bins floor(x), floor(x) + 1 per lookup; otherwise the nearest
   int B, Bpad, S, Spad;
   float* psi;
   float* S_out;
@@ -293,6 +297,9 @@ struct BankGenParams {
 };
 cudaError_t launch_gen_bank(const BankGenParams& p, int64_t first, int64_t count, int64_t pad_to, double* f0,
                             double* tau, double* nbr, int32_t* perm, cudaStream_t st);
+// Templates at the indices at[0 .. count) (device, each inside the bank).
+cudaError_t launch_gen_bank_at(const BankGenParams& p, const int64_t* at, int64_t count, double* f0, double* tau,
+                               double* nbr, cudaStream_t st);
 // Per sky: the first k of the merge of a (ra entries) and b (rb entries, local
 // indices + b_base) by (Psi desc, index asc) into o; rows of a and o hold k.
 cudaError_t launch_merge_topk(const float* a_psi, const int64_t* a_idx, int ra, const float* b_psi,

@@ -169,13 +169,17 @@ __device__ __forceinline__ void compute_entry(const GroupParams& p, const EventD
     set_none<RhoT>(e, win_dst, p.n_det);
     return;
   }
-  e.cls = (base + kMLo >= 0 && (int64_t)base + kMHi <= p.n_bin - 1) ? kEntryInside : kEntryEdge;
+  // nearest bin: the decision boundaries are the bin edges c_K = f_min + (K + 1/2) df;
+  // two-bin lookups (floor(x), floor(x) + 1): the bin centres f_min + (K + 1) df
+  const bool two = p.track_bins == 2;
+  const int top = kMHi + (two ? 1 : 0);   // highest bin the candidates read
+  e.cls = (base + kMLo >= 0 && (int64_t)base + top <= p.n_bin - 1) ? kEntryInside : kEntryEdge;
   e.F = f * inv_df_f;
-  e.Cm = (x - (float)base) - 0.5f;
+  e.Cm = (x - (float)base) - (two ? 1.0f : 0.5f);
   e.kb = base - kMagicBits;
   e.tha = smem_addr(&e.th[0]) - 4u * (uint32_t)(kMagicBits + kMLo);
   const double Q = p.df * h;
-  const double A0 = fma((double)(base + kMLo) + 0.5, Q, fma(p.f_min, h, -1.0));
+  const double A0 = fma((double)(base + kMLo) + (two ? 1.0 : 0.5), Q, fma(p.f_min, h, -1.0));
   const double sc = p.inv_q * 256.0;
   const long long a = __double2ll_rn(A0 * sc), st = __double2ll_rn(Q * sc);
 #pragma unroll
@@ -185,23 +189,44 @@ __device__ __forceinline__ void compute_entry(const GroupParams& p, const EventD
     e.th[i] = (int)v;
   }
   if constexpr (sizeof(RhoT) == 4) {
-    if (ev.bits) {
-      // number count: the window holds nu = [rho > rho_th] of bins base + kMLo
-      // .. base + kMLo + 15 as fp32 0/1, unpacked from the bit map (0 outside
-      // the band), so the consumers run unchanged
+    if (ev.bits || two) {
+      // windows built by the producer as fp32 values of bins base + kMLo + i,
+      // i < 16 (0 outside the band), so the consumers run unchanged:
+      //   number count  nu = [rho > rho_th], unpacked from the bit map
+      //   two-bin       the pair sum v_i + v_{i+1} of powers (or counts)
       const int g0 = base + kMLo;
-      const int wi = g0 >> 5, sh = g0 & 31;   // floor division: g0 may be negative at the low edge
       for (int d = 0; d < p.n_det; ++d) {
-        const uint32_t* row = ev.bits + ((int64_t)d * ev.n_seg + j) * ev.bit_pitch;
-        const uint32_t lo = (unsigned)wi < (unsigned)ev.bit_pitch ? __ldg(row + wi) : 0u;
-        const uint32_t hi = (unsigned)(wi + 1) < (unsigned)ev.bit_pitch ? __ldg(row + wi + 1) : 0u;
-        const uint32_t m = __funnelshift_r(lo, hi, sh);
+        const int64_t rw = (int64_t)d * ev.n_seg + j;
+        float v[kWinBytes / 4 + 1];
+        if (ev.bits) {
+          const int wi = g0 >> 5, sh = g0 & 31;   // floor division: g0 may be negative at the low edge
+          const uint32_t* row = ev.bits + rw * ev.bit_pitch;
+          const uint32_t lo = (unsigned)wi < (unsigned)ev.bit_pitch ? __ldg(row + wi) : 0u;
+          const uint32_t hi = (unsigned)(wi + 1) < (unsigned)ev.bit_pitch ? __ldg(row + wi + 1) : 0u;
+          const uint32_t m = __funnelshift_r(lo, hi, sh);
+#pragma unroll
+          for (int i = 0; i <= kWinBytes / 4; ++i) v[i] = (float)((m >> i) & 1u);
+        } else {
+#pragma unroll
+          for (int i = 0; i <= kWinBytes / 4; ++i) {
+            const int64_t k = (int64_t)g0 + i;
+            const bool in = k >= 0 && k < p.n_bin && i <= kNThr + 1;   // the pair sums read bins <= kNThr + 1
+            v[i] = 0.f;
+            if (in) {
+              const int64_t o = rw * p.pitch + k;
+              v[i] = p.map_half ? __half2float(__ldg(static_cast<const __half*>(ev.rho) + o))
+                                : __ldg(static_cast<const float*>(ev.rho) + o);
+            }
+          }
+        }
+        if (two) {
+#pragma unroll
+          for (int i = 0; i < kWinBytes / 4; ++i) v[i] += v[i + 1];
+        }
         const uint32_t dst = win_dst + d * kWinBytes;
         e.wa[d] = dst - 4u * (uint32_t)(kMagicBits + kMLo);
 #pragma unroll
-        for (int c = 0; c < kWinBytes / 16; ++c)
-          sts_f4(dst + 16 * c, (float)((m >> (4 * c)) & 1u), (float)((m >> (4 * c + 1)) & 1u),
-                 (float)((m >> (4 * c + 2)) & 1u), (float)((m >> (4 * c + 3)) & 1u));
+        for (int c = 0; c < kWinBytes / 16; ++c) sts_f4(dst + 16 * c, v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
       }
       return;
     }
@@ -452,8 +477,10 @@ __global__ void __launch_bounds__(Geo<LN>::kThreads, 1) group_kernel(GroupParams
                     }
                   continue;
                 }
-                const bool vlo = (unsigned)K0 < (unsigned)p.n_bin;
-                const bool vhi = (unsigned)(K0 + 1) < (unsigned)p.n_bin;
+                // a lookup is valid when every bin it reads lies in the band
+                const int tb1 = p.track_bins == 2 ? 1 : 0;
+                const bool vlo = K0 >= 0 && (int64_t)K0 + tb1 < p.n_bin;
+                const bool vhi = K0 + 1 >= 0 && (int64_t)K0 + 1 + tb1 < p.n_bin;
                 const uint32_t a = wdt + ESZ * (uint32_t)zb;
                 const float rlo = vlo ? lds_pow(a, RhoT()) : 0.f;
                 const float rhi = vhi ? lds_pow(a + ESZ, RhoT()) : 0.f;
@@ -502,8 +529,10 @@ __global__ void __launch_bounds__(Geo<LN>::kThreads, 1) group_kernel(GroupParams
       }
       if (!ok || !gval) continue;
       // Eq. 4: <s> = mq W1, sigma^2 = vq W2 (power: 1, 1; number count: q, q(1-q))
-      const double mq = p.nc_q > 0.0 ? p.nc_q : 1.0;
-      const float vq = p.nc_q > 0.0 ? (float)(p.nc_q * (1.0 - p.nc_q)) : 1.0f;
+      // and both doubled for two-bin lookups (two independent bins)
+      const double nbins = p.track_bins == 2 ? 2.0 : 1.0;
+      const double mq = nbins * (p.nc_q > 0.0 ? p.nc_q : 1.0);
+      const float vq = (float)(nbins * (p.nc_q > 0.0 ? p.nc_q * (1.0 - p.nc_q) : 1.0));
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
         const int b = b0 + 2 * u + t;
@@ -694,7 +723,8 @@ cudaError_t group_prepare(int n_det, int lanes, bool half, int weighting) {
 cudaError_t launch_group(const GroupParams& p, int grid, bool half, bool record, int weighting,
                          cudaStream_t st) {
   if (p.n_det < 1 || p.n_det > kMaxStageDet) return cudaErrorInvalidValue;
-  if (p.nc_q > 0.0 && half) return cudaErrorInvalidValue;   // counts are staged as fp32 windows
+  // counts and pair sums are staged as fp32 windows
+  if ((p.nc_q > 0.0 || p.track_bins == 2) && half) return cudaErrorInvalidValue;
   if (p.amp_power > 0 && weighting != kAmplitudeWeights && !record) return cudaErrorInvalidValue;
   if (grid <= 0) return cudaSuccess;
   return half ? launch_group_r<__half>(p, record, weighting, grid, st)

@@ -89,25 +89,31 @@ __global__ void lookup_kernel(LookupParams p) {
         for (int e = 0; e < p.amp_power; ++e) amp *= f / f0;   // (f/f0)^p, Eq. 3
         const double* v = p.vel + dj * 3;
         const double fh = f * (1.0 + (v[0] * n[0] + v[1] * n[1] + v[2] * n[2]) / kLightSpeed);
-        const double kk = floor((fh - p.f_min) / p.df + 0.5);
-        if (kk >= 0.0 && kk < (double)p.n_bin) k = (int64_t)kk;
+        // nearest bin, or the lower bin of the two-bin pair (both in band)
+        const int tb1 = p.track_bins == 2 ? 1 : 0;
+        const double kk = floor((fh - p.f_min) / p.df + (tb1 ? 0.0 : 0.5));
+        if (kk >= 0.0 && kk + tb1 < (double)p.n_bin) k = (int64_t)kk;
       }
       if (rec)
         p.rec[(((int64_t)p.sky_perm[s] * p.B + p.bank_perm[b]) * p.n_det + d) * p.n_seg + j] =
             (int32_t)k;
       if (k < 0) continue;
       const double w = (double)p.weights[dj] * amp;
-      double r = (double)load_rho(rho + dj * p.n_bin, k);
-      if (p.number_count) r = r > p.rho_th ? 1.0 : 0.0;
+      double r = 0.0;
+      for (int64_t kb = k; kb <= k + (p.track_bins == 2 ? 1 : 0); ++kb) {
+        const double rb = (double)load_rho(rho + dj * p.n_bin, kb);
+        r += p.number_count ? (rb > p.rho_th ? 1.0 : 0.0) : rb;
+      }
       S += w * r;
       W1 += w;
       W2 += w * w;
     }
   }
   const int64_t o = (int64_t)s * p.Bpad + b;
-  const double q = p.number_count ? exp(-p.rho_th) : 1.0;        // <s> = q W1
-  const double var = p.number_count ? q * (1.0 - q) : 1.0;        // sigma^2 = var W2
-  p.psi[o] = W2 > 0.0 ? (float)((S - q * W1) / sqrt(var * W2)) : -INFINITY;
+  const double nb = p.track_bins == 2 ? 2.0 : 1.0;               // bins summed per lookup
+  const double q = p.number_count ? exp(-p.rho_th) : 1.0;        // <s> = nb q W1
+  const double var = p.number_count ? q * (1.0 - q) : 1.0;        // sigma^2 = nb var W2
+  p.psi[o] = W2 > 0.0 ? (float)((S - nb * q * W1) / sqrt(nb * var * W2)) : -INFINITY;
   if (p.S_out) {
     p.S_out[o] = (float)S;
     p.W1_out[o] = (float)W1;

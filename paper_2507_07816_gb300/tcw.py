@@ -22,7 +22,7 @@ F32, F16 = 0, 1
 KERNEL_AUTO, KERNEL_GROUP, KERNEL_LOOKUP = 0, 1, 2
 OPT_KERNEL, OPT_KEEP_STATS, OPT_TILE_SEGMENTS, OPT_BANK_CHUNK = 1, 2, 3, 4
 OPT_AUTOTUNE, OPT_BATCH_MEMORY, OPT_SKY_LANES, OPT_TRIAGE_SPREAD = 5, 6, 7, 8
-OPT_AMPLITUDE_POWER, OPT_GEN_CHUNK = 9, 10
+OPT_AMPLITUDE_POWER, OPT_GEN_CHUNK, OPT_TRACK_BINS = 9, 10, 11
 STAT_POWER, STAT_NUMBER_COUNT = 0, 1
 
 _lock = threading.Lock()
@@ -141,6 +141,7 @@ def load_library(build_if_missing: bool = True):
             "tcw_bank_size": [ctypes.POINTER(_BankSpec), ctypes.POINTER(i64)],
             "tcw_generate_bank": [p, ctypes.POINTER(_BankSpec), i64, i64, p, p, p, i],
             "tcw_search_generated": [p, ctypes.POINTER(_BankSpec), d, i, p, p, i],
+            "tcw_generate_bank_at": [p, ctypes.POINTER(_BankSpec), p, i64, p, p, p, i],
             "tcw_get_generated_info": [p, ctypes.POINTER(_GenInfo)],
             "tcw_probe_read_bandwidth": [i64, i, i, ctypes.POINTER(d)],
         }
@@ -451,6 +452,16 @@ class Search:
             raise ValueError("outputs must all be host or all device")
         self._check(self._lib.tcw_generate_bank(self._h, ctypes.byref(spec), int(first), int(count), *ptrs,
                                                 flags.pop()))
+        return out
+
+    def generate_bank_at(self, spec, idx):
+        """Templates of `spec` at the int64 indices `idx` (any shape): (f0, tau, n)
+        float64 arrays of that shape."""
+        ix = np.ascontiguousarray(np.asarray(idx, np.int64))
+        out = tuple(np.empty(ix.shape, np.float64) for _ in range(3))
+        self._check(self._lib.tcw_generate_bank_at(self._h, ctypes.byref(spec), ix.ctypes.data_as(ctypes.c_void_p),
+                                                   ix.size, *(o.ctypes.data_as(ctypes.c_void_p) for o in out),
+                                                   HOST))
         return out
 
     def search_generated(self, spec, T0, k, psi_out=None, idx_out=None):

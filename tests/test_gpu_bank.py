@@ -48,6 +48,11 @@ def test_generated_templates_bit_exact(kind, kw, first, count):
                                 okw["n_n"], okw["seed"])
     for g, r in zip(got, ref):
         np.testing.assert_array_equal(g, r)
+    # by index, in any order
+    perm = np.random.default_rng(1).permutation(count)[:500] + first
+    at = s.generate_bank_at(sp, perm)
+    for g, r in zip(at, ref):
+        np.testing.assert_array_equal(g, r[perm - first])
     # into device memory
     import torch
     dev = tuple(torch.empty(count, dtype=torch.float64, device="cuda:0") for _ in range(3))
@@ -72,6 +77,8 @@ def test_invalid_specs_and_ranges():
     sp = tcw.bank_spec(tcw.BANK_RANDOM, LO, HI, n_tmpl=100)
     with pytest.raises(tcw.TcwError):
         s.generate_bank(sp, 50, 51)
+    with pytest.raises(tcw.TcwError):
+        s.generate_bank_at(sp, [0, 100])
     with pytest.raises(tcw.TcwError):
         s.set_option(tcw.OPT_GEN_CHUNK, 100)      # not a multiple of 32
     s.close()
