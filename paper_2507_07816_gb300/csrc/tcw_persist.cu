@@ -397,7 +397,6 @@ __global__ void __launch_bounds__(Geo<LN>::kThreads, 1) group_kernel(GroupParams
           const int4 wa0 = lds_v4(e0 + 16), wa1 = lds_v4(e1 + 16);
           const int c0 = __float_as_int(h0.w), c1 = __float_as_int(h1.w);
           const float4 wseg = lds_f4(sbase + (uint32_t)L.hdr + (uint32_t)(kseg * 16));
-#pragma unroll
           const float am0 = WT == kAmplitudeWeights ? __int_as_float(wa0.z) : 1.0f;
           const float am1 = WT == kAmplitudeWeights ? __int_as_float(wa1.z) : 1.0f;
           static_assert(kAmpSlot == 2, "wa[kAmpSlot] is the .z word of the entry's second vector");
