@@ -128,6 +128,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def kernel_source_digest():
+    """First 16 hex digits of the sha256 of the group kernel's sources
+    (tcw_persist.cuh followed by tcw_ptx.cuh)."""
+    h = hashlib.sha256()
+    for f in ("tcw_persist.cuh", "tcw_ptx.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2507_07816_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def read_profile_value(name, key):
     """A figure from a committed ncu summary, if it was taken on the current kernel source."""
     path = os.path.join(ROOT, "profiles", name)
@@ -138,8 +147,7 @@ def read_profile_value(name, key):
         if ":" in line and not line.startswith(" "):
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip()
-    src = os.path.join(ROOT, "paper_2507_07816_gb300", "csrc", "tcw_persist.cu")
-    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    digest = kernel_source_digest()
     if vals.get("kernel_source_sha256_16") != digest:
         return None
     try:
@@ -441,6 +449,44 @@ def bench_ours(args):
                 extras[name] = {"error": f"{type(exc).__name__}: {exc}"}
             finally:
                 off()
+
+        # the same data searched with a device-generated uniform random bank of the
+        # same size and box (streamed in 2^18-template chunks, running top-k), and
+        # the generation rate of a 1e8-template range written to device memory
+        try:
+            f_hi = p.f_min + p.rho.shape[2] * p.df
+            gspec = tcw.bank_spec(tcw.BANK_RANDOM, (p.f_min, 3500.0, 3.0), (f_hi, 35000.0, 7.0),
+                                  n_tmpl=len(p.bank), seed=20250712)
+            s.search_generated(gspec, p.T0, k, psi_out, idx_out)          # warm-up
+            torch.cuda.synchronize()
+            g_ms = []
+            for _ in range(max(1, min(2, args.steps))):
+                s.search_generated(gspec, p.T0, k, psi_out, idx_out)
+                g_ms.append(s.generated_info()["total_ms"])
+            gi = s.generated_info()
+            n_gen = 10**8
+            bufs = tuple(torch.empty(n_gen, dtype=torch.float64, device=f"cuda:{dev}") for _ in range(3))
+            big = tcw.bank_spec(tcw.BANK_RANDOM, (500.0, 3500.0, 3.0), (3000.0, 35000.0, 7.0), n_tmpl=10**9,
+                                seed=1)
+            s.generate_bank(big, 0, n_gen, out=bufs)
+            torch.cuda.synchronize()
+            t_g = time.perf_counter()
+            s.generate_bank(big, 10**9 - n_gen, n_gen, out=bufs)
+            torch.cuda.synchronize()
+            gen_rate = n_gen / (time.perf_counter() - t_g)
+            del bufs
+            gms = statistics.mean(g_ms)
+            extras["generated"] = {"value": U / (gms / 1000.0), "unit": UNIT, "ms_per_step": gms,
+                                   "search_ms": gi["search_ms"], "chunks": gi["chunks"],
+                                   "chunk_templates": gi["chunk_templates"], "vs_plain": (U / (gms / 1000.0)) / value,
+                                   "bank": "uniform random (Philox), same size and box as the plain bank",
+                                   "generate_templates_per_s": gen_rate,
+                                   "generate_sample": f"{n_gen} templates (f0, tau, n) of a 1e9-template bank, "
+                                                      f"written to device memory, host-timed"}
+        except Exception as exc:
+            extras["generated"] = {"error": f"{type(exc).__name__}: {exc}"}
+        s.define_bank(p.bank.f0, p.bank.tau, p.bank.n, p.T0)      # the plain bank again
+        torch.cuda.empty_cache()
 
         variant("amplitude", lambda: s.set_option(tcw.OPT_AMPLITUDE_POWER, 4),
                 lambda: s.set_option(tcw.OPT_AMPLITUDE_POWER, 0), {"amp_power": 4})

@@ -16,8 +16,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libtcw.so")
-SOURCES = ["tcw_api.cu", "tcw_batched.cu", "tcw_search.cu", "tcw_persist.cu", "tcw_topk.cu", "tcw_triage.cu",
-           "tcw_noalloc.cu", "tcw_probe.cu", "tcw_bank.cu"]
+SOURCES = ["tcw_persist_f32.cu", "tcw_persist_f16.cu", "tcw_persist_pw.cu", "tcw_api.cu", "tcw_batched.cu",
+           "tcw_search.cu", "tcw_persist.cu", "tcw_topk.cu", "tcw_triage.cu", "tcw_noalloc.cu", "tcw_probe.cu",
+           "tcw_bank.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]

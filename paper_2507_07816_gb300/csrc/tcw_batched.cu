@@ -465,7 +465,8 @@ tcw_status capture(tcw_ctx* c, BatchState* b, int k) {
   if ((st = upload_items(c, b, b->bank_chunk, INT32_MAX, &sums)) != TCW_OK) return st;
   TCW_CUDA(c, b->out_psi.ensure((size_t)b->total_sky * k * sizeof(float)), "output");
   TCW_CUDA(c, b->out_idx.ensure((size_t)b->total_sky * k * sizeof(int64_t)), "output");
-  TCW_CUDA(c, group_prepare(b->D, b->lanes, half_windows(c, b), weighting(c, b)), "group_kernel attributes");
+  TCW_CUDA(c, group_prepare(b->D, b->lanes, half_windows(c, b), weighting(c, b),
+                            c->statistic == TCW_STAT_NUMBER_COUNT || c->track_bins == 2), "group_kernel attributes");
   TCW_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "graph capture");
   cudaError_t err = cudaMemsetAsync(b->flags.p, 0, 64, c->stream);
   int nodes = 0;

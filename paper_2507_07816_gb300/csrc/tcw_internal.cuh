@@ -283,7 +283,8 @@ cudaError_t launch_doppler(const DopplerParams& p, cudaStream_t st);
 // Weighting of the group kernel's lookups: unit weights, the per-segment
 // weights, or the weights times the template's amplitude weight.
 enum Weighting { kUnitWeights = 0, kSegmentWeights = 1, kAmplitudeWeights = 2 };
-cudaError_t group_prepare(int n_det, int lanes, bool half, int weighting);
+// pw: windows built by the producer (number count or two-bin lookups; fp32 only).
+cudaError_t group_prepare(int n_det, int lanes, bool half, int weighting, bool pw);
 // grid = number of CTAs (the length of p.cta_items minus one); one CTA per SM at most
 cudaError_t launch_group(const GroupParams& p, int grid, bool half, bool record, int weighting,
                          cudaStream_t st);

@@ -1,0 +1,12 @@
+// tcw_persist_pw.cu -- group-kernel variants for fp32 windows built by the producer (number count, two-bin lookups).
+#include "tcw_persist.cuh"
+
+namespace tcw {
+
+cudaError_t launch_group_pw(const GroupParams& p, bool record, int wt, int grid, cudaStream_t st) {
+  return launch_group_r<float, true>(p, record, wt, grid, st);
+}
+
+cudaError_t prepare_group_pw(int n_det, int lanes, int wt) { return prepare_r<float, true>(n_det, lanes, wt); }
+
+}  // namespace tcw
