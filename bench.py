@@ -285,7 +285,7 @@ def bench_learned(args, dev):
 
     make(0)
     r = TR.evaluate(mlp, make, args.learned_events, bank, frac=float(meta["frac"]),
-                    patch_size=int(meta["patch_size"]), k=TOPK)
+                    patch_size=int(meta["patch_size"]), k=TOPK, templates_permille=TR.TEMPLATES_PERMILLE)
     r["value"] = r["sums_full"] / r["time_triaged_s"]
     r["unit"] = UNIT
     r["plain_value"] = r["sums_full"] / r["time_full_s"]

@@ -105,7 +105,7 @@ enum {
                                   the exhaustive part of tcw_search_triaged */
     TCW_OPT_GEN_CHUNK = 10,    /* tcw_search_generated: templates per chunk, a multiple
                                   of 32 in [32, 2^24] (default 2^18) */
-    TCW_OPT_TRACK_BINS = 11    /* bins per lookup: 1 (default) = the nearest bin, as
+    TCW_OPT_TRACK_BINS = 11,   /* bins per lookup: 1 (default) = the nearest bin, as
                                   in the paper; 2 = the two bins whose centres
                                   bracket the track, k = floor((fhat - f_min)/df)
                                   and k + 1, both required in the band, their
@@ -116,6 +116,12 @@ enum {
                                   tcw_track_bins reports k.  Applies like
                                   TCW_OPT_AMPLITUDE_POWER, and to
                                   tcw_search_generated */
+    TCW_OPT_TRIAGE_TEMPLATES = 12 /* triaged search: parameter regions too.  Per
+                                  mille of the bank searched at each chosen patch:
+                                  the templates with the highest coarse Psi at that
+                                  patch's representative sky; the union over the
+                                  chosen patches is searched at all their skies.
+                                  In [1, 1000], default 1000 (every template) */
 };
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
@@ -396,6 +402,7 @@ typedef struct {
     int64_t lookups_coarse;     /* sums of the coarse pass */
     int64_t lookups_searched;   /* sums of the exhaustive search of the selected skies */
     float coarse_ms, mlp_ms, search_ms;  /* device times */
+    int64_t templates_searched; /* templates of the exhaustive part (TCW_OPT_TRIAGE_TEMPLATES) */
 } tcw_triage_info;
 
 tcw_status tcw_get_triage_info(tcw_ctx *ctx, tcw_triage_info *info);

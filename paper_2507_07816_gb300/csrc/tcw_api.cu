@@ -91,7 +91,7 @@ tcw_status prepare_sky(tcw_ctx* c) {
   std::vector<int32_t> perm(S);
   std::iota(perm.begin(), perm.end(), 0);
   std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
-  c->lanes = c->opt_lanes ? c->opt_lanes : choose_lanes(S);
+  c->lanes = c->opt_lanes ? c->opt_lanes : choose_lanes(S, c->have_bank ? c->B : 0, c->bank_chunk, c->grid);
   c->NG = (int)((S + kGroupSkies - 1) / kGroupSkies);
   c->Spad = padded_skies(S, c->lanes);
   c->NGpad = c->Spad / kGroupSkies;
@@ -131,6 +131,9 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
   if (!c->have_vel) return fail(c, TCW_ERR_STATE, "no velocities loaded");
   if (!c->have_bank) return fail(c, TCW_ERR_STATE, "no template bank defined");
   if (!c->have_sky) return fail(c, TCW_ERR_STATE, "no sky defined");
+  if (c->grid == 0) TCW_CUDA(c, group_grid(&c->grid), "device query");
+  // the chunk width depends on the bank size too (enough work items for every SM)
+  if (!c->opt_lanes && choose_lanes(c->S, c->B, c->bank_chunk, c->grid) != c->lanes) c->sky_dirty = true;
   tcw_status st = prepare_sky(c);
   if (st != TCW_OK) return st;
   Plan pl = make_plan(c);
@@ -350,6 +353,48 @@ tcw_status finish(tcw_ctx* c) {
   return TCW_OK;
 }
 
+// Sets the defined bank aside (device buffers, permutation, bounds) so that a
+// temporary bank can be defined, and puts it back on restore() or destruction.
+struct BankSwap {
+  tcw_ctx* c;
+  DevBuf f0, tau, nbr, perm, pos;
+  std::vector<int32_t> h_perm;
+  int64_t B;
+  int Bpad;
+  double T0, f0max, tau_min, r_max;
+  bool done = false;
+  explicit BankSwap(tcw_ctx* ctx) : c(ctx), B(ctx->B), Bpad(ctx->Bpad), T0(ctx->T0),
+                                     f0max(ctx->bank_f0max), tau_min(ctx->bank_tau_min), r_max(ctx->bank_r_max) {
+    std::swap(f0, c->f0);
+    std::swap(tau, c->tau);
+    std::swap(nbr, c->nbr);
+    std::swap(perm, c->bank_perm);
+    std::swap(pos, c->bank_pos);
+    h_perm.swap(c->h_bank_perm);
+  }
+  void restore() {
+    if (done) return;
+    done = true;
+    cudaStreamSynchronize(c->stream);
+    std::swap(f0, c->f0);
+    std::swap(tau, c->tau);
+    std::swap(nbr, c->nbr);
+    std::swap(perm, c->bank_perm);
+    std::swap(pos, c->bank_pos);
+    h_perm.swap(c->h_bank_perm);
+    for (DevBuf* b : {&f0, &tau, &nbr, &perm, &pos}) b->release();   // the temporary bank's buffers
+    c->B = B;
+    c->Bpad = Bpad;
+    c->T0 = T0;
+    c->bank_f0max = f0max;
+    c->bank_tau_min = tau_min;
+    c->bank_r_max = r_max;
+    c->have_bank = true;
+    ++c->bank_epoch;
+  }
+  ~BankSwap() { restore(); }
+};
+
 // Coarse pass of the triage on the loaded search: features in c->tri_feat
 // ([P][128]) and, when keep_psi, Psi in c->tri_psi ([P][Bpad], sorted bank).
 tcw_status run_coarse(tcw_ctx* c, int patch_size, float lo, float hi, bool keep_psi, int* P_out) {
@@ -525,6 +570,10 @@ tcw_status tcw_set_option(tcw_ctx* c, int option, int64_t value) {
         return fail(c, TCW_ERR_INVALID_ARGUMENT, "sky lanes must be 0, 16, 32 or 64");
       c->opt_lanes = (int)value;
       c->sky_dirty = true;
+      return TCW_OK;
+    case TCW_OPT_TRIAGE_TEMPLATES:
+      if (value < 1 || value > 1000) return fail(c, TCW_ERR_INVALID_ARGUMENT, "triage templates must be in [1, 1000]");
+      c->triage_templates = (int)value;
       return TCW_OK;
     case TCW_OPT_TRACK_BINS:
       if (value != 1 && value != 2) return fail(c, TCW_ERR_INVALID_ARGUMENT, "track_bins must be 1 or 2");
@@ -1080,8 +1129,9 @@ tcw_status tcw_search_triaged(tcw_ctx* c, const uint16_t* wbf, const float* thet
     }
   } guard{e0, e1, e2};
   int P = 0;
+  const bool regions = c->triage_templates < 1000;   // parameter regions: keep the coarse Psi
   TCW_CUDA(c, cudaEventRecord(e0, c->stream), "event");
-  tcw_status st = run_coarse(c, patch_size, psi_lo, psi_hi, false, &P);
+  tcw_status st = run_coarse(c, patch_size, psi_lo, psi_hi, regions, &P);
   if (st != TCW_OK) return st;
   TCW_CUDA(c, cudaEventRecord(e1, c->stream), "event");
   TCW_CUDA(c, c->tri_h1.ensure((size_t)P * kMlpH * sizeof(float)), "triage buffers");
@@ -1110,6 +1160,28 @@ tcw_status tcw_search_triaged(tcw_ctx* c, const uint16_t* wbf, const float* thet
       sub.push_back(c->h_sky_perm[i]);
   }
   std::sort(sub.begin(), sub.end());
+  // parameter regions: the union over the chosen patches of each patch's
+  // best templates by coarse Psi (sorted-bank indices)
+  std::vector<int32_t> tsub;
+  if (regions) {
+    const int64_t M = std::max<int64_t>(1, (c->B * c->triage_templates + 999) / 1000);
+    std::vector<float> row(c->Bpad);
+    std::vector<char> keep(c->B, 0);
+    std::vector<int32_t> ord(c->B);
+    for (int p = 0; p < P; ++p) {
+      if (!sel[p]) continue;
+      TCW_CUDA(c, cudaMemcpy(row.data(), c->tri_psi.as<float>() + (size_t)p * c->Bpad, c->Bpad * sizeof(float),
+                             cudaMemcpyDeviceToHost),
+               "coarse Psi");
+      std::iota(ord.begin(), ord.end(), 0);
+      std::nth_element(ord.begin(), ord.begin() + (M - 1), ord.end(), [&](int32_t a, int32_t b) {
+        return row[a] > row[b] || (row[a] == row[b] && a < b);
+      });
+      for (int64_t i = 0; i < M; ++i) keep[ord[i]] = 1;
+    }
+    for (int32_t b = 0; b < (int32_t)c->B; ++b)
+      if (keep[b]) tsub.push_back(b);
+  }
   const int64_t S_full = c->S;
   std::vector<double> full_nhat = c->h_nhat, sub_nhat(sub.size() * 3);
   for (size_t i = 0; i < sub.size(); ++i)
@@ -1119,7 +1191,43 @@ tcw_status tcw_search_triaged(tcw_ctx* c, const uint16_t* wbf, const float* thet
   c->sky_dirty = true;
   std::vector<float> sp(sub.size() * k);
   std::vector<int64_t> si(sub.size() * k);
-  st = tcw_search(c, k, sp.data(), si.data(), TCW_HOST);
+  const int64_t B_full = c->B;
+  std::vector<int32_t> perm_full;
+  if (!tsub.empty() && (int64_t)tsub.size() < B_full) {
+    // search the template subset: the full bank's buffers are set aside and restored below
+    const size_t n = tsub.size();
+    std::vector<double> f0(c->Bpad), tau(c->Bpad), nbr(c->Bpad), sf(n), st_(n), sn(n);
+    TCW_CUDA(c, cudaMemcpy(f0.data(), c->f0.p, c->Bpad * sizeof(double), cudaMemcpyDeviceToHost), "bank");
+    TCW_CUDA(c, cudaMemcpy(tau.data(), c->tau.p, c->Bpad * sizeof(double), cudaMemcpyDeviceToHost), "bank");
+    TCW_CUDA(c, cudaMemcpy(nbr.data(), c->nbr.p, c->Bpad * sizeof(double), cudaMemcpyDeviceToHost), "bank");
+    for (size_t i = 0; i < n; ++i) {
+      sf[i] = f0[tsub[i]];
+      st_[i] = tau[tsub[i]];
+      sn[i] = nbr[tsub[i]];
+    }
+    perm_full = c->h_bank_perm;
+    BankSwap saved(c);
+    st = tcw_define_bank(c, (int64_t)n, sf.data(), st_.data(), sn.data(), saved.T0, TCW_HOST);
+    if (st == TCW_OK) st = tcw_search(c, std::min<int>(k, (int)n), sp.data(), si.data(), TCW_HOST);
+    saved.restore();
+    if (st == TCW_OK && (int)n < k) {
+      // fewer templates than k: widen the rows (the remaining entries stay empty)
+      std::vector<float> sp2(sub.size() * k, -INFINITY);
+      std::vector<int64_t> si2(sub.size() * k, -1);
+      for (size_t i = 0; i < sub.size(); ++i)
+        for (int j = 0; j < (int)n; ++j) {
+          sp2[i * k + j] = sp[i * n + j];
+          si2[i * k + j] = si[i * n + j];
+        }
+      sp.swap(sp2);
+      si.swap(si2);
+    }
+    // subset index -> sorted index of the full bank -> caller index
+    for (auto& x : si)
+      if (x >= 0) x = perm_full[tsub[x]];
+  } else {
+    st = tcw_search(c, k, sp.data(), si.data(), TCW_HOST);
+  }
   c->h_nhat = std::move(full_nhat);
   c->S = S_full;
   c->sky_dirty = true;
@@ -1140,7 +1248,9 @@ tcw_status tcw_search_triaged(tcw_ctx* c, const uint16_t* wbf, const float* thet
     TCW_CUDA(c, cudaMemcpy(searched_out, searched.data(), searched.size() * sizeof(int32_t), kind), "copy out");
   c->tri_info.n_selected = m;
   c->tri_info.skies_searched = (int64_t)sub.size();
-  c->tri_info.lookups_searched = (int64_t)sub.size() * c->B * c->D * c->Nseg;
+  const int64_t n_tmpl = tsub.empty() ? c->B : (int64_t)tsub.size();
+  c->tri_info.templates_searched = n_tmpl;
+  c->tri_info.lookups_searched = (int64_t)sub.size() * n_tmpl * c->D * c->Nseg;
   c->tri_info.coarse_ms = coarse_ms;
   c->tri_info.mlp_ms = mlp_ms;
   c->tri_info.search_ms = c->info.search_ms;

@@ -50,7 +50,8 @@ struct tcw_ctx {
   int amp_power = 0;       // weights times (f(t_j)/f0)^amp_power (Eq. 3)
   int gen_chunk = 1 << 18; // generated-bank search: templates per chunk
   int track_bins = 1;      // bins per lookup: 1 nearest, 2 the bracketing pair
-  int triage_spread = 2;   // triage: patches within this distance of a chosen one are suppressed
+  int triage_spread = 2;
+  int triage_templates = 1000;  // triage: per mille of the bank searched per chosen patch   // triage: patches within this distance of a chosen one are suppressed
   int64_t batch_memory = (int64_t)48 << 30;  // batched search: Psi + anchor bytes per wave
   unsigned bank_epoch = 0; // bumped by every tcw_define_bank
   int statistic = TCW_STAT_POWER;

@@ -340,5 +340,26 @@ inline int choose_lanes(int64_t S) {
     if (padded_skies(S, l) * lanes_cost(l) < padded_skies(S, best) * lanes_cost(best)) best = l;
   return best;
 }
+// With the bank and the grid known: a work item is one chunk (16 L skies) x
+// bank_chunk passes of 512 / L templates, 8192 padded sky-templates per pass
+// whatever L, so the search takes ceil(items / grid) rounds of items costing
+// lanes_cost(L) each.  Few templates give few items at narrow chunks, and a
+// wider chunk can then fill more SMs.
+inline int choose_lanes(int64_t S, int64_t B, int bank_chunk, int grid) {
+  if (B <= 0 || grid <= 0) return choose_lanes(S);
+  int best = 0;
+  double best_cost = 0;
+  for (int l : {64, 32, 16}) {
+    const int64_t chunks = padded_skies(S, l) / (16 * l);
+    const int64_t groups = (B + 512 / l - 1) / (512 / l);
+    const int64_t items = chunks * ((groups + bank_chunk - 1) / bank_chunk);
+    const double cost = (double)((items + grid - 1) / grid) * bank_chunk * lanes_cost(l);
+    if (best == 0 || cost < best_cost) {
+      best = l;
+      best_cost = cost;
+    }
+  }
+  return best;
+}
 
 }  // namespace tcw

@@ -22,7 +22,7 @@ F32, F16 = 0, 1
 KERNEL_AUTO, KERNEL_GROUP, KERNEL_LOOKUP = 0, 1, 2
 OPT_KERNEL, OPT_KEEP_STATS, OPT_TILE_SEGMENTS, OPT_BANK_CHUNK = 1, 2, 3, 4
 OPT_AUTOTUNE, OPT_BATCH_MEMORY, OPT_SKY_LANES, OPT_TRIAGE_SPREAD = 5, 6, 7, 8
-OPT_AMPLITUDE_POWER, OPT_GEN_CHUNK, OPT_TRACK_BINS = 9, 10, 11
+OPT_AMPLITUDE_POWER, OPT_GEN_CHUNK, OPT_TRACK_BINS, OPT_TRIAGE_TEMPLATES = 9, 10, 11, 12
 STAT_POWER, STAT_NUMBER_COUNT = 0, 1
 
 _lock = threading.Lock()
@@ -87,7 +87,7 @@ class _TriageInfo(ctypes.Structure):
                 ("skies_searched", ctypes.c_int64), ("lookups_full", ctypes.c_int64),
                 ("lookups_coarse", ctypes.c_int64), ("lookups_searched", ctypes.c_int64),
                 ("coarse_ms", ctypes.c_float), ("mlp_ms", ctypes.c_float),
-                ("search_ms", ctypes.c_float)]
+                ("search_ms", ctypes.c_float), ("templates_searched", ctypes.c_int64)]
 
 
 MLP_PARAMS, MLP_WEIGHTS = 99073, 98560

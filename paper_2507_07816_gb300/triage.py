@@ -31,6 +31,9 @@ PSI_LO, PSI_HI = -4.0, 12.0
 # the injected template at any sky within JUDGE_RADIUS Doppler-sorted skies.
 LABEL_RADIUS = 1
 JUDGE_RADIUS = 64
+# Parameter regions: each chosen patch searches this many per mille of the bank,
+# its best templates by coarse Psi (TCW_OPT_TRIAGE_TEMPLATES).
+TEMPLATES_PERMILLE = 50
 
 
 def load_event(search, ev, bank, define_bank=True):
@@ -133,9 +136,13 @@ def judge(ev, psi, idx, pos, k_det=10, psi_det=6.5, radius=JUDGE_RADIUS):
 
 
 def evaluate(mlp, make_event, n_events, bank, frac=0.1, k=100, patch_size=PATCH_SIZE, lo=PSI_LO, hi=PSI_HI,
-             k_det=10, psi_det=6.5):
-    """Judge the triaged search against the exhaustive one on fresh events."""
+             k_det=10, psi_det=6.5, templates_permille=TEMPLATES_PERMILLE):
+    """Judge the triaged search against the exhaustive one on fresh events.
+    templates_permille < 1000 also restricts each chosen patch to its best
+    templates by coarse Psi (TCW_OPT_TRIAGE_TEMPLATES)."""
+    from .tcw import OPT_TRIAGE_TEMPLATES
     s = Search(0)
+    s.set_option(OPT_TRIAGE_TEMPLATES, templates_permille)
     full_found = tri_found = 0
     missed = 0
     t_full = t_tri = 0.0
@@ -164,4 +171,4 @@ def evaluate(mlp, make_event, n_events, bank, frac=0.1, k=100, patch_size=PATCH_
             "missed": missed, "loss": missed / max(full_found, 1), "time_full_s": t_full,
             "time_triaged_s": t_tri, "speedup": t_full / max(t_tri, 1e-12),
             "sums_full": sums_full, "sums_executed_triaged": sums_tri, "frac": frac,
-            "patch_size": patch_size}
+            "patch_size": patch_size, "templates_permille": templates_permille}

@@ -167,3 +167,44 @@ def test_triaged_search_rows_equal_exhaustive_rows(amp, count):
     assert len(chosen) == s.triage_info()["n_selected"] == 3
     assert all(b - a > 2 for a, b in zip(chosen, chosen[1:])), chosen
     s.close()
+
+
+def test_parameter_regions_search_a_template_subset():
+    """TCW_OPT_TRIAGE_TEMPLATES: each chosen patch keeps its best templates by
+    coarse Psi; the returned entries are exhaustive-search values of those
+    (sky, template) pairs, and the injections are still found."""
+    ev, bank = small_event(84, n_sky=200, n_inj=2, snr=(14.0, 16.0), n_bin=9600, t_sft=32.0)
+    theta = np.zeros(OT.N_PARAMS, np.float32)
+    p = OT.unpack(theta)
+    p["W1"][100:, 0] = 1.0
+    p["W2"][0, 0] = 1.0
+    p["w3"][0] = 1.0
+    mlp = tcw.Mlp(theta, device=DEV)
+    s = tcw.Search(0)
+    s.set_option(tcw.OPT_TRIAGE_SPREAD, 0)
+    s.set_option(tcw.OPT_KEEP_STATS, 1)
+    TR.load_event(s, ev, bank)
+    k = 8
+    s.search(k)
+    full = s.statistics(("psi",))["psi"]
+    s.set_option(tcw.OPT_TRIAGE_TEMPLATES, 100)        # 10 % of the bank per chosen patch
+    pt, xt, searched = s.search_triaged(mlp, 16, -4.0, 12.0, 0.25, k)
+    info = s.triage_info()
+    n_sel = info["n_selected"]
+    assert 0 < info["templates_searched"] <= n_sel * int(np.ceil(0.1 * len(bank.f0)))
+    assert info["lookups_searched"] == info["skies_searched"] * info["templates_searched"] * ev.rho.shape[0] * ev.rho.shape[1]
+    rows = np.nonzero(searched)[0]
+    assert len(set(xt[rows].ravel().tolist()) - {-1}) <= info["templates_searched"]
+    for r in rows:
+        got = pt[r][xt[r] >= 0]
+        ref = full[r, xt[r][xt[r] >= 0]]
+        assert np.all(np.abs(got - ref) <= 1e-5 * np.abs(ref) + 1e-4)
+        assert np.all(np.diff(got) <= 0)
+    # the injections sit at chosen patches and their templates are kept
+    pos = TR.sorted_positions(s)
+    for inj in ev.injections:
+        near = np.nonzero(np.abs(pos - pos[inj.sky]) <= 16)[0]
+        assert np.any(xt[near] == inj.template)
+    s.set_option(tcw.OPT_TRIAGE_TEMPLATES, 1000)
+    s.close()
+

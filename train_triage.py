@@ -9,15 +9,18 @@ example per sky patch (32 Doppler-sorted skies), label 1 for the patches
 within one patch of an injected sky.  The features come from the library's coarse pass and
 the network is trained by the library's own forward/backward/Adam kernels.
 
-Judge: on held-out events the triaged search (best 10 % of patches searched
-exhaustively) is compared with the exhaustive search of every sky; an
-injection counts as found when its template is within the first 10 entries,
-with Psi >= 6.5, of a searched sky within 64 Doppler-sorted positions of the
-injected sky.
+Judge: on held-out events the triaged search (best 10 % of patches, each
+searched over its best 5 % of templates by coarse Psi) is compared with the
+exhaustive search of every sky; an injection counts as found when its
+template is within the first 10 entries, with Psi >= 6.5, of a searched sky
+within 64 Doppler-sorted positions of the injected sky.
 
   python train_triage.py [--train-events 3125] [--valid-events 1000]
+                         [--templates-permille 50] [--judge-only]
                          [--out paper_2507_07816_gb300/triage_weights.npz]
                          [--report gpurun_out/triage_report.json]
+
+--judge-only skips the training and judges the weights in --out.
 """
 from __future__ import annotations
 
@@ -46,6 +49,8 @@ def main():
     ap.add_argument("--injections", type=int, default=1)
     ap.add_argument("--out", default=os.path.join(ROOT, "paper_2507_07816_gb300", "triage_weights.npz"))
     ap.add_argument("--report", default=None)
+    ap.add_argument("--templates-permille", type=int, default=None)
+    ap.add_argument("--judge-only", action="store_true")
     args = ap.parse_args()
 
     import torch
@@ -56,10 +61,31 @@ def main():
     dev = torch.device("cuda:0")
     bank_seed, train_seed, valid_seed = 20250715, 30_000_000, 40_000_000
     bank = syn.random_bank(syn.rng(bank_seed), args.n_tmpl, f0_range=(500.0, 3000.0))
+    tpm = TR.TEMPLATES_PERMILLE if args.templates_permille is None else args.templates_permille
 
     def make(seed0):
         return lambda i: syn.training_event(seed0 + i, bank, n_inj=args.injections, snr_range=(6.0, 12.0),
                                             device=dev)
+
+    if args.judge_only:
+        mlp = tcw.Mlp.load(args.out, device=dev)
+        untrained = tcw.Mlp(seed=1, device=dev)
+        t0 = time.perf_counter()
+        judged = TR.evaluate(mlp, make(valid_seed + 1000), args.valid_events, bank, frac=args.frac,
+                             patch_size=args.patch_size, templates_permille=tpm)
+        judged_all = TR.evaluate(mlp, make(valid_seed + 1000), min(args.valid_events, 200), bank, frac=args.frac,
+                                 patch_size=args.patch_size, templates_permille=1000)
+        judged_un = TR.evaluate(untrained, make(valid_seed + 1000), min(args.valid_events, 50), bank,
+                                frac=args.frac, patch_size=args.patch_size, templates_permille=tpm)
+        report = {"weights": os.path.relpath(args.out, ROOT), "judged_trained": judged,
+                  "judged_trained_all_templates": judged_all, "judged_untrained": judged_un,
+                  "valid_s": time.perf_counter() - t0}
+        print(json.dumps(report), flush=True)
+        if args.report:
+            os.makedirs(os.path.dirname(os.path.abspath(args.report)), exist_ok=True)
+            with open(args.report, "w") as f:
+                json.dump(report, f, indent=1)
+        return 0
 
     t0 = time.perf_counter()
     X, y, sizes = TR.collect(make(train_seed), args.train_events, bank, patch_size=args.patch_size)
@@ -82,9 +108,9 @@ def main():
              injections=args.injections)
     t0 = time.perf_counter()
     judged = TR.evaluate(mlp, make(valid_seed + 1000), args.valid_events, bank, frac=args.frac,
-                         patch_size=args.patch_size)
+                         patch_size=args.patch_size, templates_permille=tpm)
     judged_un = TR.evaluate(untrained, make(valid_seed + 1000), min(args.valid_events, 50), bank,
-                            frac=args.frac, patch_size=args.patch_size)
+                            frac=args.frac, patch_size=args.patch_size, templates_permille=tpm)
     t_valid = time.perf_counter() - t0
     report = {"train_examples": int(X.shape[0]), "train_positive": int(y.sum().item()),
               "train_events": args.train_events, "n_tmpl": args.n_tmpl, "steps": args.steps,
