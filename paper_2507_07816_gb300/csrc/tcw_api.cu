@@ -464,6 +464,8 @@ tcw_status run_coarse(tcw_ctx* c, int patch_size, float lo, float hi, bool keep_
   cp.hi = hi;
   cp.psi = keep_psi ? c->tri_psi.as<float>() : nullptr;
   cp.hist = c->tri_hist.as<unsigned>();
+  TCW_CUDA(c, c->tri_part.ensure(coarse_part_elems(P, c->Bpad) * sizeof(double)), "triage buffers");
+  cp.part_acc = c->tri_part.as<double>();
   cp.feat = c->tri_feat.as<float>();
   TCW_CUDA(c, launch_coarse(cp, c->dtype == TCW_F16, c->stream), "coarse_kernel launch");
   c->tri_info.n_patch = P;
@@ -532,7 +534,7 @@ tcw_status tcw_destroy(tcw_ctx* c) {
                     &c->dq, &c->anchors, &c->psi, &c->st_S, &c->st_W1, &c->st_W2, &c->dev,
                     &c->flags, &c->stage_f, &c->stage_i, &c->evtab, &c->items, &c->tri_dop,
                     &c->tri_hist, &c->tri_feat, &c->tri_psi, &c->tri_anchor, &c->tri_h1, &c->tri_h2,
-                    &c->tri_score, &c->tri_sel, &c->bits, &c->gen_psi[0], &c->gen_psi[1],
+                    &c->tri_score, &c->tri_sel, &c->tri_part, &c->bits, &c->gen_psi[0], &c->gen_psi[1],
                     &c->gen_idx[0], &c->gen_idx[1], &c->gen_cpsi, &c->gen_cidx};
   for (DevBuf* b : bufs) b->release();
   batch_free(c);

@@ -102,7 +102,7 @@ struct tcw_ctx {
   tcw_generated_info gen_info{};
   // learned triage
   std::vector<int32_t> h_sky_perm, h_bank_perm;  // sorted -> caller (host copies)
-  tcw::DevBuf tri_dop, tri_hist, tri_feat, tri_psi, tri_anchor, tri_h1, tri_h2, tri_score, tri_sel;
+  tcw::DevBuf tri_dop, tri_hist, tri_feat, tri_psi, tri_anchor, tri_h1, tri_h2, tri_score, tri_sel, tri_part;
   tcw_triage_info tri_info{};
 };
 

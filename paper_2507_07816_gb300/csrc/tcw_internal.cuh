@@ -238,7 +238,11 @@ struct CoarseParams {
   float* psi;               // optional [P][Bpad]
   unsigned* hist;           // [P][128], zero at launch
   float* feat;              // [P][128] log(1 + count)
+  int parts;                // segment ranges the tiles are split into (set by launch_coarse)
+  double* part_acc;         // [parts][P][Bpad][3] partial S, W1, W2 when parts > 1 (size from coarse_part_elems)
 };
+// Elements of CoarseParams::part_acc that launch_coarse may use.
+size_t coarse_part_elems(int P, int Bpad);
 
 cudaError_t launch_patch_doppler(const PatchDopplerParams& p, cudaStream_t st);
 cudaError_t launch_coarse(const CoarseParams& p, bool half, cudaStream_t st);

@@ -38,6 +38,8 @@ constexpr int kCoarseThreads = 256;  // one thread per (template, patch): 256 / 
 constexpr int kCoarseTile = 32;   // segments per tile (= anchor tile of the coarse pass)
 constexpr int kCoarseMaxDet = 2;  // detectors staged in shared memory
 constexpr int kCoarseWin = 8;     // staged bins per (template, segment, detector): base - 3 .. base + 4
+constexpr int kCoarseBlocksPerSM = 6;  // the launch bound below
+constexpr int kCoarseMaxParts = 8;     // segment ranges of one (patch, template) block
 
 __device__ __forceinline__ float load_rho(const float* p, int64_t i) { return __ldg(p + i); }
 __device__ __forceinline__ float load_rho(const __half* p, int64_t i) { return __half2float(__ldg(p + i)); }
@@ -55,10 +57,23 @@ __global__ void patch_doppler_kernel(PatchDopplerParams p) {
   }
 }
 
+// Psi (Eq. 4) of (patch pi, template b) and its histogram bin.
+__device__ __forceinline__ void coarse_store(const CoarseParams& p, int pi, int b, double S, double W1, double W2) {
+  const float W2f = (float)W2;
+  const float psi = W2f > 0.f ? (float)(S - W1) * rsqrtf(W2f) : -INFINITY;
+  if (p.psi) p.psi[(int64_t)pi * p.Bpad + b] = psi;
+  int bin = 0;
+  if (psi > -INFINITY) {
+    const float u = floorf((psi - p.lo) / (p.hi - p.lo) * (float)kTriageBins);
+    bin = u < 0.f ? 0 : (u > (float)(kTriageBins - 1) ? kTriageBins - 1 : (int)u);
+  }
+  atomicAdd(p.hist + (int64_t)pi * kTriageBins + bin, 1u);
+}
+
 template <typename RhoT, int D, int kCoarseLanes>
 // 6 blocks per SM (<= 40 registers): the kernel is latency-bound between its
 // per-tile barriers, and 6 resident blocks instead of 4 halve its time on GB300
-__global__ void __launch_bounds__(kCoarseThreads, 6) coarse_kernel(CoarseParams p) {
+__global__ void __launch_bounds__(kCoarseThreads, kCoarseBlocksPerSM) coarse_kernel(CoarseParams p) {
   constexpr int kCoarseTmpl = kCoarseThreads / kCoarseLanes;   // templates per block
   static_assert(kCoarseTile <= kCoarseLanes, "at most one track entry per thread per tile");
   // per (template, segment) of the tile: {base, frac bits, F bits, window inside the band}
@@ -88,7 +103,10 @@ __global__ void __launch_bounds__(kCoarseThreads, 6) coarse_kernel(CoarseParams 
   }
   double S = 0.0, W1 = 0.0, W2 = 0.0;
   const int n_tiles = (p.n_seg + kCoarseTile - 1) / kCoarseTile;
-  for (int ti = 0; ti < n_tiles; ++ti) {
+  // part blockIdx.z of the segment tiles (several parts fill the last wave of blocks)
+  const int z = blockIdx.z;
+  const int t_begin = (int)((int64_t)z * n_tiles / p.parts), t_end = (int)((int64_t)(z + 1) * n_tiles / p.parts);
+  for (int ti = t_begin; ti < t_end; ++ti) {
     const int j0 = ti * kCoarseTile;
     const int jn = min(kCoarseTile, p.n_seg - j0);
     __syncthreads();
@@ -194,15 +212,29 @@ __global__ void __launch_bounds__(kCoarseThreads, 6) coarse_kernel(CoarseParams 
     W2 += (double)w2t + (double)s_wsum[tl][1];
   }
   if (!active || b >= p.B) return;
-  const float W2f = (float)W2;
-  const float psi = W2f > 0.f ? (float)(S - W1) * rsqrtf(W2f) : -INFINITY;
-  if (p.psi) p.psi[(int64_t)pi * p.Bpad + b] = psi;
-  int bin = 0;
-  if (psi > -INFINITY) {
-    const float u = floorf((psi - p.lo) / (p.hi - p.lo) * (float)kTriageBins);
-    bin = u < 0.f ? 0 : (u > (float)(kTriageBins - 1) ? kTriageBins - 1 : (int)u);
+  if (p.parts > 1) {
+    double* acc = p.part_acc + (((int64_t)z * p.P + pi) * p.Bpad + b) * 3;
+    acc[0] = S;
+    acc[1] = W1;
+    acc[2] = W2;
+    return;
   }
-  atomicAdd(p.hist + (int64_t)pi * kTriageBins + bin, 1u);
+  coarse_store(p, pi, b, S, W1, W2);
+}
+
+// Sums the parts in order (deterministic), then Psi and the histogram.
+__global__ void coarse_finalize_kernel(CoarseParams p) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)p.P * p.B) return;
+  const int pi = (int)(i / p.B), b = (int)(i % p.B);
+  double S = 0.0, W1 = 0.0, W2 = 0.0;
+  for (int z = 0; z < p.parts; ++z) {
+    const double* acc = p.part_acc + (((int64_t)z * p.P + pi) * p.Bpad + b) * 3;
+    S += acc[0];
+    W1 += acc[1];
+    W2 += acc[2];
+  }
+  coarse_store(p, pi, b, S, W1, W2);
 }
 
 __global__ void features_kernel(const unsigned* hist, int64_t n, float* feat) {
@@ -402,7 +434,7 @@ cudaError_t launch_patch_doppler(const PatchDopplerParams& p, cudaStream_t st) {
 
 template <int PL>
 void launch_coarse_l(const CoarseParams& p, bool half, cudaStream_t st) {
-  dim3 grid((p.P + PL - 1) / PL, p.Bpad / (kCoarseThreads / PL));
+  dim3 grid((p.P + PL - 1) / PL, p.Bpad / (kCoarseThreads / PL), p.parts);
   if (half) {
     if (p.n_det == 1)
       coarse_kernel<__half, 1, PL><<<grid, kCoarseThreads, 0, st>>>(p);
@@ -416,14 +448,47 @@ void launch_coarse_l(const CoarseParams& p, bool half, cudaStream_t st) {
   }
 }
 
-cudaError_t launch_coarse(const CoarseParams& p, bool half, cudaStream_t st) {
-  if (p.n_det < 1 || p.n_det > kCoarseMaxDet) return cudaErrorInvalidValue;
-  if (p.P <= 32)
+size_t coarse_part_elems(int P, int Bpad) { return (size_t)kCoarseMaxParts * P * Bpad * 3; }
+
+// Split the tiles into the number of parts (<= kCoarseMaxParts, each >= 16
+// tiles) whose blocks fill the resident slots best: the last wave of a
+// 2500-block grid at 6 x 152 slots is 74 % full, of 4 x 2500 blocks 96 %.
+int coarse_parts(int64_t blocks, int n_tiles) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 1;
+  const double slots = (double)kCoarseBlocksPerSM * sms;
+  int best = 1;
+  double best_eff = 0.0;
+  for (int parts = 1; parts <= kCoarseMaxParts && n_tiles / parts >= 16; ++parts) {
+    const double waves = (double)(blocks * parts) / slots;
+    const double eff = waves / std::ceil(waves);
+    if (eff > best_eff + 0.02) {
+      best = parts;
+      best_eff = eff;
+    }
+  }
+  return best;
+}
+
+cudaError_t launch_coarse(const CoarseParams& p_in, bool half, cudaStream_t st) {
+  if (p_in.n_det < 1 || p_in.n_det > kCoarseMaxDet) return cudaErrorInvalidValue;
+  CoarseParams p = p_in;
+  const int PL = p.P <= 32 ? 32 : 64;
+  const int n_tiles = (p.n_seg + kCoarseTile - 1) / kCoarseTile;
+  p.parts = p.part_acc ? coarse_parts((int64_t)((p.P + PL - 1) / PL) * (p.Bpad / (kCoarseThreads / PL)), n_tiles) : 1;
+  if (PL == 32)
     launch_coarse_l<32>(p, half, st);
   else
     launch_coarse_l<64>(p, half, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (p.parts > 1) {
+    const int64_t n = (int64_t)p.P * p.B;
+    coarse_finalize_kernel<<<blocks_for(n, 256), 256, 0, st>>>(p);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   const int64_t n = (int64_t)p.P * kTriageBins;
   features_kernel<<<blocks_for(n, 256), 256, 0, st>>>(p.hist, n, p.feat);
   return cudaGetLastError();
