@@ -284,7 +284,7 @@ def bench_learned(args, dev):
                                   device=torch.device(f"cuda:{dev}"))
 
     make(0)
-    r = TR.evaluate(mlp, make, args.learned_events, bank, frac=float(meta["frac"]),
+    r = TR.evaluate(mlp, make, args.learned_events, bank, frac=TR.FRAC,
                     patch_size=int(meta["patch_size"]), k=TOPK, templates_permille=TR.TEMPLATES_PERMILLE)
     r["value"] = r["sums_full"] / r["time_triaged_s"]
     r["unit"] = UNIT

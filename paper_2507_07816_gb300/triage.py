@@ -31,9 +31,12 @@ PSI_LO, PSI_HI = -4.0, 12.0
 # the injected template at any sky within JUDGE_RADIUS Doppler-sorted skies.
 LABEL_RADIUS = 1
 JUDGE_RADIUS = 64
-# Parameter regions: each chosen patch searches this many per mille of the bank,
-# its best templates by coarse Psi (TCW_OPT_TRIAGE_TEMPLATES).
-TEMPLATES_PERMILLE = 50
+# Operating point of the triaged search: the best FRAC of the patches are
+# searched, each over its best TEMPLATES_PERMILLE per mille of the bank by
+# coarse Psi (TCW_OPT_TRIAGE_TEMPLATES); the union of those templates is
+# searched at every chosen sky.
+FRAC = 0.35
+TEMPLATES_PERMILLE = 12
 
 
 def load_event(search, ev, bank, define_bank=True):
@@ -135,7 +138,7 @@ def judge(ev, psi, idx, pos, k_det=10, psi_det=6.5, radius=JUDGE_RADIUS):
     return found
 
 
-def evaluate(mlp, make_event, n_events, bank, frac=0.1, k=100, patch_size=PATCH_SIZE, lo=PSI_LO, hi=PSI_HI,
+def evaluate(mlp, make_event, n_events, bank, frac=FRAC, k=100, patch_size=PATCH_SIZE, lo=PSI_LO, hi=PSI_HI,
              k_det=10, psi_det=6.5, templates_permille=TEMPLATES_PERMILLE):
     """Judge the triaged search against the exhaustive one on fresh events.
     templates_permille < 1000 also restricts each chosen patch to its best

@@ -9,14 +9,14 @@ example per sky patch (32 Doppler-sorted skies), label 1 for the patches
 within one patch of an injected sky.  The features come from the library's coarse pass and
 the network is trained by the library's own forward/backward/Adam kernels.
 
-Judge: on held-out events the triaged search (best 10 % of patches, each
-searched over its best 5 % of templates by coarse Psi) is compared with the
+Judge: on held-out events the triaged search (best 35 % of patches, each
+contributing its best 1.2 % of templates by coarse Psi) is compared with the
 exhaustive search of every sky; an injection counts as found when its
 template is within the first 10 entries, with Psi >= 6.5, of a searched sky
 within 64 Doppler-sorted positions of the injected sky.
 
   python train_triage.py [--train-events 3125] [--valid-events 1000]
-                         [--templates-permille 50] [--judge-only]
+                         [--frac 0.35] [--templates-permille 12] [--judge-only]
                          [--out paper_2507_07816_gb300/triage_weights.npz]
                          [--report gpurun_out/triage_report.json]
 
@@ -44,7 +44,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--batch", type=int, default=4096)
     ap.add_argument("--lr", type=float, default=1e-3)
-    ap.add_argument("--frac", type=float, default=0.1)
+    ap.add_argument("--frac", type=float, default=None)
     ap.add_argument("--patch-size", type=int, default=32)
     ap.add_argument("--injections", type=int, default=1)
     ap.add_argument("--out", default=os.path.join(ROOT, "paper_2507_07816_gb300", "triage_weights.npz"))
@@ -62,6 +62,8 @@ def main():
     bank_seed, train_seed, valid_seed = 20250715, 30_000_000, 40_000_000
     bank = syn.random_bank(syn.rng(bank_seed), args.n_tmpl, f0_range=(500.0, 3000.0))
     tpm = TR.TEMPLATES_PERMILLE if args.templates_permille is None else args.templates_permille
+    if args.frac is None:
+        args.frac = TR.FRAC
 
     def make(seed0):
         return lambda i: syn.training_event(seed0 + i, bank, n_inj=args.injections, snr_range=(6.0, 12.0),
