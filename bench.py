@@ -64,6 +64,28 @@ def parse():
     return ap.parse_args()
 
 
+def rank_sky(rank, world, per_rank=1024):
+    """Rank `rank`'s slice of an equal-area lattice of world * per_rank skies
+    (weak scaling: every rank searches its own skies over the same data)."""
+    import tcw_synth as syn
+    return np.ascontiguousarray(syn.fibonacci_sky(per_rank * world)[rank * per_rank:(rank + 1) * per_rank])
+
+
+def max_over_ranks(x, dist=None, device=None):
+    """The largest x over the ranks (the job's time is its slowest rank's)."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, units_per_rank, steps, seconds):
+    """Whole-job throughput: the units every rank processed / the max-over-ranks time."""
+    return world * units_per_rank * steps / seconds
+
+
 def make_problem(workload, rank, world):
     import tcw_synth as syn
     if workload == "small":
@@ -74,8 +96,7 @@ def make_problem(workload, rank, world):
         return syn.config_full(seed=20250712, n_seg=2000, n_tmpl=8000, n_inj=2)
     p = syn.config_full(seed=20250712)
     if world > 1:
-        sky = syn.fibonacci_sky(1024 * world)[rank * 1024:(rank + 1) * 1024]
-        p.nhat = np.ascontiguousarray(sky)
+        p.nhat = rank_sky(rank, world)
     return p
 
 
@@ -349,13 +370,9 @@ def bench_ours(args):
     torch.cuda.synchronize()
     barrier()
     clocks = clk.stop()
-    elapsed = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([elapsed], device=f"cuda:{dev}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = max_over_ranks(e0.elapsed_time(e1), dist, f"cuda:{dev}")
     ms_per_step = elapsed / args.steps
-    value = world * U * args.steps / (elapsed / 1000.0)
+    value = job_rate(world, U, args.steps, elapsed / 1000.0)
     info = s.info()
 
     # end to end through the public API: host (pinned) inputs in, host top-k out
@@ -384,12 +401,8 @@ def bench_ours(args):
         for _ in range(n_e2e):
             e2e_step()
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([dt], device=f"cuda:{dev}")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        e2e = {"value": world * U * n_e2e / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        dt = max_over_ranks(time.perf_counter() - t0, dist, f"cuda:{dev}")
+        e2e = {"value": job_rate(world, U, n_e2e, dt), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "steps": n_e2e}
         s2.close()
 
