@@ -428,6 +428,32 @@ def bench_ours(args):
     except (OSError, ValueError):
         peaks = {}
     hbm = float(peaks.get("hbm_gbs", 6782.8))
+    fma = {}
+    try:
+        fma = {"fp64_tflops": tcw.probe_fma_rate(True), "fp32_tflops": tcw.probe_fma_rate(False),
+               "basis": "8 independent fma chains per thread, 8 x 256 threads per SM, best of 5"}
+    except Exception as exc:
+        fma = {"error": f"{type(exc).__name__}: {exc}"}
+    # share of the evaluated lookups that add nothing (segment before T0, bin out of
+    # band): from W1 of a search of a sample of the bank (unit weights: W1 counts the
+    # valid lookups of a pair)
+    invalid = None
+    if rank == 0 and p.weights is None and len(p.bank) >= 2048:
+        try:
+            import tcw_synth as syn
+            sub = syn.rng(7).choice(len(p.bank), 2048, replace=False)
+            s3 = tcw.Search(dev, stream=stream)
+            s3.set_option(tcw.OPT_KEEP_STATS, 1)
+            s3.load_problem(p)
+            s3.define_bank(p.bank.f0[sub], p.bank.tau[sub], p.bank.n[sub], p.T0)
+            s3.search(k)
+            w1 = s3.statistics(("W1",))["W1"]
+            s3.close()
+            D, Nseg = p.rho.shape[:2]
+            invalid = {"share": float(1.0 - w1.astype(np.float64).mean() / (D * Nseg)),
+                       "sample": f"2048 random templates of the bank x {S} skies (W1 of unit weights)"}
+        except Exception as exc:
+            invalid = {"error": f"{type(exc).__name__}: {exc}"}
     gather = {"algorithmic_GBps": achieved * p.rho.itemsize / 1e9,
               "measured_l2_read_GBps": l2_gbps,
               "frac_of_measured_l2": (achieved * p.rho.itemsize / 1e9 / l2_gbps) if l2_gbps else None,
@@ -539,7 +565,9 @@ def bench_ours(args):
             "e2e": e2e, "gpu_launches": launches, "roofline": roof, "gather": gather,
             "cpu_baseline": cpu, "clocks": clocks,
             "search": {"general_path_lanes": info.general_path_lanes,
-                       "doppler_bins_max": info.doppler_bins_max, "quantum": info.quantum},
+                       "doppler_bins_max": info.doppler_bins_max, "quantum": info.quantum,
+                       "invalid_lookups": invalid},
+            "fma_rate": fma,
         }
         line.update(extras)
         print(json.dumps(line))

@@ -419,6 +419,13 @@ tcw_status tcw_sky_order(tcw_ctx *ctx, int32_t *order_out);
  * < 1, NULL), CUDA. */
 tcw_status tcw_probe_read_bandwidth(int64_t bytes, int passes, int reps, double *gbps_out);
 
+/* Measurement helper (not part of the method): best-of-`reps` rate in TFLOP/s
+ * (2 flops per fused multiply-add) of a kernel running 8 independent fma
+ * chains of `iters` steps per thread, 8 x 256 threads per SM, in double
+ * (fp64 != 0) or float, on the current device.  Errors: INVALID_ARGUMENT
+ * (iters or reps < 1, NULL), CUDA. */
+tcw_status tcw_probe_fma_rate(int fp64, int iters, int reps, double *tflops_out);
+
 /* Information about the last search. */
 /* ---------------------------------------------------------------------------
  * Template banks generated on the device (Sec. 2 of arXiv:2507.07816 uses a

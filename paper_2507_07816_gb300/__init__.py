@@ -9,4 +9,4 @@ from .tcw import (BANK_LATTICE, BANK_RANDOM, DEVICE, F16, F32, HOST, KERNEL_AUTO
                   OPT_KERNEL, OPT_SKY_LANES, OPT_TILE_SEGMENTS, OPT_TRACK_BINS, OPT_TRIAGE_SPREAD,
                   OPT_TRIAGE_TEMPLATES,
                   STAT_NUMBER_COUNT, STAT_POWER, Info, Mlp, Search, TcwError, bank_spec, library_path,
-                  load_library, probe_read_bandwidth)
+                  load_library, probe_fma_rate, probe_read_bandwidth)

@@ -144,6 +144,7 @@ def load_library(build_if_missing: bool = True):
             "tcw_generate_bank_at": [p, ctypes.POINTER(_BankSpec), p, i64, p, p, p, i],
             "tcw_get_generated_info": [p, ctypes.POINTER(_GenInfo)],
             "tcw_probe_read_bandwidth": [i64, i, i, ctypes.POINTER(d)],
+            "tcw_probe_fma_rate": [i, i, i, ctypes.POINTER(d)],
         }
         for name, args in sig.items():
             fn = getattr(lib, name)
@@ -164,6 +165,16 @@ def probe_read_bandwidth(nbytes, passes=50, reps=5):
     st = lib.tcw_probe_read_bandwidth(int(nbytes), int(passes), int(reps), ctypes.byref(out))
     if st != OK:
         raise TcwError(st, "tcw_probe_read_bandwidth: " + lib.tcw_status_string(st).decode())
+    return out.value
+
+
+def probe_fma_rate(fp64, iters=4096, reps=5):
+    """Fused multiply-add rate (TFLOP/s) in double (fp64) or float."""
+    lib = load_library()
+    out = ctypes.c_double()
+    st = lib.tcw_probe_fma_rate(1 if fp64 else 0, int(iters), int(reps), ctypes.byref(out))
+    if st != OK:
+        raise TcwError(st, "tcw_probe_fma_rate: " + lib.tcw_status_string(st).decode())
     return out.value
 
 
