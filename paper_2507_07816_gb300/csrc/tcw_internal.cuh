@@ -260,7 +260,7 @@ cudaError_t mlp_adam(float* theta, float* m, float* v, const float* grad, int64_
                      float b2, float eps, __nv_bfloat16* wbf, cudaStream_t st);
 cudaError_t mlp_pack(const float* theta, __nv_bfloat16* wbf, cudaStream_t st);
 
-// Host helpers of the group kernel (tcw_persist.cu).
+// Host helpers of the group kernel (tcw_persist.cu; the kernel is in tcw_persist.cuh).
 // CTAs of a group-kernel launch on the current device: one per SM.
 cudaError_t group_grid(int* grid);
 // Longest-processing-time-first schedule: items in decreasing cost, each to

@@ -2,7 +2,7 @@
 //
 //   doppler_kernel  Eq. 2 factor per (detector, segment, sky): v.nhat/c in FP64,
 //                   stored as floor(./q) int32 plus the fp32 mid-range per sky group
-//   (the hot loop, group_kernel, is in tcw_persist.cu)
+//   (the hot loop, group_kernel, is in tcw_persist.cuh)
 //   lookup_kernel   one thread per (sky, template), FP64 per lookup; used when
 //                   the group kernel's exactness conditions do not hold
 //   count_bits_kernel number-count bit map [rho > rho_th]
