@@ -139,6 +139,7 @@ __device__ __forceinline__ void compute_entry(const GroupParams& p, const EventD
     const double2 an = reinterpret_cast<const double2*>(ev.anchors)[(int64_t)b * ev.n_tiles + ti];
     const double delta = (tj - tile_anchor_time(ev.t_mid, ev.n_seg, ev.T0, p.tile_shift, ti)) * an.y;
     double R = coef[p.nterms - 1];
+#pragma unroll 4
     for (int k = p.nterms - 2; k >= 0; --k) R = fma(R, delta, coef[k]);
     h = an.x * R;
   } else {

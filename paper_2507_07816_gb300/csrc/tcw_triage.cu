@@ -136,6 +136,7 @@ __global__ void __launch_bounds__(kCoarseThreads, kCoarseBlocksPerSM) coarse_ker
           const double ta = fmax(p.t_mid[j0 + (jn - 1) / 2], p.T0);
           const double delta = (tj - ta) * an.y;
           double R = s_coef[tl][p.nterms - 1];
+#pragma unroll 4
           for (int k = p.nterms - 2; k >= 0; --k) R = fma(R, delta, s_coef[tl][k]);
           h = an.x * R;
         } else {
