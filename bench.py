@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--no-amplitude", action="store_true", help="skip the amplitude and count variants")
     ap.add_argument("--batched-events", type=int, default=64)
     ap.add_argument("--batched-templates", type=int, default=20000)
-    ap.add_argument("--learned-events", type=int, default=6)
+    ap.add_argument("--learned-events", type=int, default=10)
     return ap.parse_args()
 
 
@@ -304,7 +304,9 @@ def bench_learned(args, dev):
         return syn.training_event(seed0 + i, bank, n_inj=int(meta["injections"]), snr_range=(6.0, 12.0),
                                   device=torch.device(f"cuda:{dev}"))
 
-    make(0)
+    # one untimed event first: buffers, library state and the subset bank path warm up
+    TR.evaluate(mlp, lambda i: make(10**6 + i), 1, bank, frac=TR.FRAC, patch_size=int(meta["patch_size"]), k=TOPK,
+                templates_permille=TR.TEMPLATES_PERMILLE)
     r = TR.evaluate(mlp, make, args.learned_events, bank, frac=TR.FRAC,
                     patch_size=int(meta["patch_size"]), k=TOPK, templates_permille=TR.TEMPLATES_PERMILLE)
     r["value"] = r["sums_full"] / r["time_triaged_s"]
