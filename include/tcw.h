@@ -89,7 +89,8 @@ enum {
                                   wave of events (default 48 GiB, minimum 1 MiB) */
     TCW_OPT_SKY_LANES = 7,     /* sky groups of 16 per chunk of the group kernel: 16,
                                   32 or 64 (a pass covers 16*lanes skies x 512/lanes
-                                  templates); 0 (default) = the lowest padded cost */
+                                  templates); 0 (default) = the lowest cost for the
+                                  sky count, the bank size and the SM count */
     TCW_OPT_TRIAGE_SPREAD = 8, /* triaged search: a chosen patch suppresses the patches
                                   within this many positions (default 2; 0 = plain
                                   ranking); best suppressed ones fill up if needed */
@@ -383,10 +384,14 @@ tcw_status tcw_triage_features(tcw_ctx *ctx, int patch_size, float psi_lo, float
 
 /* Triaged search: coarse pass, network score per patch, the ceil(frac *
  * n_patch) best patches (spread apart by TCW_OPT_TRIAGE_SPREAD) searched
- * exhaustively as tcw_search does.
- * psi_out/idx_out [n_sky][k] as tcw_search for searched skies; rows of
- * skipped skies hold -inf and -1.  searched_out [n_sky] (may be NULL): 1 for
- * searched skies.  wbf and theta are device pointers.
+ * exhaustively as tcw_search does, over every template or, with
+ * TCW_OPT_TRIAGE_TEMPLATES < 1000, over the union of each chosen patch's best
+ * templates by coarse Psi (then a row's entries are the best of that union).
+ * psi_out/idx_out [n_sky][k] as tcw_search for searched skies (caller
+ * template indices); rows of skipped skies hold -inf and -1, and so do the
+ * entries past the union's size when it holds fewer than k templates.
+ * searched_out [n_sky] (may be NULL): 1 for searched skies.  wbf and theta
+ * are device pointers.
  * Errors: as tcw_search and tcw_triage_features, INVALID_ARGUMENT (frac not
  * in (0, 1]). */
 tcw_status tcw_search_triaged(tcw_ctx *ctx, const uint16_t *wbf, const float *theta,
