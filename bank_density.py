@@ -25,7 +25,7 @@ injection are excluded): "near", the template's source frequency within 2 Hz
 against SNR.  The exact-track row searches each injection's own template.
 
   python bank_density.py [--n-list 1e4,1e5,1e6,1e7] [--n-big 1e8]
-                         [--snr 6,10,15,20,30] [--report gpurun_out/bank_density.json]
+                         [--snr 6,10,15,20,30] [--report bank_density.json]
 """
 from __future__ import annotations
 

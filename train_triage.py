@@ -18,7 +18,7 @@ within 64 Doppler-sorted positions of the injected sky.
   python train_triage.py [--train-events 3125] [--valid-events 1000]
                          [--frac 0.35] [--templates-permille 12] [--judge-only]
                          [--out paper_2507_07816_gb300/triage_weights.npz]
-                         [--report gpurun_out/triage_report.json]
+                         [--report triage_report.json]
 
 --judge-only skips the training and judges the weights in --out.
 """
