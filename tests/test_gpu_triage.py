@@ -200,8 +200,22 @@ def test_parameter_regions_search_a_template_subset():
         ref = full[r, xt[r][xt[r] >= 0]]
         assert np.all(np.abs(got - ref) <= 1e-5 * np.abs(ref) + 1e-4)
         assert np.all(np.diff(got) <= 0)
-    # the injections sit at chosen patches and their templates are kept
+    # the union of the chosen patches' best templates, recomputed from the coarse
+    # Psi in the library's sorted-bank order (f0, ties by caller index), ties in Psi
+    # broken by that order
+    _, cpsi = s.triage_features(16, -4.0, 12.0, with_psi=True)
     pos = TR.sorted_positions(s)
+    chosen = sorted({int(pos[i]) // 16 for i in rows})
+    order = np.argsort(bank.f0, kind="stable")                  # sorted index -> caller index
+    M = int(np.ceil(100 * len(bank.f0) / 1000))
+    union = set()
+    for pch in chosen:
+        v = cpsi[pch][order]
+        top = np.lexsort((np.arange(len(order)), -v))[:M]       # Psi desc, sorted index asc
+        union |= set(order[top].tolist())
+    assert len(union) == info["templates_searched"]
+    assert set(xt[rows].ravel().tolist()) - {-1} <= union
+    # the injections sit at chosen patches and their templates are kept
     for inj in ev.injections:
         near = np.nonzero(np.abs(pos - pos[inj.sky]) <= 16)[0]
         assert np.any(xt[near] == inj.template)
