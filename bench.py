@@ -57,7 +57,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
-    ap.add_argument("--no-amplitude", action="store_true", help="skip the amplitude and count variants")
+    ap.add_argument("--no-amplitude", action="store_true",
+                    help="skip the generated-bank, amplitude, count and two-bin variants")
     ap.add_argument("--batched-events", type=int, default=64)
     ap.add_argument("--batched-templates", type=int, default=20000)
     ap.add_argument("--learned-events", type=int, default=10)
@@ -466,7 +467,8 @@ def bench_ours(args):
     extras = {}
     if rank == 0 and world == 1 and args.workload == "full" and not args.no_amplitude:
         # the same search with the Eq. 3 amplitude weight (f(t_j)/f0)^4 on every
-        # lookup, and with the number count (rho > 1.6) in place of the power
+        # lookup, with the number count (rho > 1.6) in place of the power, and
+        # with two-bin lookups
         def variant(name, on, off, meta):
             try:
                 on()
@@ -533,6 +535,8 @@ def bench_ours(args):
                 lambda: s.set_option(tcw.OPT_AMPLITUDE_POWER, 0), {"amp_power": 4})
         variant("number_count", lambda: s.set_statistic(tcw.STAT_NUMBER_COUNT, 1.6),
                 lambda: s.set_statistic(tcw.STAT_POWER), {"rho_th": 1.6})
+        variant("two_bin", lambda: s.set_option(tcw.OPT_TRACK_BINS, 2),
+                lambda: s.set_option(tcw.OPT_TRACK_BINS, 1), {"track_bins": 2})
     if rank == 0 and world == 1 and args.workload == "full":
         for name, fn, skip in (("batched", bench_batched, args.no_batched),
                                ("learned", bench_learned, args.no_learned)):
