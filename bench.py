@@ -537,6 +537,49 @@ def bench_ours(args):
                 lambda: s.set_statistic(tcw.STAT_POWER), {"rho_th": 1.6})
         variant("two_bin", lambda: s.set_option(tcw.OPT_TRACK_BINS, 2),
                 lambda: s.set_option(tcw.OPT_TRACK_BINS, 1), {"track_bins": 2})
+
+        # the precision form: the same workload with the map stored in FP16
+        # (fp32 accumulation), and the change of S against the fp32 map on a
+        # 2048-template sample
+        try:
+            rho16 = p.rho.astype(np.float16)
+            s16 = tcw.Search(dev, stream=stream)
+            s16.load_spectrogram(rho16, p.f_min, p.df, p.t_mid, p.weights)
+            s16.load_velocity(p.velocity)
+            s16.define_bank(p.bank.f0, p.bank.tau, p.bank.n, p.T0)
+            s16.define_sky(p.nhat)
+            s16.search(k, psi_out, idx_out)
+            torch.cuda.synchronize()
+            h0 = torch.cuda.Event(enable_timing=True)
+            h1 = torch.cuda.Event(enable_timing=True)
+            n16 = max(1, min(3, args.steps))
+            h0.record(stream)
+            for _ in range(n16):
+                s16.search(k, psi_out, idx_out)
+            h1.record(stream)
+            torch.cuda.synchronize()
+            ms16 = h0.elapsed_time(h1) / n16
+            import tcw_synth as syn
+            sub = syn.rng(11).choice(len(p.bank), 2048, replace=False)
+            svals = []
+            for ctx in (s, s16):
+                ctx.set_option(tcw.OPT_KEEP_STATS, 1)
+                ctx.define_bank(p.bank.f0[sub], p.bank.tau[sub], p.bank.n[sub], p.T0)
+                ctx.search(k)
+                svals.append(ctx.statistics(("S",))["S"].astype(np.float64))
+                ctx.set_option(tcw.OPT_KEEP_STATS, 0)
+            s.define_bank(p.bank.f0, p.bank.tau, p.bank.n, p.T0)
+            s16.close()
+            ok = svals[0] > 0
+            rel = np.abs(svals[1] - svals[0])[ok] / svals[0][ok]
+            extras["fp16"] = {"value": U / (ms16 / 1000.0), "unit": UNIT, "ms_per_step": ms16, "steps": n16,
+                              "vs_plain": (U / (ms16 / 1000.0)) / value,
+                              "s_rel_change_vs_fp32_map": {"max": float(rel.max()),
+                                                           "rms": float(np.sqrt(np.mean(rel ** 2))),
+                                                           "sample": "2048 templates x all skies"}}
+        except Exception as exc:
+            extras["fp16"] = {"error": f"{type(exc).__name__}: {exc}"}
+        torch.cuda.empty_cache()
     if rank == 0 and world == 1 and args.workload == "full":
         for name, fn, skip in (("batched", bench_batched, args.no_batched),
                                ("learned", bench_learned, args.no_learned)):

@@ -121,6 +121,28 @@ def test_fp16_power_map():
     _check_all(p, tcw.KERNEL_GROUP, rho_for_oracle=widened)
 
 
+def test_fp16_storage_error_against_the_fp32_map():
+    """The FP16 form against the FP64 oracle on the unrounded fp32 map: bins stay
+    exact, and storing each power in half precision moves S by at most 2^-11 of
+    it (relative rounding of each positive term; tiny subnormal terms add at most
+    2^-25 each) plus the fp32 accumulation's 1e-5.  Reports max and RMS error."""
+    p = multi_problem(seed=38)
+    rho32 = p.rho
+    p16 = multi_problem(seed=38)
+    p16.rho = rho32.astype(np.float16)
+    s, val, idx, st, info = run(p16, kernel=tcw.KERNEL_GROUP)
+    ora = oracle_stats(p)                                  # fp32 map, FP64 arithmetic
+    S, oS = st["S"].astype(np.float64), ora[0]
+    n_look = p.rho.shape[0] * p.rho.shape[1]
+    bound = (2.0 ** -11 + 1e-5) * oS + n_look * 2.0 ** -25 * np.abs(p.weights).max() + 1e-6
+    err = np.abs(S - oS)
+    assert np.all(err <= bound)
+    rel = err[oS > 0] / oS[oS > 0]
+    print(f"fp16 storage: S relative error max {rel.max():.2e} rms {np.sqrt(np.mean(rel ** 2)):.2e} "
+          f"(2^-11 = {2.0 ** -11:.2e})")
+    assert np.sqrt(np.mean(rel ** 2)) < 2.0 ** -11
+
+
 def test_unit_weights_and_zero_weights():
     p = multi_problem(seed=34, weights=False)
     _check_all(p, tcw.KERNEL_GROUP)
