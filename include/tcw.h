@@ -78,7 +78,7 @@ enum {
     TCW_OPT_TILE_SEGMENTS = 3, /* segments per tile of the group kernel: the spacing of
                                   the FP64 track anchors and of the fp32 partial sums;
                                   a power of two in [8, 128], default 32 */
-    TCW_OPT_BANK_CHUNK = 4,    /* template groups of one pass (512/lanes sorted
+    TCW_OPT_BANK_CHUNK = 4,    /* template groups of one pass (1024/lanes sorted
                                   templates) per work item of the group kernel,
                                   in [1, 4096], default 1 */
     TCW_OPT_AUTOTUNE = 5,      /* batched search: 1 (default) = choose the bank chunk
@@ -88,7 +88,7 @@ enum {
     TCW_OPT_BATCH_MEMORY = 6,  /* batched search: bytes of Psi and anchor buffers per
                                   wave of events (default 48 GiB, minimum 1 MiB) */
     TCW_OPT_SKY_LANES = 7,     /* sky groups of 16 per chunk of the group kernel: 16,
-                                  32 or 64 (a pass covers 16*lanes skies x 512/lanes
+                                  32 or 64 (a pass covers 16*lanes skies x 1024/lanes
                                   templates); 0 (default) = the lowest cost for the
                                   sky count, the bank size and the SM count */
     TCW_OPT_TRIAGE_SPREAD = 8, /* triaged search: a chosen patch suppresses the patches
@@ -105,7 +105,7 @@ enum {
                                   Applies to tcw_search, tcw_search_batched and
                                   the exhaustive part of tcw_search_triaged */
     TCW_OPT_GEN_CHUNK = 10,    /* tcw_search_generated: templates per chunk, a multiple
-                                  of 32 in [32, 2^24] (default 2^18) */
+                                  of 64 in [64, 2^24] (default 2^18) */
     TCW_OPT_TRACK_BINS = 11,   /* bins per lookup: 1 (default) = the nearest bin, as
                                   in the paper; 2 = the two bins whose centres
                                   bracket the track, k = floor((fhat - f_min)/df)

@@ -320,10 +320,9 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
       TCW_CUDA(c, launch_anchors(ap, c->stream), "anchor_kernel launch");
       ++launches;
     }
-    const int wt = c->amp_power > 0 ? kAmplitudeWeights : (c->unit_weights ? kUnitWeights : kSegmentWeights);
     // counts and two-bin sums are staged as fp32 windows whatever the map's type
     const bool half = c->dtype == TCW_F16 && !count && c->track_bins == 1;
-    TCW_CUDA(c, launch_group(gp, c->grid, half, record, wt, c->stream),
+    TCW_CUDA(c, launch_group(gp, c->grid, half, record, c->stream),
              "group_kernel launch");
     TCW_CUDA(c, cudaEventRecord(c->ev1, c->stream), "event");
     ++launches;
@@ -618,8 +617,8 @@ tcw_status tcw_set_option(tcw_ctx* c, int option, int64_t value) {
       c->track_bins = (int)value;
       return TCW_OK;
     case TCW_OPT_GEN_CHUNK:
-      if (value < 32 || value > ((int64_t)1 << 24) || value % kBankAlign)
-        return fail(c, TCW_ERR_INVALID_ARGUMENT, "gen_chunk must be a multiple of 32 in [32, 2^24]");
+      if (value < kBankAlign || value > ((int64_t)1 << 24) || value % kBankAlign)
+        return fail(c, TCW_ERR_INVALID_ARGUMENT, "gen_chunk must be a multiple of 64 in [64, 2^24]");
       c->gen_chunk = (int)value;
       return TCW_OK;
     case TCW_OPT_AMPLITUDE_POWER:

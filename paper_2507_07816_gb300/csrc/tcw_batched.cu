@@ -280,10 +280,6 @@ void wave_items(const tcw_ctx* c, const BatchState* b, int w, int bank_chunk, in
   schedule_items(items, cost, b->grid, order, cta);
 }
 
-int weighting(const tcw_ctx* c, const BatchState* b) {
-  return c->amp_power > 0 ? kAmplitudeWeights : (b->unit_weights ? kUnitWeights : kSegmentWeights);
-}
-
 GroupParams base_params(const tcw_ctx* c, BatchState* b, int tile, int nterms) {
   GroupParams gp{};
   gp.events = b->evtab.as<EventDesc>();
@@ -417,7 +413,7 @@ tcw_status autotune(tcw_ctx* c, BatchState* b) {
         cudaEventRecord(e0, c->stream);
         for (int w = 0; w < b->waves; ++w) {
           const GroupParams gp = wave_params(c, b, w, tile, nterms);
-          cudaError_t err = launch_group(gp, b->grid, half_windows(c, b), false, weighting(c, b), c->stream);
+          cudaError_t err = launch_group(gp, b->grid, half_windows(c, b), false, c->stream);
           if (err != cudaSuccess) {
             st = cuda_fail(c, err, "group_kernel launch");
             break;
@@ -465,7 +461,7 @@ tcw_status capture(tcw_ctx* c, BatchState* b, int k) {
   if ((st = upload_items(c, b, b->bank_chunk, INT32_MAX, &sums)) != TCW_OK) return st;
   TCW_CUDA(c, b->out_psi.ensure((size_t)b->total_sky * k * sizeof(float)), "output");
   TCW_CUDA(c, b->out_idx.ensure((size_t)b->total_sky * k * sizeof(int64_t)), "output");
-  TCW_CUDA(c, group_prepare(b->D, b->lanes, half_windows(c, b), weighting(c, b),
+  TCW_CUDA(c, group_prepare(b->D, b->lanes, half_windows(c, b),
                             c->statistic == TCW_STAT_NUMBER_COUNT || c->track_bins == 2), "group_kernel attributes");
   TCW_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "graph capture");
   cudaError_t err = cudaMemsetAsync(b->flags.p, 0, 64, c->stream);
@@ -494,7 +490,7 @@ tcw_status capture(tcw_ctx* c, BatchState* b, int k) {
     }
     if (err != cudaSuccess) break;
     const GroupParams gp = wave_params(c, b, w, b->tile, nterms);
-    err = launch_group(gp, b->grid, half_windows(c, b), false, weighting(c, b), c->stream);
+    err = launch_group(gp, b->grid, half_windows(c, b), false, c->stream);
     ++nodes;
     for (const EventHost& e : b->ev) {
       if (e.wave != w || err != cudaSuccess) continue;

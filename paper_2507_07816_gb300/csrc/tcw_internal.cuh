@@ -39,7 +39,7 @@ constexpr int kMLo = -4;
 constexpr int kMHi = 4;
 constexpr int kNThr = kMHi - kMLo;  // 8 thresholds
 
-// Precomputed per (template, segment): 80 bytes, lives in shared memory.
+// Precomputed per (template, segment): 96 bytes, lives in shared memory.
 //   F, Cm  fp32 estimates that choose the candidate bin pair: for a sky group
 //          whose mean Doppler factor is g, the pair starts at
 //          base + n0 with n0 = round(F*g + Cm)   (Cm = (f - f_min)/df - base - 1/2),
@@ -47,24 +47,28 @@ constexpr int kNThr = kMHi - kMLo;  // 8 thresholds
 //   tha    shared address of th[] minus 4*(kMagicBits + kMLo): threshold of
 //          the pair is at tha + 4*zb
 //   cls    kEntryNone / kEntryInside / kEntryEdge
-//   wa[d]  shared address of detector d's staged power window minus
-//          elem*(kMagicBits + woff_d): power of bin base + n0 is at wa[d] + elem*zb
-//          (d < kMaxStageDet = 2); wa[kAmpSlot] holds the fp32 bits of the
-//          template's amplitude weight (f(t_j)/f0)^p of Eq. 3 (1 when p = 0)
+//   wa[d], wf[d]  group-uniform path: window address (power of bin base + n0
+//          at wa[d] + elem*zb) and weight; for entries that are not wholly in
+//          the band wa points at a zero window and wf = 0
 //   kb     base - kMagicBits, so that base + n0 = kb + zb
+//   xa[d], we[d]  per-sky path: the staged power window of detector d and the
+//          lookup weight w_{d,j} (f(t_j)/f0)^p (Eq. 3 factor, 1 when p = 0)
 //   th[i]  round((c_K/f - 1)/q) with c_K = f_min + (K + 1/2) df, K = base + kMLo + i
 struct __align__(16) TrackEntry {
   float F;
   float Cm;
   uint32_t tha;
   int cls;
-  uint32_t wa[4];
+  uint32_t wa[2];
+  float wf[2];
   int kb;
-  int pad[3];
+  uint32_t xa[2];
+  int pad0;
+  float we[2];
+  float pad1[2];
   int th[kNThr];
 };
-
-constexpr int kAmpSlot = 2;      // wa[] word of the amplitude weight
+static_assert(sizeof(TrackEntry) == 96, "track entry layout");
 
 constexpr int kEntryNone = 0;    // segment before T0, or every candidate bin outside the band
 constexpr int kEntryInside = 1;  // every candidate bin inside the band
@@ -118,7 +122,7 @@ struct GroupParams {
   int map_half;            // the events' maps are fp16 (read by the two-bin producers)
   int B, Bpad;
   int lanes;               // sky groups per chunk: 16, 32 or 64
-  float2* dev;             // scratch [gridDim.x][8192]: per-sky weight sums at band edges
+  float2* dev;             // scratch [gridDim.x][kPassUnits * 16]: per-sky weight sums at band edges
   int32_t* rec;            // optional [S][B][D][Nseg], caller order (single-event searches)
   const int32_t* bank_perm;  // sorted -> caller template index
   const int32_t* sky_perm;   // sorted -> caller sky index (event 0)
@@ -166,10 +170,11 @@ struct LookupParams {
 
 // One Doppler block per (sky chunk of 16 L sorted skies, segment, detector),
 // L = lanes (sky groups) per chunk:
-//   words [0, 16 L): floor(v.nhat/c / q) of sky 16 g + 4 v + k at (v L + g) * 4 + k
-//   words [16 L, 17 L): fp32 mid-range of v.nhat/c over sky group g (bits)
+//   words [0, 16 L): floor(v.nhat/c / q) of sky 16 g + k at 16 g + k
+//   words [16 L + 4 g, 16 L + 4 g + 4): sky group g's fp32 mid-range of v.nhat/c
+//                    (bits), the smallest and the largest of its 16 grid values, 0
 // so that one bulk copy moves a chunk's segment for every detector.
-__host__ __device__ constexpr int block_words(int lanes) { return 17 * lanes; }
+__host__ __device__ constexpr int block_words(int lanes) { return 20 * lanes; }
 
 struct DopplerParams {
   const double* vel;       // [D][Nseg][3]
@@ -181,9 +186,8 @@ struct DopplerParams {
   unsigned* spread_max;    // float bits of max (hi - lo) of v.nhat/c over the groups
 };
 
-constexpr int kMaxSeriesTerms = 24;
+constexpr int kMaxSeriesTerms = 20;   // longest track series (more: pow per entry)
 constexpr int kMaxStageDet = 2;          // detectors the group kernel stages in shared memory
-static_assert(kAmpSlot >= kMaxStageDet && kAmpSlot < 4, "the amplitude word is a free wa[] slot");
 constexpr int kTileShift = 5;           // default tile: 32 segments
 
 // dynamic shared memory of the group kernel for D detectors
@@ -284,14 +288,12 @@ inline int ilog2(int v) {
 cudaError_t launch_doppler(const DopplerParams& p, cudaStream_t st);
 // Set the shared-memory attribute of the group-kernel variant (also done by
 // launch_group on first use); call before capturing a launch into a graph.
-// Weighting of the group kernel's lookups: unit weights, the per-segment
-// weights, or the weights times the template's amplitude weight.
-enum Weighting { kUnitWeights = 0, kSegmentWeights = 1, kAmplitudeWeights = 2 };
 // pw: windows built by the producer (number count or two-bin lookups; fp32 only).
-cudaError_t group_prepare(int n_det, int lanes, bool half, int weighting, bool pw);
-// grid = number of CTAs (the length of p.cta_items minus one); one CTA per SM at most
-cudaError_t launch_group(const GroupParams& p, int grid, bool half, bool record, int weighting,
-                         cudaStream_t st);
+cudaError_t group_prepare(int n_det, int lanes, bool half, bool pw);
+// grid = number of CTAs (the length of p.cta_items minus one); one CTA per SM at most.
+// Every lookup is weighted by p.events[].weights (times the amplitude factor
+// when p.amp_power > 0).
+cudaError_t launch_group(const GroupParams& p, int grid, bool half, bool record, cudaStream_t st);
 cudaError_t launch_lookup(const LookupParams& p, bool half, bool record, cudaStream_t st);
 // A generated template bank (tcw_bank_spec on the device).
 struct BankGenParams {
@@ -324,11 +326,12 @@ cudaError_t launch_unpermute(const float* src, int Spad, int Bpad, int S, int B,
 
 // group-kernel geometry (shared by the host planner and the kernels): a sky
 // chunk is `lanes` groups of kGroupSkies sorted skies (lanes = 16, 32 or 64),
-// and one pass of the kernel covers one chunk x 512 / lanes templates.
-constexpr int kGroupSkies = 16;     // skies per thread
-constexpr int kBankAlign = 32;      // Bpad is a multiple of every pass's template count
+// and one pass of the kernel covers one chunk x 1024 / lanes templates.
+constexpr int kGroupSkies = 16;     // skies of one sky group
+constexpr int kPassUnits = 1024;    // (template, sky group) units of one pass of the group kernel
+constexpr int kBankAlign = 64;      // Bpad is a multiple of every pass's template count
 __host__ __device__ constexpr int chunk_skies(int lanes) { return kGroupSkies * lanes; }
-__host__ __device__ constexpr int pass_templates(int lanes) { return 512 / lanes; }
+__host__ __device__ constexpr int pass_templates(int lanes) { return kPassUnits / lanes; }
 inline int padded_skies(int64_t S, int lanes) {
   const int64_t ng = (S + kGroupSkies - 1) / kGroupSkies;
   return (int)((ng + lanes - 1) / lanes) * chunk_skies(lanes);
@@ -345,7 +348,7 @@ inline int choose_lanes(int64_t S) {
   return best;
 }
 // With the bank and the grid known: a work item is one chunk (16 L skies) x
-// bank_chunk passes of 512 / L templates, 8192 padded sky-templates per pass
+// bank_chunk passes of 1024 / L templates, 16384 padded sky-templates per pass
 // whatever L, so the search takes ceil(items / grid) rounds of items costing
 // lanes_cost(L) each.  Few templates give few items at narrow chunks, and a
 // wider chunk can then fill more SMs.
@@ -355,7 +358,7 @@ inline int choose_lanes(int64_t S, int64_t B, int bank_chunk, int grid) {
   double best_cost = 0;
   for (int l : {64, 32, 16}) {
     const int64_t chunks = padded_skies(S, l) / (16 * l);
-    const int64_t groups = (B + 512 / l - 1) / (512 / l);
+    const int64_t groups = (B + pass_templates(l) - 1) / pass_templates(l);
     const int64_t items = chunks * ((groups + bank_chunk - 1) / bank_chunk);
     const double cost = (double)((items + grid - 1) / grid) * bank_chunk * lanes_cost(l);
     if (best == 0 || cost < best_cost) {

@@ -297,7 +297,7 @@ extern "C" tcw_status tcw_search_noalloc(int n_det, int64_t n_seg, int64_t n_bin
     gp.sky_perm = pp.sky_perm;
     gp.n_general = ngen;
     gp.err = err;
-    if (launch_group(gp, grid, dtype == TCW_F16, false, kSegmentWeights, st) != cudaSuccess) return TCW_ERR_CUDA;
+    if (launch_group(gp, grid, dtype == TCW_F16, false, st) != cudaSuccess) return TCW_ERR_CUDA;
   } else {
     // sky groups too wide for one candidate pair: per-lookup FP64 kernel
     LookupParams lp{};

@@ -31,7 +31,7 @@ __global__ void anchor_kernel(AnchorParams p) {
 
 
 size_t group_smem_bytes(int n_det, int lanes) { return PersistLayout(n_det, lanes).total; }
-size_t group_dev_elems(int grid) { return (size_t)grid * 2 * kConsumers * kGroupSkies; }
+size_t group_dev_elems(int grid) { return (size_t)grid * kPassUnits * kGroupSkies; }
 
 cudaError_t group_grid(int* grid) {
   int dev = 0, sms = 0;
@@ -101,24 +101,22 @@ cudaError_t launch_anchors(const AnchorParams& p, cudaStream_t st) {
 // Windows built by the producer (fp32): the number count and two-bin lookups.
 bool producer_windows(const GroupParams& p) { return p.nc_q > 0.0 || p.track_bins == 2; }
 
-cudaError_t group_prepare(int n_det, int lanes, bool half, int weighting, bool pw) {
+cudaError_t group_prepare(int n_det, int lanes, bool half, bool pw) {
   if (n_det < 1 || n_det > kMaxStageDet) return cudaErrorInvalidValue;
   if (pw && half) return cudaErrorInvalidValue;
-  if (half) return prepare_group_f16(n_det, lanes, weighting);
-  return pw ? prepare_group_pw(n_det, lanes, weighting) : prepare_group_f32(n_det, lanes, weighting);
+  if (half) return prepare_group_f16(n_det, lanes);
+  return pw ? prepare_group_pw(n_det, lanes) : prepare_group_f32(n_det, lanes);
 }
 
 // Needs 1 <= p.n_det <= kMaxStageDet, p.lanes in {16, 32, 64}, and the
 // anchors of launch_anchors when p.nterms > 0.
-cudaError_t launch_group(const GroupParams& p, int grid, bool half, bool record, int weighting,
-                         cudaStream_t st) {
+cudaError_t launch_group(const GroupParams& p, int grid, bool half, bool record, cudaStream_t st) {
   if (p.n_det < 1 || p.n_det > kMaxStageDet) return cudaErrorInvalidValue;
   const bool pw = producer_windows(p);
   if (pw && half) return cudaErrorInvalidValue;   // counts and pair sums are staged as fp32 windows
-  if (p.amp_power > 0 && weighting != kAmplitudeWeights && !record) return cudaErrorInvalidValue;
   if (grid <= 0) return cudaSuccess;
-  if (half) return launch_group_f16(p, record, weighting, grid, st);
-  return pw ? launch_group_pw(p, record, weighting, grid, st) : launch_group_f32(p, record, weighting, grid, st);
+  if (half) return launch_group_f16(p, record, grid, st);
+  return pw ? launch_group_pw(p, record, grid, st) : launch_group_f32(p, record, grid, st);
 }
 
 }  // namespace tcw

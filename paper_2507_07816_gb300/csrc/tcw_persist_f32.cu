@@ -3,10 +3,10 @@
 
 namespace tcw {
 
-cudaError_t launch_group_f32(const GroupParams& p, bool record, int wt, int grid, cudaStream_t st) {
-  return launch_group_r<float, false>(p, record, wt, grid, st);
+cudaError_t launch_group_f32(const GroupParams& p, bool record, int grid, cudaStream_t st) {
+  return launch_group_r<float, false>(p, record, grid, st);
 }
 
-cudaError_t prepare_group_f32(int n_det, int lanes, int wt) { return prepare_r<float, false>(n_det, lanes, wt); }
+cudaError_t prepare_group_f32(int n_det, int lanes) { return prepare_r<float, false>(n_det, lanes); }
 
 }  // namespace tcw

@@ -1,6 +1,6 @@
 // tcw_ptx.cuh -- inline-PTX helpers shared by the search kernels: mbarriers,
-// bulk and per-thread asynchronous copies into shared memory, shared loads by
-// 32-bit address, and the predicated accumulate of the inner loop.
+// bulk and per-thread asynchronous copies into shared memory, shared loads,
+// stores and reductions by 32-bit address.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -83,10 +83,22 @@ __device__ __forceinline__ float4 lds_f4(uint32_t a) {
                : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(a));
   return v;
 }
-// acc += dw when q >= th: one compare and one predicated add per lookup
-__device__ __forceinline__ void pred_add(float& acc, int q, int th, float dw) {
-  asm("{\n\t.reg .pred p;\n\tsetp.ge.s32 p, %1, %2;\n\t@p add.f32 %0, %0, %3;\n\t}"
-      : "+f"(acc) : "r"(q), "r"(th), "f"(dw));
+// *a += v in shared memory (a reduction: no value returned).  No memory
+// clobber, so that plain shared loads may be scheduled around it; callers
+// put a compiler barrier before anything that reads the sums back.
+__device__ __forceinline__ void red_add_shared(uint32_t a, float v) {
+  asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(a), "f"(v));
+}
+__device__ __forceinline__ void sts_v4(uint32_t a, int x, int y, int z, int w) {
+  asm volatile("st.shared.v4.s32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(x), "r"(y), "r"(z), "r"(w) : "memory");
+}
+// Not a compiler memory barrier: only for stores read back after a later
+// barrier or by asm loads (volatile asm statements keep their order).
+__device__ __forceinline__ void sts_v4_nc(uint32_t a, int x, int y, int z, int w) {
+  asm volatile("st.shared.v4.s32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(x), "r"(y), "r"(z), "r"(w));
+}
+__device__ __forceinline__ void sts_u32(uint32_t a, uint32_t v) {
+  asm volatile("st.shared.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
 }
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {

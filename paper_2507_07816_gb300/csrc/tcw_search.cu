@@ -21,16 +21,17 @@ __device__ __forceinline__ float load_rho(const __half* row, int64_t k) {
 
 // ---------------------------------------------------------------------------
 // Doppler tables (Eq. 2): one thread per (detector, segment, sorted sky).
-// Sky groups are `group` consecutive sorted skies; group is a power of two
-// <= 32 and Spad is a multiple of 32, so a group never straddles a warp.
-// Writes floor(v.nhat/c / q) per sky, the fp32 mid-range of v.nhat/c per group
-// and the largest group range (one atomic per block).
+// Sky groups are `group` = 16 consecutive sorted skies; Spad is a multiple of
+// 32, so a group never straddles a warp.  Writes floor(v.nhat/c / q) per sky
+// and, per group, the fp32 mid-range of v.nhat/c with the smallest and largest
+// grid value of its skies, plus the largest group range (one atomic per block).
 // ---------------------------------------------------------------------------
 __global__ void doppler_kernel(DopplerParams p) {
   __shared__ float s_red[32];
   const int64_t total = (int64_t)p.n_det * p.n_seg * p.Spad;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   float spread = 0.f;
+  // every lane of a warp runs the same number of iterations (total is a multiple of 32)
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
     const int s = (int)(i % p.Spad);
     const int64_t dj = i / p.Spad;
@@ -40,16 +41,21 @@ __global__ void doppler_kernel(DopplerParams p) {
     const double dD = (v[0] * n[0] + v[1] * n[1] + v[2] * n[2]) / kLightSpeed;
     const double qd = floor(dD * p.inv_q);
     const int L = p.lanes;
-    const int c = s / chunk_skies(L), gl = (s >> 4) & (L - 1), sv = (s >> 2) & 3, sk = s & 3;
+    const int c = s / chunk_skies(L), sl = s % chunk_skies(L), gl = sl / kGroupSkies;
     int32_t* blk = p.blk + (((int64_t)c * p.n_seg + j) * p.n_det + d) * block_words(L);
-    blk[(sv * L + gl) * 4 + sk] = (int32_t)fmax(fmin(qd, 2147483647.0), -2147483648.0);
+    const int qi = (int32_t)fmax(fmin(qd, 2147483647.0), -2147483648.0);
+    blk[sl] = qi;
     float lo = (float)dD, hi = lo;
+    int qlo = qi, qhi = qi;
     for (int off = 1; off < p.group; off <<= 1) {
       lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, off));
       hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, off));
+      qlo = min(qlo, __shfl_xor_sync(0xffffffffu, qlo, off));
+      qhi = max(qhi, __shfl_xor_sync(0xffffffffu, qhi, off));
     }
     if (s % p.group == 0) {
-      blk[16 * L + gl] = __float_as_int(0.5f * (lo + hi));
+      int4* gi = reinterpret_cast<int4*>(blk + kGroupSkies * L) + gl;
+      *gi = make_int4(__float_as_int(0.5f * (lo + hi)), qlo, qhi, 0);
       if (s / p.group < p.NG) spread = fmaxf(spread, hi - lo);
     }
   }

@@ -80,7 +80,7 @@ def test_invalid_specs_and_ranges():
     with pytest.raises(tcw.TcwError):
         s.generate_bank_at(sp, [0, 100])
     with pytest.raises(tcw.TcwError):
-        s.set_option(tcw.OPT_GEN_CHUNK, 100)      # not a multiple of 32
+        s.set_option(tcw.OPT_GEN_CHUNK, 96)       # not a multiple of 64
     s.close()
 
 
