@@ -41,6 +41,7 @@
 #include <cmath>
 #include <numeric>
 #include <queue>
+#include <type_traits>
 
 #include "tcw_internal.cuh"
 #include "tcw_ptx.cuh"
@@ -146,9 +147,9 @@ __device__ __forceinline__ float rho_at(const unsigned char* p) {
 // so no sky group is mixed), so the consumers can read them unconditionally.
 // Written as 16-byte vectors (entries lie 96 bytes apart, so field-wise stores
 // of a warp would conflict in the shared-memory banks).
-__device__ __forceinline__ void set_none(TrackEntry& e, uint32_t zero_wa) {
+__device__ __forceinline__ void set_none(TrackEntry& e, uint32_t zero_wa, uint32_t smem0) {
   const uint32_t a = smem_addr(&e);
-  const uint32_t tha = a + (uint32_t)offsetof(TrackEntry, th) - 4u * (uint32_t)(kMagicBits + kMLo);
+  const uint32_t tha = a - smem0 + (uint32_t)offsetof(TrackEntry, th) - 4u * (uint32_t)(kMagicBits + kMLo);
   sts_v4(a, 0, 0, (int)tha, kEntryNone);                      // F, Cm, tha, cls
   sts_v4(a + 16, (int)zero_wa, (int)zero_wa, 0, 0);           // wa, wf
   sts_v4(a + 32, -kMagicBits, (int)zero_wa, (int)zero_wa, 0);  // kb, xa
@@ -217,9 +218,10 @@ __device__ __forceinline__ EntryPrep prepare_entry(const GroupParams& p, const E
 // entry's detectors when every candidate bin is in the band, else 0.
 template <typename RhoT, bool PW>
 __device__ __forceinline__ float2 store_entry(const GroupParams& p, const EventDesc& ev, const EntryPrep& r, int j,
-                                              int D, bool two, TrackEntry& e, uint32_t win_dst, uint32_t zero_wa) {
+                                              int D, bool two, TrackEntry& e, uint32_t win_dst, uint32_t zero_wa,
+                                              uint32_t smem0) {
   if (r.base == INT_MIN) {
-    set_none(e, zero_wa);
+    set_none(e, zero_wa, smem0);
     return make_float2(0.f, 0.f);
   }
   const int base = r.base;
@@ -235,7 +237,7 @@ __device__ __forceinline__ float2 store_entry(const GroupParams& p, const EventD
   }
   sts_v4(ea + 64, th[0], th[1], th[2], th[3]);
   sts_v4(ea + 80, th[4], th[5], th[6], th[7]);
-  const uint32_t tha = ea + (uint32_t)offsetof(TrackEntry, th) - 4u * (uint32_t)(kMagicBits + kMLo);
+  const uint32_t tha = ea - smem0 + (uint32_t)offsetof(TrackEntry, th) - 4u * (uint32_t)(kMagicBits + kMLo);
   sts_v4(ea, __float_as_int(r.F), __float_as_int(r.Cm), (int)tha, inside ? kEntryInside : kEntryEdge);
   uint32_t xa[kMaxStageDet] = {zero_wa, zero_wa};
   if constexpr (PW) {
@@ -276,7 +278,7 @@ __device__ __forceinline__ float2 store_entry(const GroupParams& p, const EventD
         for (int i = 0; i < kWinBytes / 4; ++i) v[i] += v[i + 1];
       }
       const uint32_t dst = win_dst + d * kWinBytes;
-      xa[d] = dst - 4u * (uint32_t)(kMagicBits + kMLo);
+      xa[d] = dst - smem0 - 4u * (uint32_t)(kMagicBits + kMLo);
 #pragma unroll
       for (int c = 0; c < kWinBytes / 16; ++c) sts_f4(dst + 16 * c, v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
     }
@@ -294,7 +296,7 @@ __device__ __forceinline__ float2 store_entry(const GroupParams& p, const EventD
       gs = gs < 0 ? 0 : (gs > ev.total_elems - W ? ev.total_elems - W : gs);
       const int woff = (int)(gs - row - base);
       const uint32_t dst = win_dst + d * kWinBytes;
-      xa[d] = dst - (uint32_t)sizeof(RhoT) * (uint32_t)(kMagicBits + woff);
+      xa[d] = dst - smem0 - (uint32_t)sizeof(RhoT) * (uint32_t)(kMagicBits + woff);
       const char* src = reinterpret_cast<const char*>(rho + gs);
 #pragma unroll
       for (int c = 0; c < kWinBytes / 16; ++c) cp_async16(dst + 16 * c, src + 16 * c);
@@ -325,7 +327,7 @@ __global__ void __launch_bounds__(Geo<LN>::kThreads, 1) group_kernel(GroupParams
   const uint32_t diff0 = smem0 + (uint32_t)L.diff;
   // zero window: entries without in-band candidates read bin offset n0 + {0, 1},
   // |n0| <= 5, around its middle
-  const uint32_t zero_wa = smem0 + (uint32_t)L.zero + 8u * ESZ - ESZ * (uint32_t)kMagicBits;
+  const uint32_t zero_wa = (uint32_t)L.zero + 8u * ESZ - ESZ * (uint32_t)kMagicBits;
   const int tid = threadIdx.x, lane = tid & 31;
   const uint32_t dq_seg = (uint32_t)(D * kBlockBytes);   // Doppler bytes of one segment
   const int it0 = p.cta_items[blockIdx.x], it1 = p.cta_items[blockIdx.x + 1];
@@ -416,7 +418,7 @@ __global__ void __launch_bounds__(Geo<LN>::kThreads, 1) group_kernel(GroupParams
               TrackEntry& e = *reinterpret_cast<TrackEntry*>(st + L.ent + slot * sizeof(TrackEntry));
               const float2 w = store_entry<RhoT, PW>(
                   p, ev, pr[r], jb + lk, D, two, e,
-                  smem0 + s * (uint32_t)L.stage + (uint32_t)L.win + slot * D * kWinBytes, zero_wa);
+                  smem0 + s * (uint32_t)L.stage + (uint32_t)L.win + slot * D * kWinBytes, zero_wa, smem0);
               ws[r % kSums].x += w.x;
               ws[r % kSums].y += w.y;
             }
@@ -510,9 +512,10 @@ __global__ void __launch_bounds__(Geo<LN>::kThreads, 1) group_kernel(GroupParams
         // entry with the threshold and the difference w (rho_hi - rho_lo) that
         // the skies at or above it add to their own sums (the group-wide sum
         // took rho_lo)
-#pragma unroll
-        for (int kseg = 0; kseg < kBatch; ++kseg) {
-          if (kseg > 0 && kseg >= nb) break;
+        // one segment of the stage; EDGES: the warp has band-edge entries (or
+        // records bins) in it, so the band-edge logic is compiled in
+        auto segment = [&](const int kseg, auto edges_tag) {
+          constexpr bool EDGES = decltype(edges_tag)::value;
           const unsigned char* const ep = st + L.ent + (kseg * kPT + kUT * u) * sizeof(TrackEntry);
           float4 h[kUT];   // F, Cm, tha, cls
           int4 v[kUT];     // wa0, wa1, wf0, wf1
@@ -530,13 +533,13 @@ __global__ void __launch_bounds__(Geo<LN>::kThreads, 1) group_kernel(GroupParams
             const uint32_t qa = smem0 + so + (uint32_t)((kseg * D + d) * kBlockBytes) + 4u * (uint32_t)(G * l);
 #pragma unroll
             for (int t = 0; t < kUT; ++t) {
-              const bool edge = __float_as_int(h[t].w) == kEntryEdge;
+              const bool edge = EDGES && __float_as_int(h[t].w) == kEntryEdge;
               const int zb = __float_as_int(fmaf(h[t].x, gm, h[t].y) + kMagic);
-              const int th = *reinterpret_cast<const int*>(smem + (__float_as_uint(h[t].z) + 4u * (uint32_t)zb - smem0));
+              const int th = *reinterpret_cast<const int*>(smem + (__float_as_uint(h[t].z) + 4u * (uint32_t)zb));
               const bool up = gi.y >= th;            // every sky of the group above the boundary
               const bool down = !(gi.z >= th);       // every sky below it
               // window at bin base + n0 of the candidate pair
-              const unsigned char* const wp = smem + ((uint32_t)(d == 0 ? v[t].x : v[t].y) + ESZ * (uint32_t)zb - smem0);
+              const unsigned char* const wp = smem + ((uint32_t)(d == 0 ? v[t].x : v[t].y) + ESZ * (uint32_t)zb);
               const float wf = __int_as_float(d == 0 ? v[t].z : v[t].w);
               const float rl = rho_at<RhoT>(wp), rh = rho_at<RhoT>(wp + ESZ);
               bs[t] = fmaf(wf, up ? rh : rl, bs[t]);
@@ -546,7 +549,7 @@ __global__ void __launch_bounds__(Geo<LN>::kThreads, 1) group_kernel(GroupParams
               // or none does, the unit stays group-wide (its weight sums in eg1, eg2)
               bool vlo = true, vhi = true;
               const unsigned char* const et = ep + t * sizeof(TrackEntry);
-              if (edge) {
+              if (EDGES && edge) {
                 const int K0 = *reinterpret_cast<const int*>(et + 32) + zb;
                 vlo = (unsigned)K0 < (unsigned)p.n_bin;
                 vhi = (unsigned)(K0 + 1) < (unsigned)p.n_bin;
@@ -565,7 +568,7 @@ __global__ void __launch_bounds__(Geo<LN>::kThreads, 1) group_kernel(GroupParams
               const int pos = cnt + __popc(m & lt_mask);
               cnt += __popc(m);
               const bool queued = mine && pos < kQueueCap;
-              if (edge) {
+              if (EDGES && edge) {
                 // per sky (every sky of the unit, its group-wide part not added): recording,
                 // a mixed group with one valid candidate, a mixed group without a queue place
                 if (RECORD || (!up && !down && vlo != vhi) || (mine && !queued)) {
@@ -579,7 +582,7 @@ __global__ void __launch_bounds__(Geo<LN>::kThreads, 1) group_kernel(GroupParams
                 } else if (up ? vhi : (down ? vlo : (vlo && vhi))) {
                   const float w = *reinterpret_cast<const float*>(et + 48 + 4 * d);
                   const unsigned char* const wpx =
-                      smem + (*reinterpret_cast<const uint32_t*>(et + 36 + 4 * d) + ESZ * (uint32_t)zb - smem0);
+                      smem + (*reinterpret_cast<const uint32_t*>(et + 36 + 4 * d) + ESZ * (uint32_t)zb);
                   const float rlx = rho_at<RhoT>(wpx), rhx = rho_at<RhoT>(wpx + ESZ);
                   bs[t] = fmaf(w, up ? rhx : rlx, bs[t]);
                   eg1[t] += w;
@@ -595,6 +598,19 @@ __global__ void __launch_bounds__(Geo<LN>::kThreads, 1) group_kernel(GroupParams
                           (int)(diff0 + 4u * (uint32_t)((kUT * u + t) * kChunk + G * l)));
             }
           }
+        };
+#pragma unroll
+        for (int kseg = 0; kseg < kBatch; ++kseg) {
+          if (kseg > 0 && kseg >= nb) break;
+          bool e = RECORD;
+#pragma unroll
+          for (int t = 0; t < kUT; ++t)
+            e = e || *reinterpret_cast<const int*>(st + L.ent + (kseg * kPT + kUT * u + t) * sizeof(TrackEntry) + 12) ==
+                         kEntryEdge;
+          if (__any_sync(kFull, e))
+            segment(kseg, std::true_type{});
+          else
+            segment(kseg, std::false_type{});
         }
         const int nq = min(cnt, kQueueCap);
         // phase B: the queued mixed units, one per half-warp, one sky per lane
@@ -646,11 +662,11 @@ __global__ void __launch_bounds__(Geo<LN>::kThreads, 1) group_kernel(GroupParams
           const unsigned char* const bp = st + (ksx * D + dx) * kBlockBytes;
           const int4 gi = *reinterpret_cast<const int4*>(bp + 4 * (G * LN + 4 * lx));
           const int zb = __float_as_int(fmaf(hx.x, __int_as_float(gi.x), hx.y) + kMagic);
-          const int th = *reinterpret_cast<const int*>(smem + (__float_as_uint(hx.z) + 4u * (uint32_t)zb - smem0));
+          const int th = *reinterpret_cast<const int*>(smem + (__float_as_uint(hx.z) + 4u * (uint32_t)zb));
           const int sl = G * lx + (lane & 15);     // sky in the chunk
           const bool up = *reinterpret_cast<const int*>(bp + 4 * sl) >= th;
           const int cls = __float_as_int(hx.w);
-          const unsigned char* const wp = smem + ((uint32_t)(dx ? v2.z : v2.y) + ESZ * (uint32_t)zb - smem0);
+          const unsigned char* const wp = smem + ((uint32_t)(dx ? v2.z : v2.y) + ESZ * (uint32_t)zb);
           const float we = dx ? v3.y : v3.x;
           const int K0 = v2.x + zb;
           int rbin = -1;

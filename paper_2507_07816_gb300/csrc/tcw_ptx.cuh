@@ -11,7 +11,9 @@ namespace tcw {
 // ---------------------------------------------------------------------------
 // Shared-memory staging: mbarriers and bulk asynchronous copies (PTX).
 // ---------------------------------------------------------------------------
-constexpr int kMaxSpin = 1 << 26;              // bound on every mbarrier wait
+constexpr int kMaxSpin = 1 << 24;              // bound on the polls of every mbarrier wait
+constexpr unsigned long long kWaitLimitNs = 4000000000ull;   // and on its duration (4 s)
+constexpr unsigned kSuspendNs = 20000;         // a poll may suspend the thread for up to 20 us
 constexpr int kWinBytes = 64;                  // staged power window per (entry, detector)
 
 __device__ __forceinline__ uint32_t smem_addr(const void* ptr) {
@@ -35,10 +37,31 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
       : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
   return ok != 0;
 }
-// Bounded wait: false (and bit 1 of *err) when the phase never completes.
+// try_wait that lets the hardware suspend the thread until the phase
+// completes or kSuspendNs pass, so that long waits issue few instructions.
+__device__ __forceinline__ bool mbar_try_wait_suspend(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok) : "r"(bar), "r"(parity), "n"(kSuspendNs) : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Bounded wait: false (and bit 1 of *err) when the phase does not complete
+// within kWaitLimitNs (or kMaxSpin polls).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
-  for (int it = 0; it < kMaxSpin; ++it)
-    if (mbar_try_wait(bar, parity)) return true;
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (int it = 0; it < kMaxSpin; ++it) {
+    if (mbar_try_wait_suspend(bar, parity)) return true;
+    if (global_ns() - t0 > kWaitLimitNs) break;
+  }
   atomicOr(err, 2);
   return false;
 }
