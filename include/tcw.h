@@ -122,7 +122,10 @@ enum {
                                   the templates with the highest coarse Psi at that
                                   patch's representative sky; the union over the
                                   chosen patches is searched at all their skies.
-                                  In [1, 1000], default 1000 (every template) */
+                                  In [1, 1000], default 1000 (every template) */,
+    TCW_OPT_TRIAGE_STRIDE = 13 /* triage coarse pass: use every stride-th segment
+                                  (segments 0, s, 2s, ...) for the coarse Psi and its
+                                  features; in [1, 64], default 1 (every segment) */
 };
 
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
@@ -241,18 +244,27 @@ tcw_status tcw_track_bins(tcw_ctx *ctx, int32_t *bins_out, int out_flags);
  *   has finished.
  * Every intermediate buffer comes from one fixed device array of 64 MiB
  * inside the library (held by each GPU on which the library's device code is
- * loaded, until the process exits).  Problems whose intermediates do not fit
- * (about (n_sky rounded up to 32) * n_tmpl * 12 bytes plus
- * n_det * n_seg * n_sky * 4 bytes) are rejected with TCW_ERR_UNSUPPORTED, as
- * are inputs outside the group kernel's exactness conditions.  The first
- * call made with a given device current looks up the array's device address
- * (cudaGetSymbolAddress) and caches it; make that first call before any
- * stream capture.  All calls share the array and it keeps the previous
- * call's contents: each call clears what must start at zero, and calls that
- * overlap on the GPU (e.g. on two streams) race on it.
+ * loaded, until the process exits).  The intermediates take about
+ *   4 Spad Bpad + 5 n_det n_seg Spad + 28 Bpad + 28 Spad + 131072 n_SM bytes
+ * (+ 4 n_det n_seg when weights is NULL), with Spad = n_sky rounded up to
+ * the sky chunk tcw_search picks (256, 512 or 1024 skies), Bpad = n_tmpl
+ * rounded up to a multiple of 64 and n_SM the device's SM count (152 on
+ * GB300: 19 MiB of per-CTA scratch); problems beyond 64 MiB are rejected
+ * with TCW_ERR_UNSUPPORTED.  The sky is taken in tcw_search's Doppler order
+ * (sorted on the host from the middle segment's velocity of detector 0), and
+ * inputs outside the group kernel's exactness conditions run the per-lookup
+ * FP64 kernel, as in tcw_search.  The track is evaluated with pow per
+ * (template, segment) (no anchor table).  The first call made with a given
+ * device current looks up the array's device address (cudaGetSymbolAddress)
+ * and caches it.  The call synchronises cuda_stream several times and reads
+ * results back, so it cannot be made while that stream is being captured
+ * into a graph (it then returns TCW_ERR_STATE).  All calls share the array
+ * and it keeps the previous call's contents: each call clears what must
+ * start at zero, and calls that overlap on the GPU (e.g. on two streams)
+ * race on it.
  * Errors: INVALID_ARGUMENT (sizes, NULL, k, or element values: f0 <= 0,
  * tau <= 0, n <= 1, non-unit nhat, |v| >= c/100, bad weights, unsorted
- * t_mid), UNSUPPORTED, DEVICE, CUDA. */
+ * t_mid), STATE (stream capture), UNSUPPORTED, DEVICE, CUDA. */
 tcw_status tcw_search_noalloc(int n_det, int64_t n_seg, int64_t n_bin, int dtype, const void *rho,
                               double f_min, double df, const double *t_mid, const float *weights,
                               const double *v, int64_t n_tmpl, const double *f0, const double *tau,
@@ -374,7 +386,8 @@ tcw_status tcw_mlp_adam(float *theta, float *m, float *v, const float *grad, int
                         float lr, float beta1, float beta2, float eps, uint16_t *wbf,
                         void *stream);
 
-/* Coarse pass of the loaded search: feat_out [n_patch][128] float32,
+/* Coarse pass of the loaded search (on the segments 0, s, 2s, ... with s =
+ * TCW_OPT_TRIAGE_STRIDE): feat_out [n_patch][128] float32,
  * n_patch = ceil(n_sky / patch_size); psi_out [n_patch][n_tmpl] (caller
  * template order) may be NULL.  Errors: STATE, INVALID_ARGUMENT (patch_size
  * < 1, psi_hi <= psi_lo), UNSUPPORTED (more than 2 detectors, or a Doppler
@@ -399,6 +412,23 @@ tcw_status tcw_search_triaged(tcw_ctx *ctx, const uint16_t *wbf, const float *th
                               float *psi_out, int64_t *idx_out, int32_t *searched_out,
                               int out_flags);
 
+/* Ranking of the triage (the first step of tcw_search_triaged, returned to
+ * the caller): the coarse pass as tcw_triage_features, the network's score
+ * (logit y of the MLP above) of every patch, and the patches by (score desc,
+ * patch index asc).  score_out [n_patch] float32 and patch_order_out
+ * [n_patch] int32 (patch indices) may be NULL; sky_order_out [n_sky] int32
+ * (may be NULL) lists the caller sky indices patch by patch in that order,
+ * each patch's skies in the search's Doppler-sorted order, so its first
+ * skies are those a triaged search with frac = m / n_patch and
+ * TCW_OPT_TRIAGE_SPREAD = 0 searches.  A caller can drive its own
+ * follow-up from it (another frac, another search of the best skies)
+ * without repeating the coarse pass.  wbf and theta are device pointers;
+ * outputs are host or device memory by out_flags.  Errors: as
+ * tcw_triage_features; INVALID_ARGUMENT (null weights). */
+tcw_status tcw_triage_rank(tcw_ctx *ctx, const uint16_t *wbf, const float *theta, int patch_size,
+                           float psi_lo, float psi_hi, float *score_out, int32_t *patch_order_out,
+                           int32_t *sky_order_out, int out_flags);
+
 typedef struct {
     int n_patch;
     int n_selected;             /* patches searched exhaustively */
@@ -408,6 +438,10 @@ typedef struct {
     int64_t lookups_searched;   /* sums of the exhaustive search of the selected skies */
     float coarse_ms, mlp_ms, search_ms;  /* device times */
     int64_t templates_searched; /* templates of the exhaustive part (TCW_OPT_TRIAGE_TEMPLATES) */
+    int coarse_kernel;          /* coarse pass of the last call: 1 = the sweep form (one thread
+                                   per template, the representatives' Doppler factors sorted at
+                                   every detector and segment), 0 = one thread per (template,
+                                   patch) */
 } tcw_triage_info;
 
 tcw_status tcw_get_triage_info(tcw_ctx *ctx, tcw_triage_info *info);

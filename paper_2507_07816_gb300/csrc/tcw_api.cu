@@ -257,6 +257,10 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
     ev.weights = c->weights.as<float>();
     ev.t_mid = c->t_mid.as<double>();
     ev.blk = c->dq.as<int32_t>();
+    ev.f0 = c->f0.as<double>();
+    ev.tau = c->tau.as<double>();
+    ev.nbr = c->nbr.as<double>();
+    ev.Bpad = c->Bpad;
     ev.psi = c->psi.as<float>();
     ev.S_out = keep ? c->st_S.as<float>() : nullptr;
     ev.W1_out = keep ? c->st_W1.as<float>() : nullptr;
@@ -294,9 +298,6 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
     gp.n_bin = c->Nbin;
     gp.pitch = c->Nbin;
     gp.n_det = c->D;
-    gp.f0 = c->f0.as<double>();
-    gp.tau = c->tau.as<double>();
-    gp.nbr = c->nbr.as<double>();
     gp.f_min = c->f_min;
     gp.df = c->df;
     gp.inv_q = pl.inv_q;
@@ -307,7 +308,6 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
     gp.track_bins = c->track_bins;
     gp.map_half = c->dtype == TCW_F16 ? 1 : 0;
     gp.B = (int)c->B;
-    gp.Bpad = c->Bpad;
     gp.lanes = c->lanes;
     gp.dev = c->dev.as<float2>();
     gp.rec = rec_dev;
@@ -432,6 +432,74 @@ struct BankSwap {
 
 // Coarse pass of the triage on the loaded search: features in c->tri_feat
 // ([P][128]) and, when keep_psi, Psi in c->tri_psi ([P][Bpad], sorted bank).
+// Tiles of the sweep form of the coarse pass: the largest tile (<= 64 coarse
+// segments) for which the anchor-to-anchor step |u'/u - 1| is <= 0.1 and its
+// FP64 binomial series (<= kSweepMaxTerms terms) is truncated below 1e-17,
+// and the in-tile fp32 remainder (cubic and higher terms) stays below 0.5
+// bins and is truncated below 2e-8 bins.  The segment table holds dt = t -
+// t_anchor and dt^2 as fp32 pairs.
+struct SweepPlan {
+  bool ok = false;
+  int shift = 0, n_tiles = 0, nt64 = 0, nc = 0;
+  std::vector<double> ta;
+  std::vector<float4> seg;
+};
+
+SweepPlan plan_sweep(const std::vector<double>& tc, double T0, double tau_min, double r_max, double x_max) {
+  const int n = (int)tc.size();
+  auto cbound = [&](int k) {   // |C(e, k)| for |e| <= r_max
+    double c = 1.0;
+    for (int i = 0; i < k; ++i) c *= (r_max + i) / (i + 1);
+    return c;
+  };
+  for (int shift = 6; shift >= 0; --shift) {
+    SweepPlan p;
+    p.shift = shift;
+    const int tile = 1 << shift;
+    p.n_tiles = (n + tile - 1) / tile;
+    p.ta.assign(p.n_tiles, NAN);
+    double dmax = 0.0, Dmax = 0.0, prev = NAN;
+    for (int k = 0; k < p.n_tiles; ++k) {
+      const int j0 = k * tile, jn = std::min(tile, n - j0);
+      bool any = false;
+      for (int j = j0; j < j0 + jn; ++j) any = any || tc[j] >= T0;
+      if (!any) continue;
+      const double ta = std::max(tc[j0 + (jn - 1) / 2], T0);
+      p.ta[k] = ta;
+      for (int j = j0; j < j0 + jn; ++j)
+        if (tc[j] >= T0) dmax = std::max(dmax, std::fabs(tc[j] - ta) / tau_min);
+      if (!std::isnan(prev)) Dmax = std::max(Dmax, std::fabs(ta - prev) / tau_min);
+      prev = ta;
+    }
+    if (!(Dmax <= 0.1) || !(dmax <= 0.1)) continue;
+    int nt = 1;
+    while (nt < kSweepMaxTerms && cbound(nt) * std::pow(Dmax, nt) > 1e-17) ++nt;
+    if (cbound(nt) * std::pow(Dmax, nt) > 1e-17) continue;
+    if (x_max * cbound(3) * std::pow(dmax, 3) > 0.5 || x_max * r_max * dmax > 4.0e6) continue;
+    for (int nc : {4, 6, 8})
+      if (x_max * cbound(nc + 3) * std::pow(dmax, nc + 3) <= 2e-8) {
+        p.nc = nc;
+        break;
+      }
+    if (!p.nc) continue;
+    p.nt64 = nt;
+    p.seg.resize(n);
+    for (int j = 0; j < n; ++j) {
+      const double ta = p.ta[j >> shift];
+      if (!(tc[j] >= T0)) {
+        p.seg[j] = make_float4(NAN, 0.f, 0.f, 0.f);
+        continue;
+      }
+      const double dt = tc[j] - ta, d2 = dt * dt;
+      const float hi = (float)dt, h2 = (float)d2;
+      p.seg[j] = make_float4(hi, (float)(dt - hi), h2, (float)(d2 - h2));
+    }
+    p.ok = true;
+    return p;
+  }
+  return SweepPlan{};
+}
+
 tcw_status run_coarse(tcw_ctx* c, int patch_size, float lo, float hi, bool keep_psi, int* P_out) {
   if (!c->have_spec || !c->have_vel || !c->have_bank || !c->have_sky)
     return fail(c, TCW_ERR_STATE, "inputs not loaded");
@@ -442,20 +510,104 @@ tcw_status run_coarse(tcw_ctx* c, int patch_size, float lo, float hi, bool keep_
   if (pl.doppler_bins > 2.9) return fail(c, TCW_ERR_UNSUPPORTED, "coarse pass: Doppler shift exceeds 2.9 bins");
   const int P = (int)((c->S + patch_size - 1) / patch_size);
   const int tile = 32;
-  const int n_tiles = (int)((c->Nseg + tile - 1) / tile);
+  // the coarse segments: every stride-th one
+  const int stride = c->triage_stride;
+  const int n_cs = (int)((c->Nseg + stride - 1) / stride);
+  std::vector<double> tc(n_cs);
+  for (int j = 0; j < n_cs; ++j) tc[j] = c->h_t[(size_t)j * stride];
+  TCW_CUDA(c, upload(c, c->tri_tmid, tc.data(), tc.size() * sizeof(double), TCW_HOST), "triage buffers");
+  const int n_tiles = (n_cs + tile - 1) / tile;
   const double tau_min = c->bank_tau_min, r_max = c->bank_r_max;
-  const int nterms = series_terms_for(c->h_t.data(), c->Nseg, c->T0, tile, tau_min, r_max);
-  TCW_CUDA(c, c->tri_dop.ensure((size_t)c->D * c->Nseg * P * sizeof(float)), "triage buffers");
+  const int nterms = series_terms_for(tc.data(), n_cs, c->T0, tile, tau_min, r_max);
+  TCW_CUDA(c, c->tri_dop.ensure((size_t)c->D * n_cs * P * sizeof(float)), "triage buffers");
   TCW_CUDA(c, c->tri_hist.ensure((size_t)P * kTriageBins * sizeof(unsigned)), "triage buffers");
   TCW_CUDA(c, c->tri_feat.ensure((size_t)P * kTriageBins * sizeof(float)), "triage buffers");
   if (keep_psi) TCW_CUDA(c, c->tri_psi.ensure((size_t)P * c->Bpad * sizeof(float)), "triage buffers");
   if (nterms > 0) TCW_CUDA(c, c->tri_anchor.ensure((size_t)c->Bpad * n_tiles * 2 * sizeof(double)), "triage buffers");
   TCW_CUDA(c, cudaMemsetAsync(c->tri_hist.p, 0, (size_t)P * kTriageBins * sizeof(unsigned), c->stream), "triage");
+  c->tri_info.n_patch = P;
+  c->tri_info.lookups_coarse = (int64_t)P * c->B * c->D * n_cs;
+  c->tri_info.lookups_full = c->S * c->B * c->D * c->Nseg;
+  c->tri_info.coarse_kernel = 0;
+  *P_out = P;
+  // the sweep form when its series bounds hold and the representatives' Doppler
+  // factors are sorted at every (detector, segment)
+  SweepPlan sp;
+  if (c->D <= 2 && P <= kSweepMaxPatches) sp = plan_sweep(tc, c->T0, tau_min, r_max, c->bank_f0max / c->df);
+  if (sp.ok) {
+    int P2 = 1;
+    while (P2 < P) P2 <<= 1;
+    TCW_CUDA(c, c->tri_dop.ensure((size_t)c->D * n_cs * P2 * sizeof(float)), "triage buffers");
+    TCW_CUDA(c, c->tri_flag.ensure(sizeof(int)), "triage buffers");
+    TCW_CUDA(c, cudaMemsetAsync(c->tri_flag.p, 0, sizeof(int), c->stream), "triage");
+    SweepDopplerParams sd{};
+    sd.vel = c->vel.as<double>();
+    sd.nhat = c->nhat_sorted.as<double>();
+    sd.n_det = c->D;
+    sd.n_seg = n_cs;
+    sd.S = (int)c->S;
+    sd.patch_size = patch_size;
+    sd.P = P;
+    sd.P2 = P2;
+    sd.stride = stride;
+    sd.n_seg_full = (int)c->Nseg;
+    sd.dop = c->tri_dop.as<float>();
+    sd.unsorted = c->tri_flag.as<int>();
+    TCW_CUDA(c, launch_sweep_doppler(sd, c->stream), "sweep_doppler_kernel launch");
+    int unsorted = 1;
+    TCW_CUDA(c, cudaMemcpyAsync(&unsorted, c->tri_flag.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+             "triage");
+    TCW_CUDA(c, cudaStreamSynchronize(c->stream), "triage");
+    if (!unsorted) {
+      TCW_CUDA(c, upload(c, c->tri_seg, sp.seg.data(), sp.seg.size() * sizeof(float4), TCW_HOST), "triage buffers");
+      TCW_CUDA(c, upload(c, c->tri_ta, sp.ta.data(), sp.ta.size() * sizeof(double), TCW_HOST), "triage buffers");
+      TCW_CUDA(c, c->tri_coef.ensure((size_t)sp.nt64 * c->Bpad * sizeof(double)), "triage buffers");
+      TCW_CUDA(c, c->tri_w2e.ensure((size_t)(P + 1) * c->Bpad * sizeof(double)), "triage buffers");
+      TCW_CUDA(c, c->tri_ne.ensure((size_t)(P + 1) * c->Bpad * sizeof(int)), "triage buffers");
+      CoarseSweepParams cs{};
+      cs.rho = c->rho.p;
+      cs.n_bin = c->Nbin;
+      cs.n_det = c->D;
+      cs.n_seg = n_cs;
+      cs.stride = stride;
+      cs.n_seg_full = (int)c->Nseg;
+      cs.weights = c->weights.as<float>();
+      cs.seg = c->tri_seg.as<float4>();
+      cs.ta = c->tri_ta.as<double>();
+      cs.tile_shift = sp.shift;
+      cs.n_tiles = sp.n_tiles;
+      cs.nt64 = sp.nt64;
+      cs.T0 = c->T0;
+      cs.f_min = c->f_min;
+      cs.df = c->df;
+      cs.dop = sd.dop;
+      cs.P = P;
+      cs.P2 = P2;
+      cs.f0 = c->f0.as<double>();
+      cs.tau = c->tau.as<double>();
+      cs.nbr = c->nbr.as<double>();
+      cs.B = (int)c->B;
+      cs.Bpad = c->Bpad;
+      cs.coef64 = c->tri_coef.as<double>();
+      cs.w2edge = c->tri_w2e.as<double>();
+      cs.nedge = c->tri_ne.as<int>();
+      cs.lo = lo;
+      cs.hi = hi;
+      cs.psi = keep_psi ? c->tri_psi.as<float>() : nullptr;
+      cs.hist = c->tri_hist.as<unsigned>();
+      cs.feat = c->tri_feat.as<float>();
+      TCW_CUDA(c, launch_coarse_sweep(cs, c->dtype == TCW_F16, sp.nc, c->stream), "coarse_sweep_kernel launch");
+      c->tri_info.coarse_kernel = 1;
+      return TCW_OK;
+    }
+  }
   PatchDopplerParams dp{};
   dp.vel = c->vel.as<double>();
   dp.nhat = c->nhat_sorted.as<double>();
   dp.n_det = c->D;
-  dp.n_seg = (int)c->Nseg;
+  dp.n_seg = n_cs;
+  dp.stride = stride;
+  dp.n_seg_full = (int)c->Nseg;
   dp.S = (int)c->S;
   dp.patch_size = patch_size;
   dp.P = P;
@@ -463,12 +615,12 @@ tcw_status run_coarse(tcw_ctx* c, int patch_size, float lo, float hi, bool keep_
   TCW_CUDA(c, launch_patch_doppler(dp, c->stream), "patch_doppler_kernel launch");
   if (nterms > 0) {
     AnchorParams ap{};
-    ap.t_mid = c->t_mid.as<double>();
+    ap.t_mid = c->tri_tmid.as<double>();
     ap.f0 = c->f0.as<double>();
     ap.tau = c->tau.as<double>();
     ap.nbr = c->nbr.as<double>();
     ap.T0 = c->T0;
-    ap.n_seg = (int)c->Nseg;
+    ap.n_seg = n_cs;
     ap.n_tiles = n_tiles;
     ap.tile_shift = 5;
     ap.Bpad = c->Bpad;
@@ -479,9 +631,11 @@ tcw_status run_coarse(tcw_ctx* c, int patch_size, float lo, float hi, bool keep_
   cp.rho = c->rho.p;
   cp.n_bin = c->Nbin;
   cp.n_det = c->D;
-  cp.n_seg = (int)c->Nseg;
+  cp.n_seg = n_cs;
+  cp.stride = stride;
+  cp.n_seg_full = (int)c->Nseg;
   cp.weights = c->weights.as<float>();
-  cp.t_mid = c->t_mid.as<double>();
+  cp.t_mid = c->tri_tmid.as<double>();
   cp.T0 = c->T0;
   cp.f_min = c->f_min;
   cp.df = c->df;
@@ -503,10 +657,6 @@ tcw_status run_coarse(tcw_ctx* c, int patch_size, float lo, float hi, bool keep_
   cp.part_acc = c->tri_part.as<double>();
   cp.feat = c->tri_feat.as<float>();
   TCW_CUDA(c, launch_coarse(cp, c->dtype == TCW_F16, c->stream), "coarse_kernel launch");
-  c->tri_info.n_patch = P;
-  c->tri_info.lookups_coarse = (int64_t)P * c->B * c->D * c->Nseg;
-  c->tri_info.lookups_full = c->S * c->B * c->D * c->Nseg;
-  *P_out = P;
   return TCW_OK;
 }
 
@@ -611,6 +761,10 @@ tcw_status tcw_set_option(tcw_ctx* c, int option, int64_t value) {
     case TCW_OPT_TRIAGE_TEMPLATES:
       if (value < 1 || value > 1000) return fail(c, TCW_ERR_INVALID_ARGUMENT, "triage templates must be in [1, 1000]");
       c->triage_templates = (int)value;
+      return TCW_OK;
+    case TCW_OPT_TRIAGE_STRIDE:
+      if (value < 1 || value > 64) return fail(c, TCW_ERR_INVALID_ARGUMENT, "triage stride must be in [1, 64]");
+      c->triage_stride = (int)value;
       return TCW_OK;
     case TCW_OPT_TRACK_BINS:
       if (value != 1 && value != 2) return fail(c, TCW_ERR_INVALID_ARGUMENT, "track_bins must be 1 or 2");
@@ -1136,6 +1290,50 @@ tcw_status tcw_triage_features(tcw_ctx* c, int patch_size, float psi_lo, float p
              "copy out");
   }
   TCW_CUDA(c, cudaStreamSynchronize(c->stream), "coarse pass");
+  return TCW_OK;
+}
+
+tcw_status tcw_triage_rank(tcw_ctx* c, const uint16_t* wbf, const float* theta, int patch_size, float psi_lo,
+                           float psi_hi, float* score_out, int32_t* patch_order_out, int32_t* sky_order_out,
+                           int out_flags) {
+  if (!c) return TCW_ERR_INVALID_ARGUMENT;
+  if (!wbf || !theta) return fail(c, TCW_ERR_INVALID_ARGUMENT, "null network weights");
+  if (patch_size < 1 || !(psi_hi > psi_lo) || !std::isfinite(psi_lo) || !std::isfinite(psi_hi))
+    return fail(c, TCW_ERR_INVALID_ARGUMENT, "bad patch size or histogram range");
+  if (out_flags != TCW_HOST && out_flags != TCW_DEVICE) return fail(c, TCW_ERR_INVALID_ARGUMENT, "bad flags");
+  cudaSetDevice(c->device);
+  int P = 0;
+  tcw_status st = run_coarse(c, patch_size, psi_lo, psi_hi, false, &P);
+  if (st != TCW_OK) return st;
+  TCW_CUDA(c, c->tri_h1.ensure((size_t)P * kMlpH * sizeof(float)), "triage buffers");
+  TCW_CUDA(c, c->tri_h2.ensure((size_t)P * kMlpH * sizeof(float)), "triage buffers");
+  TCW_CUDA(c, c->tri_score.ensure((size_t)P * sizeof(float)), "triage buffers");
+  TCW_CUDA(c, mlp_forward(reinterpret_cast<const __nv_bfloat16*>(wbf), theta, c->tri_feat.as<float>(), P,
+                          c->tri_h1.as<float>(), c->tri_h2.as<float>(), c->tri_score.as<float>(), c->stream),
+           "mlp forward");
+  std::vector<float> score(P);
+  TCW_CUDA(c, cudaMemcpyAsync(score.data(), c->tri_score.p, P * sizeof(float), cudaMemcpyDeviceToHost, c->stream),
+           "scores");
+  TCW_CUDA(c, cudaStreamSynchronize(c->stream), "scores");
+  // (score desc, patch index asc); NaN scores last
+  std::vector<int32_t> order(P);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+    const bool na = std::isnan(score[a]), nb = std::isnan(score[b]);
+    if (na != nb) return nb;
+    return !na && score[a] > score[b];
+  });
+  const cudaMemcpyKind kind = out_flags == TCW_HOST ? cudaMemcpyHostToHost : cudaMemcpyHostToDevice;
+  if (score_out) TCW_CUDA(c, cudaMemcpy(score_out, score.data(), P * sizeof(float), kind), "copy out");
+  if (patch_order_out) TCW_CUDA(c, cudaMemcpy(patch_order_out, order.data(), P * sizeof(int32_t), kind), "copy out");
+  if (sky_order_out) {
+    std::vector<int32_t> skies;
+    skies.reserve(c->S);
+    for (int32_t p : order)
+      for (int64_t i = (int64_t)p * patch_size; i < std::min<int64_t>(c->S, (int64_t)(p + 1) * patch_size); ++i)
+        skies.push_back(c->h_sky_perm[i]);
+    TCW_CUDA(c, cudaMemcpy(sky_order_out, skies.data(), skies.size() * sizeof(int32_t), kind), "copy out");
+  }
   return TCW_OK;
 }
 

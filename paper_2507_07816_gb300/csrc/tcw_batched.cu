@@ -214,6 +214,10 @@ EventDesc make_desc(const tcw_ctx* c, BatchState* b, const EventHost& e, int til
   d.t_mid = at<double>(b->small, e.o_t);
   d.blk = at<int32_t>(b->blk, e.o_blk);
   d.anchors = anchors ? at<double>(b->anchors, e.o_anchor) : nullptr;
+  d.f0 = c->f0.as<double>();
+  d.tau = c->tau.as<double>();
+  d.nbr = c->nbr.as<double>();
+  d.Bpad = c->Bpad;
   d.psi = at<float>(b->psi, e.o_psi);
   d.total_elems = (int64_t)b->D * e.n_seg * b->n_bin;
   d.T0 = e.T0;
@@ -286,9 +290,6 @@ GroupParams base_params(const tcw_ctx* c, BatchState* b, int tile, int nterms) {
   gp.n_bin = b->n_bin;
   gp.pitch = b->n_bin;
   gp.n_det = b->D;
-  gp.f0 = c->f0.as<double>();
-  gp.tau = c->tau.as<double>();
-  gp.nbr = c->nbr.as<double>();
   gp.f_min = b->f_min;
   gp.df = b->df;
   gp.inv_q = b->inv_q;
@@ -299,7 +300,6 @@ GroupParams base_params(const tcw_ctx* c, BatchState* b, int tile, int nterms) {
   gp.track_bins = c->track_bins;
   gp.map_half = b->dtype == TCW_F16 ? 1 : 0;
   gp.B = (int)c->B;
-  gp.Bpad = c->Bpad;
   gp.lanes = b->lanes;
   gp.dev = b->dev.as<float2>();
   gp.bank_perm = c->bank_perm.as<int32_t>();

@@ -50,8 +50,9 @@ struct tcw_ctx {
   int amp_power = 0;       // weights times (f(t_j)/f0)^amp_power (Eq. 3)
   int gen_chunk = 1 << 18; // generated-bank search: templates per chunk
   int track_bins = 1;      // bins per lookup: 1 nearest, 2 the bracketing pair
-  int triage_spread = 2;
-  int triage_templates = 1000;  // triage: per mille of the bank searched per chosen patch   // triage: patches within this distance of a chosen one are suppressed
+  int triage_spread = 2;        // triage: patches within this distance of a chosen one are suppressed
+  int triage_stride = 1;        // triage: coarse pass on every triage_stride-th segment
+  int triage_templates = 1000;  // triage: per mille of the bank searched per chosen patch
   int64_t batch_memory = (int64_t)48 << 30;  // batched search: Psi + anchor bytes per wave
   unsigned bank_epoch = 0; // bumped by every tcw_define_bank
   int statistic = TCW_STAT_POWER;
@@ -102,7 +103,9 @@ struct tcw_ctx {
   tcw_generated_info gen_info{};
   // learned triage
   std::vector<int32_t> h_sky_perm, h_bank_perm;  // sorted -> caller (host copies)
+  tcw::DevBuf tri_tmid;   // coarse-pass segment times (every stride-th segment)
   tcw::DevBuf tri_dop, tri_hist, tri_feat, tri_psi, tri_anchor, tri_h1, tri_h2, tri_score, tri_sel, tri_part;
+  tcw::DevBuf tri_seg, tri_ta, tri_coef, tri_w2e, tri_ne, tri_flag;   // sweep form of the coarse pass
   tcw_triage_info tri_info{};
 };
 

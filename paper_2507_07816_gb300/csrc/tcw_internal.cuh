@@ -85,6 +85,10 @@ struct EventDesc {
   const int32_t* blk;      // Doppler blocks [Spad / (16 lanes)][n_seg][D][block_words(lanes)]
   const double* anchors;   // [Bpad][n_tiles][2]: 1/f and 1/(tau + t_a - T0) at each tile's
                            // anchor t_a; read only when nterms > 0
+  const double* f0;        // the event's sorted bank [Bpad] (events may share one)
+  const double* tau;
+  const double* nbr;
+  int Bpad;                // templates of the bank arrays (a multiple of every pass)
   float* psi;              // [Spad][Bpad]
   float* S_out;            // optional [Spad][Bpad]
   float* W1_out;
@@ -108,9 +112,6 @@ struct GroupParams {
   int64_t n_bin;           // bins per row that belong to the band
   int64_t pitch;           // elements between rows (>= n_bin)
   int n_det;               // <= kMaxStageDet
-  const double* f0;        // sorted bank, [Bpad]
-  const double* tau;
-  const double* nbr;
   double f_min, df, inv_q;
   int nterms;              // binomial-series length for the track; 0 = pow per entry
   int tile_shift;          // tiles of 2^tile_shift segments: anchors and fp32 partial sums
@@ -120,7 +121,7 @@ struct GroupParams {
   int track_bins;          // 2: each lookup sums the bins floor(x), floor(x) + 1 (staged as fp32
                            // pair sums; <s> and sigma^2 doubled); otherwise the nearest bin
   int map_half;            // the events' maps are fp16 (read by the two-bin producers)
-  int B, Bpad;
+  int B;                   // templates of the bank (recording only)
   int lanes;               // sky groups per chunk: 16, 32 or 64
   float2* dev;             // scratch [gridDim.x][kPassUnits * 16]: per-sky weight sums at band edges
   int32_t* rec;            // optional [S][B][D][Nseg], caller order (single-event searches)
@@ -217,18 +218,20 @@ __host__ __device__ inline int64_t mlp_weight_index(int64_t i) {
 }
 
 struct PatchDopplerParams {
-  const double* vel;        // [D][n_seg][3]
+  const double* vel;        // [D][n_seg_full][3]
   const double* nhat;       // sorted sky [S][3]
-  int n_det, n_seg, S, patch_size, P;
+  int n_det, n_seg, S, patch_size, P;   // n_seg: coarse segments (segment j' is j' stride)
+  int stride, n_seg_full;
   float* dop;               // [D][n_seg][P]
 };
 
 struct CoarseParams {
-  const void* rho;          // [D][n_seg][n_bin]
+  const void* rho;          // [D][n_seg_full][n_bin]
   int64_t n_bin;
-  int n_det, n_seg;
-  const float* weights;     // [D][n_seg]
-  const double* t_mid;
+  int n_det, n_seg;         // n_seg: coarse segments; coarse segment j' is segment j' stride
+  int stride, n_seg_full;
+  const float* weights;     // [D][n_seg_full]
+  const double* t_mid;      // [n_seg] times of the coarse segments
   double T0, f_min, df;
   const float* dop;         // [D][n_seg][P]
   int P;
@@ -250,6 +253,55 @@ size_t coarse_part_elems(int P, int Bpad);
 
 cudaError_t launch_patch_doppler(const PatchDopplerParams& p, cudaStream_t st);
 cudaError_t launch_coarse(const CoarseParams& p, bool half, cudaStream_t st);
+
+// Coarse pass, sweep form.  When the representatives' Doppler factors are
+// non-decreasing in patch order at every (detector, segment), the bin of a
+// (template, segment, detector) lookup is a non-decreasing step function of
+// the representative, so one thread per template gathers the first
+// representative's bin and records each step's power difference in a
+// per-template difference array; a prefix sum over the representatives
+// gives every S (Eq. 4 numerator).
+constexpr int kSweepThreads = 256;
+constexpr int kSweepMaxPatches = 128;   // shared memory: (P + 1) x kSweepThreads floats
+constexpr int kSweepMaxTerms = 24;      // FP64 binomial terms of the anchor-to-anchor step
+
+struct SweepDopplerParams {
+  const double* vel;        // [D][n_seg_full][3]
+  const double* nhat;       // sorted sky [S][3]
+  int n_det, n_seg, S, patch_size, P, P2;   // P2: power of two >= P
+  int stride, n_seg_full;
+  float* dop;               // [D][n_seg][P2] v.nhat/c of each representative, +inf beyond P
+  int* unsorted;            // set to 1 where the factor decreases from one representative to the next
+};
+
+struct CoarseSweepParams {
+  const void* rho;          // [D][n_seg_full][n_bin]
+  int64_t n_bin;
+  int n_det, n_seg, stride, n_seg_full;   // n_seg: coarse segments
+  const float* weights;     // [D][n_seg_full]
+  const float4* seg;        // [n_seg] {dt hi, dt lo, dt^2 hi, dt^2 lo}, dt = t - anchor time of the
+                            // segment's tile (fp32 pairs of the FP64 values); dt hi = NaN where t < T0
+  const double* ta;         // [n_tiles] anchor times, NaN for tiles without a segment at or after T0
+  int tile_shift, n_tiles, nt64;
+  double T0, f_min, df;
+  const float* dop;         // [D][n_seg][P2] from SweepDopplerParams
+  int P, P2;
+  const double* f0;         // sorted bank [Bpad]
+  const double* tau;
+  const double* nbr;
+  int B, Bpad;
+  double* coef64;           // [nt64][Bpad] scratch: binomial coefficients of each template
+  double* w2edge;           // [P + 1][Bpad] scratch: W2 steps of band-edge lookups
+  int* nedge;               // [P + 1][Bpad] scratch: valid-lookup count steps of band-edge lookups
+  float lo, hi;
+  float* psi;               // optional [P][Bpad]
+  unsigned* hist;           // [P][128], zero at launch
+  float* feat;              // [P][128] log(1 + count)
+};
+
+cudaError_t launch_sweep_doppler(const SweepDopplerParams& p, cudaStream_t st);
+// nc: fp32 terms of the in-tile series beyond the quadratic one (4, 6 or 8)
+cudaError_t launch_coarse_sweep(const CoarseSweepParams& p, bool half, int nc, cudaStream_t st);
 // selected[p] = 1 for the m best patches; a chosen patch suppresses the
 // patches within `radius` of it (0 = plain ranking)
 cudaError_t launch_rank(const float* score, int P, int m, int radius, int* selected, cudaStream_t st);

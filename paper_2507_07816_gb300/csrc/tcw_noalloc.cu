@@ -9,7 +9,9 @@
 // group kernel, top-k) on caller-owned inputs and outputs, and takes every
 // intermediate buffer from one file-scope device array of fixed size,
 // kTcwNoallocScratchBytes (64 MiB).  Every GPU on which this device code is
-// loaded holds that array until the process exits.
+// loaded holds that array until the process exits.  Host memory is used
+// freely (the sky order is sorted on the host); only device allocation is
+// avoided.
 //
 // The array's name is only a host-side stand-in; the device address is
 // obtained once per device with cudaGetSymbolAddress (on the first call made
@@ -17,6 +19,7 @@
 // and keeps the previous call's contents: the entry point clears what has to
 // start at zero (the flag words) on every call, and calls that overlap on the
 // GPU (for example on two streams at once) race on it.
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstring>
@@ -49,10 +52,10 @@ struct NoallocPrep {
   unsigned long long* f0max_bits;
 };
 
-// Pads the bank and the sky (repeating the last entry), writes identity
-// permutations, fills unit weights when none are given, checks the inputs
-// element-wise and takes max |v| and max f0 (bit patterns of non-negative
-// doubles order like unsigned integers).
+// Pads the bank (repeating the last template) with an identity permutation,
+// gathers the sky in the host's Doppler-sorted order, fills unit weights when
+// none are given, checks the inputs element-wise and takes max |v| and max f0
+// (bit patterns of non-negative doubles order like unsigned integers).
 __global__ void noalloc_prepare_kernel(NoallocPrep p) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -71,12 +74,11 @@ __global__ void noalloc_prepare_kernel(NoallocPrep p) {
     }
   }
   for (int64_t i = t0; i < p.Spad; i += stride) {
-    const int src = (int)(i < p.S ? i : (int64_t)p.S - 1);
+    const int src = p.sky_perm[i];   // Doppler-sorted order from the host (padding repeats the last)
     const double x = p.nhat[3 * src], y = p.nhat[3 * src + 1], z = p.nhat[3 * src + 2];
     p.nhatp[3 * i] = x;
     p.nhatp[3 * i + 1] = y;
     p.nhatp[3 * i + 2] = z;
-    p.sky_perm[i] = src;
     if (i < p.S && !(fabs(sqrt(x * x + y * y + z * z) - 1.0) <= 1e-9)) atomicOr(p.err, 4);
   }
   const int64_t nv = (int64_t)p.n_det * p.n_seg;
@@ -121,15 +123,20 @@ extern "C" tcw_status tcw_search_noalloc(int n_det, int64_t n_seg, int64_t n_bin
     return TCW_ERR_INVALID_ARGUMENT;
   if (k < 1 || k > 1024 || (int64_t)k > n_tmpl) return TCW_ERR_INVALID_ARGUMENT;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  // the call synchronises and reads flags back: it cannot run inside a stream capture
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return TCW_ERR_CUDA;
+  if (cap != cudaStreamCaptureStatusNone) return TCW_ERR_STATE;
+  int grid = 0;
+  if (group_grid(&grid) != cudaSuccess) return TCW_ERR_CUDA;
 
-  // Scratch layout (every region 256-byte aligned).
+  // Scratch layout (every region 256-byte aligned); the chunk width as tcw_search chooses it.
   const int B = (int)n_tmpl, S = (int)n_sky, D = n_det, Nseg = (int)n_seg;
-  constexpr int kLanes = 64;   // sky groups per chunk of the group kernel
-  const int ptmpl = pass_templates(kLanes);
+  const int lanes = choose_lanes(S, B, 1, grid);   // sky groups per chunk of the group kernel
+  const int ptmpl = pass_templates(lanes);
   const int Bpad = (B + ptmpl - 1) / ptmpl * ptmpl;
   const int NG = (S + kGroupSkies - 1) / kGroupSkies;
-  const int NGpad = (NG + kLanes - 1) / kLanes * kLanes;
-  const int Spad = NGpad * kGroupSkies;
+  const int Spad = padded_skies(S, lanes);
   size_t off = 0;
   auto take = [&](size_t bytes) {
     const size_t at = off;
@@ -141,11 +148,9 @@ extern "C" tcw_status tcw_search_noalloc(int n_det, int64_t n_seg, int64_t n_bin
   const size_t o_bperm = take((size_t)Bpad * 4), o_sperm = take((size_t)Spad * 4);
   const size_t o_nhat = take((size_t)Spad * 24);
   const size_t o_ones = take(weights ? 0 : (size_t)D * Nseg * 4);
-  const size_t o_dq = take((size_t)(Spad / chunk_skies(kLanes)) * Nseg * D * block_words(kLanes) * 4);
+  const size_t o_dq = take((size_t)(Spad / chunk_skies(lanes)) * Nseg * D * block_words(lanes) * 4);
   const size_t o_psi = take((size_t)Spad * Bpad * 4);
-  int grid = 0;
-  if (group_grid(&grid) != cudaSuccess) return TCW_ERR_CUDA;
-  const int n_chunks = Spad / chunk_skies(kLanes), n_groups = Bpad / ptmpl;
+  const int n_chunks = Spad / chunk_skies(lanes), n_groups = Bpad / ptmpl;
   const int64_t n_items = (int64_t)n_chunks * n_groups;
   const size_t o_dev = take(group_dev_elems(grid) * 8);
   const size_t o_ev = take(sizeof(EventDesc));
@@ -166,6 +171,26 @@ extern "C" tcw_status tcw_search_noalloc(int n_det, int64_t n_seg, int64_t n_bin
     g_scratch_addr[dev] = static_cast<unsigned char*>(ptr);
   }
   unsigned char* base = g_scratch_addr[dev];
+  // The sky in the order tcw_search uses: by v.nhat of detector 0 at the middle
+  // segment (ties by index), so that 16 consecutive skies form a tight group.
+  std::vector<double> vm(3), hn((size_t)S * 3);
+  if (cudaMemcpyAsync(vm.data(), v + (size_t)(Nseg / 2) * 3, 3 * sizeof(double), cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(hn.data(), nhat, hn.size() * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return TCW_ERR_CUDA;
+  std::vector<int32_t> sperm(Spad);
+  {
+    std::vector<double> key(S);
+    for (int i = 0; i < S; ++i) key[i] = vm[0] * hn[3 * i] + vm[1] * hn[3 * i + 1] + vm[2] * hn[3 * i + 2];
+    std::vector<int32_t> ord(S);
+    for (int i = 0; i < S; ++i) ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
+    for (int i = 0; i < Spad; ++i) sperm[i] = ord[i < S ? i : S - 1];
+  }
+  if (cudaMemcpyAsync(base + o_sperm, sperm.data(), sperm.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st) !=
+      cudaSuccess)
+    return TCW_ERR_CUDA;
   int* err = reinterpret_cast<int*>(base + o_flags);
   unsigned long long* ngen = reinterpret_cast<unsigned long long*>(base + o_flags + 8);
   unsigned long long* maxes = reinterpret_cast<unsigned long long*>(base + o_flags + 16);
@@ -213,8 +238,8 @@ extern "C" tcw_status tcw_search_noalloc(int n_det, int64_t n_seg, int64_t n_bin
   if (e < -80) e = -80;
   const double q = std::ldexp(1.0, e);
   const double fmax_bins = std::fmin(f0max, f_min + ((double)n_bin + 5.0) * df) * (1.0 + dmax) / df;
-  if (fmax_bins * q * 0.5 > 0.75 * std::ldexp(1.0, -30) || fmax_bins * dmax > 2.9)
-    return TCW_ERR_UNSUPPORTED;
+  // outside the group kernel's exactness conditions the per-lookup FP64 kernel runs, as in tcw_search
+  const bool exact_ok = !(fmax_bins * q * 0.5 > 0.75 * std::ldexp(1.0, -30) || fmax_bins * dmax > 2.9);
 
   DopplerParams dp{};
   dp.vel = v;
@@ -224,29 +249,35 @@ extern "C" tcw_status tcw_search_noalloc(int n_det, int64_t n_seg, int64_t n_bin
   dp.Spad = Spad;
   dp.NG = NG;
   dp.group = kGroupSkies;
-  dp.lanes = kLanes;
+  dp.lanes = lanes;
   dp.inv_q = std::ldexp(1.0, -e);
   dp.blk = reinterpret_cast<int32_t*>(base + o_dq);
   dp.spread_max = reinterpret_cast<unsigned*>(base + o_flags + 32);
-  if (launch_doppler(dp, st) != cudaSuccess) return TCW_ERR_CUDA;
-  unsigned spread_bits = 0;
-  if (cudaMemcpyAsync(&spread_bits, dp.spread_max, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-      cudaStreamSynchronize(st) != cudaSuccess)
-    return TCW_ERR_CUDA;
-  float spread = 0.f;
-  std::memcpy(&spread, &spread_bits, 4);
+  float spread = 1.f;
+  if (exact_ok) {
+    if (launch_doppler(dp, st) != cudaSuccess) return TCW_ERR_CUDA;
+    unsigned spread_bits = 0;
+    if (cudaMemcpyAsync(&spread_bits, dp.spread_max, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return TCW_ERR_CUDA;
+    std::memcpy(&spread, &spread_bits, 4);
+  }
   float* psi = reinterpret_cast<float*>(base + o_psi);
   const float* wts = weights ? weights : pp.ones;
   const size_t esz = dtype == TCW_F16 ? 2 : 4;
-  const bool group_ok = fmax_bins * (double)spread * 0.5 + 0.02 <= 0.45 && D <= kMaxStageDet &&
+  const bool group_ok = exact_ok && fmax_bins * (double)spread * 0.5 + 0.02 <= 0.45 && D <= kMaxStageDet &&
                         ((uintptr_t)rho % 16) == 0 && (size_t)D * Nseg * n_bin * esz >= 64;
   if (group_ok) {
-    // one event; items of one group of 8 templates x one sky chunk, dealt round robin
+    // one event; items of one pass (1024 / lanes templates x one sky chunk), longest first
     EventDesc ev{};
     ev.rho = rho;
     ev.weights = wts;
     ev.t_mid = t_mid;
     ev.blk = dp.blk;
+    ev.f0 = pp.f0p;
+    ev.tau = pp.taup;
+    ev.nbr = pp.nbrp;
+    ev.Bpad = Bpad;
     ev.psi = psi;
     ev.total_elems = (int64_t)D * Nseg * n_bin;
     ev.T0 = T0;
@@ -281,17 +312,13 @@ extern "C" tcw_status tcw_search_noalloc(int n_det, int64_t n_seg, int64_t n_bin
     gp.n_bin = n_bin;
     gp.pitch = n_bin;
     gp.n_det = D;
-    gp.f0 = pp.f0p;
-    gp.tau = pp.taup;
-    gp.nbr = pp.nbrp;
     gp.f_min = f_min;
     gp.df = df;
     gp.inv_q = dp.inv_q;
     gp.nterms = 0;
     gp.tile_shift = kTileShift;
     gp.B = B;
-    gp.Bpad = Bpad;
-    gp.lanes = kLanes;
+    gp.lanes = lanes;
     gp.dev = reinterpret_cast<float2*>(base + o_dev);
     gp.bank_perm = pp.bank_perm;
     gp.sky_perm = pp.sky_perm;
@@ -299,7 +326,8 @@ extern "C" tcw_status tcw_search_noalloc(int n_det, int64_t n_seg, int64_t n_bin
     gp.err = err;
     if (launch_group(gp, grid, dtype == TCW_F16, false, st) != cudaSuccess) return TCW_ERR_CUDA;
   } else {
-    // sky groups too wide for one candidate pair: per-lookup FP64 kernel
+    // outside the exactness conditions, or sky groups too wide for one candidate
+    // pair: per-lookup FP64 kernel
     LookupParams lp{};
     lp.rho = rho;
     lp.n_bin = n_bin;

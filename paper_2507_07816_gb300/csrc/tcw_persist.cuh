@@ -183,13 +183,13 @@ __device__ __forceinline__ EntryPrep prepare_entry(const GroupParams& p, const E
     for (int k = p.nterms - 2; k >= 0; --k) R = fma(R, delta, coef[k]);
     h = an.x * R;
   } else {
-    h = pow((tj - ev.T0) / p.tau[b] + 1.0, 1.0 / (p.nbr[b] - 1.0)) / p.f0[b];
+    h = pow((tj - ev.T0) / ev.tau[b] + 1.0, 1.0 / (ev.nbr[b] - 1.0)) / ev.f0[b];
   }
   const float f = __frcp_rn((float)h);
   float amp = 1.0f;
   if (p.amp_power > 0) {
     // amplitude weight (f/f0)^p = (f0 h)^-p (Eq. 3: power grows as h0^2 ~ f^4)
-    const float rr = (float)(h * p.f0[b]);
+    const float rr = (float)(h * ev.f0[b]);
     float rp = rr;
     for (int k = 1; k < p.amp_power; ++k) rp *= rr;
     amp = __frcp_rn(rp);
@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(Geo<LN>::kThreads, 1) group_kernel(GroupParams
         if (p.nterms > 0) {
           __syncwarp();
           for (int lt = lane; lt < kPT; lt += 32) {
-            const double r = 1.0 / (p.nbr[b0 + lt] - 1.0);
+            const double r = 1.0 / (ev.nbr[b0 + lt] - 1.0);
             double c = 1.0;
             for (int k = 0; k < p.nterms; ++k) {
               coef[lt * kMaxSeriesTerms + k] = c;
@@ -739,7 +739,7 @@ __global__ void __launch_bounds__(Geo<LN>::kThreads, 1) group_kernel(GroupParams
             num = (float)(bd[t] - mq * (w1u + (double)dv.x)) + dval;
             rs = W2 > 0.f ? rsqrtf(vq * W2) : 0.f;
           }
-          const int64_t o = (int64_t)(g * G + k) * p.Bpad + b;
+          const int64_t o = (int64_t)(g * G + k) * ev.Bpad + b;
           ev.psi[o] = W2 > 0.f ? num * rs : -INFINITY;
           if (ev.S_out) {
             ev.S_out[o] = (float)bd[t] + dval;

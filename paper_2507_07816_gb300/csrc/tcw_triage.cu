@@ -49,9 +49,10 @@ __global__ void patch_doppler_kernel(PatchDopplerParams p) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int pi = (int)(i % p.P);
-    const int64_t dj = i / p.P;  // d * n_seg + j
+    const int64_t dj = i / p.P;  // d * n_seg + j'
+    const int64_t d = dj / p.n_seg, jc = dj % p.n_seg;
     const int r = min(pi * p.patch_size + (min(p.patch_size, p.S - pi * p.patch_size) - 1) / 2, p.S - 1);
-    const double* v = p.vel + dj * 3;
+    const double* v = p.vel + (d * p.n_seg_full + jc * p.stride) * 3;
     const double* n = p.nhat + (int64_t)r * 3;
     p.dop[i] = (float)((v[0] * n[0] + v[1] * n[1] + v[2] * n[2]) / kLightSpeed);
   }
@@ -113,7 +114,7 @@ __global__ void __launch_bounds__(kCoarseThreads, kCoarseBlocksPerSM) coarse_ker
     if (tid < kCoarseTmpl * 2) s_wsum[tid / 2][tid % 2] = 0.f;
     for (int i = tid; i < D * kCoarseTile; i += kCoarseThreads) {
       const int d = i / kCoarseTile, jj = i % kCoarseTile;
-      s_w[d][jj] = jj < jn ? p.weights[(int64_t)d * p.n_seg + j0 + jj] : 0.f;
+      s_w[d][jj] = jj < jn ? p.weights[(int64_t)d * p.n_seg_full + (int64_t)(j0 + jj) * p.stride] : 0.f;
     }
 #pragma unroll
     for (int r = 0; r < D * kCoarseTile * kCoarseLanes / kCoarseThreads; ++r) {
@@ -170,7 +171,8 @@ __global__ void __launch_bounds__(kCoarseThreads, kCoarseBlocksPerSM) coarse_ker
       const int base = s_ent[t][jj].x;
       float v = 0.f;
       const int64_t k = (int64_t)base - 3 + o;
-      if (base != INT_MIN && k >= 0 && k < p.n_bin) v = load_rho(rho, ((int64_t)d * p.n_seg + j0 + jj) * p.n_bin + k);
+      if (base != INT_MIN && k >= 0 && k < p.n_bin)
+        v = load_rho(rho, ((int64_t)d * p.n_seg_full + (int64_t)(j0 + jj) * p.stride) * p.n_bin + k);
       s_win[t][jj][d][o] = v;
     }
     if (pl < kCoarseTile && pl < jn && s_ent[tl][pl].w && s_ent[tl][pl].x != INT_MIN) {
@@ -241,6 +243,260 @@ __global__ void coarse_finalize_kernel(CoarseParams p) {
 __global__ void features_kernel(const unsigned* hist, int64_t n, float* feat) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     feat[i] = log1pf((float)hist[i]);
+}
+
+// ---------------------------------------------------------------------------
+// Coarse pass, sweep form
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float rep_doppler(const SweepDopplerParams& p, int d, int j, int q) {
+  const int r = min(q * p.patch_size + (min(p.patch_size, p.S - q * p.patch_size) - 1) / 2, p.S - 1);
+  const double* v = p.vel + ((int64_t)d * p.n_seg_full + (int64_t)j * p.stride) * 3;
+  const double* n = p.nhat + (int64_t)r * 3;
+  return (float)((v[0] * n[0] + v[1] * n[1] + v[2] * n[2]) / kLightSpeed);   // Eq. 2
+}
+
+__global__ void sweep_doppler_kernel(SweepDopplerParams p) {
+  const int64_t total = (int64_t)p.n_det * p.n_seg * p.P2;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(i % p.P2);
+    const int64_t dj = i / p.P2;
+    const int d = (int)(dj / p.n_seg), j = (int)(dj % p.n_seg);
+    float v = INFINITY;
+    if (q < p.P) {
+      v = rep_doppler(p, d, j, q);
+      if (q > 0 && rep_doppler(p, d, j, q - 1) > v) *p.unsorted = 1;
+    }
+    p.dop[i] = v;
+  }
+}
+
+constexpr int kSweepChunk = 32;   // segments staged per block step of the sweep form
+
+// shared memory of coarse_sweep_kernel: the staged chunk and the difference arrays
+inline int sweep_smem_bytes(int P, int P2, int D) {
+  return kSweepChunk * (16 + 8 * D + 4 * D * P2) + (P + 1) * kSweepThreads * 4;
+}
+
+__device__ __forceinline__ void sweep_store(const CoarseSweepParams& p, int r, int b, float psi) {
+  if (p.psi) p.psi[(int64_t)r * p.Bpad + b] = psi;
+  int bin = 0;
+  if (psi > -INFINITY) {
+    const float u = floorf((psi - p.lo) / (p.hi - p.lo) * (float)kTriageBins);
+    bin = u < 0.f ? 0 : (u > (float)(kTriageBins - 1) ? kTriageBins - 1 : (int)u);
+  }
+  atomicAdd(p.hist + (int64_t)r * kTriageBins + bin, 1u);
+}
+
+// One thread per template (sorted bank index b) walks the coarse segments;
+// the threads of a block walk them together, in chunks of kSweepChunk
+// segments whose times, weights and representatives' Doppler factors the
+// block stages in shared memory.  Track (Eq. 1): f = f0 u^e, u = (t - T0)/tau
+// + 1, e = 1/(1 - n).  At each tile's anchor time the FP64 f_a comes from the
+// previous anchor, f_a' = f_a (u'/u)^e (binomial series), or from pow at the
+// first anchor.  Inside the tile x = (f - f_min)/df = x_a + X_a g(delta), with
+// X_a = f_a/df, delta = (t - t_a)/(tau u_a) and g = (1 + delta)^e - 1
+// = e delta + C(e,2) delta^2 + ...: the linear and quadratic terms are
+// products of fp32 pairs (hi + lo) whose rounding errors are recovered by fma
+// and whose integer parts are split off exactly, the rest is an fp32 series;
+// the position relative to the integer base keeps an error of ~1e-7 bins.
+// Representative q's bin is base + floor(frac5 + F v_q/c), F = f/df (Eq. 2);
+// the thread gathers representative 0's bin and, for each later bin of the
+// step function, finds the first representative that reaches it (a guess from
+// the factors' nearly even spacing, corrected by exact comparisons) and adds
+// the power difference to that representative's entry of the difference array
+// (shared memory, one column per thread).  Lookups where
+// some representatives leave the band take every representative one by one
+// and record their W2 and count steps in global scratch.  Psi (Eq. 4) =
+// (S - W1)/sqrt(W2), accumulated as sum w (rho - 1).
+template <typename RhoT, int D, int NC>
+__global__ void __launch_bounds__(kSweepThreads, 4) coarse_sweep_kernel(CoarseSweepParams p) {
+  extern __shared__ float4 s_sweep[];
+  float4* s_seg = s_sweep;                                              // [kSweepChunk]
+  float* s_w = reinterpret_cast<float*>(s_seg + kSweepChunk);           // [D][kSweepChunk]
+  float* s_step = s_w + D * kSweepChunk;                                // [kSweepChunk][D] (P-1)/span
+  float* s_dop = s_step + D * kSweepChunk;                              // [kSweepChunk][D][P2]
+  float* s_diff = s_dop + kSweepChunk * D * p.P2;                       // [P + 1][kSweepThreads]
+  const int tid = threadIdx.x;
+  const int b = blockIdx.x * kSweepThreads + tid;
+  const bool live = b < p.B;
+  float* col = s_diff + tid;
+  for (int r = 0; r <= p.P; ++r) col[r * kSweepThreads] = 0.f;
+  const RhoT* rho = static_cast<const RhoT*>(p.rho);
+  const int bb = live ? b : 0;
+  const double tau = p.tau[bb], e = -1.0 / (p.nbr[bb] - 1.0);
+  if (live) {
+    double c = 1.0;
+    for (int k = 0; k < p.nt64; ++k) {
+      p.coef64[(int64_t)k * p.Bpad + b] = c;   // C(e, k)
+      c = c * (e - k) / (k + 1);
+    }
+  }
+  const double c2 = 0.5 * e * (e - 1.0);
+  float cf[NC];   // C(e, k + 3)
+  {
+    double c = c2;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+      c = c * (e - (k + 2)) / (k + 3);
+      cf[k] = (float)c;
+    }
+  }
+  const double inv_tau = 1.0 / tau, inv_df = 1.0 / p.df, xmin = p.f_min * inv_df;
+  double fa = 0.0, ua = 0.0, inv_ua = 0.0;
+  bool have = false, edge = false, tile_ok = false;
+  int base_a = 0;
+  float frac_a = 0.f, A_hi = 0.f, A_lo = 0.f, Q_hi = 0.f, Q_lo = 0.f, Xf = 0.f, sg = 0.f;
+  float Sb = 0.f, W2b = 0.f;
+  const int P2 = p.P2;
+  for (int c0 = 0; c0 < p.n_seg; c0 += kSweepChunk) {
+    const int cn = min(kSweepChunk, p.n_seg - c0);
+    __syncthreads();
+    for (int i = tid; i < cn; i += kSweepThreads) s_seg[i] = p.seg[c0 + i];
+    for (int i = tid; i < D * cn; i += kSweepThreads) {
+      const int d = i / cn, jj = i % cn;
+      s_w[d * kSweepChunk + jj] = p.weights[(int64_t)d * p.n_seg_full + (int64_t)(c0 + jj) * p.stride];
+    }
+    for (int i = tid; i < D * cn * P2; i += kSweepThreads) {
+      const int q = i % P2, dj = i / P2, d = dj / cn, jj = dj % cn;
+      s_dop[(jj * D + d) * P2 + q] = p.dop[((int64_t)d * p.n_seg + c0 + jj) * P2 + q];
+    }
+    for (int i = tid; i < D * cn; i += kSweepThreads) {
+      const int d = i / cn, jj = i % cn;
+      const float* dr = p.dop + ((int64_t)d * p.n_seg + c0 + jj) * P2;
+      const float span = dr[p.P - 1] - dr[0];
+      s_step[jj * D + d] = span > 0.f ? (float)(p.P - 1) / span : 0.f;
+    }
+    __syncthreads();
+    if (!live) continue;
+    for (int jj = 0; jj < cn; ++jj) {
+      const int j = c0 + jj;
+      if ((j & ((1 << p.tile_shift) - 1)) == 0) {
+        // anchor of tile k (FP64)
+        const double ta = p.ta[j >> p.tile_shift];
+        tile_ok = false;
+        if (!isnan(ta)) {
+          const double u = fma(ta - p.T0, inv_tau, 1.0);
+          if (!have) {
+            fa = p.f0[b] * pow(u, e);
+            have = true;
+          } else {
+            const double dl = (u - ua) * inv_ua;   // u / u_a - 1
+            double R = p.coef64[(int64_t)(p.nt64 - 1) * p.Bpad + b];
+            for (int i = p.nt64 - 2; i >= 0; --i) R = fma(R, dl, p.coef64[(int64_t)i * p.Bpad + b]);
+            fa *= R;
+          }
+          ua = u;
+          inv_ua = 1.0 / u;
+          const double X = fa * inv_df;
+          const double xa = X - xmin;
+          const double xr = rint(xa);
+          if (fabs(xr) < 1.0e9) {
+            tile_ok = true;
+            base_a = (int)xr;
+            frac_a = (float)(xa - xr);
+            const double s = inv_tau * inv_ua;
+            const double A = X * e * s, Q = X * c2 * s * s;
+            A_hi = (float)A;
+            A_lo = (float)(A - (double)A_hi);
+            Q_hi = (float)Q;
+            Q_lo = (float)(Q - (double)Q_hi);
+            Xf = (float)X;
+            sg = (float)s;
+          }
+        }
+      }
+      const float4 sj = s_seg[jj];
+      if (!tile_ok || isnan(sj.x)) continue;
+      const float pl = A_hi * sj.x, plr = rintf(pl);
+      const float pq = Q_hi * sj.z, pqr = rintf(pq);
+      const float dl = sj.x * sg;
+      float h = cf[NC - 1];
+#pragma unroll
+      for (int i = NC - 2; i >= 0; --i) h = fmaf(h, dl, cf[i]);
+      const float p3 = Xf * (dl * dl * dl * h);
+      const float small = (fmaf(A_hi, sj.x, -pl) + fmaf(A_hi, sj.y, A_lo * sj.x)) +
+                          (fmaf(Q_hi, sj.z, -pq) + fmaf(Q_hi, sj.w, Q_lo * sj.z)) + p3;
+      const float frac5 = ((frac_a + (pl - plr)) + ((pq - pqr) + small)) + 0.5f;
+      const float F = Xf + pl + pq;
+      const int base = base_a + (int)plr + (int)pqr;
+      // both detectors' first gathers before either is used
+      int olo[D], ohi[D];
+      float r0[D];
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        const float* dr = s_dop + (jj * D + d) * P2;
+        olo[d] = __float2int_rd(fmaf(F, dr[0], frac5));
+        ohi[d] = __float2int_rd(fmaf(F, dr[p.P - 1], frac5));
+        const int64_t k0 = (int64_t)base + olo[d];
+        const int64_t kc = k0 < 0 ? 0 : (k0 >= p.n_bin ? p.n_bin - 1 : k0);
+        r0[d] = load_rho(rho, ((int64_t)d * p.n_seg_full + (int64_t)j * p.stride) * p.n_bin + kc);
+      }
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        const float w = s_w[d * kSweepChunk + jj];
+        const float* dr = s_dop + (jj * D + d) * P2;
+        const int64_t k0 = (int64_t)base + olo[d], k1 = (int64_t)base + ohi[d];
+        const RhoT* row = rho + ((int64_t)d * p.n_seg_full + (int64_t)j * p.stride) * p.n_bin;
+        if (k0 >= 0 && k1 < p.n_bin) {
+          float rp = r0[d];
+          Sb = fmaf(w, rp - 1.f, Sb);
+          W2b = fmaf(w, w, W2b);
+          if (ohi[d] > olo[d]) {
+            const float step = s_step[jj * D + d], d0 = dr[0], rF = __frcp_rn(F);
+            for (int o = olo[d] + 1; o <= ohi[d]; ++o) {
+              const float r1 = load_rho(row, (int64_t)base + o);
+              // first representative q with fmaf(F, v_q/c, frac5) >= o: q is in
+              // [1, P-1] (representative 0 is below o, the last one reaches it);
+              // guessed from the nearly even spacing of the factors, then moved
+              // until representative q-1 is below o and q is not
+              const float thr = (float)o;
+              int q = (int)(((thr - frac5) * rF - d0) * step) + 1;
+              q = min(max(q, 1), p.P - 1);
+              while (q > 1 && fmaf(F, dr[q - 1], frac5) >= thr) --q;
+              while (q < p.P - 1 && fmaf(F, dr[q], frac5) < thr) ++q;
+              col[q * kSweepThreads] += w * (r1 - rp);
+              rp = r1;
+            }
+          }
+        } else if (k1 >= 0 && k0 < p.n_bin) {
+          if (!edge) {
+            edge = true;
+            for (int r = 0; r <= p.P; ++r) {
+              p.w2edge[(int64_t)r * p.Bpad + b] = 0.0;
+              p.nedge[(int64_t)r * p.Bpad + b] = 0;
+            }
+          }
+          const double w2 = (double)w * (double)w;
+          for (int r = 0; r < p.P; ++r) {
+            const int64_t kr = (int64_t)base + __float2int_rd(fmaf(F, dr[r], frac5));
+            if (kr < 0 || kr >= p.n_bin) continue;
+            const float v = w * (load_rho(row, kr) - 1.f);
+            col[r * kSweepThreads] += v;
+            col[(r + 1) * kSweepThreads] -= v;
+            p.w2edge[(int64_t)r * p.Bpad + b] += w2;
+            p.w2edge[(int64_t)(r + 1) * p.Bpad + b] -= w2;
+            p.nedge[(int64_t)r * p.Bpad + b] += 1;
+            p.nedge[(int64_t)(r + 1) * p.Bpad + b] -= 1;
+          }
+        }
+      }
+    }
+  }
+  if (!live) return;
+  float acc = Sb;
+  double w2e = 0.0;
+  int ne = 0;
+  for (int r = 0; r < p.P; ++r) {
+    acc += col[r * kSweepThreads];
+    if (edge) {
+      w2e += p.w2edge[(int64_t)r * p.Bpad + b];
+      ne += p.nedge[(int64_t)r * p.Bpad + b];
+    }
+    // a representative with no in-band edge lookup takes the interior W2 alone
+    const double W2 = (double)W2b + (ne > 0 ? w2e : 0.0);
+    sweep_store(p, r, b, W2 > 0.0 ? acc * rsqrtf((float)W2) : -INFINITY);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -447,6 +703,44 @@ void launch_coarse_l(const CoarseParams& p, bool half, cudaStream_t st) {
     else
       coarse_kernel<float, 2, PL><<<grid, kCoarseThreads, 0, st>>>(p);
   }
+}
+
+cudaError_t launch_sweep_doppler(const SweepDopplerParams& p, cudaStream_t st) {
+  const int64_t total = (int64_t)p.n_det * p.n_seg * p.P2;
+  sweep_doppler_kernel<<<blocks_for(total, 256), 256, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <typename RhoT, int D, int NC>
+cudaError_t launch_sweep_t(const CoarseSweepParams& p, cudaStream_t st) {
+  const int smem = sweep_smem_bytes(p.P, p.P2, D);
+  auto kern = coarse_sweep_kernel<RhoT, D, NC>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  kern<<<(p.B + kSweepThreads - 1) / kSweepThreads, kSweepThreads, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+template <typename RhoT, int D>
+cudaError_t launch_sweep_d(const CoarseSweepParams& p, int nc, cudaStream_t st) {
+  if (nc <= 4) return launch_sweep_t<RhoT, D, 4>(p, st);
+  if (nc <= 6) return launch_sweep_t<RhoT, D, 6>(p, st);
+  return launch_sweep_t<RhoT, D, 8>(p, st);
+}
+
+cudaError_t launch_coarse_sweep(const CoarseSweepParams& p, bool half, int nc, cudaStream_t st) {
+  if (p.n_det < 1 || p.n_det > kCoarseMaxDet || p.P < 1 || p.P > kSweepMaxPatches || nc > 8 ||
+      p.nt64 < 1 || p.nt64 > kSweepMaxTerms || p.P2 < p.P || (p.P2 & (p.P2 - 1)))
+    return cudaErrorInvalidValue;
+  cudaError_t e;
+  if (half)
+    e = p.n_det == 1 ? launch_sweep_d<__half, 1>(p, nc, st) : launch_sweep_d<__half, 2>(p, nc, st);
+  else
+    e = p.n_det == 1 ? launch_sweep_d<float, 1>(p, nc, st) : launch_sweep_d<float, 2>(p, nc, st);
+  if (e != cudaSuccess) return e;
+  const int64_t n = (int64_t)p.P * kTriageBins;
+  features_kernel<<<blocks_for(n, 256), 256, 0, st>>>(p.hist, n, p.feat);
+  return cudaGetLastError();
 }
 
 size_t coarse_part_elems(int P, int Bpad) { return (size_t)kCoarseMaxParts * P * Bpad * 3; }

@@ -23,6 +23,7 @@ KERNEL_AUTO, KERNEL_GROUP, KERNEL_LOOKUP = 0, 1, 2
 OPT_KERNEL, OPT_KEEP_STATS, OPT_TILE_SEGMENTS, OPT_BANK_CHUNK = 1, 2, 3, 4
 OPT_AUTOTUNE, OPT_BATCH_MEMORY, OPT_SKY_LANES, OPT_TRIAGE_SPREAD = 5, 6, 7, 8
 OPT_AMPLITUDE_POWER, OPT_GEN_CHUNK, OPT_TRACK_BINS, OPT_TRIAGE_TEMPLATES = 9, 10, 11, 12
+OPT_TRIAGE_STRIDE = 13
 STAT_POWER, STAT_NUMBER_COUNT = 0, 1
 
 _lock = threading.Lock()
@@ -87,7 +88,8 @@ class _TriageInfo(ctypes.Structure):
                 ("skies_searched", ctypes.c_int64), ("lookups_full", ctypes.c_int64),
                 ("lookups_coarse", ctypes.c_int64), ("lookups_searched", ctypes.c_int64),
                 ("coarse_ms", ctypes.c_float), ("mlp_ms", ctypes.c_float),
-                ("search_ms", ctypes.c_float), ("templates_searched", ctypes.c_int64)]
+                ("search_ms", ctypes.c_float), ("templates_searched", ctypes.c_int64),
+                ("coarse_kernel", ctypes.c_int)]
 
 
 MLP_PARAMS, MLP_WEIGHTS = 99073, 98560
@@ -134,6 +136,7 @@ def load_library(build_if_missing: bool = True):
             "tcw_mlp_adam": [p, p, p, p, i64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                              ctypes.c_float, p, p],
             "tcw_triage_features": [p, i, ctypes.c_float, ctypes.c_float, p, p, i],
+            "tcw_triage_rank": [p, p, p, i, ctypes.c_float, ctypes.c_float, p, p, p, i],
             "tcw_search_triaged": [p, p, p, i, ctypes.c_float, ctypes.c_float, ctypes.c_float, i,
                                    p, p, p, i],
             "tcw_get_triage_info": [p, ctypes.POINTER(_TriageInfo)],
@@ -428,6 +431,19 @@ class Search:
             self._h, int(patch_size), float(psi_lo), float(psi_hi), ctypes.c_void_p(out.data_ptr()),
             None, DEVICE))
         return out
+
+    def triage_rank(self, mlp, patch_size, psi_lo, psi_hi):
+        """Network scores [n_patch], patch order [n_patch] and ranked sky order
+        [n_sky] (caller indices) as numpy."""
+        P = -(-self.n_sky // max(int(patch_size), 1))   # the library rejects patch_size < 1
+        score = np.empty(P, np.float32)
+        order = np.empty(P, np.int32)
+        skies = np.empty(self.n_sky, np.int32)
+        self._check(self._lib.tcw_triage_rank(
+            self._h, ctypes.c_void_p(mlp.wbf.data_ptr()), ctypes.c_void_p(mlp.theta.data_ptr()),
+            int(patch_size), float(psi_lo), float(psi_hi), score.ctypes.data_as(ctypes.c_void_p),
+            order.ctypes.data_as(ctypes.c_void_p), skies.ctypes.data_as(ctypes.c_void_p), HOST))
+        return score, order, skies
 
     def search_triaged(self, mlp, patch_size, psi_lo, psi_hi, frac, k):
         """Triaged search: (psi [S][k], idx [S][k], searched [S]) as numpy."""

@@ -68,6 +68,40 @@ def test_coarse_features_match_oracle(P_SIZE):
     s.close()
 
 
+def test_coarse_pass_on_every_third_segment_matches_oracle():
+    """TCW_OPT_TRIAGE_STRIDE = 3: the coarse Psi equals the oracle's Psi at
+    the patch representatives computed on segments 0, 3, 6, ... (the
+    representatives come from the full search's sky order)."""
+    ev, bank = small_event(87, n_inj=2, n_seg=151)
+    LO, HI, PS, ST = -4.0, 12.0, 8, 3
+    s = tcw.Search(0)
+    s.set_option(tcw.OPT_TRIAGE_STRIDE, ST)
+    TR.load_event(s, ev, bank)
+    feat, psi = s.triage_features(PS, LO, HI, with_psi=True)
+    assert s.triage_info()["lookups_coarse"] == psi.shape[0] * len(bank) * 2 * (-(-151 // ST))
+    order = OT.sky_order(ev.velocity, ev.nhat)
+    reps = [order[r] for _, _, r in OT.patches(len(order), PS)]
+    sl = slice(None, None, ST)
+    w = None if ev.weights is None else ev.weights[:, sl]
+    S_, _, W2, ora = oracle.search_stats(ev.rho[:, sl], ev.f_min, ev.df, ev.t_mid[sl], w, ev.velocity[:, sl],
+                                         ev.nhat[reps], bank.f0, bank.tau, bank.n, ev.T0)
+    pairs = np.array([(pi, b) for pi in range(len(reps)) for b in range(len(bank))])
+    x = oracle.track_coordinates(2, ev.f_min, ev.df, ev.t_mid[sl], ev.velocity[:, sl], ev.nhat[reps],
+                                 bank.f0, bank.tau, bank.n, ev.T0, pairs)
+    fr = x - np.floor(x)
+    near = (np.isfinite(x) & (np.abs(fr - 0.5) <= COARSE_TIE)).any(axis=(1, 2)).reshape(len(reps), len(bank))
+    fin = np.isfinite(ora)
+    np.testing.assert_array_equal(np.isfinite(psi), fin)
+    tol = REL * np.abs(S_) / np.sqrt(np.maximum(W2, 1e-30)) + 1e-5
+    ok = fin & ~near
+    assert ok.mean() > 0.9
+    err = np.abs(psi.astype(np.float64) - ora)
+    assert np.all(err[ok] <= tol[ok]), err[ok].max()
+    with pytest.raises(tcw.TcwError):
+        s.set_option(tcw.OPT_TRIAGE_STRIDE, 0)
+    s.close()
+
+
 def test_mlp_forward_backward_bce_adam_match_oracle():
     r = np.random.default_rng(82)
     theta = (r.normal(size=OT.N_PARAMS) * 0.1).astype(np.float32)
@@ -166,6 +200,40 @@ def test_triaged_search_rows_equal_exhaustive_rows(amp, count):
     chosen = sorted({int(pos[i]) // 16 for i in np.nonzero(searched)[0]})
     assert len(chosen) == s.triage_info()["n_selected"] == 3
     assert all(b - a > 2 for a, b in zip(chosen, chosen[1:])), chosen
+    s.close()
+
+
+def test_triage_rank_matches_forward_of_features_and_drives_the_triaged_search():
+    """tcw_triage_rank: the scores equal tcw_mlp_forward on tcw_triage_features'
+    output, the patch order is argsort(-score) with ties by patch index, the
+    sky order lists the patches' Doppler-sorted skies in that order, and a
+    triaged search with spread 0 searches exactly the first ceil(frac P)
+    patches of it."""
+    ev, bank = small_event(86, n_sky=200, n_inj=2, snr=(14.0, 16.0), n_bin=9600, t_sft=32.0)
+    r = np.random.default_rng(86)
+    mlp = tcw.Mlp((r.normal(size=OT.N_PARAMS) * 0.05).astype(np.float32), device=DEV)
+    s = tcw.Search(0)
+    s.set_option(tcw.OPT_TRIAGE_SPREAD, 0)
+    TR.load_event(s, ev, bank)
+    PS, LO, HI = 16, -4.0, 12.0
+    score, order, skies = s.triage_rank(mlp, PS, LO, HI)
+    feat = s.triage_features(PS, LO, HI)
+    _, _, y = mlp.forward(torch.as_tensor(feat, device=DEV))
+    np.testing.assert_array_equal(score, y.cpu().numpy())
+    P = len(score)
+    assert P == -(-ev.nhat.shape[0] // PS)
+    expect = np.array(sorted(range(P), key=lambda i: (-float(score[i]), i)), np.int32)
+    np.testing.assert_array_equal(order, expect)
+    sorted_sky = s.sky_order()
+    np.testing.assert_array_equal(skies, np.concatenate([sorted_sky[i * PS:(i + 1) * PS] for i in order]))
+    assert sorted(skies.tolist()) == list(range(ev.nhat.shape[0]))
+    for frac in (0.25, 0.5):
+        m = int(np.ceil(frac * P))
+        _, _, searched = s.search_triaged(mlp, PS, LO, HI, frac, 4)
+        first = np.concatenate([sorted_sky[i * PS:(i + 1) * PS] for i in order[:m]])
+        np.testing.assert_array_equal(np.sort(np.nonzero(searched)[0]), np.sort(first))
+    with pytest.raises(tcw.TcwError):
+        s.triage_rank(mlp, 0, LO, HI)
     s.close()
 
 
