@@ -8,7 +8,9 @@ module drives the library's kernels only:
   patch features   tcw_triage_features (coarse pass + histogram), on device
   network          Mlp: tcw_mlp_forward / backward / bce / adam, on device
   triaged search   tcw_search_triaged
-  judge            the exhaustive tcw_search of every sky
+  judge            the exhaustive tcw_search of every sky, with the detection
+                   threshold of Sec. 3: Psi above the largest Psi of
+                   noise-only searches with the same bank
 
 Events come from a caller-supplied ``make_event(i)`` returning an object with
 rho, t_mid, weights, velocity, f_min, df, T0, nhat and ``injections`` (each
@@ -37,6 +39,10 @@ JUDGE_RADIUS = 64
 # searched at every chosen sky.
 FRAC = 0.35
 TEMPLATES_PERMILLE = 12
+# The coarse pass runs on every STRIDE-th segment (TCW_OPT_TRIAGE_STRIDE).
+# Every segment: with a stride of 2 the coarse Psi of an injection loses a
+# factor sqrt(2) and falls into the noise of the other patches' maxima.
+STRIDE = 1
 
 
 def load_event(search, ev, bank, define_bank=True):
@@ -66,11 +72,14 @@ def patch_labels(search, ev, patch_size=PATCH_SIZE, radius=LABEL_RADIUS):
     return lab
 
 
-def collect(make_event, n_events, bank, patch_size=PATCH_SIZE, lo=PSI_LO, hi=PSI_HI, device="cuda:0"):
+def collect(make_event, n_events, bank, patch_size=PATCH_SIZE, lo=PSI_LO, hi=PSI_HI, device="cuda:0",
+            stride=STRIDE):
     """Features [N][128] and labels [N] (CUDA tensors) of n_events events, and
     the number of patches of each event."""
     import torch
+    from .tcw import OPT_TRIAGE_STRIDE
     s = Search(0)
+    s.set_option(OPT_TRIAGE_STRIDE, stride)
     feats, labs, sizes = [], [], []
     for i in range(n_events):
         ev = make_event(i)
@@ -125,27 +134,43 @@ def recall_at(mlp, X, y, sizes, frac):
     return hit / max(tot, 1)
 
 
-def judge(ev, psi, idx, pos, k_det=10, psi_det=6.5, radius=JUDGE_RADIUS):
+def noise_threshold(make_noise_event, n_events, bank):
+    """Detection threshold of Sec. 3: the largest Psi over every sky and
+    template of exhaustive searches of n_events noise-only events with the
+    same bank (so at most one detection per n_events noise searches)."""
+    s = Search(0)
+    top = -np.inf
+    for i in range(n_events):
+        load_event(s, make_noise_event(i), bank)
+        psi, _ = s.search(1)
+        top = max(top, float(np.max(psi)))
+    s.close()
+    return top
+
+
+def judge(ev, psi, idx, pos, psi_det, k_det=10, radius=JUDGE_RADIUS):
     """Injections found: the injected template within the first k_det entries,
-    with Psi >= psi_det, of some sky within `radius` Doppler-sorted positions
-    (pos) of the injected sky."""
+    with Psi > psi_det (the noise-only maximum), of some sky within `radius`
+    Doppler-sorted positions (pos) of the injected sky."""
     found = []
     for inj in ev.injections:
         near = np.nonzero(np.abs(pos - pos[inj.sky]) <= radius)[0]
         rows_i, rows_p = idx[near, :k_det], psi[near, :k_det]
-        hit = (rows_i == inj.template) & (rows_p >= psi_det)
+        hit = (rows_i == inj.template) & (rows_p > psi_det)
         found.append(bool(hit.any()))
     return found
 
 
-def evaluate(mlp, make_event, n_events, bank, frac=FRAC, k=100, patch_size=PATCH_SIZE, lo=PSI_LO, hi=PSI_HI,
-             k_det=10, psi_det=6.5, templates_permille=TEMPLATES_PERMILLE):
-    """Judge the triaged search against the exhaustive one on fresh events.
+def evaluate(mlp, make_event, n_events, bank, psi_det, frac=FRAC, k=100, patch_size=PATCH_SIZE, lo=PSI_LO,
+             hi=PSI_HI, k_det=10, templates_permille=TEMPLATES_PERMILLE, stride=STRIDE):
+    """Judge the triaged search against the exhaustive one on fresh events
+    (psi_det: the detection threshold, see noise_threshold).
     templates_permille < 1000 also restricts each chosen patch to its best
     templates by coarse Psi (TCW_OPT_TRIAGE_TEMPLATES)."""
-    from .tcw import OPT_TRIAGE_TEMPLATES
+    from .tcw import OPT_TRIAGE_STRIDE, OPT_TRIAGE_TEMPLATES
     s = Search(0)
     s.set_option(OPT_TRIAGE_TEMPLATES, templates_permille)
+    s.set_option(OPT_TRIAGE_STRIDE, stride)
     full_found = tri_found = 0
     missed = 0
     t_full = t_tri = 0.0
@@ -164,8 +189,8 @@ def evaluate(mlp, make_event, n_events, bank, frac=FRAC, k=100, patch_size=PATCH
         t_tri += t2 - t1
         sums_full += info["lookups_full"]
         sums_tri += info["lookups_coarse"] + info["lookups_searched"]
-        ff = judge(ev, pf, xf, pos, k_det, psi_det)
-        tf = judge(ev, pt, xt, pos, k_det, psi_det)
+        ff = judge(ev, pf, xf, pos, psi_det, k_det)
+        tf = judge(ev, pt, xt, pos, psi_det, k_det)
         full_found += sum(ff)
         tri_found += sum(tf)
         missed += sum(a and not b for a, b in zip(ff, tf))
@@ -174,4 +199,5 @@ def evaluate(mlp, make_event, n_events, bank, frac=FRAC, k=100, patch_size=PATCH
             "missed": missed, "loss": missed / max(full_found, 1), "time_full_s": t_full,
             "time_triaged_s": t_tri, "speedup": t_full / max(t_tri, 1e-12),
             "sums_full": sums_full, "sums_executed_triaged": sums_tri, "frac": frac,
-            "patch_size": patch_size, "templates_permille": templates_permille}
+            "patch_size": patch_size, "templates_permille": templates_permille, "stride": stride,
+            "psi_det": psi_det}

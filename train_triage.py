@@ -4,18 +4,22 @@
 Training set: method-generated events at the shapes of the plain 2-detector
 workload (10^4 segments x 10^4 bins, T_SFT = 4 s, 500-3000 Hz, 1024
 Fibonacci-sphere skies), each with one injected track of SNR uniform in
-[6, 12] whose template comes from a 2e4-template uniform-random bank; one
-example per sky patch (32 Doppler-sorted skies), label 1 for the patches
-within one patch of an injected sky.  The features come from the library's coarse pass and
-the network is trained by the library's own forward/backward/Adam kernels.
+[6, 12] whose template comes from the workload's 2e5-template uniform-random
+bank; one example per sky patch (32 Doppler-sorted skies), label 1 for the
+patches within one patch of an injected sky: 3125 events give 1.0e5
+examples.  The features come from the library's coarse pass (every segment)
+and the network is trained by the library's own forward/backward/Adam
+kernels.
 
-Judge: on held-out events the triaged search (best 35 % of patches, each
-contributing its best 1.2 % of templates by coarse Psi) is compared with the
-exhaustive search of every sky; an injection counts as found when its
-template is within the first 10 entries, with Psi >= 6.5, of a searched sky
-within 64 Doppler-sorted positions of the injected sky.
+Judge (Sec. 3): the detection threshold is the largest Psi of exhaustive
+searches of noise-only events with the same bank; on held-out events the
+triaged search (best 35 % of patches, each contributing its best 1.2 % of
+templates by coarse Psi) is compared with the exhaustive search of every
+sky; an injection counts as found when its template is within the first 10
+entries, with Psi above the threshold, of a searched sky within 64
+Doppler-sorted positions of the injected sky.
 
-  python train_triage.py [--train-events 3125] [--valid-events 1000]
+  python train_triage.py [--train-events 3125] [--valid-events 100]
                          [--frac 0.35] [--templates-permille 12] [--judge-only]
                          [--out paper_2507_07816_gb300/triage_weights.npz]
                          [--report triage_report.json]
@@ -39,8 +43,10 @@ sys.path.insert(0, ROOT)
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--train-events", type=int, default=3125)   # x 32 patches = 1.0e5 examples
-    ap.add_argument("--valid-events", type=int, default=1000)
-    ap.add_argument("--n-tmpl", type=int, default=20000)
+    ap.add_argument("--valid-events", type=int, default=100)
+    ap.add_argument("--noise-events", type=int, default=4)
+    ap.add_argument("--n-tmpl", type=int, default=200000)
+    ap.add_argument("--stride", type=int, default=None)
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--batch", type=int, default=4096)
     ap.add_argument("--lr", type=float, default=1e-3)
@@ -64,22 +70,29 @@ def main():
     tpm = TR.TEMPLATES_PERMILLE if args.templates_permille is None else args.templates_permille
     if args.frac is None:
         args.frac = TR.FRAC
+    stride = TR.STRIDE if args.stride is None else args.stride
 
-    def make(seed0):
-        return lambda i: syn.training_event(seed0 + i, bank, n_inj=args.injections, snr_range=(6.0, 12.0),
-                                            device=dev)
+    def make(seed0, n_inj=None):
+        n = args.injections if n_inj is None else n_inj
+        return lambda i: syn.training_event(seed0 + i, bank, n_inj=n, snr_range=(6.0, 12.0), device=dev)
+
+    noise_seed = valid_seed + 500_000
+    t0 = time.perf_counter()
+    psi_det = TR.noise_threshold(make(noise_seed, 0), args.noise_events, bank)
+    print(f"noise-only threshold {psi_det:.4f} from {args.noise_events} events in "
+          f"{time.perf_counter() - t0:.0f} s", flush=True)
 
     if args.judge_only:
         mlp = tcw.Mlp.load(args.out, device=dev)
         untrained = tcw.Mlp(seed=1, device=dev)
         t0 = time.perf_counter()
-        judged = TR.evaluate(mlp, make(valid_seed + 1000), args.valid_events, bank, frac=args.frac,
-                             patch_size=args.patch_size, templates_permille=tpm)
-        judged_all = TR.evaluate(mlp, make(valid_seed + 1000), min(args.valid_events, 200), bank, frac=args.frac,
-                                 patch_size=args.patch_size, templates_permille=1000)
-        judged_un = TR.evaluate(untrained, make(valid_seed + 1000), min(args.valid_events, 50), bank,
-                                frac=args.frac, patch_size=args.patch_size, templates_permille=tpm)
-        report = {"weights": os.path.relpath(args.out, ROOT), "judged_trained": judged,
+        judged = TR.evaluate(mlp, make(valid_seed + 1000), args.valid_events, bank, psi_det, frac=args.frac,
+                             patch_size=args.patch_size, templates_permille=tpm, stride=stride)
+        judged_all = TR.evaluate(mlp, make(valid_seed + 1000), min(args.valid_events, 200), bank, psi_det,
+                                 frac=args.frac, patch_size=args.patch_size, templates_permille=1000, stride=stride)
+        judged_un = TR.evaluate(untrained, make(valid_seed + 1000), min(args.valid_events, 50), bank, psi_det,
+                                frac=args.frac, patch_size=args.patch_size, templates_permille=tpm, stride=stride)
+        report = {"weights": os.path.relpath(args.out, ROOT), "psi_det": psi_det, "judged_trained": judged,
                   "judged_trained_all_templates": judged_all, "judged_untrained": judged_un,
                   "valid_s": time.perf_counter() - t0}
         print(json.dumps(report), flush=True)
@@ -90,10 +103,10 @@ def main():
         return 0
 
     t0 = time.perf_counter()
-    X, y, sizes = TR.collect(make(train_seed), args.train_events, bank, patch_size=args.patch_size)
+    X, y, sizes = TR.collect(make(train_seed), args.train_events, bank, patch_size=args.patch_size, stride=stride)
     t_collect = time.perf_counter() - t0
     print(f"collected {X.shape[0]} examples ({int(y.sum().item())} positive) in {t_collect:.0f} s", flush=True)
-    Xh, yh, sizes_h = TR.collect(make(valid_seed), 64, bank, patch_size=args.patch_size)
+    Xh, yh, sizes_h = TR.collect(make(valid_seed), 64, bank, patch_size=args.patch_size, stride=stride)
     untrained = tcw.Mlp(seed=1, device=dev)
     t0 = time.perf_counter()
     mlp, losses = TR.train(X, y, steps=args.steps, batch=args.batch, lr=args.lr, seed=1,
@@ -107,19 +120,24 @@ def main():
     np.savez(args.out, theta=mlp.parameters(), bank_seed=bank_seed, n_tmpl=args.n_tmpl,
              patch_size=args.patch_size, frac=args.frac, psi_lo=TR.PSI_LO, psi_hi=TR.PSI_HI,
              valid_seed=valid_seed, train_events=args.train_events, train_examples=int(X.shape[0]),
-             injections=args.injections)
+             injections=args.injections, stride=stride, psi_det=psi_det, noise_seed=noise_seed,
+             noise_events=args.noise_events)
     t0 = time.perf_counter()
-    judged = TR.evaluate(mlp, make(valid_seed + 1000), args.valid_events, bank, frac=args.frac,
-                         patch_size=args.patch_size, templates_permille=tpm)
-    judged_un = TR.evaluate(untrained, make(valid_seed + 1000), min(args.valid_events, 50), bank,
-                            frac=args.frac, patch_size=args.patch_size, templates_permille=tpm)
+    judged = TR.evaluate(mlp, make(valid_seed + 1000), args.valid_events, bank, psi_det, frac=args.frac,
+                         patch_size=args.patch_size, templates_permille=tpm, stride=stride)
+    judged_un = TR.evaluate(untrained, make(valid_seed + 1000), min(args.valid_events, 50), bank, psi_det,
+                            frac=args.frac, patch_size=args.patch_size, templates_permille=tpm, stride=stride)
+    # the literal form: the best 10 % of the patches, every template
+    judged_lit = TR.evaluate(mlp, make(valid_seed + 1000), args.valid_events, bank, psi_det, frac=0.1,
+                             patch_size=args.patch_size, templates_permille=1000, stride=stride)
     t_valid = time.perf_counter() - t0
-    report = {"train_examples": int(X.shape[0]), "train_positive": int(y.sum().item()),
+    report = {"psi_det": psi_det, "stride": stride,
+              "train_examples": int(X.shape[0]), "train_positive": int(y.sum().item()),
               "train_events": args.train_events, "n_tmpl": args.n_tmpl, "steps": args.steps,
               "batch": args.batch, "lr": args.lr, "losses": losses, "collect_s": t_collect,
               "train_s": t_train, "valid_s": t_valid, "patch_recall_trained": rec,
               "patch_recall_untrained": rec_un, "judged_trained": judged,
-              "judged_untrained": judged_un}
+              "judged_untrained": judged_un, "judged_trained_top10pct_all_templates": judged_lit}
     print(json.dumps(report), flush=True)
     if args.report:
         os.makedirs(os.path.dirname(os.path.abspath(args.report)), exist_ok=True)
