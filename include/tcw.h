@@ -412,6 +412,30 @@ tcw_status tcw_search_triaged(tcw_ctx *ctx, const uint16_t *wbf, const float *th
                               float *psi_out, int64_t *idx_out, int32_t *searched_out,
                               int out_flags);
 
+/* Batched triaged search over the events of tcw_load_events against the
+ * context's bank: the coarse pass of every event (patches of patch_size
+ * Doppler-sorted skies of that event; patch_size = 0: ceil(n_sky / 32)
+ * skies, i.e. 32 patches per event), ONE network call over all events'
+ * patches, per event the ceil(frac * n_patch) best patches (spread apart by
+ * TCW_OPT_TRIAGE_SPREAD), and one persistent group-kernel launch per wave over
+ * the chosen (event, sky chunk, template group) items.  With
+ * TCW_OPT_TRIAGE_TEMPLATES < 1000 each chosen patch contributes its
+ * max(ceil(n_tmpl * permille / 1000), k) best templates by coarse Psi and an
+ * event's chosen skies are searched over the union of its patches' templates;
+ * otherwise over the whole bank, so that a searched row equals the row of
+ * tcw_search_batched.  psi_out/idx_out [total_sky][k] as tcw_search_batched
+ * for searched skies; rows of skipped skies hold -inf and -1.
+ * searched_out [total_sky] (may be NULL): 1 for searched skies.  wbf and
+ * theta are device pointers.  Runs eagerly (the selection changes with the
+ * data, so it is not recorded as a graph); tcw_get_triage_info reports its
+ * totals over the batch.
+ * Errors: as tcw_search_batched and tcw_triage_features, INVALID_ARGUMENT
+ * (frac not in (0, 1], patch_size < 0). */
+tcw_status tcw_search_batched_triaged(tcw_ctx *ctx, const uint16_t *wbf, const float *theta,
+                                      int patch_size, float psi_lo, float psi_hi, float frac, int k,
+                                      float *psi_out, int64_t *idx_out, int32_t *searched_out,
+                                      int out_flags);
+
 /* Ranking of the triage (the first step of tcw_search_triaged, returned to
  * the caller): the coarse pass as tcw_triage_features, the network's score
  * (logit y of the MLP above) of every patch, and the patches by (score desc,

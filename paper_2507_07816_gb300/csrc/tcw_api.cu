@@ -500,57 +500,46 @@ SweepPlan plan_sweep(const std::vector<double>& tc, double T0, double tau_min, d
   return SweepPlan{};
 }
 
-tcw_status run_coarse(tcw_ctx* c, int patch_size, float lo, float hi, bool keep_psi, int* P_out) {
-  if (!c->have_spec || !c->have_vel || !c->have_bank || !c->have_sky)
-    return fail(c, TCW_ERR_STATE, "inputs not loaded");
-  if (c->D > 2) return fail(c, TCW_ERR_UNSUPPORTED, "coarse pass handles at most 2 detectors");
-  tcw_status st = prepare_sky(c);
-  if (st != TCW_OK) return st;
-  const Plan pl = make_plan(c);
-  if (pl.doppler_bins > 2.9) return fail(c, TCW_ERR_UNSUPPORTED, "coarse pass: Doppler shift exceeds 2.9 bins");
-  const int P = (int)((c->S + patch_size - 1) / patch_size);
+}  // namespace
+
+tcw_status tcw::coarse_pass(tcw_ctx* c, const CoarseEvent& ev, int patch_size, float lo, float hi, float* feat,
+                       float* psi, int* P_out, int* sweep_out) {
+  if (ev.D > 2) return fail(c, TCW_ERR_UNSUPPORTED, "coarse pass handles at most 2 detectors");
+  if (ev.doppler_bins > 2.9) return fail(c, TCW_ERR_UNSUPPORTED, "coarse pass: Doppler shift exceeds 2.9 bins");
+  const int P = (int)((ev.S + patch_size - 1) / patch_size);
   const int tile = 32;
   // the coarse segments: every stride-th one
   const int stride = c->triage_stride;
-  const int n_cs = (int)((c->Nseg + stride - 1) / stride);
+  const int n_cs = (int)((ev.n_seg + stride - 1) / stride);
   std::vector<double> tc(n_cs);
-  for (int j = 0; j < n_cs; ++j) tc[j] = c->h_t[(size_t)j * stride];
-  TCW_CUDA(c, upload(c, c->tri_tmid, tc.data(), tc.size() * sizeof(double), TCW_HOST), "triage buffers");
+  for (int j = 0; j < n_cs; ++j) tc[j] = ev.t_host[(size_t)j * stride];
   const int n_tiles = (n_cs + tile - 1) / tile;
   const double tau_min = c->bank_tau_min, r_max = c->bank_r_max;
-  const int nterms = series_terms_for(tc.data(), n_cs, c->T0, tile, tau_min, r_max);
-  TCW_CUDA(c, c->tri_dop.ensure((size_t)c->D * n_cs * P * sizeof(float)), "triage buffers");
   TCW_CUDA(c, c->tri_hist.ensure((size_t)P * kTriageBins * sizeof(unsigned)), "triage buffers");
-  TCW_CUDA(c, c->tri_feat.ensure((size_t)P * kTriageBins * sizeof(float)), "triage buffers");
-  if (keep_psi) TCW_CUDA(c, c->tri_psi.ensure((size_t)P * c->Bpad * sizeof(float)), "triage buffers");
-  if (nterms > 0) TCW_CUDA(c, c->tri_anchor.ensure((size_t)c->Bpad * n_tiles * 2 * sizeof(double)), "triage buffers");
   TCW_CUDA(c, cudaMemsetAsync(c->tri_hist.p, 0, (size_t)P * kTriageBins * sizeof(unsigned), c->stream), "triage");
-  c->tri_info.n_patch = P;
-  c->tri_info.lookups_coarse = (int64_t)P * c->B * c->D * n_cs;
-  c->tri_info.lookups_full = c->S * c->B * c->D * c->Nseg;
-  c->tri_info.coarse_kernel = 0;
   *P_out = P;
+  *sweep_out = 0;
   // the sweep form when its series bounds hold and the representatives' Doppler
   // factors are sorted at every (detector, segment)
   SweepPlan sp;
-  if (c->D <= 2 && P <= kSweepMaxPatches) sp = plan_sweep(tc, c->T0, tau_min, r_max, c->bank_f0max / c->df);
+  if (P <= kSweepMaxPatches) sp = plan_sweep(tc, ev.T0, tau_min, r_max, c->bank_f0max / ev.df);
   if (sp.ok) {
     int P2 = 1;
     while (P2 < P) P2 <<= 1;
-    TCW_CUDA(c, c->tri_dop.ensure((size_t)c->D * n_cs * P2 * sizeof(float)), "triage buffers");
+    TCW_CUDA(c, c->tri_dop.ensure((size_t)ev.D * n_cs * P2 * sizeof(float)), "triage buffers");
     TCW_CUDA(c, c->tri_flag.ensure(sizeof(int)), "triage buffers");
     TCW_CUDA(c, cudaMemsetAsync(c->tri_flag.p, 0, sizeof(int), c->stream), "triage");
     SweepDopplerParams sd{};
-    sd.vel = c->vel.as<double>();
-    sd.nhat = c->nhat_sorted.as<double>();
-    sd.n_det = c->D;
+    sd.vel = ev.vel;
+    sd.nhat = ev.nhat;
+    sd.n_det = ev.D;
     sd.n_seg = n_cs;
-    sd.S = (int)c->S;
+    sd.S = (int)ev.S;
     sd.patch_size = patch_size;
     sd.P = P;
     sd.P2 = P2;
     sd.stride = stride;
-    sd.n_seg_full = (int)c->Nseg;
+    sd.n_seg_full = (int)ev.n_seg;
     sd.dop = c->tri_dop.as<float>();
     sd.unsorted = c->tri_flag.as<int>();
     TCW_CUDA(c, launch_sweep_doppler(sd, c->stream), "sweep_doppler_kernel launch");
@@ -565,21 +554,21 @@ tcw_status run_coarse(tcw_ctx* c, int patch_size, float lo, float hi, bool keep_
       TCW_CUDA(c, c->tri_w2e.ensure((size_t)(P + 1) * c->Bpad * sizeof(double)), "triage buffers");
       TCW_CUDA(c, c->tri_ne.ensure((size_t)(P + 1) * c->Bpad * sizeof(int)), "triage buffers");
       CoarseSweepParams cs{};
-      cs.rho = c->rho.p;
-      cs.n_bin = c->Nbin;
-      cs.n_det = c->D;
+      cs.rho = ev.rho;
+      cs.n_bin = ev.n_bin;
+      cs.n_det = ev.D;
       cs.n_seg = n_cs;
       cs.stride = stride;
-      cs.n_seg_full = (int)c->Nseg;
-      cs.weights = c->weights.as<float>();
+      cs.n_seg_full = (int)ev.n_seg;
+      cs.weights = ev.weights;
       cs.seg = c->tri_seg.as<float4>();
       cs.ta = c->tri_ta.as<double>();
       cs.tile_shift = sp.shift;
       cs.n_tiles = sp.n_tiles;
       cs.nt64 = sp.nt64;
-      cs.T0 = c->T0;
-      cs.f_min = c->f_min;
-      cs.df = c->df;
+      cs.T0 = ev.T0;
+      cs.f_min = ev.f_min;
+      cs.df = ev.df;
       cs.dop = sd.dop;
       cs.P = P;
       cs.P2 = P2;
@@ -593,22 +582,26 @@ tcw_status run_coarse(tcw_ctx* c, int patch_size, float lo, float hi, bool keep_
       cs.nedge = c->tri_ne.as<int>();
       cs.lo = lo;
       cs.hi = hi;
-      cs.psi = keep_psi ? c->tri_psi.as<float>() : nullptr;
+      cs.psi = psi;
       cs.hist = c->tri_hist.as<unsigned>();
-      cs.feat = c->tri_feat.as<float>();
-      TCW_CUDA(c, launch_coarse_sweep(cs, c->dtype == TCW_F16, sp.nc, c->stream), "coarse_sweep_kernel launch");
-      c->tri_info.coarse_kernel = 1;
+      cs.feat = feat;
+      TCW_CUDA(c, launch_coarse_sweep(cs, ev.half, sp.nc, c->stream), "coarse_sweep_kernel launch");
+      *sweep_out = 1;
       return TCW_OK;
     }
   }
+  const int nterms = series_terms_for(tc.data(), n_cs, ev.T0, tile, tau_min, r_max);
+  TCW_CUDA(c, upload(c, c->tri_tmid, tc.data(), tc.size() * sizeof(double), TCW_HOST), "triage buffers");
+  TCW_CUDA(c, c->tri_dop.ensure((size_t)ev.D * n_cs * P * sizeof(float)), "triage buffers");
+  if (nterms > 0) TCW_CUDA(c, c->tri_anchor.ensure((size_t)c->Bpad * n_tiles * 2 * sizeof(double)), "triage buffers");
   PatchDopplerParams dp{};
-  dp.vel = c->vel.as<double>();
-  dp.nhat = c->nhat_sorted.as<double>();
-  dp.n_det = c->D;
+  dp.vel = ev.vel;
+  dp.nhat = ev.nhat;
+  dp.n_det = ev.D;
   dp.n_seg = n_cs;
   dp.stride = stride;
-  dp.n_seg_full = (int)c->Nseg;
-  dp.S = (int)c->S;
+  dp.n_seg_full = (int)ev.n_seg;
+  dp.S = (int)ev.S;
   dp.patch_size = patch_size;
   dp.P = P;
   dp.dop = c->tri_dop.as<float>();
@@ -619,7 +612,7 @@ tcw_status run_coarse(tcw_ctx* c, int patch_size, float lo, float hi, bool keep_
     ap.f0 = c->f0.as<double>();
     ap.tau = c->tau.as<double>();
     ap.nbr = c->nbr.as<double>();
-    ap.T0 = c->T0;
+    ap.T0 = ev.T0;
     ap.n_seg = n_cs;
     ap.n_tiles = n_tiles;
     ap.tile_shift = 5;
@@ -628,17 +621,17 @@ tcw_status run_coarse(tcw_ctx* c, int patch_size, float lo, float hi, bool keep_
     TCW_CUDA(c, launch_anchors(ap, c->stream), "anchor_kernel launch");
   }
   CoarseParams cp{};
-  cp.rho = c->rho.p;
-  cp.n_bin = c->Nbin;
-  cp.n_det = c->D;
+  cp.rho = ev.rho;
+  cp.n_bin = ev.n_bin;
+  cp.n_det = ev.D;
   cp.n_seg = n_cs;
   cp.stride = stride;
-  cp.n_seg_full = (int)c->Nseg;
-  cp.weights = c->weights.as<float>();
+  cp.n_seg_full = (int)ev.n_seg;
+  cp.weights = ev.weights;
   cp.t_mid = c->tri_tmid.as<double>();
-  cp.T0 = c->T0;
-  cp.f_min = c->f_min;
-  cp.df = c->df;
+  cp.T0 = ev.T0;
+  cp.f_min = ev.f_min;
+  cp.df = ev.df;
   cp.dop = dp.dop;
   cp.P = P;
   cp.f0 = c->f0.as<double>();
@@ -651,12 +644,52 @@ tcw_status run_coarse(tcw_ctx* c, int patch_size, float lo, float hi, bool keep_
   cp.nterms = nterms;
   cp.lo = lo;
   cp.hi = hi;
-  cp.psi = keep_psi ? c->tri_psi.as<float>() : nullptr;
+  cp.psi = psi;
   cp.hist = c->tri_hist.as<unsigned>();
   TCW_CUDA(c, c->tri_part.ensure(coarse_part_elems(P, c->Bpad) * sizeof(double)), "triage buffers");
   cp.part_acc = c->tri_part.as<double>();
-  cp.feat = c->tri_feat.as<float>();
-  TCW_CUDA(c, launch_coarse(cp, c->dtype == TCW_F16, c->stream), "coarse_kernel launch");
+  cp.feat = feat;
+  TCW_CUDA(c, launch_coarse(cp, ev.half, c->stream), "coarse_kernel launch");
+  return TCW_OK;
+}
+
+namespace {
+
+// The coarse pass of the loaded event (features in tri_feat, coarse Psi in
+// tri_psi when keep_psi).
+tcw_status run_coarse(tcw_ctx* c, int patch_size, float lo, float hi, bool keep_psi, int* P_out) {
+  if (!c->have_spec || !c->have_vel || !c->have_bank || !c->have_sky)
+    return fail(c, TCW_ERR_STATE, "inputs not loaded");
+  tcw_status st = prepare_sky(c);
+  if (st != TCW_OK) return st;
+  const Plan pl = make_plan(c);
+  CoarseEvent ev{};
+  ev.rho = c->rho.p;
+  ev.half = c->dtype == TCW_F16;
+  ev.D = c->D;
+  ev.n_seg = c->Nseg;
+  ev.n_bin = c->Nbin;
+  ev.f_min = c->f_min;
+  ev.df = c->df;
+  ev.t_host = c->h_t.data();
+  ev.weights = c->weights.as<float>();
+  ev.vel = c->vel.as<double>();
+  ev.nhat = c->nhat_sorted.as<double>();
+  ev.S = c->S;
+  ev.T0 = c->T0;
+  ev.doppler_bins = pl.doppler_bins;
+  const int P = (int)((c->S + patch_size - 1) / patch_size);
+  TCW_CUDA(c, c->tri_feat.ensure((size_t)P * kTriageBins * sizeof(float)), "triage buffers");
+  if (keep_psi) TCW_CUDA(c, c->tri_psi.ensure((size_t)P * c->Bpad * sizeof(float)), "triage buffers");
+  int sweep = 0;
+  st = coarse_pass(c, ev, patch_size, lo, hi, c->tri_feat.as<float>(), keep_psi ? c->tri_psi.as<float>() : nullptr,
+                   P_out, &sweep);
+  if (st != TCW_OK) return st;
+  const int n_cs = (int)((c->Nseg + c->triage_stride - 1) / c->triage_stride);
+  c->tri_info.n_patch = P;
+  c->tri_info.lookups_coarse = (int64_t)P * c->B * c->D * n_cs;
+  c->tri_info.lookups_full = c->S * c->B * c->D * c->Nseg;
+  c->tri_info.coarse_kernel = sweep;
   return TCW_OK;
 }
 

@@ -39,6 +39,15 @@ struct EventHost {
   size_t o_anchor = 0, o_psi = 0;  // byte offsets in the wave buffers
   int64_t out_row = 0;             // first output row (sum of earlier events' n_sky)
   int wave = 0;
+  // a triaged batch's event: its chosen skies (sorted, with their caller
+  // indices within the event) and its template regions (a sub-bank); null
+  // pointers / 0 sizes: the event's own sky at o_nhat / o_perm, the context's bank
+  const double* nhat_p = nullptr;
+  const int32_t* perm_p = nullptr;
+  const double *f0_p = nullptr, *tau_p = nullptr, *nbr_p = nullptr;
+  const int32_t* bperm_p = nullptr;
+  int64_t B_e = 0;
+  int Bpad_e = 0;
 };
 
 struct TuneResult {
@@ -51,6 +60,8 @@ size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
 }  // namespace
 
 struct BatchState {
+  BatchState* tri = nullptr;       // the triaged batch built by tcw_search_batched_triaged (owned)
+  DevBuf sub;                      // its sky subsets, sub-banks and selections
   // inputs
   int D = 0, dtype = TCW_F32;
   int64_t n_bin = 0;
@@ -88,14 +99,30 @@ struct BatchState {
   int64_t general = 0;
 };
 
+namespace {
+
+// Buffers a batch owns; a triaged batch shares its parent's maps, segment
+// arrays, bit maps and outputs.
+void release_batch(BatchState* b, bool shared) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  DevBuf* own[] = {&b->blk, &b->anchors, &b->psi, &b->evtab, &b->items, &b->dev, &b->flags, &b->sub};
+  for (DevBuf* d : own) d->release();
+  if (!shared) {
+    DevBuf* bufs[] = {&b->rho, &b->small, &b->out_psi, &b->out_idx, &b->bits};
+    for (DevBuf* d : bufs) d->release();
+  }
+  if (b->tri) {
+    release_batch(b->tri, true);
+    delete b->tri;
+  }
+}
+
+}  // namespace
+
 void batch_free(tcw_ctx* c) {
   if (!c->batch) return;
-  BatchState* b = c->batch;
-  if (b->exec) cudaGraphExecDestroy(b->exec);
-  DevBuf* bufs[] = {&b->rho, &b->small, &b->blk, &b->anchors, &b->psi, &b->out_psi,
-                    &b->out_idx, &b->evtab, &b->items, &b->dev, &b->flags, &b->bits};
-  for (DevBuf* d : bufs) d->release();
-  delete b;
+  release_batch(c->batch, false);
+  delete c->batch;
   c->batch = nullptr;
 }
 
@@ -110,6 +137,22 @@ void drop_graph(BatchState* b) {
 template <typename T>
 T* at(DevBuf& buf, size_t off) {
   return reinterpret_cast<T*>(buf.as<char>() + off);
+}
+
+// The event's sorted sky and its caller indices, and its bank.
+const double* ev_nhat(BatchState* b, const EventHost& e) {
+  return e.nhat_p ? e.nhat_p : at<double>(b->small, e.o_nhat);
+}
+const int32_t* ev_perm(BatchState* b, const EventHost& e) {
+  return e.perm_p ? e.perm_p : at<int32_t>(b->small, e.o_perm);
+}
+int64_t ev_B(const tcw_ctx* c, const EventHost& e) { return e.Bpad_e ? e.B_e : c->B; }
+int ev_Bpad(const tcw_ctx* c, const EventHost& e) { return e.Bpad_e ? e.Bpad_e : c->Bpad; }
+const double* ev_f0(const tcw_ctx* c, const EventHost& e) { return e.Bpad_e ? e.f0_p : c->f0.as<double>(); }
+const double* ev_tau(const tcw_ctx* c, const EventHost& e) { return e.Bpad_e ? e.tau_p : c->tau.as<double>(); }
+const double* ev_nbr(const tcw_ctx* c, const EventHost& e) { return e.Bpad_e ? e.nbr_p : c->nbr.as<double>(); }
+const int32_t* ev_bperm(const tcw_ctx* c, const EventHost& e) {
+  return e.Bpad_e ? e.bperm_p : c->bank_perm.as<int32_t>();
 }
 
 // Fixed-point step, exactness conditions and series length for the whole
@@ -139,7 +182,7 @@ tcw_status plan_batch(tcw_ctx* c, BatchState* b) {
     EventHost& e = b->ev[i];
     DopplerParams dp{};
     dp.vel = at<double>(b->small, e.o_v);
-    dp.nhat = at<double>(b->small, e.o_nhat);
+    dp.nhat = ev_nhat(b, e);
     dp.n_det = b->D;
     dp.n_seg = (int)e.n_seg;
     dp.Spad = e.Spad;
@@ -160,7 +203,7 @@ tcw_status plan_batch(tcw_ctx* c, BatchState* b) {
       return fail(c, TCW_ERR_UNSUPPORTED,
                   "batched search: sky groups of event " + std::to_string(i) + " span too many bins");
   b->lookups = 0;
-  for (const EventHost& e : b->ev) b->lookups += e.n_sky * c->B * b->D * e.n_seg;
+  for (const EventHost& e : b->ev) b->lookups += e.n_sky * ev_B(c, e) * b->D * e.n_seg;
   TCW_CUDA(c, group_grid(&b->grid), "device query");
   TCW_CUDA(c, b->dev.ensure(group_dev_elems(b->grid) * sizeof(float2)), "scratch");
   b->planned = true;
@@ -188,8 +231,8 @@ void layout_waves(const tcw_ctx* c, BatchState* b, int tile, bool anchors, size_
   size_t psi_w = 0, anc_w = 0, psi_max = 0, anc_max = 0;
   int wave = 0;
   for (EventHost& e : b->ev) {
-    const size_t p = align256((size_t)e.Spad * c->Bpad * 4);
-    const size_t a = anchors ? align256((size_t)c->Bpad * n_tiles_of(e.n_seg, tile) * 16) : 0;
+    const size_t p = align256((size_t)e.Spad * ev_Bpad(c, e) * 4);
+    const size_t a = anchors ? align256((size_t)ev_Bpad(c, e) * n_tiles_of(e.n_seg, tile) * 16) : 0;
     if ((psi_w + anc_w) > 0 && psi_w + anc_w + p + a > budget) {
       ++wave;
       psi_w = anc_w = 0;
@@ -214,10 +257,10 @@ EventDesc make_desc(const tcw_ctx* c, BatchState* b, const EventHost& e, int til
   d.t_mid = at<double>(b->small, e.o_t);
   d.blk = at<int32_t>(b->blk, e.o_blk);
   d.anchors = anchors ? at<double>(b->anchors, e.o_anchor) : nullptr;
-  d.f0 = c->f0.as<double>();
-  d.tau = c->tau.as<double>();
-  d.nbr = c->nbr.as<double>();
-  d.Bpad = c->Bpad;
+  d.f0 = ev_f0(c, e);
+  d.tau = ev_tau(c, e);
+  d.nbr = ev_nbr(c, e);
+  d.Bpad = ev_Bpad(c, e);
   d.psi = at<float>(b->psi, e.o_psi);
   d.total_elems = (int64_t)b->D * e.n_seg * b->n_bin;
   d.T0 = e.T0;
@@ -267,11 +310,11 @@ void wave_items(const tcw_ctx* c, const BatchState* b, int w, int bank_chunk, in
   std::vector<int4> items;
   std::vector<int64_t> cost;
   const int ptmpl = pass_templates(b->lanes), chunk = chunk_skies(b->lanes);
-  const int groups = std::min(groups_limit, c->Bpad / ptmpl);
   *sums = 0;
   for (size_t i = 0; i < b->ev.size(); ++i) {
     const EventHost& e = b->ev[i];
     if (e.wave != w) continue;
+    const int groups = std::min(groups_limit, ev_Bpad(c, e) / ptmpl);
     for (int g0 = 0; g0 < groups; g0 += bank_chunk)
       for (int ch = 0; ch < e.n_chunks; ++ch) {
         const int ng = std::min(bank_chunk, groups - g0);
@@ -328,14 +371,14 @@ cudaError_t launch_wave_anchors(const tcw_ctx* c, BatchState* b, int w, int tile
     if (e.wave != w) continue;
     AnchorParams ap{};
     ap.t_mid = at<double>(b->small, e.o_t);
-    ap.f0 = c->f0.as<double>();
-    ap.tau = c->tau.as<double>();
-    ap.nbr = c->nbr.as<double>();
+    ap.f0 = ev_f0(c, e);
+    ap.tau = ev_tau(c, e);
+    ap.nbr = ev_nbr(c, e);
     ap.T0 = e.T0;
     ap.n_seg = (int)e.n_seg;
     ap.n_tiles = n_tiles_of(e.n_seg, tile);
     ap.tile_shift = ilog2(tile);
-    ap.Bpad = c->Bpad;
+    ap.Bpad = ev_Bpad(c, e);
     ap.anchors = at<double>(b->anchors, e.o_anchor);
     cudaError_t err = launch_anchors(ap, st);
     if (err != cudaSuccess) return err;
@@ -470,7 +513,7 @@ tcw_status capture(tcw_ctx* c, BatchState* b, int k) {
     const EventHost& e = b->ev[i];
     DopplerParams dp{};
     dp.vel = at<double>(b->small, e.o_v);
-    dp.nhat = at<double>(b->small, e.o_nhat);
+    dp.nhat = ev_nhat(b, e);
     dp.n_det = b->D;
     dp.n_seg = (int)e.n_seg;
     dp.Spad = e.Spad;
@@ -494,8 +537,8 @@ tcw_status capture(tcw_ctx* c, BatchState* b, int k) {
     ++nodes;
     for (const EventHost& e : b->ev) {
       if (e.wave != w || err != cudaSuccess) continue;
-      err = launch_topk(at<float>(b->psi, e.o_psi), c->Bpad, (int)c->B, (int)e.n_sky, k,
-                        c->bank_perm.as<int32_t>(), at<int32_t>(b->small, e.o_perm),
+      err = launch_topk(at<float>(b->psi, e.o_psi), ev_Bpad(c, e), (int)ev_B(c, e), (int)e.n_sky, k,
+                        ev_bperm(c, e), ev_perm(b, e),
                         b->out_psi.as<float>() + e.out_row * k, b->out_idx.as<int64_t>() + e.out_row * k,
                         c->stream);
       ++nodes;
@@ -517,6 +560,21 @@ tcw_status capture(tcw_ctx* c, BatchState* b, int k) {
   b->graph_bins = c->track_bins;
   b->graph_nodes = nodes;
   return TCW_OK;
+}
+
+// The batch's plan (q, exactness conditions, Doppler blocks) and number-count
+// bit maps; the plan, the tuning and the graph depend on the bank and the options.
+tcw_status ensure_plan(tcw_ctx* c, BatchState* b) {
+  const int64_t key[4] = {c->B, (int64_t)c->bank_epoch, c->autotune ? 1 : 0,
+                          c->autotune ? 0 : ((int64_t)c->bank_chunk << 16 | c->tile_segments)};
+  if (!std::equal(key, key + 4, b->tune_key)) {
+    drop_graph(b);
+    b->planned = b->tuned = false;
+    std::copy(key, key + 4, b->tune_key);
+  }
+  tcw_status st = TCW_OK;
+  if (!b->planned && (st = plan_batch(c, b)) != TCW_OK) return st;
+  return ensure_batch_bits(c, b);
 }
 
 }  // namespace
@@ -705,17 +763,8 @@ tcw_status tcw_search_batched(tcw_ctx* c, int k, float* psi_out, int64_t* idx_ou
   cudaSetDevice(c->device);
   BatchState* b = c->batch;
   b->have_result = false;
-  // the plan, the tuning and the graph depend on the bank and the options
-  const int64_t key[4] = {c->B, (int64_t)c->bank_epoch, c->autotune ? 1 : 0,
-                          c->autotune ? 0 : ((int64_t)c->bank_chunk << 16 | c->tile_segments)};
-  if (!std::equal(key, key + 4, b->tune_key)) {
-    drop_graph(b);
-    b->planned = b->tuned = false;
-    std::copy(key, key + 4, b->tune_key);
-  }
-  tcw_status st = TCW_OK;
-  if (!b->planned && (st = plan_batch(c, b)) != TCW_OK) return st;
-  if ((st = ensure_batch_bits(c, b)) != TCW_OK) return st;
+  tcw_status st = ensure_plan(c, b);
+  if (st != TCW_OK) return st;
   if (!b->tuned) {
     if (c->autotune) {
       if ((st = autotune(c, b)) != TCW_OK) return st;
@@ -788,6 +837,311 @@ tcw_status tcw_get_tune_results(tcw_ctx* c, int max_results, int* bank_chunk, in
     if (tile_segments) tile_segments[i] = b->tune[i].tile;
     if (sums_per_s) sums_per_s[i] = b->tune[i].rate;
   }
+  return TCW_OK;
+}
+
+tcw_status tcw_search_batched_triaged(tcw_ctx* c, const uint16_t* wbf, const float* theta, int patch_size,
+                                      float psi_lo, float psi_hi, float frac, int k, float* psi_out,
+                                      int64_t* idx_out, int32_t* searched_out, int out_flags) {
+  if (!c) return TCW_ERR_INVALID_ARGUMENT;
+  if (!wbf || !theta || !psi_out || !idx_out) return fail(c, TCW_ERR_INVALID_ARGUMENT, "null pointer");
+  if (patch_size < 0 || !(psi_hi > psi_lo) || !std::isfinite(psi_lo) || !std::isfinite(psi_hi))
+    return fail(c, TCW_ERR_INVALID_ARGUMENT, "bad patch size or histogram range");
+  if (!(frac > 0.f && frac <= 1.f)) return fail(c, TCW_ERR_INVALID_ARGUMENT, "frac must be in (0, 1]");
+  if (out_flags != TCW_HOST && out_flags != TCW_DEVICE) return fail(c, TCW_ERR_INVALID_ARGUMENT, "bad flags");
+  if (!c->batch) return fail(c, TCW_ERR_STATE, "no events loaded");
+  if (!c->have_bank) return fail(c, TCW_ERR_STATE, "no template bank defined");
+  if (k < 1 || k > 1024 || (int64_t)k > c->B)
+    return fail(c, TCW_ERR_INVALID_ARGUMENT, "k must be in [1, min(n_tmpl, 1024)]");
+  if (c->batch->D > 2) return fail(c, TCW_ERR_UNSUPPORTED, "coarse pass handles at most 2 detectors");
+  cudaSetDevice(c->device);
+  BatchState* b = c->batch;
+  b->have_result = false;
+  tcw_status st = ensure_plan(c, b);
+  if (st != TCW_OK) return st;
+  const int E = (int)b->ev.size();
+  cudaEvent_t ev[5];
+  for (auto& e : ev) TCW_CUDA(c, cudaEventCreate(&e), "event");
+  struct Guard {
+    cudaEvent_t* e;
+    ~Guard() {
+      for (int i = 0; i < 5; ++i) cudaEventDestroy(e[i]);
+    }
+  } guard{ev};
+  // patches of every event, rows of the feature matrix
+  std::vector<int> ps(E), P(E), row0(E + 1, 0);
+  for (int e = 0; e < E; ++e) {
+    const int64_t S = b->ev[e].n_sky;
+    ps[e] = patch_size > 0 ? patch_size : (int)std::max<int64_t>(1, (S + 31) / 32);
+    P[e] = (int)((S + ps[e] - 1) / ps[e]);
+    row0[e + 1] = row0[e] + P[e];
+  }
+  const int PT = row0[E];
+  const bool regions = c->triage_templates < 1000;
+  TCW_CUDA(c, c->tri_feat.ensure((size_t)PT * kTriageBins * sizeof(float)), "triage buffers");
+  if (regions) TCW_CUDA(c, c->tri_psi.ensure((size_t)PT * c->Bpad * sizeof(float)), "triage buffers");
+  TCW_CUDA(c, cudaEventRecord(ev[0], c->stream), "event");
+  int sweeps = 0;
+  int64_t lookups_coarse = 0, lookups_full = 0;
+  for (int e = 0; e < E; ++e) {
+    const EventHost& h = b->ev[e];
+    CoarseEvent ce{};
+    ce.rho = at<char>(b->rho, h.o_rho);
+    ce.half = b->dtype == TCW_F16;
+    ce.D = b->D;
+    ce.n_seg = h.n_seg;
+    ce.n_bin = b->n_bin;
+    ce.f_min = b->f_min;
+    ce.df = b->df;
+    ce.t_host = h.t.data();
+    ce.weights = at<float>(b->small, h.o_w);
+    ce.vel = at<double>(b->small, h.o_v);
+    ce.nhat = at<double>(b->small, h.o_nhat);
+    ce.S = h.n_sky;
+    ce.T0 = h.T0;
+    ce.doppler_bins = b->doppler_bins;
+    int Pe = 0, sweep = 0;
+    st = coarse_pass(c, ce, ps[e], psi_lo, psi_hi, c->tri_feat.as<float>() + (size_t)row0[e] * kTriageBins,
+                     regions ? c->tri_psi.as<float>() + (size_t)row0[e] * c->Bpad : nullptr, &Pe, &sweep);
+    if (st != TCW_OK) return st;
+    sweeps += sweep;
+    const int64_t n_cs = (h.n_seg + c->triage_stride - 1) / c->triage_stride;
+    lookups_coarse += (int64_t)P[e] * c->B * b->D * n_cs;
+    lookups_full += h.n_sky * c->B * b->D * h.n_seg;
+  }
+  TCW_CUDA(c, cudaEventRecord(ev[1], c->stream), "event");
+  // one network call over every event's patches, then the best patches of each event
+  TCW_CUDA(c, c->tri_h1.ensure((size_t)PT * kMlpH * sizeof(float)), "triage buffers");
+  TCW_CUDA(c, c->tri_h2.ensure((size_t)PT * kMlpH * sizeof(float)), "triage buffers");
+  TCW_CUDA(c, c->tri_score.ensure((size_t)PT * sizeof(float)), "triage buffers");
+  TCW_CUDA(c, c->tri_sel.ensure((size_t)PT * sizeof(int)), "triage buffers");
+  TCW_CUDA(c, mlp_forward(reinterpret_cast<const __nv_bfloat16*>(wbf), theta, c->tri_feat.as<float>(), PT,
+                          c->tri_h1.as<float>(), c->tri_h2.as<float>(), c->tri_score.as<float>(), c->stream),
+           "mlp forward");
+  int n_selected = 0;
+  for (int e = 0; e < E; ++e) {
+    const int m = std::max(1, std::min(P[e], (int)std::ceil((double)frac * P[e] - 1e-9)));
+    n_selected += m;
+    TCW_CUDA(c, launch_rank(c->tri_score.as<float>() + row0[e], P[e], m, c->triage_spread,
+                            c->tri_sel.as<int>() + row0[e], c->stream),
+             "rank");
+  }
+  TCW_CUDA(c, cudaEventRecord(ev[2], c->stream), "event");
+  std::vector<int> sel(PT);
+  TCW_CUDA(c, cudaMemcpyAsync(sel.data(), c->tri_sel.p, PT * sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+           "selection");
+  TCW_CUDA(c, cudaStreamSynchronize(c->stream), "selection");
+  // chosen skies of every event (sorted positions), and the chosen rows for the template regions
+  std::vector<std::vector<int32_t>> pos(E);
+  std::vector<int32_t> rows;
+  std::vector<int> row_off(E + 1, 0);
+  for (int e = 0; e < E; ++e) {
+    const int64_t S = b->ev[e].n_sky;
+    for (int p = 0; p < P[e]; ++p) {
+      if (!sel[row0[e] + p]) continue;
+      rows.push_back(row0[e] + p);
+      for (int64_t i = (int64_t)p * ps[e]; i < std::min<int64_t>(S, (int64_t)(p + 1) * ps[e]); ++i)
+        pos[e].push_back((int32_t)i);
+    }
+    row_off[e + 1] = (int)rows.size();
+  }
+  std::vector<std::vector<int32_t>> tsub(E);
+  if (regions) {
+    const int M = (int)std::max<int64_t>((c->B * c->triage_templates + 999) / 1000, k);
+    const size_t keep_bytes = align256((size_t)E * c->Bpad), rows_bytes = align256(rows.size() * sizeof(int32_t));
+    TCW_CUDA(c, b->sub.ensure(keep_bytes + rows_bytes), "triage buffers");
+    unsigned char* keep = b->sub.as<unsigned char>();
+    int32_t* drows = reinterpret_cast<int32_t*>(b->sub.as<char>() + keep_bytes);
+    TCW_CUDA(c, cudaMemsetAsync(keep, 0, (size_t)E * c->Bpad, c->stream), "triage");
+    TCW_CUDA(c, cudaMemcpyAsync(drows, rows.data(), rows.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                c->stream), "triage");
+    for (int e = 0; e < E; ++e)
+      TCW_CUDA(c, launch_region_select(c->tri_psi.as<float>(), c->Bpad, (int)c->B, drows + row_off[e],
+                                       row_off[e + 1] - row_off[e], M, keep + (size_t)e * c->Bpad, c->stream),
+               "region_select_kernel launch");
+    std::vector<unsigned char> hk((size_t)E * c->Bpad);
+    TCW_CUDA(c, cudaMemcpyAsync(hk.data(), keep, hk.size(), cudaMemcpyDeviceToHost, c->stream), "triage");
+    TCW_CUDA(c, cudaStreamSynchronize(c->stream), "triage");
+    for (int e = 0; e < E; ++e)
+      for (int32_t t = 0; t < (int32_t)c->B; ++t)
+        if (hk[(size_t)e * c->Bpad + t]) tsub[e].push_back(t);
+  }
+  // the triaged batch: every event restricted to its chosen skies (and template regions)
+  if (!b->tri) b->tri = new BatchState();
+  BatchState* tb = b->tri;
+  drop_graph(tb);
+  tb->rho = b->rho;
+  tb->small = b->small;
+  tb->bits = b->bits;
+  tb->bits_th = b->bits_th;
+  tb->D = b->D;
+  tb->dtype = b->dtype;
+  tb->n_bin = b->n_bin;
+  tb->f_min = b->f_min;
+  tb->df = b->df;
+  tb->unit_weights = b->unit_weights;
+  tb->total_sky = b->total_sky;
+  tb->planned = false;
+  tb->ev.assign(b->ev.begin(), b->ev.end());
+  auto bank_pad = [&](int e) {
+    return regions ? (int)((tsub[e].size() + kBankAlign - 1) / kBankAlign * kBankAlign) : c->Bpad;
+  };
+  tb->lanes = c->opt_lanes;
+  if (!tb->lanes) {
+    double best = -1;
+    for (int l : {64, 32, 16}) {
+      double cost = 0;
+      for (int e = 0; e < E; ++e)
+        cost += (double)padded_skies((int64_t)pos[e].size(), l) * (double)b->ev[e].n_seg * bank_pad(e) *
+                lanes_cost(l);
+      if (best < 0 || cost < best) {
+        best = cost;
+        tb->lanes = l;
+      }
+    }
+  }
+  // device layout of the subsets: sky rows, caller indices, sub-banks, index lists
+  size_t sub_bytes = 0, blk_bytes = 0;
+  std::vector<size_t> o_nh(E), o_pm(E), o_f0(E), o_tau(E), o_nbr(E), o_bp(E), o_ip(E), o_it(E);
+  for (int e = 0; e < E; ++e) {
+    EventHost& h = tb->ev[e];
+    const int64_t n = (int64_t)pos[e].size();
+    h.n_sky = n;
+    h.NG = (int)((n + kGroupSkies - 1) / kGroupSkies);
+    h.Spad = padded_skies(n, tb->lanes);
+    h.n_chunks = h.Spad / chunk_skies(tb->lanes);
+    h.o_blk = blk_bytes;
+    blk_bytes += align256((size_t)h.n_chunks * h.n_seg * tb->D * block_words(tb->lanes) * 4);
+    o_nh[e] = sub_bytes;
+    sub_bytes += align256((size_t)h.Spad * 24);
+    o_pm[e] = sub_bytes;
+    sub_bytes += align256((size_t)h.Spad * 4);
+    o_ip[e] = sub_bytes;
+    sub_bytes += align256((size_t)n * 4);
+    if (regions) {
+      const int Bp = bank_pad(e);
+      o_f0[e] = sub_bytes;
+      sub_bytes += align256((size_t)Bp * 8);
+      o_tau[e] = sub_bytes;
+      sub_bytes += align256((size_t)Bp * 8);
+      o_nbr[e] = sub_bytes;
+      sub_bytes += align256((size_t)Bp * 8);
+      o_bp[e] = sub_bytes;
+      sub_bytes += align256((size_t)Bp * 4);
+      o_it[e] = sub_bytes;
+      sub_bytes += align256(tsub[e].size() * 4);
+    }
+  }
+  TCW_CUDA(c, tb->sub.ensure(sub_bytes), "triage buffers");
+  TCW_CUDA(c, tb->blk.ensure(blk_bytes), "triage buffers");
+  TCW_CUDA(c, tb->flags.ensure(64 + 4 * (size_t)E), "triage buffers");
+  std::vector<char> host_idx(sub_bytes, 0);
+  for (int e = 0; e < E; ++e) {
+    std::memcpy(host_idx.data() + o_ip[e], pos[e].data(), pos[e].size() * 4);
+    if (regions) std::memcpy(host_idx.data() + o_it[e], tsub[e].data(), tsub[e].size() * 4);
+  }
+  TCW_CUDA(c, cudaMemcpyAsync(tb->sub.p, host_idx.data(), sub_bytes, cudaMemcpyHostToDevice, c->stream), "triage");
+  int64_t lookups_searched = 0, templates_searched = 0, skies_searched = 0;
+  for (int e = 0; e < E; ++e) {
+    EventHost& h = tb->ev[e];
+    const EventHost& f = b->ev[e];
+    const int32_t* ip = at<int32_t>(tb->sub, o_ip[e]);
+    h.nhat_p = at<double>(tb->sub, o_nh[e]);
+    h.perm_p = at<int32_t>(tb->sub, o_pm[e]);
+    TCW_CUDA(c, launch_gather_rows(at<double>(b->small, f.o_nhat), ip, h.n_sky, h.Spad, 3,
+                                   at<double>(tb->sub, o_nh[e]), c->stream), "gather");
+    TCW_CUDA(c, launch_gather_rows(at<int32_t>(b->small, f.o_perm), ip, h.n_sky, h.Spad, 1,
+                                   at<int32_t>(tb->sub, o_pm[e]), c->stream), "gather");
+    if (regions) {
+      const int32_t* it = at<int32_t>(tb->sub, o_it[e]);
+      const int64_t nt = (int64_t)tsub[e].size();
+      h.B_e = nt;
+      h.Bpad_e = bank_pad(e);
+      h.f0_p = at<double>(tb->sub, o_f0[e]);
+      h.tau_p = at<double>(tb->sub, o_tau[e]);
+      h.nbr_p = at<double>(tb->sub, o_nbr[e]);
+      h.bperm_p = at<int32_t>(tb->sub, o_bp[e]);
+      TCW_CUDA(c, launch_gather_rows(c->f0.as<double>(), it, nt, h.Bpad_e, 1, at<double>(tb->sub, o_f0[e]),
+                                     c->stream), "gather");
+      TCW_CUDA(c, launch_gather_rows(c->tau.as<double>(), it, nt, h.Bpad_e, 1, at<double>(tb->sub, o_tau[e]),
+                                     c->stream), "gather");
+      TCW_CUDA(c, launch_gather_rows(c->nbr.as<double>(), it, nt, h.Bpad_e, 1, at<double>(tb->sub, o_nbr[e]),
+                                     c->stream), "gather");
+      TCW_CUDA(c, launch_gather_rows(c->bank_perm.as<int32_t>(), it, nt, h.Bpad_e, 1,
+                                     at<int32_t>(tb->sub, o_bp[e]), c->stream), "gather");
+    }
+    lookups_searched += h.n_sky * ev_B(c, h) * tb->D * h.n_seg;
+    templates_searched += ev_B(c, h);
+    skies_searched += h.n_sky;
+  }
+  if ((st = plan_batch(c, tb)) != TCW_OK) return st;
+  const int tile = (c->autotune && b->tuned) ? b->tile : c->tile_segments;
+  const int bank_chunk = c->autotune ? 1 : c->bank_chunk;
+  const int nterms = batch_series_terms(c, tb, tile);
+  if ((st = prepare_shape(c, tb, tile, nterms)) != TCW_OK) return st;
+  int64_t sums = 0;
+  if ((st = upload_items(c, tb, bank_chunk, INT32_MAX, &sums)) != TCW_OK) return st;
+  TCW_CUDA(c, b->out_psi.ensure((size_t)b->total_sky * k * sizeof(float)), "output");
+  TCW_CUDA(c, b->out_idx.ensure((size_t)b->total_sky * k * sizeof(int64_t)), "output");
+  TCW_CUDA(c, group_prepare(tb->D, tb->lanes, half_windows(c, tb),
+                            c->statistic == TCW_STAT_NUMBER_COUNT || c->track_bins == 2), "group_kernel attributes");
+  TCW_CUDA(c, launch_fill_empty(b->out_psi.as<float>(), b->out_idx.as<int64_t>(), b->total_sky * k, c->stream),
+           "fill");
+  TCW_CUDA(c, cudaMemsetAsync(tb->flags.p, 0, 64, c->stream), "flags");
+  TCW_CUDA(c, cudaEventRecord(ev[3], c->stream), "event");
+  for (int w = 0; w < tb->waves; ++w) {
+    if (nterms > 0) TCW_CUDA(c, launch_wave_anchors(c, tb, w, tile, c->stream), "anchor_kernel launch");
+    const GroupParams gp = wave_params(c, tb, w, tile, nterms);
+    TCW_CUDA(c, launch_group(gp, tb->grid, half_windows(c, tb), false, c->stream), "group_kernel launch");
+    for (const EventHost& h : tb->ev) {
+      if (h.wave != w) continue;
+      TCW_CUDA(c, launch_topk(at<float>(tb->psi, h.o_psi), ev_Bpad(c, h), (int)ev_B(c, h), (int)h.n_sky, k,
+                              ev_bperm(c, h), ev_perm(tb, h), b->out_psi.as<float>() + h.out_row * k,
+                              b->out_idx.as<int64_t>() + h.out_row * k, c->stream),
+               "topk_kernel launch");
+    }
+  }
+  TCW_CUDA(c, cudaEventRecord(ev[4], c->stream), "event");
+  const size_t n = (size_t)b->total_sky * k;
+  const cudaMemcpyKind kind = out_flags == TCW_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  TCW_CUDA(c, cudaMemcpyAsync(psi_out, b->out_psi.p, n * sizeof(float), kind, c->stream), "copy out");
+  TCW_CUDA(c, cudaMemcpyAsync(idx_out, b->out_idx.p, n * sizeof(int64_t), kind, c->stream), "copy out");
+  int64_t fl[2] = {0, 0};
+  TCW_CUDA(c, cudaMemcpyAsync(fl, tb->flags.p, sizeof(fl), cudaMemcpyDeviceToHost, c->stream), "flags");
+  // searched rows: the caller indices of the chosen skies
+  std::vector<int32_t> searched((size_t)b->total_sky, 0);
+  std::vector<std::vector<int32_t>> caller(E);
+  for (int e = 0; e < E; ++e) {
+    caller[e].resize(pos[e].size());
+    TCW_CUDA(c, cudaMemcpyAsync(caller[e].data(), tb->ev[e].perm_p, pos[e].size() * 4, cudaMemcpyDeviceToHost,
+                                c->stream), "searched rows");
+  }
+  TCW_CUDA(c, cudaStreamSynchronize(c->stream), "batched triaged search");
+  for (int e = 0; e < E; ++e)
+    for (int32_t r : caller[e]) searched[(size_t)b->ev[e].out_row + r] = 1;
+  if (searched_out) {
+    const cudaMemcpyKind sk = out_flags == TCW_HOST ? cudaMemcpyHostToHost : cudaMemcpyHostToDevice;
+    TCW_CUDA(c, cudaMemcpy(searched_out, searched.data(), searched.size() * sizeof(int32_t), sk), "copy out");
+  }
+  if ((int)(fl[0] & 0xffffffff) != 0) return fail(c, TCW_ERR_DEVICE, "batched triaged search: device-side error");
+  float coarse_ms = 0, mlp_ms = 0, search_ms = 0;
+  cudaEventElapsedTime(&coarse_ms, ev[0], ev[1]);
+  cudaEventElapsedTime(&mlp_ms, ev[1], ev[2]);
+  cudaEventElapsedTime(&search_ms, ev[3], ev[4]);
+  tcw_triage_info& ti = c->tri_info;
+  ti = tcw_triage_info{};
+  ti.n_patch = PT;
+  ti.n_selected = n_selected;
+  ti.skies_searched = skies_searched;
+  ti.lookups_full = lookups_full;
+  ti.lookups_coarse = lookups_coarse;
+  ti.lookups_searched = lookups_searched;
+  ti.coarse_ms = coarse_ms;
+  ti.mlp_ms = mlp_ms;
+  ti.search_ms = search_ms;
+  ti.templates_searched = templates_searched;
+  ti.coarse_kernel = sweeps == E ? 1 : 0;
+  b->general = fl[1];
   return TCW_OK;
 }
 

@@ -158,4 +158,29 @@ inline bool finite_all(const std::vector<double>& v) {
 
 void batch_free(tcw_ctx* c);
 
+// One event as the coarse pass of the triage reads it: device arrays, host
+// segment times, the Doppler-sorted sky.
+struct CoarseEvent {
+  const void* rho;          // [D][n_seg][n_bin]
+  bool half;                // FP16 map
+  int D;
+  int64_t n_seg, n_bin;
+  double f_min, df;
+  const double* t_host;     // [n_seg] (host)
+  const float* weights;     // [D][n_seg]
+  const double* vel;        // [D][n_seg][3]
+  const double* nhat;       // [S][3] in Doppler-sorted order
+  int64_t S;
+  double T0;
+  double doppler_bins;      // largest Doppler shift in bins
+};
+
+// Coarse pass of one event against the context's bank (TCW_OPT_TRIAGE_STRIDE
+// segments, patches of patch_size sorted skies): the features [P][128] into
+// feat and, when psi is not null, the coarse Psi [P][Bpad] (sorted bank) into
+// psi.  *sweep_out = 1 when the sweep form ran.  Uses the context's triage
+// scratch buffers; asynchronous on the context's stream after its checks.
+tcw_status coarse_pass(tcw_ctx* c, const CoarseEvent& ev, int patch_size, float lo, float hi, float* feat,
+                       float* psi, int* P_out, int* sweep_out);
+
 }  // namespace tcw

@@ -300,6 +300,18 @@ struct CoarseSweepParams {
 };
 
 cudaError_t launch_sweep_doppler(const SweepDopplerParams& p, cudaStream_t st);
+// Template regions of a triaged search: for each listed row r of the coarse
+// Psi [P][Bpad] (sorted bank, first B valid), keep[b] = 1 for its M best
+// templates by (Psi desc, index asc); rows OR into one keep [B].
+cudaError_t launch_region_select(const float* psi, int Bpad, int B, const int* rows, int n_rows, int M,
+                                 unsigned char* keep, cudaStream_t st);
+// dst[i][:width] = src[idx[min(i, n - 1)]][:width] for i < npad (64-bit elements)
+cudaError_t launch_gather_rows(const double* src, const int32_t* idx, int64_t n, int64_t npad, int width,
+                               double* dst, cudaStream_t st);
+cudaError_t launch_gather_rows(const int32_t* src, const int32_t* idx, int64_t n, int64_t npad, int width,
+                               int32_t* dst, cudaStream_t st);
+// psi[i] = -inf and idx[i] = -1 for i < n
+cudaError_t launch_fill_empty(float* psi, int64_t* idx, int64_t n, cudaStream_t st);
 // nc: fp32 terms of the in-tile series beyond the quadratic one (4, 6 or 8)
 cudaError_t launch_coarse_sweep(const CoarseSweepParams& p, bool half, int nc, cudaStream_t st);
 // selected[p] = 1 for the m best patches; a chosen patch suppresses the

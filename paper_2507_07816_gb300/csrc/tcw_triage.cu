@@ -705,6 +705,120 @@ void launch_coarse_l(const CoarseParams& p, bool half, cudaStream_t st) {
   }
 }
 
+namespace {
+
+// Order-preserving key of a float: larger value, larger key.
+__device__ __forceinline__ unsigned ord_key(float x) {
+  const unsigned u = __float_as_uint(x);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+constexpr int kSelectThreads = 1024;
+
+// One block per row: the M-th largest key by four 8-bit radix passes, then
+// every key above it and the first (by index) of the keys equal to it.
+__global__ void __launch_bounds__(kSelectThreads) region_select_kernel(const float* psi, int Bpad, int B,
+                                                                     const int* rows, int M, unsigned char* keep) {
+  __shared__ unsigned hist[256];
+  __shared__ unsigned s_prefix, s_need;
+  __shared__ int s_ties[kSelectThreads];
+  const float* x = psi + (int64_t)rows[blockIdx.x] * Bpad;
+  const int tid = threadIdx.x;
+  unsigned prefix = 0, mask = 0, need = (unsigned)min(M, B);
+  for (int shift = 24; shift >= 0; shift -= 8) {
+    for (int i = tid; i < 256; i += kSelectThreads) hist[i] = 0;
+    __syncthreads();
+    for (int b = tid; b < B; b += kSelectThreads) {
+      const unsigned key = ord_key(x[b]);
+      if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      unsigned cum = 0;
+      int d = 255;
+      for (; d > 0; --d) {
+        if (cum + hist[d] >= need) break;
+        cum += hist[d];
+      }
+      s_prefix = prefix | ((unsigned)d << shift);
+      s_need = need - cum;
+    }
+    __syncthreads();
+    prefix = s_prefix;
+    need = s_need;
+    mask |= 255u << shift;
+  }
+  // prefix: the M-th largest key; need: how many keys equal to it are taken
+  const int per = (B + kSelectThreads - 1) / kSelectThreads;
+  const int b0 = min(B, tid * per), b1 = min(B, b0 + per);
+  int ties = 0;
+  for (int b = b0; b < b1; ++b) ties += ord_key(x[b]) == prefix;
+  s_ties[tid] = ties;
+  __syncthreads();
+  for (int off = 1; off < kSelectThreads; off <<= 1) {
+    const int v = tid >= off ? s_ties[tid - off] : 0;
+    __syncthreads();
+    s_ties[tid] += v;
+    __syncthreads();
+  }
+  int rank = s_ties[tid] - ties;   // ties at smaller indices
+  for (int b = b0; b < b1; ++b) {
+    const unsigned key = ord_key(x[b]);
+    if (key > prefix) {
+      keep[b] = 1;
+    } else if (key == prefix) {
+      if (rank < (int)need) keep[b] = 1;
+      ++rank;
+    }
+  }
+}
+
+template <typename T>
+__global__ void gather_rows_kernel(const T* src, const int32_t* idx, int64_t n, int64_t npad, int width, T* dst) {
+  const int64_t total = npad * width;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / width;
+    const int a = (int)(i % width);
+    dst[i] = src[(int64_t)idx[r < n ? r : n - 1] * width + a];
+  }
+}
+
+__global__ void fill_empty_kernel(float* psi, int64_t* idx, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    psi[i] = -INFINITY;
+    idx[i] = -1;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_region_select(const float* psi, int Bpad, int B, const int* rows, int n_rows, int M,
+                                 unsigned char* keep, cudaStream_t st) {
+  if (n_rows <= 0 || B <= 0 || M <= 0) return cudaSuccess;
+  region_select_kernel<<<n_rows, kSelectThreads, 0, st>>>(psi, Bpad, B, rows, M, keep);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_rows(const double* src, const int32_t* idx, int64_t n, int64_t npad, int width,
+                               double* dst, cudaStream_t st) {
+  if (npad <= 0 || n <= 0) return cudaSuccess;
+  gather_rows_kernel<double><<<blocks_for(npad * width, 256), 256, 0, st>>>(src, idx, n, npad, width, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_rows(const int32_t* src, const int32_t* idx, int64_t n, int64_t npad, int width,
+                               int32_t* dst, cudaStream_t st) {
+  if (npad <= 0 || n <= 0) return cudaSuccess;
+  gather_rows_kernel<int32_t><<<blocks_for(npad * width, 256), 256, 0, st>>>(src, idx, n, npad, width, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_empty(float* psi, int64_t* idx, int64_t n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  fill_empty_kernel<<<blocks_for(n, 256), 256, 0, st>>>(psi, idx, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_sweep_doppler(const SweepDopplerParams& p, cudaStream_t st) {
   const int64_t total = (int64_t)p.n_det * p.n_seg * p.P2;
   sweep_doppler_kernel<<<blocks_for(total, 256), 256, 0, st>>>(p);

@@ -139,6 +139,8 @@ def load_library(build_if_missing: bool = True):
             "tcw_triage_rank": [p, p, p, i, ctypes.c_float, ctypes.c_float, p, p, p, i],
             "tcw_search_triaged": [p, p, p, i, ctypes.c_float, ctypes.c_float, ctypes.c_float, i,
                                    p, p, p, i],
+            "tcw_search_batched_triaged": [p, p, p, i, ctypes.c_float, ctypes.c_float, ctypes.c_float, i,
+                                           p, p, p, i],
             "tcw_get_triage_info": [p, ctypes.POINTER(_TriageInfo)],
             "tcw_sky_order": [p, p],
             "tcw_bank_size": [ctypes.POINTER(_BankSpec), ctypes.POINTER(i64)],
@@ -451,6 +453,21 @@ class Search:
         idx = np.empty((self.n_sky, k), np.int64)
         searched = np.empty(self.n_sky, np.int32)
         self._check(self._lib.tcw_search_triaged(
+            self._h, ctypes.c_void_p(mlp.wbf.data_ptr()), ctypes.c_void_p(mlp.theta.data_ptr()),
+            int(patch_size), float(psi_lo), float(psi_hi), float(frac), int(k),
+            psi.ctypes.data_as(ctypes.c_void_p), idx.ctypes.data_as(ctypes.c_void_p),
+            searched.ctypes.data_as(ctypes.c_void_p), HOST))
+        return psi, idx, searched
+
+    def search_batched_triaged(self, mlp, patch_size, psi_lo, psi_hi, frac, k):
+        """Triaged search of every loaded event: (psi [total_sky][k], idx
+        [total_sky][k], searched [total_sky]) as numpy, rows as search_batched.
+        patch_size 0: 32 patches per event."""
+        total = sum(self.batch_sky)
+        psi = np.empty((total, k), np.float32)
+        idx = np.empty((total, k), np.int64)
+        searched = np.empty(total, np.int32)
+        self._check(self._lib.tcw_search_batched_triaged(
             self._h, ctypes.c_void_p(mlp.wbf.data_ptr()), ctypes.c_void_p(mlp.theta.data_ptr()),
             int(patch_size), float(psi_lo), float(psi_hi), float(frac), int(k),
             psi.ctypes.data_as(ctypes.c_void_p), idx.ctypes.data_as(ctypes.c_void_p),

@@ -290,3 +290,89 @@ def test_parameter_regions_search_a_template_subset():
     s.set_option(tcw.OPT_TRIAGE_TEMPLATES, 1000)
     s.close()
 
+
+
+def _batch(seeds, n_segs, n_skies, n_bin=1200, n_tmpl=96):
+    r = syn.rng(seeds[0] + 7)
+    f_min, t_sft = 500.0, 4.0
+    bank = syn.random_bank(r, n_tmpl, f0_range=(f_min - 3, f_min + n_bin / t_sft + 3),
+                           tau_range=(3500.0, 35000.0))
+    evs = [syn.training_event(sd, bank, n_det=2, n_seg=ns, n_bin=n_bin, n_sky=S, n_inj=2,
+                              snr_range=(12.0, 16.0), t_sft=t_sft)
+           for sd, ns, S in zip(seeds, n_segs, n_skies)]
+    return evs, bank
+
+
+def _hand_network():
+    # score = sum of the log-counts of the 28 highest histogram bins
+    theta = np.zeros(OT.N_PARAMS, np.float32)
+    p = OT.unpack(theta)
+    p["W1"][100:, 0] = 1.0
+    p["W2"][0, 0] = 1.0
+    p["w3"][0] = 1.0
+    return tcw.Mlp(theta, device=DEV)
+
+
+def test_batched_triaged_rows_equal_exhaustive_batched_rows():
+    """tcw_search_batched_triaged with every template: each event's chosen
+    patches (ceil(frac * n_patch) of them) are searched in one launch and
+    their rows equal tcw_search_batched's rows bit for bit; the other rows
+    are empty."""
+    evs, bank = _batch([91, 92, 93], [150, 90, 200], [120, 208, 64])
+    mlp = _hand_network()
+    s = tcw.Search(0)
+    s.define_bank(bank.f0, bank.tau, bank.n, 0.0)
+    s.load_events(evs, evs[0].f_min, evs[0].df)
+    k = 6
+    vx, ix = s.search_batched(k)
+    pt, it, searched = s.search_batched_triaged(mlp, 16, -4.0, 12.0, 0.3, k)
+    rows = searched.astype(bool)
+    info = s.triage_info()
+    P = [-(-e.nhat.shape[0] // 16) for e in evs]
+    assert info["n_patch"] == sum(P)
+    assert info["n_selected"] == sum(int(np.ceil(0.3 * p)) for p in P)
+    assert info["skies_searched"] == rows.sum() and 0 < rows.sum() < rows.shape[0]
+    assert info["lookups_full"] == sum(e.nhat.shape[0] * len(bank) * 2 * e.rho.shape[1] for e in evs)
+    assert info["templates_searched"] == len(evs) * len(bank)
+    np.testing.assert_array_equal(it[rows], ix[rows])
+    np.testing.assert_array_equal(pt[rows], vx[rows])
+    assert np.all(it[~rows] == -1) and np.all(np.isneginf(pt[~rows]))
+    # every event has whole patches searched
+    row = 0
+    for e, p in zip(evs, P):
+        S = e.nhat.shape[0]
+        assert rows[row:row + S].sum() >= 16 * int(np.ceil(0.3 * p)) - 15
+        row += S
+    s.close()
+
+
+def test_batched_triaged_regions_match_the_single_event_triaged_search():
+    """With TCW_OPT_TRIAGE_TEMPLATES < 1000 every event searches its chosen
+    skies over the union of its patches' best templates: the same skies and
+    rows (within the parity tolerance) as tcw_search_triaged on that event
+    alone."""
+    evs, bank = _batch([94, 95], [120, 160], [96, 150], n_tmpl=200)
+    mlp = _hand_network()
+    k, tpm, frac = 5, 100, 0.35      # 20 templates per chosen patch (>= k)
+    s = tcw.Search(0)
+    s.set_option(tcw.OPT_TRIAGE_TEMPLATES, tpm)
+    s.define_bank(bank.f0, bank.tau, bank.n, 0.0)
+    s.load_events(evs, evs[0].f_min, evs[0].df)
+    pt, it, searched = s.search_batched_triaged(mlp, 16, -4.0, 12.0, frac, k)
+    assert s.triage_info()["templates_searched"] < len(evs) * len(bank)
+    row = 0
+    for e in evs:
+        S = e.nhat.shape[0]
+        s1 = tcw.Search(0)
+        s1.set_option(tcw.OPT_TRIAGE_TEMPLATES, tpm)
+        s1.set_option(tcw.OPT_KEEP_STATS, 1)
+        TR.load_event(s1, e, bank)
+        p1, i1, sr1 = s1.search_triaged(mlp, 16, -4.0, 12.0, frac, k)
+        np.testing.assert_array_equal(searched[row:row + S], sr1)
+        r = sr1.astype(bool)
+        np.testing.assert_allclose(pt[row:row + S][r], p1[r], rtol=1e-5, atol=1e-5)
+        same = (it[row:row + S][r] == i1[r]).mean()
+        assert same > 0.99, same
+        row += S
+        s1.close()
+    s.close()
