@@ -27,6 +27,11 @@ own synthetic workload:
              events with one injection each and the full 2e5-template bank,
              judged by the exhaustive search with the noise-only maximum of Psi
              as the detection threshold (Sec. 3)
+  "batched_learned"  the batched triaged search (one coarse pass per event,
+             one network call, one launch over the chosen items) against the
+             exhaustive batched search of the same 16 events (2000-20000
+             segments x 10^4 bins, 2 detectors, 1024 skies, 2e5 templates, one
+             injection each), judged by the exhaustive batched search
 """
 from __future__ import annotations
 
@@ -67,6 +72,7 @@ def parse():
     ap.add_argument("--batched-events", type=int, default=64)
     ap.add_argument("--batched-templates", type=int, default=20000)
     ap.add_argument("--learned-events", type=int, default=100)
+    ap.add_argument("--batched-learned-events", type=int, default=16)
     return ap.parse_args()
 
 
@@ -322,6 +328,90 @@ def bench_learned(args, dev):
     r["judge"] = ("exhaustive search of every sky; found = injected template in the first 10 of a sky within 64 "
                   "Doppler-sorted positions with Psi above the noise-only maximum psi_det (Sec. 3)")
     return r
+
+
+def sorted_positions_of(ev):
+    """Position of every sky of an event in the library's Doppler-sorted order
+    (key: v.nhat of detector 0 at the middle segment, stable)."""
+    vm = np.asarray(ev.velocity[0][ev.rho.shape[1] // 2], np.float64)
+    order = np.argsort(np.asarray(ev.nhat, np.float64) @ vm, kind="stable")
+    pos = np.empty_like(order)
+    pos[order] = np.arange(order.shape[0])
+    return pos
+
+
+def bench_batched_learned(args, dev):
+    """Batched triaged search against the exhaustive batched search of the same
+    events (uneven segment counts, own start time and T0, one injection each),
+    effective rate = the exhaustive search's sums / wall time of the triaged call,
+    loss judged by the exhaustive batched search."""
+    import torch
+    import paper_2507_07816_gb300 as tcw
+    from paper_2507_07816_gb300 import triage as TR
+    import tcw_synth as syn
+    wpath = os.path.join(ROOT, "paper_2507_07816_gb300", "triage_weights.npz")
+    if not os.path.exists(wpath):
+        return {"skipped": "no trained weights (paper_2507_07816_gb300/triage_weights.npz)"}
+    meta = dict(np.load(wpath, allow_pickle=False))
+    bank = syn.random_bank(syn.rng(int(meta["bank_seed"])), int(meta["n_tmpl"]), f0_range=(500.0, 3000.0))
+    mlp = tcw.Mlp.load(wpath, device=f"cuda:{dev}")
+    psi_det = float(meta["psi_det"]) if "psi_det" in meta else 6.5
+    stride = int(meta["stride"]) if "stride" in meta else 1
+    ps = int(meta["patch_size"])
+    seed0 = int(meta["valid_seed"]) + 20_000
+    n_segs = syn.rng(seed0).integers(2000, 20001, args.batched_learned_events)
+    t0 = time.perf_counter()
+    events = [syn.training_event(seed0 + i, bank, n_seg=int(n_segs[i]), n_inj=1, snr_range=(6.0, 12.0),
+                                 device=torch.device(f"cuda:{dev}")) for i in range(len(n_segs))]
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    s = tcw.Search(dev)
+    s.set_option(tcw.OPT_TRIAGE_TEMPLATES, TR.TEMPLATES_PERMILLE)
+    s.set_option(tcw.OPT_TRIAGE_STRIDE, stride)
+    s.define_bank(bank.f0, bank.tau, bank.n, 0.0)
+    s.load_events(events, events[0].f_min, events[0].df)
+    t0 = time.perf_counter()
+    s.search_batched(TOPK)              # plans, autotunes and records the graph
+    first_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    vx, ix = s.search_batched(TOPK)
+    wall_x = time.perf_counter() - t0
+    sums_full = s.batch_info()["lookups"]
+    s.search_batched_triaged(mlp, ps, TR.PSI_LO, TR.PSI_HI, TR.FRAC, TOPK)   # buffers warm up
+    walls = []
+    for _ in range(2):
+        t0 = time.perf_counter()
+        pt, it, searched = s.search_batched_triaged(mlp, ps, TR.PSI_LO, TR.PSI_HI, TR.FRAC, TOPK)
+        walls.append(time.perf_counter() - t0)
+    info = s.triage_info()
+    s.close()
+    found_x = found_t = missed = 0
+    row = 0
+    for e in events:
+        S = e.nhat.shape[0]
+        pos = sorted_positions_of(e)
+        fx = TR.judge(e, vx[row:row + S], ix[row:row + S], pos, psi_det)
+        ft = TR.judge(e, pt[row:row + S], it[row:row + S], pos, psi_det)
+        found_x += sum(fx)
+        found_t += sum(ft)
+        missed += sum(a and not b for a, b in zip(fx, ft))
+        row += S
+    wall_t = min(walls)
+    return {"workload": f"batched-learned-{len(events)}ev-{int(n_segs.min())}..{int(n_segs.max())}seg-"
+                        f"2det-x10000-f32-sky1024-bank{len(bank)}",
+            "value": sums_full / wall_t, "unit": UNIT, "plain_value": sums_full / wall_x,
+            "speedup": wall_x / wall_t, "wall_triaged_s": wall_t, "wall_exhaustive_s": wall_x,
+            "sums_full": sums_full,
+            "sums_executed_triaged": info["lookups_coarse"] + info["lookups_searched"],
+            "coarse_ms": info["coarse_ms"], "mlp_ms": info["mlp_ms"], "search_ms": info["search_ms"],
+            "skies_searched": info["skies_searched"], "templates_searched": info["templates_searched"],
+            "coarse_kernel": "sweep" if info["coarse_kernel"] else "per pair",
+            "events": len(events), "detected_exhaustive": found_x, "detected_triaged": found_t,
+            "missed": missed, "loss": missed / max(found_x, 1), "psi_det": psi_det,
+            "frac": TR.FRAC, "templates_permille": TR.TEMPLATES_PERMILLE, "patch_size": ps, "stride": stride,
+            "first_exhaustive_call_s": first_s, "generate_s": gen_s,
+            "judge": ("the exhaustive batched search of every sky; found = injected template in the first 10 of "
+                      "a sky within 64 Doppler-sorted positions with Psi above psi_det (Sec. 3)")}
 
 
 def bench_small(args, dev):
@@ -620,7 +710,9 @@ def bench_ours(args):
     if rank == 0 and world == 1 and args.workload == "full":
         for name, fn, skip in (("small", bench_small, False),
                                ("batched", bench_batched, args.no_batched),
-                               ("learned", bench_learned, args.no_learned)):
+                               ("learned", bench_learned, args.no_learned),
+                               ("batched_learned", bench_batched_learned,
+                                args.no_learned or args.no_batched)):
             if skip:
                 continue
             try:

@@ -463,9 +463,9 @@ typedef struct {
     float coarse_ms, mlp_ms, search_ms;  /* device times */
     int64_t templates_searched; /* templates of the exhaustive part (TCW_OPT_TRIAGE_TEMPLATES) */
     int coarse_kernel;          /* coarse pass of the last call: 1 = the sweep form (one thread
-                                   per template, the representatives' Doppler factors sorted at
-                                   every detector and segment), 0 = one thread per (template,
-                                   patch) */
+                                   per template over every segment; used when the track series
+                                   meet its error bounds and n_patch <= 128), 0 = one thread per
+                                   (template, patch) */
 } tcw_triage_info;
 
 tcw_status tcw_get_triage_info(tcw_ctx *ctx, tcw_triage_info *info);

@@ -519,16 +519,16 @@ tcw_status tcw::coarse_pass(tcw_ctx* c, const CoarseEvent& ev, int patch_size, f
   TCW_CUDA(c, cudaMemsetAsync(c->tri_hist.p, 0, (size_t)P * kTriageBins * sizeof(unsigned), c->stream), "triage");
   *P_out = P;
   *sweep_out = 0;
-  // the sweep form when its series bounds hold and the representatives' Doppler
-  // factors are sorted at every (detector, segment)
+  // the sweep form when its series bounds hold (the per-(template, patch)
+  // kernel otherwise)
   SweepPlan sp;
   if (P <= kSweepMaxPatches) sp = plan_sweep(tc, ev.T0, tau_min, r_max, c->bank_f0max / ev.df);
   if (sp.ok) {
     int P2 = 1;
     while (P2 < P) P2 <<= 1;
     TCW_CUDA(c, c->tri_dop.ensure((size_t)ev.D * n_cs * P2 * sizeof(float)), "triage buffers");
-    TCW_CUDA(c, c->tri_flag.ensure(sizeof(int)), "triage buffers");
-    TCW_CUDA(c, cudaMemsetAsync(c->tri_flag.p, 0, sizeof(int), c->stream), "triage");
+    TCW_CUDA(c, c->tri_flag.ensure((size_t)ev.D * n_cs * sizeof(int)), "triage buffers");
+    TCW_CUDA(c, cudaMemsetAsync(c->tri_flag.p, 0, (size_t)ev.D * n_cs * sizeof(int), c->stream), "triage");
     SweepDopplerParams sd{};
     sd.vel = ev.vel;
     sd.nhat = ev.nhat;
@@ -543,11 +543,7 @@ tcw_status tcw::coarse_pass(tcw_ctx* c, const CoarseEvent& ev, int patch_size, f
     sd.dop = c->tri_dop.as<float>();
     sd.unsorted = c->tri_flag.as<int>();
     TCW_CUDA(c, launch_sweep_doppler(sd, c->stream), "sweep_doppler_kernel launch");
-    int unsorted = 1;
-    TCW_CUDA(c, cudaMemcpyAsync(&unsorted, c->tri_flag.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
-             "triage");
-    TCW_CUDA(c, cudaStreamSynchronize(c->stream), "triage");
-    if (!unsorted) {
+    {
       TCW_CUDA(c, upload(c, c->tri_seg, sp.seg.data(), sp.seg.size() * sizeof(float4), TCW_HOST), "triage buffers");
       TCW_CUDA(c, upload(c, c->tri_ta, sp.ta.data(), sp.ta.size() * sizeof(double), TCW_HOST), "triage buffers");
       TCW_CUDA(c, c->tri_coef.ensure((size_t)sp.nt64 * c->Bpad * sizeof(double)), "triage buffers");
@@ -570,6 +566,7 @@ tcw_status tcw::coarse_pass(tcw_ctx* c, const CoarseEvent& ev, int patch_size, f
       cs.f_min = ev.f_min;
       cs.df = ev.df;
       cs.dop = sd.dop;
+      cs.unsorted = sd.unsorted;
       cs.P = P;
       cs.P2 = P2;
       cs.f0 = c->f0.as<double>();

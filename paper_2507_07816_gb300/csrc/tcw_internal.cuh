@@ -254,13 +254,14 @@ size_t coarse_part_elems(int P, int Bpad);
 cudaError_t launch_patch_doppler(const PatchDopplerParams& p, cudaStream_t st);
 cudaError_t launch_coarse(const CoarseParams& p, bool half, cudaStream_t st);
 
-// Coarse pass, sweep form.  When the representatives' Doppler factors are
-// non-decreasing in patch order at every (detector, segment), the bin of a
+// Coarse pass, sweep form.  Where the representatives' Doppler factors are
+// non-decreasing in patch order at a (detector, segment), the bin of a
 // (template, segment, detector) lookup is a non-decreasing step function of
 // the representative, so one thread per template gathers the first
 // representative's bin and records each step's power difference in a
 // per-template difference array; a prefix sum over the representatives
-// gives every S (Eq. 4 numerator).
+// gives every S (Eq. 4 numerator).  The other (detector, segment) pairs (two
+// representatives' factors cross there) take every representative's own bin.
 constexpr int kSweepThreads = 256;
 constexpr int kSweepMaxPatches = 128;   // shared memory: (P + 1) x kSweepThreads floats
 constexpr int kSweepMaxTerms = 24;      // FP64 binomial terms of the anchor-to-anchor step
@@ -271,7 +272,8 @@ struct SweepDopplerParams {
   int n_det, n_seg, S, patch_size, P, P2;   // P2: power of two >= P
   int stride, n_seg_full;
   float* dop;               // [D][n_seg][P2] v.nhat/c of each representative, +inf beyond P
-  int* unsorted;            // set to 1 where the factor decreases from one representative to the next
+  int* unsorted;            // [D][n_seg], zero at launch: set to 1 where the factor decreases
+                            // from one representative to the next
 };
 
 struct CoarseSweepParams {
@@ -285,6 +287,8 @@ struct CoarseSweepParams {
   int tile_shift, n_tiles, nt64;
   double T0, f_min, df;
   const float* dop;         // [D][n_seg][P2] from SweepDopplerParams
+  const int* unsorted;      // [D][n_seg] from SweepDopplerParams: those lookups take every
+                            // representative one by one
   int P, P2;
   const double* f0;         // sorted bank [Bpad]
   const double* tau;

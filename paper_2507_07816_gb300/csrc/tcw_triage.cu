@@ -265,7 +265,7 @@ __global__ void sweep_doppler_kernel(SweepDopplerParams p) {
     float v = INFINITY;
     if (q < p.P) {
       v = rep_doppler(p, d, j, q);
-      if (q > 0 && rep_doppler(p, d, j, q - 1) > v) *p.unsorted = 1;
+      if (q > 0 && rep_doppler(p, d, j, q - 1) > v) p.unsorted[dj] = 1;
     }
     p.dop[i] = v;
   }
@@ -275,7 +275,7 @@ constexpr int kSweepChunk = 32;   // segments staged per block step of the sweep
 
 // shared memory of coarse_sweep_kernel: the staged chunk and the difference arrays
 inline int sweep_smem_bytes(int P, int P2, int D) {
-  return kSweepChunk * (16 + 8 * D + 4 * D * P2) + (P + 1) * kSweepThreads * 4;
+  return kSweepChunk * (16 + 12 * D + 4 * D * P2) + (P + 1) * kSweepThreads * 4;
 }
 
 __device__ __forceinline__ void sweep_store(const CoarseSweepParams& p, int r, int b, float psi) {
@@ -306,8 +306,9 @@ __device__ __forceinline__ void sweep_store(const CoarseSweepParams& p, int r, i
 // the factors' nearly even spacing, corrected by exact comparisons) and adds
 // the power difference to that representative's entry of the difference array
 // (shared memory, one column per thread).  Lookups where
-// some representatives leave the band take every representative one by one
-// and record their W2 and count steps in global scratch.  Psi (Eq. 4) =
+// some representatives leave the band, and lookups at a (detector, segment)
+// whose factors are out of order, take every representative one by one and
+// record their W2 and count steps in global scratch.  Psi (Eq. 4) =
 // (S - W1)/sqrt(W2), accumulated as sum w (rho - 1).
 template <typename RhoT, int D, int NC>
 __global__ void __launch_bounds__(kSweepThreads, 4) coarse_sweep_kernel(CoarseSweepParams p) {
@@ -315,7 +316,8 @@ __global__ void __launch_bounds__(kSweepThreads, 4) coarse_sweep_kernel(CoarseSw
   float4* s_seg = s_sweep;                                              // [kSweepChunk]
   float* s_w = reinterpret_cast<float*>(s_seg + kSweepChunk);           // [D][kSweepChunk]
   float* s_step = s_w + D * kSweepChunk;                                // [kSweepChunk][D] (P-1)/span
-  float* s_dop = s_step + D * kSweepChunk;                              // [kSweepChunk][D][P2]
+  int* s_uns = reinterpret_cast<int*>(s_step + D * kSweepChunk);        // [kSweepChunk][D] unsorted
+  float* s_dop = reinterpret_cast<float*>(s_uns + D * kSweepChunk);     // [kSweepChunk][D][P2]
   float* s_diff = s_dop + kSweepChunk * D * p.P2;                       // [P + 1][kSweepThreads]
   const int tid = threadIdx.x;
   const int b = blockIdx.x * kSweepThreads + tid;
@@ -366,6 +368,7 @@ __global__ void __launch_bounds__(kSweepThreads, 4) coarse_sweep_kernel(CoarseSw
       const float* dr = p.dop + ((int64_t)d * p.n_seg + c0 + jj) * P2;
       const float span = dr[p.P - 1] - dr[0];
       s_step[jj * D + d] = span > 0.f ? (float)(p.P - 1) / span : 0.f;
+      s_uns[jj * D + d] = p.unsorted[(int64_t)d * p.n_seg + c0 + jj];
     }
     __syncthreads();
     if (!live) continue;
@@ -438,7 +441,8 @@ __global__ void __launch_bounds__(kSweepThreads, 4) coarse_sweep_kernel(CoarseSw
         const float* dr = s_dop + (jj * D + d) * P2;
         const int64_t k0 = (int64_t)base + olo[d], k1 = (int64_t)base + ohi[d];
         const RhoT* row = rho + ((int64_t)d * p.n_seg_full + (int64_t)j * p.stride) * p.n_bin;
-        if (k0 >= 0 && k1 < p.n_bin) {
+        const bool uns = s_uns[jj * D + d] != 0;
+        if (!uns && k0 >= 0 && k1 < p.n_bin) {
           float rp = r0[d];
           Sb = fmaf(w, rp - 1.f, Sb);
           W2b = fmaf(w, w, W2b);
@@ -459,7 +463,8 @@ __global__ void __launch_bounds__(kSweepThreads, 4) coarse_sweep_kernel(CoarseSw
               rp = r1;
             }
           }
-        } else if (k1 >= 0 && k0 < p.n_bin) {
+        } else if (uns || (k1 >= 0 && k0 < p.n_bin)) {
+          // band edge, or factors out of order: every representative's own bin
           if (!edge) {
             edge = true;
             for (int r = 0; r <= p.P; ++r) {
