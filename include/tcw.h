@@ -466,6 +466,8 @@ typedef struct {
                                    per template over every segment; used when the track series
                                    meet its error bounds and n_patch <= 128), 0 = one thread per
                                    (template, patch) */
+    int coarse_parts;           /* sweep form: segment ranges per template (chosen to fill the
+                                   device's resident blocks), 0 otherwise */
 } tcw_triage_info;
 
 tcw_status tcw_get_triage_info(tcw_ctx *ctx, tcw_triage_info *info);

@@ -582,8 +582,18 @@ tcw_status tcw::coarse_pass(tcw_ctx* c, const CoarseEvent& ev, int patch_size, f
       cs.psi = psi;
       cs.hist = c->tri_hist.as<unsigned>();
       cs.feat = feat;
+      TCW_CUDA(c, cudaMemsetAsync(c->tri_w2e.p, 0, (size_t)(P + 1) * c->Bpad * sizeof(double), c->stream), "triage");
+      TCW_CUDA(c, cudaMemsetAsync(c->tri_ne.p, 0, (size_t)(P + 1) * c->Bpad * sizeof(int), c->stream), "triage");
+      cs.parts = 1;
+      cs.parts = sweep_parts(cs, ev.half, sp.nc);
+      if (cs.parts > 1) {
+        TCW_CUDA(c, c->tri_pS.ensure((size_t)cs.parts * P * c->Bpad * sizeof(float)), "triage buffers");
+        TCW_CUDA(c, c->tri_pW.ensure((size_t)cs.parts * c->Bpad * sizeof(float)), "triage buffers");
+        cs.part_S = c->tri_pS.as<float>();
+        cs.part_W2 = c->tri_pW.as<float>();
+      }
       TCW_CUDA(c, launch_coarse_sweep(cs, ev.half, sp.nc, c->stream), "coarse_sweep_kernel launch");
-      *sweep_out = 1;
+      *sweep_out = cs.parts;
       return TCW_OK;
     }
   }
@@ -686,7 +696,8 @@ tcw_status run_coarse(tcw_ctx* c, int patch_size, float lo, float hi, bool keep_
   c->tri_info.n_patch = P;
   c->tri_info.lookups_coarse = (int64_t)P * c->B * c->D * n_cs;
   c->tri_info.lookups_full = c->S * c->B * c->D * c->Nseg;
-  c->tri_info.coarse_kernel = sweep;
+  c->tri_info.coarse_kernel = sweep > 0 ? 1 : 0;
+  c->tri_info.coarse_parts = sweep;
   return TCW_OK;
 }
 

@@ -904,7 +904,7 @@ tcw_status tcw_search_batched_triaged(tcw_ctx* c, const uint16_t* wbf, const flo
     st = coarse_pass(c, ce, ps[e], psi_lo, psi_hi, c->tri_feat.as<float>() + (size_t)row0[e] * kTriageBins,
                      regions ? c->tri_psi.as<float>() + (size_t)row0[e] * c->Bpad : nullptr, &Pe, &sweep);
     if (st != TCW_OK) return st;
-    sweeps += sweep;
+    sweeps += sweep > 0 ? 1 : 0;
     const int64_t n_cs = (h.n_seg + c->triage_stride - 1) / c->triage_stride;
     lookups_coarse += (int64_t)P[e] * c->B * b->D * n_cs;
     lookups_full += h.n_sky * c->B * b->D * h.n_seg;

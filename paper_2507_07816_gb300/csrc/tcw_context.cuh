@@ -105,7 +105,7 @@ struct tcw_ctx {
   std::vector<int32_t> h_sky_perm, h_bank_perm;  // sorted -> caller (host copies)
   tcw::DevBuf tri_tmid;   // coarse-pass segment times (every stride-th segment)
   tcw::DevBuf tri_dop, tri_hist, tri_feat, tri_psi, tri_anchor, tri_h1, tri_h2, tri_score, tri_sel, tri_part;
-  tcw::DevBuf tri_seg, tri_ta, tri_coef, tri_w2e, tri_ne, tri_flag;   // sweep form of the coarse pass
+  tcw::DevBuf tri_seg, tri_ta, tri_coef, tri_w2e, tri_ne, tri_flag, tri_pS, tri_pW;   // sweep form
   tcw_triage_info tri_info{};
 };
 
@@ -178,7 +178,8 @@ struct CoarseEvent {
 // Coarse pass of one event against the context's bank (TCW_OPT_TRIAGE_STRIDE
 // segments, patches of patch_size sorted skies): the features [P][128] into
 // feat and, when psi is not null, the coarse Psi [P][Bpad] (sorted bank) into
-// psi.  *sweep_out = 1 when the sweep form ran.  Uses the context's triage
+// psi.  *sweep_out = the sweep form's segment ranges per template, 0 when the
+// per-(template, patch) kernel ran.  Uses the context's triage
 // scratch buffers; asynchronous on the context's stream after its checks.
 tcw_status coarse_pass(tcw_ctx* c, const CoarseEvent& ev, int patch_size, float lo, float hi, float* feat,
                        float* psi, int* P_out, int* sweep_out);

@@ -295,8 +295,11 @@ struct CoarseSweepParams {
   const double* nbr;
   int B, Bpad;
   double* coef64;           // [nt64][Bpad] scratch: binomial coefficients of each template
-  double* w2edge;           // [P + 1][Bpad] scratch: W2 steps of band-edge lookups
-  int* nedge;               // [P + 1][Bpad] scratch: valid-lookup count steps of band-edge lookups
+  double* w2edge;           // [P + 1][Bpad] zero at launch: W2 steps of band-edge lookups
+  int* nedge;               // [P + 1][Bpad] zero at launch: valid-lookup count steps of them
+  int parts;                // segment ranges per template (a multiple of 64 segments each)
+  float* part_S;            // [parts][P][Bpad] when parts > 1: S - W1 per range
+  float* part_W2;           // [parts][Bpad] when parts > 1: W2 of in-band lookups per range
   float lo, hi;
   float* psi;               // optional [P][Bpad]
   unsigned* hist;           // [P][128], zero at launch
@@ -318,6 +321,9 @@ cudaError_t launch_gather_rows(const int32_t* src, const int32_t* idx, int64_t n
 cudaError_t launch_fill_empty(float* psi, int64_t* idx, int64_t n, cudaStream_t st);
 // nc: fp32 terms of the in-tile series beyond the quadratic one (4, 6 or 8)
 cudaError_t launch_coarse_sweep(const CoarseSweepParams& p, bool half, int nc, cudaStream_t st);
+// Segment ranges per template for the sweep form: the count in [1, 4] whose
+// blocks finish soonest on the device's resident slots.
+int sweep_parts(const CoarseSweepParams& p, bool half, int nc);
 // selected[p] = 1 for the m best patches; a chosen patch suppresses the
 // patches within `radius` of it (0 = plain ranking)
 cudaError_t launch_rank(const float* score, int P, int m, int radius, int* selected, cudaStream_t st);

@@ -351,8 +351,11 @@ __global__ void __launch_bounds__(kSweepThreads, 4) coarse_sweep_kernel(CoarseSw
   float frac_a = 0.f, A_hi = 0.f, A_lo = 0.f, Q_hi = 0.f, Q_lo = 0.f, Xf = 0.f, sg = 0.f;
   float Sb = 0.f, W2b = 0.f;
   const int P2 = p.P2;
-  for (int c0 = 0; c0 < p.n_seg; c0 += kSweepChunk) {
-    const int cn = min(kSweepChunk, p.n_seg - c0);
+  // segment range blockIdx.y of p.parts (whole multiples of 64 segments)
+  const int per = (p.n_seg + 64 * p.parts - 1) / (64 * p.parts) * 64;
+  const int jb = min(p.n_seg, (int)blockIdx.y * per), je = min(p.n_seg, jb + per);
+  for (int c0 = jb; c0 < je; c0 += kSweepChunk) {
+    const int cn = min(kSweepChunk, je - c0);
     __syncthreads();
     for (int i = tid; i < cn; i += kSweepThreads) s_seg[i] = p.seg[c0 + i];
     for (int i = tid; i < D * cn; i += kSweepThreads) {
@@ -465,13 +468,7 @@ __global__ void __launch_bounds__(kSweepThreads, 4) coarse_sweep_kernel(CoarseSw
           }
         } else if (uns || (k1 >= 0 && k0 < p.n_bin)) {
           // band edge, or factors out of order: every representative's own bin
-          if (!edge) {
-            edge = true;
-            for (int r = 0; r <= p.P; ++r) {
-              p.w2edge[(int64_t)r * p.Bpad + b] = 0.0;
-              p.nedge[(int64_t)r * p.Bpad + b] = 0;
-            }
-          }
+          edge = true;
           const double w2 = (double)w * (double)w;
           for (int r = 0; r < p.P; ++r) {
             const int64_t kr = (int64_t)base + __float2int_rd(fmaf(F, dr[r], frac5));
@@ -479,10 +476,11 @@ __global__ void __launch_bounds__(kSweepThreads, 4) coarse_sweep_kernel(CoarseSw
             const float v = w * (load_rho(row, kr) - 1.f);
             col[r * kSweepThreads] += v;
             col[(r + 1) * kSweepThreads] -= v;
-            p.w2edge[(int64_t)r * p.Bpad + b] += w2;
-            p.w2edge[(int64_t)(r + 1) * p.Bpad + b] -= w2;
-            p.nedge[(int64_t)r * p.Bpad + b] += 1;
-            p.nedge[(int64_t)(r + 1) * p.Bpad + b] -= 1;
+            // other segment ranges of this template may add to the same entries
+            atomicAdd(p.w2edge + (int64_t)r * p.Bpad + b, w2);
+            atomicAdd(p.w2edge + (int64_t)(r + 1) * p.Bpad + b, -w2);
+            atomicAdd(p.nedge + (int64_t)r * p.Bpad + b, 1);
+            atomicAdd(p.nedge + (int64_t)(r + 1) * p.Bpad + b, -1);
           }
         }
       }
@@ -490,6 +488,14 @@ __global__ void __launch_bounds__(kSweepThreads, 4) coarse_sweep_kernel(CoarseSw
   }
   if (!live) return;
   float acc = Sb;
+  if (p.parts > 1) {
+    for (int r = 0; r < p.P; ++r) {
+      acc += col[r * kSweepThreads];
+      p.part_S[((int64_t)blockIdx.y * p.P + r) * p.Bpad + b] = acc;
+    }
+    p.part_W2[(int64_t)blockIdx.y * p.Bpad + b] = W2b;
+    return;
+  }
   double w2e = 0.0;
   int ne = 0;
   for (int r = 0; r < p.P; ++r) {
@@ -499,6 +505,24 @@ __global__ void __launch_bounds__(kSweepThreads, 4) coarse_sweep_kernel(CoarseSw
       ne += p.nedge[(int64_t)r * p.Bpad + b];
     }
     // a representative with no in-band edge lookup takes the interior W2 alone
+    const double W2 = (double)W2b + (ne > 0 ? w2e : 0.0);
+    sweep_store(p, r, b, W2 > 0.0 ? acc * rsqrtf((float)W2) : -INFINITY);
+  }
+}
+
+// Sums the segment ranges in order (deterministic), then Psi and the histogram.
+__global__ void sweep_finalize_kernel(CoarseSweepParams p) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= p.B) return;
+  float W2b = 0.f;
+  for (int z = 0; z < p.parts; ++z) W2b += p.part_W2[(int64_t)z * p.Bpad + b];
+  double w2e = 0.0;
+  int ne = 0;
+  for (int r = 0; r < p.P; ++r) {
+    float acc = 0.f;
+    for (int z = 0; z < p.parts; ++z) acc += p.part_S[((int64_t)z * p.P + r) * p.Bpad + b];
+    w2e += p.w2edge[(int64_t)r * p.Bpad + b];
+    ne += p.nedge[(int64_t)r * p.Bpad + b];
     const double W2 = (double)W2b + (ne > 0 ? w2e : 0.0);
     sweep_store(p, r, b, W2 > 0.0 ? acc * rsqrtf((float)W2) : -INFINITY);
   }
@@ -831,32 +855,70 @@ cudaError_t launch_sweep_doppler(const SweepDopplerParams& p, cudaStream_t st) {
 }
 
 template <typename RhoT, int D, int NC>
-cudaError_t launch_sweep_t(const CoarseSweepParams& p, cudaStream_t st) {
+cudaError_t launch_sweep_t(const CoarseSweepParams& p, cudaStream_t st, int* slots) {
   const int smem = sweep_smem_bytes(p.P, p.P2, D);
   auto kern = coarse_sweep_kernel<RhoT, D, NC>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  kern<<<(p.B + kSweepThreads - 1) / kSweepThreads, kSweepThreads, smem, st>>>(p);
+  if (slots) {   // resident blocks on the whole device
+    int per_sm = 0, dev = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSweepThreads, smem);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    *slots = per_sm * sms;
+    return e;
+  }
+  dim3 grid((p.B + kSweepThreads - 1) / kSweepThreads, p.parts);
+  kern<<<grid, kSweepThreads, smem, st>>>(p);
   return cudaGetLastError();
 }
 
 template <typename RhoT, int D>
-cudaError_t launch_sweep_d(const CoarseSweepParams& p, int nc, cudaStream_t st) {
-  if (nc <= 4) return launch_sweep_t<RhoT, D, 4>(p, st);
-  if (nc <= 6) return launch_sweep_t<RhoT, D, 6>(p, st);
-  return launch_sweep_t<RhoT, D, 8>(p, st);
+cudaError_t launch_sweep_d(const CoarseSweepParams& p, int nc, cudaStream_t st, int* slots) {
+  if (nc <= 4) return launch_sweep_t<RhoT, D, 4>(p, st, slots);
+  if (nc <= 6) return launch_sweep_t<RhoT, D, 6>(p, st, slots);
+  return launch_sweep_t<RhoT, D, 8>(p, st, slots);
+}
+
+cudaError_t launch_sweep_any(const CoarseSweepParams& p, bool half, int nc, cudaStream_t st, int* slots) {
+  if (half)
+    return p.n_det == 1 ? launch_sweep_d<__half, 1>(p, nc, st, slots) : launch_sweep_d<__half, 2>(p, nc, st, slots);
+  return p.n_det == 1 ? launch_sweep_d<float, 1>(p, nc, st, slots) : launch_sweep_d<float, 2>(p, nc, st, slots);
+}
+
+int sweep_parts(const CoarseSweepParams& p, bool half, int nc) {
+  int slots = 0;
+  if (launch_sweep_any(p, half, nc, nullptr, &slots) != cudaSuccess || slots <= 0) {
+    cudaGetLastError();
+    return 1;
+  }
+  // time in units of one whole-range block: ceil(blocks x parts / slots) waves of
+  // blocks that each walk 1/parts of the segments
+  const int64_t blocks = (p.B + kSweepThreads - 1) / kSweepThreads;
+  int best = 1;
+  double best_t = 0.0;
+  for (int parts = 1; parts <= 4 && (int64_t)p.n_seg >= 64LL * parts * 4; ++parts) {
+    const double t = std::ceil((double)(blocks * parts) / slots) / parts;
+    if (parts == 1 || t < 0.98 * best_t) {
+      best = parts;
+      best_t = t;
+    }
+  }
+  return best;
 }
 
 cudaError_t launch_coarse_sweep(const CoarseSweepParams& p, bool half, int nc, cudaStream_t st) {
   if (p.n_det < 1 || p.n_det > kCoarseMaxDet || p.P < 1 || p.P > kSweepMaxPatches || nc > 8 ||
       p.nt64 < 1 || p.nt64 > kSweepMaxTerms || p.P2 < p.P || (p.P2 & (p.P2 - 1)))
     return cudaErrorInvalidValue;
-  cudaError_t e;
-  if (half)
-    e = p.n_det == 1 ? launch_sweep_d<__half, 1>(p, nc, st) : launch_sweep_d<__half, 2>(p, nc, st);
-  else
-    e = p.n_det == 1 ? launch_sweep_d<float, 1>(p, nc, st) : launch_sweep_d<float, 2>(p, nc, st);
+  if (p.parts < 1 || (p.parts > 1 && (!p.part_S || !p.part_W2))) return cudaErrorInvalidValue;
+  cudaError_t e = launch_sweep_any(p, half, nc, st, nullptr);
   if (e != cudaSuccess) return e;
+  if (p.parts > 1) {
+    sweep_finalize_kernel<<<(p.B + 255) / 256, 256, 0, st>>>(p);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   const int64_t n = (int64_t)p.P * kTriageBins;
   features_kernel<<<blocks_for(n, 256), 256, 0, st>>>(p.hist, n, p.feat);
   return cudaGetLastError();

@@ -89,7 +89,7 @@ class _TriageInfo(ctypes.Structure):
                 ("lookups_coarse", ctypes.c_int64), ("lookups_searched", ctypes.c_int64),
                 ("coarse_ms", ctypes.c_float), ("mlp_ms", ctypes.c_float),
                 ("search_ms", ctypes.c_float), ("templates_searched", ctypes.c_int64),
-                ("coarse_kernel", ctypes.c_int)]
+                ("coarse_kernel", ctypes.c_int), ("coarse_parts", ctypes.c_int)]
 
 
 MLP_PARAMS, MLP_WEIGHTS = 99073, 98560

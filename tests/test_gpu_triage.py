@@ -34,14 +34,17 @@ def small_event(seed, n_det=2, n_seg=150, n_bin=1200, n_sky=120, n_tmpl=96, n_in
 # 15 patches (sweep form, representatives' factors in order), 120 patches (sweep
 # form; neighbouring skies' factors cross, so many (detector, segment) pairs take
 # every representative's own bin) and 200 patches (the per-(template, patch) kernel)
-@pytest.mark.parametrize("P_SIZE,N_SKY,SWEEP", [(8, 120, 1), (1, 120, 1), (1, 200, 0)])
-def test_coarse_features_match_oracle(P_SIZE, N_SKY, SWEEP):
-    ev, bank = small_event(81, n_inj=2, n_sky=N_SKY)
+# (the 1100-segment event splits every template's segments into 4 ranges)
+@pytest.mark.parametrize("P_SIZE,N_SKY,N_SEG,SWEEP,PARTS",
+                         [(8, 120, 150, 1, 1), (1, 120, 150, 1, 1), (1, 200, 150, 0, 0), (8, 120, 1100, 1, 4)])
+def test_coarse_features_match_oracle(P_SIZE, N_SKY, N_SEG, SWEEP, PARTS):
+    ev, bank = small_event(81, n_inj=2, n_sky=N_SKY, n_seg=N_SEG)
     LO, HI = -4.0, 12.0
     s = tcw.Search(0)
     TR.load_event(s, ev, bank)
     feat, psi = s.triage_features(P_SIZE, LO, HI, with_psi=True)
-    assert s.triage_info()["coarse_kernel"] == SWEEP
+    info = s.triage_info()
+    assert (info["coarse_kernel"], info["coarse_parts"]) == (SWEEP, PARTS)
     ora = OT.coarse_psi(ev.rho, ev.f_min, ev.df, ev.t_mid, ev.weights, ev.velocity, ev.nhat,
                         bank.f0, bank.tau, bank.n, ev.T0, P_SIZE)
     # pairs with a lookup within COARSE_TIE of a rounding tie may differ
