@@ -288,6 +288,7 @@ tcw_status run_search(tcw_ctx* c, bool record, int32_t* rec_dev) {
       ap.tile_shift = tile_shift;
       ap.Bpad = c->Bpad;
       ap.anchors = c->anchors.as<double>();
+      ap.chain = anchor_chain_for(c->h_t.data(), c->Nseg, c->T0, 1 << tile_shift, c->bank_tau_min, c->bank_r_max);
     }
     TCW_CUDA(c, c->evtab.ensure(sizeof(EventDesc)), "event table");
     TCW_CUDA(c, cudaMemcpyAsync(c->evtab.p, &ev, sizeof(ev), cudaMemcpyHostToDevice, c->stream), "event table");
@@ -625,6 +626,7 @@ tcw_status tcw::coarse_pass(tcw_ctx* c, const CoarseEvent& ev, int patch_size, f
     ap.tile_shift = 5;
     ap.Bpad = c->Bpad;
     ap.anchors = c->tri_anchor.as<double>();
+    ap.chain = anchor_chain_for(tc.data(), n_cs, ev.T0, tile, tau_min, r_max);
     TCW_CUDA(c, launch_anchors(ap, c->stream), "anchor_kernel launch");
   }
   CoarseParams cp{};

@@ -379,6 +379,7 @@ cudaError_t launch_wave_anchors(const tcw_ctx* c, BatchState* b, int w, int tile
     ap.n_tiles = n_tiles_of(e.n_seg, tile);
     ap.tile_shift = ilog2(tile);
     ap.Bpad = ev_Bpad(c, e);
+    ap.chain = anchor_chain_for(e.t.data(), e.n_seg, e.T0, tile, c->bank_tau_min, c->bank_r_max);
     ap.anchors = at<double>(b->anchors, e.o_anchor);
     cudaError_t err = launch_anchors(ap, st);
     if (err != cudaSuccess) return err;

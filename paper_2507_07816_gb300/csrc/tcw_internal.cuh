@@ -140,7 +140,14 @@ struct AnchorParams {
   double T0;
   int n_seg, n_tiles, tile_shift, Bpad;
   double* anchors;         // [Bpad][n_tiles][2]
+  int chain;               // 1: each run of kAnchorRun tiles takes pow at its first anchor and the
+                           // binomial series from anchor to anchor after it; 0: pow at every anchor
 };
+constexpr int kAnchorRun = 16;     // anchors per pow in the chained form
+constexpr int kAnchorTerms = 20;   // binomial-series terms of one anchor-to-anchor step
+// 1 when the anchor-to-anchor steps of these segment times allow the chained
+// form: u'/u - 1 <= 0.1 and the series' remainder below 2^-56 relative.
+int anchor_chain_for(const double* t_mid, int64_t n_seg, double T0, int tile, double tau_min, double r_max);
 
 struct LookupParams {
   const void* rho;
