@@ -176,11 +176,15 @@ def kernel_source_digest():
 
 
 # DRAM bytes (read + write) of one group-kernel launch per lookup, from an ncu
-# capture of the 2 x 2000 x 10000 map, 8000-template, 1024-sky case (one kernel,
-# one launch), keyed by the kernel source digest it was taken on; a full-size
-# launch is taken to move the same bytes per lookup.  No entry for the current
-# source: the traffic is reported as null.
-GROUP_KERNEL_DRAM_BYTES_PER_LOOKUP = {}
+# capture (dram__bytes_read.sum + dram__bytes_write.sum, one pass) of the
+# bank8000 workload: the full 2 x 10000 x 10000 map, Doppler table and sky with
+# 8000 templates, one launch; a full launch streams the same map and table once
+# per pass, 25 times as many passes, so it is taken to move the same bytes per
+# lookup.  Keyed by the kernel source digest it was taken on; no entry for the
+# current source: the traffic is reported as null.
+GROUP_KERNEL_DRAM_BYTES_PER_LOOKUP = {
+    "c816dee2c7d44e5e": (3010211584 + 39771392) / (1024 * 8000 * 2 * 10000),
+}
 
 
 def group_kernel_traffic(lookups):
