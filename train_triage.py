@@ -88,12 +88,13 @@ def main():
         t0 = time.perf_counter()
         judged = TR.evaluate(mlp, make(valid_seed + 1000), args.valid_events, bank, psi_det, frac=args.frac,
                              patch_size=args.patch_size, templates_permille=tpm, stride=stride)
+        # the literal form: the best 10 % of the patches, every template
         judged_all = TR.evaluate(mlp, make(valid_seed + 1000), min(args.valid_events, 200), bank, psi_det,
-                                 frac=args.frac, patch_size=args.patch_size, templates_permille=1000, stride=stride)
+                                 frac=0.1, patch_size=args.patch_size, templates_permille=1000, stride=stride)
         judged_un = TR.evaluate(untrained, make(valid_seed + 1000), min(args.valid_events, 50), bank, psi_det,
                                 frac=args.frac, patch_size=args.patch_size, templates_permille=tpm, stride=stride)
         report = {"weights": os.path.relpath(args.out, ROOT), "psi_det": psi_det, "judged_trained": judged,
-                  "judged_trained_all_templates": judged_all, "judged_untrained": judged_un,
+                  "judged_trained_top10pct_all_templates": judged_all, "judged_untrained": judged_un,
                   "valid_s": time.perf_counter() - t0}
         print(json.dumps(report), flush=True)
         if args.report:
