@@ -3,11 +3,21 @@
 // The paper searches every sky direction exhaustively (Sec. 2, Eq. 4).  The
 // triage ranks sky patches first and searches only the best-ranked ones:
 //
-//   patch_doppler_kernel  Eq. 2 factor v.nhat/c of each patch representative
-//   coarse_kernel         Psi (Eq. 4) of every template at every patch
-//                         representative, one thread per (template, patch)
-//                         (blocks of 32 or 64 patches x 8 or 4 templates),
-//                         and the 128-bin histogram of those Psi per patch
+//   sweep_doppler_kernel  Eq. 2 factor v.nhat/c of each patch representative,
+//                         padded to a power of two, and a flag for every
+//                         (detector, segment) whose factors are out of order
+//   coarse_sweep_kernel   Psi (Eq. 4) of every template at every patch
+//                         representative, one thread per template walking the
+//                         segments (or a range of them): the representatives'
+//                         bins of a lookup form a step function of the
+//                         representative, gathered once and stepped in a
+//                         per-template difference array; the 128-bin
+//                         histogram of those Psi per patch
+//   sweep_finalize_kernel the segment ranges' partial sums, in order
+//   patch_doppler_kernel, coarse_kernel
+//                         the same Psi, one thread per (template, patch), for
+//                         banks outside the sweep form's series bounds and for
+//                         more than 128 patches
 //   features_kernel       log(1 + count) per histogram bin
 //   MLP 128 -> 256 -> 256 -> 1 (ReLU), bfloat16 weights, fp32 accumulation:
 //     gemm_kernel         tiled C = op(A) op(B) (+ bias, ReLU) for the forward
@@ -15,15 +25,15 @@
 //     relu_mask / colsum / bce / adam kernels
 //   select_kernel         best patches by score with suppression of their
 //                         neighbours (rank_kernel: plain ranking)
+//   region_select_kernel  the best templates of a chosen patch by coarse Psi
+//                         (exact radix select), for the batched triaged search
 //
 // Patches are runs of consecutive skies in the Doppler-sorted order of the
-// search; the representative of a patch is its middle sky.  The coarse pass
-// takes the bin of every lookup from an FP64 track entry per (template,
-// segment) split into an integer base and an fp32 fraction, plus the fp32
-// Doppler term, so its bins equal the exact ones except within ~3e-7 bins of
-// a rounding tie.  The Doppler term must stay within 2.9 bins, so every bin a
-// patch can pick lies in an 8-bin window around the base that the block
-// stages in shared memory once per (template, segment, detector).
+// search; the representative of a patch is its middle sky.  Both coarse
+// kernels decide bins in fp32 around FP64 track values (an FP64 entry per
+// (template, segment), or FP64 anchors per 64-segment tile with fp32 hi/lo
+// pairs inside the tile), so their bins equal the exact ones except within
+// ~1e-7 bins of a rounding tie.  The Doppler term must stay within 2.9 bins.
 #include <cuda_bf16.h>
 
 #include <climits>
@@ -351,6 +361,8 @@ __global__ void __launch_bounds__(kSweepThreads, 4) coarse_sweep_kernel(CoarseSw
   float frac_a = 0.f, A_hi = 0.f, A_lo = 0.f, Q_hi = 0.f, Q_lo = 0.f, Xf = 0.f, sg = 0.f;
   float Sb = 0.f, W2b = 0.f;
   const int P2 = p.P2;
+  const int nbin = (int)p.n_bin;
+  const int64_t plane = (int64_t)p.n_seg_full * p.n_bin;   // one detector's map
   // segment range blockIdx.y of p.parts (whole multiples of 64 segments)
   const int per = (p.n_seg + 64 * p.parts - 1) / (64 * p.parts) * 64;
   const int jb = min(p.n_seg, (int)blockIdx.y * per), je = min(p.n_seg, jb + per);
@@ -426,7 +438,9 @@ __global__ void __launch_bounds__(kSweepThreads, 4) coarse_sweep_kernel(CoarseSw
       const float frac5 = ((frac_a + (pl - plr)) + ((pq - pqr) + small)) + 0.5f;
       const float F = Xf + pl + pq;
       const int base = base_a + (int)plr + (int)pqr;
-      // both detectors' first gathers before either is used
+      // both detectors' first gathers before either is used (bins as int32: |base| < 1e9,
+      // n_bin <= 2^30)
+      const RhoT* row0 = rho + (int64_t)j * p.stride * p.n_bin;
       int olo[D], ohi[D];
       float r0[D];
 #pragma unroll
@@ -434,25 +448,24 @@ __global__ void __launch_bounds__(kSweepThreads, 4) coarse_sweep_kernel(CoarseSw
         const float* dr = s_dop + (jj * D + d) * P2;
         olo[d] = __float2int_rd(fmaf(F, dr[0], frac5));
         ohi[d] = __float2int_rd(fmaf(F, dr[p.P - 1], frac5));
-        const int64_t k0 = (int64_t)base + olo[d];
-        const int64_t kc = k0 < 0 ? 0 : (k0 >= p.n_bin ? p.n_bin - 1 : k0);
-        r0[d] = load_rho(rho, ((int64_t)d * p.n_seg_full + (int64_t)j * p.stride) * p.n_bin + kc);
+        const int kc = min(max(base + olo[d], 0), nbin - 1);
+        r0[d] = load_rho(row0 + d * plane, kc);
       }
 #pragma unroll
       for (int d = 0; d < D; ++d) {
         const float w = s_w[d * kSweepChunk + jj];
         const float* dr = s_dop + (jj * D + d) * P2;
-        const int64_t k0 = (int64_t)base + olo[d], k1 = (int64_t)base + ohi[d];
-        const RhoT* row = rho + ((int64_t)d * p.n_seg_full + (int64_t)j * p.stride) * p.n_bin;
+        const int k0 = base + olo[d], k1 = base + ohi[d];
+        const RhoT* row = row0 + d * plane;
         const bool uns = s_uns[jj * D + d] != 0;
-        if (!uns && k0 >= 0 && k1 < p.n_bin) {
+        if (!uns && k0 >= 0 && k1 < nbin) {
           float rp = r0[d];
           Sb = fmaf(w, rp - 1.f, Sb);
           W2b = fmaf(w, w, W2b);
           if (ohi[d] > olo[d]) {
             const float step = s_step[jj * D + d], d0 = dr[0], rF = __frcp_rn(F);
             for (int o = olo[d] + 1; o <= ohi[d]; ++o) {
-              const float r1 = load_rho(row, (int64_t)base + o);
+              const float r1 = load_rho(row, base + o);
               // first representative q with fmaf(F, v_q/c, frac5) >= o: q is in
               // [1, P-1] (representative 0 is below o, the last one reaches it);
               // guessed from the nearly even spacing of the factors, then moved
@@ -466,13 +479,13 @@ __global__ void __launch_bounds__(kSweepThreads, 4) coarse_sweep_kernel(CoarseSw
               rp = r1;
             }
           }
-        } else if (uns || (k1 >= 0 && k0 < p.n_bin)) {
+        } else if (uns || (k1 >= 0 && k0 < nbin)) {
           // band edge, or factors out of order: every representative's own bin
           edge = true;
           const double w2 = (double)w * (double)w;
           for (int r = 0; r < p.P; ++r) {
-            const int64_t kr = (int64_t)base + __float2int_rd(fmaf(F, dr[r], frac5));
-            if (kr < 0 || kr >= p.n_bin) continue;
+            const int kr = base + __float2int_rd(fmaf(F, dr[r], frac5));
+            if (kr < 0 || kr >= nbin) continue;
             const float v = w * (load_rho(row, kr) - 1.f);
             col[r * kSweepThreads] += v;
             col[(r + 1) * kSweepThreads] -= v;
