@@ -350,6 +350,17 @@ def test_batched_triaged_rows_equal_exhaustive_batched_rows():
         S = e.nhat.shape[0]
         assert rows[row:row + S].sum() >= 16 * int(np.ceil(0.3 * p)) - 15
         row += S
+    # patch_size 0: 32 patches of ceil(n_sky / 32) skies per event
+    pt0, it0, searched0 = s.search_batched_triaged(mlp, 0, -4.0, 12.0, 0.3, k)
+    assert s.triage_info()["n_patch"] == sum(-(-e.nhat.shape[0] // -(-e.nhat.shape[0] // 32)) for e in evs)
+    r0 = searched0.astype(bool)
+    assert r0.any()
+    # 4-sky patches do not keep the full search's 16-sky groups, so the rows agree
+    # within the parity tolerance rather than bit for bit
+    np.testing.assert_allclose(pt0[r0], vx[r0], rtol=1e-5, atol=1e-5)
+    assert (it0[r0][:, 0] == ix[r0][:, 0]).mean() > 0.95
+    with pytest.raises(tcw.TcwError):
+        s.search_batched_triaged(mlp, -1, -4.0, 12.0, 0.3, k)
     s.close()
 
 
