@@ -1441,23 +1441,25 @@ tcw_status tcw_search_triaged(tcw_ctx* c, const uint16_t* wbf, const float* thet
   // best templates by coarse Psi (sorted-bank indices)
   std::vector<int32_t> tsub;
   if (regions) {
-    const int64_t M = std::max<int64_t>(1, (c->B * c->triage_templates + 999) / 1000);
-    std::vector<float> row(c->Bpad);
-    std::vector<char> keep(c->B, 0);
-    std::vector<int32_t> ord(c->B);
-    for (int p = 0; p < P; ++p) {
-      if (!sel[p]) continue;
-      TCW_CUDA(c, cudaMemcpy(row.data(), c->tri_psi.as<float>() + (size_t)p * c->Bpad, c->Bpad * sizeof(float),
-                             cudaMemcpyDeviceToHost),
-               "coarse Psi");
-      std::iota(ord.begin(), ord.end(), 0);
-      std::nth_element(ord.begin(), ord.begin() + (M - 1), ord.end(), [&](int32_t a, int32_t b) {
-        return row[a] > row[b] || (row[a] == row[b] && a < b);
-      });
-      for (int64_t i = 0; i < M; ++i) keep[ord[i]] = 1;
-    }
+    // each chosen patch's M best templates by (coarse Psi desc, index asc), selected
+    // on the device; the union comes back as a keep mask
+    const int M = (int)std::max<int64_t>(1, (c->B * c->triage_templates + 999) / 1000);
+    std::vector<int32_t> rows;
+    for (int p = 0; p < P; ++p)
+      if (sel[p]) rows.push_back(p);
+    TCW_CUDA(c, c->tri_keep.ensure((size_t)c->Bpad + rows.size() * sizeof(int32_t) + 256), "triage buffers");
+    unsigned char* keep = c->tri_keep.as<unsigned char>();
+    int32_t* drows = reinterpret_cast<int32_t*>(keep + ((size_t)c->Bpad + 255) / 256 * 256);
+    TCW_CUDA(c, cudaMemsetAsync(keep, 0, c->Bpad, c->stream), "triage");
+    TCW_CUDA(c, cudaMemcpyAsync(drows, rows.data(), rows.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                c->stream), "triage");
+    TCW_CUDA(c, launch_region_select(c->tri_psi.as<float>(), c->Bpad, (int)c->B, drows, (int)rows.size(), M, keep,
+                                     c->stream), "region_select_kernel launch");
+    std::vector<unsigned char> hk(c->B);
+    TCW_CUDA(c, cudaMemcpyAsync(hk.data(), keep, c->B, cudaMemcpyDeviceToHost, c->stream), "triage");
+    TCW_CUDA(c, cudaStreamSynchronize(c->stream), "triage");
     for (int32_t b = 0; b < (int32_t)c->B; ++b)
-      if (keep[b]) tsub.push_back(b);
+      if (hk[b]) tsub.push_back(b);
   }
   const int64_t S_full = c->S;
   std::vector<double> full_nhat = c->h_nhat, sub_nhat(sub.size() * 3);
@@ -1473,14 +1475,22 @@ tcw_status tcw_search_triaged(tcw_ctx* c, const uint16_t* wbf, const float* thet
   if (!tsub.empty() && (int64_t)tsub.size() < B_full) {
     // search the template subset: the full bank's buffers are set aside and restored below
     const size_t n = tsub.size();
-    std::vector<double> f0(c->Bpad), tau(c->Bpad), nbr(c->Bpad), sf(n), st_(n), sn(n);
-    TCW_CUDA(c, cudaMemcpy(f0.data(), c->f0.p, c->Bpad * sizeof(double), cudaMemcpyDeviceToHost), "bank");
-    TCW_CUDA(c, cudaMemcpy(tau.data(), c->tau.p, c->Bpad * sizeof(double), cudaMemcpyDeviceToHost), "bank");
-    TCW_CUDA(c, cudaMemcpy(nbr.data(), c->nbr.p, c->Bpad * sizeof(double), cudaMemcpyDeviceToHost), "bank");
-    for (size_t i = 0; i < n; ++i) {
-      sf[i] = f0[tsub[i]];
-      st_[i] = tau[tsub[i]];
-      sn[i] = nbr[tsub[i]];
+    std::vector<double> sf(n), st_(n), sn(n);
+    {
+      // the subset's parameters, gathered on the device
+      TCW_CUDA(c, c->tri_sub.ensure(n * (3 * sizeof(double) + sizeof(int32_t))), "triage buffers");
+      double* g = c->tri_sub.as<double>();
+      int32_t* gi = reinterpret_cast<int32_t*>(g + 3 * n);
+      TCW_CUDA(c, cudaMemcpyAsync(gi, tsub.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream), "bank");
+      TCW_CUDA(c, launch_gather_rows(c->f0.as<double>(), gi, (int64_t)n, (int64_t)n, 1, g, c->stream), "gather");
+      TCW_CUDA(c, launch_gather_rows(c->tau.as<double>(), gi, (int64_t)n, (int64_t)n, 1, g + n, c->stream), "gather");
+      TCW_CUDA(c, launch_gather_rows(c->nbr.as<double>(), gi, (int64_t)n, (int64_t)n, 1, g + 2 * n, c->stream),
+               "gather");
+      TCW_CUDA(c, cudaMemcpyAsync(sf.data(), g, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "bank");
+      TCW_CUDA(c, cudaMemcpyAsync(st_.data(), g + n, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "bank");
+      TCW_CUDA(c, cudaMemcpyAsync(sn.data(), g + 2 * n, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+               "bank");
+      TCW_CUDA(c, cudaStreamSynchronize(c->stream), "bank");
     }
     perm_full = c->h_bank_perm;
     BankSwap saved(c);
