@@ -285,7 +285,7 @@ constexpr int kSweepChunk = 32;   // segments staged per block step of the sweep
 
 // shared memory of coarse_sweep_kernel: the staged chunk and the difference arrays
 inline int sweep_smem_bytes(int P, int P2, int D) {
-  return kSweepChunk * (16 + 12 * D + 4 * D * P2) + (P + 1) * kSweepThreads * 4;
+  return kSweepChunk * (16 + 20 * D + 4 * D * P2) + (P + 1) * kSweepThreads * 4;
 }
 
 __device__ __forceinline__ void sweep_store(const CoarseSweepParams& p, int r, int b, float psi) {
@@ -327,7 +327,8 @@ __global__ void __launch_bounds__(kSweepThreads, 4) coarse_sweep_kernel(CoarseSw
   float* s_w = reinterpret_cast<float*>(s_seg + kSweepChunk);           // [D][kSweepChunk]
   float* s_step = s_w + D * kSweepChunk;                                // [kSweepChunk][D] (P-1)/span
   int* s_uns = reinterpret_cast<int*>(s_step + D * kSweepChunk);        // [kSweepChunk][D] unsorted
-  float* s_dop = reinterpret_cast<float*>(s_uns + D * kSweepChunk);     // [kSweepChunk][D][P2]
+  float2* s_rng = reinterpret_cast<float2*>(s_uns + D * kSweepChunk);   // [kSweepChunk][D] first, last factor
+  float* s_dop = reinterpret_cast<float*>(s_rng + D * kSweepChunk);     // [kSweepChunk][D][P2]
   float* s_diff = s_dop + kSweepChunk * D * p.P2;                       // [P + 1][kSweepThreads]
   const int tid = threadIdx.x;
   const int b = blockIdx.x * kSweepThreads + tid;
@@ -383,6 +384,7 @@ __global__ void __launch_bounds__(kSweepThreads, 4) coarse_sweep_kernel(CoarseSw
       const float* dr = p.dop + ((int64_t)d * p.n_seg + c0 + jj) * P2;
       const float span = dr[p.P - 1] - dr[0];
       s_step[jj * D + d] = span > 0.f ? (float)(p.P - 1) / span : 0.f;
+      s_rng[jj * D + d] = make_float2(dr[0], dr[p.P - 1]);
       s_uns[jj * D + d] = p.unsorted[(int64_t)d * p.n_seg + c0 + jj];
     }
     __syncthreads();
@@ -445,9 +447,9 @@ __global__ void __launch_bounds__(kSweepThreads, 4) coarse_sweep_kernel(CoarseSw
       float r0[D];
 #pragma unroll
       for (int d = 0; d < D; ++d) {
-        const float* dr = s_dop + (jj * D + d) * P2;
-        olo[d] = __float2int_rd(fmaf(F, dr[0], frac5));
-        ohi[d] = __float2int_rd(fmaf(F, dr[p.P - 1], frac5));
+        const float2 rg = s_rng[jj * D + d];
+        olo[d] = __float2int_rd(fmaf(F, rg.x, frac5));
+        ohi[d] = __float2int_rd(fmaf(F, rg.y, frac5));
         const int kc = min(max(base + olo[d], 0), nbin - 1);
         r0[d] = load_rho(row0 + d * plane, kc);
       }
