@@ -21,24 +21,27 @@ COARSE_TIE = 1e-6   # bins: the coarse pass decides bins in fp32 around an FP64 
 
 
 def small_event(seed, n_det=2, n_seg=150, n_bin=1200, n_sky=120, n_tmpl=96, n_inj=3, snr=(12.0, 16.0),
-                t_sft=4.0):
+                t_sft=4.0, dtype=np.float32):
     r = syn.rng(seed)
     f_min = 500.0
     bank = syn.random_bank(r, n_tmpl, f0_range=(f_min - 3, f_min + n_bin / t_sft + 3),
                            tau_range=(3500.0, 35000.0))
     ev = syn.training_event(seed, bank, n_det=n_det, n_seg=n_seg, n_bin=n_bin, n_sky=n_sky,
-                            n_inj=n_inj, snr_range=snr, t_sft=t_sft)
+                            n_inj=n_inj, snr_range=snr, t_sft=t_sft, dtype=dtype)
     return ev, bank
 
 
 # 15 patches (sweep form, representatives' factors in order), 120 patches (sweep
 # form; neighbouring skies' factors cross, so many (detector, segment) pairs take
 # every representative's own bin) and 200 patches (the per-(template, patch) kernel)
-# (the 1100-segment event splits every template's segments into 4 ranges)
-@pytest.mark.parametrize("P_SIZE,N_SKY,N_SEG,SWEEP,PARTS",
-                         [(8, 120, 150, 1, 1), (1, 120, 150, 1, 1), (1, 200, 150, 0, 0), (8, 120, 1100, 1, 4)])
-def test_coarse_features_match_oracle(P_SIZE, N_SKY, N_SEG, SWEEP, PARTS):
-    ev, bank = small_event(81, n_inj=2, n_sky=N_SKY, n_seg=N_SEG)
+# (the 1100-segment event splits every template's segments into 4 ranges); one
+# detector; an FP16 map (the oracle reads the same half values widened)
+@pytest.mark.parametrize("P_SIZE,N_SKY,N_SEG,SWEEP,PARTS,N_DET,DTYPE",
+                         [(8, 120, 150, 1, 1, 2, np.float32), (1, 120, 150, 1, 1, 2, np.float32),
+                          (1, 200, 150, 0, 0, 2, np.float32), (8, 120, 1100, 1, 4, 2, np.float32),
+                          (8, 120, 150, 1, 1, 1, np.float32), (8, 120, 150, 1, 1, 2, np.float16)])
+def test_coarse_features_match_oracle(P_SIZE, N_SKY, N_SEG, SWEEP, PARTS, N_DET, DTYPE):
+    ev, bank = small_event(81, n_inj=2, n_sky=N_SKY, n_seg=N_SEG, n_det=N_DET, dtype=DTYPE)
     LO, HI = -4.0, 12.0
     s = tcw.Search(0)
     TR.load_event(s, ev, bank)
@@ -320,14 +323,22 @@ def _hand_network():
     return tcw.Mlp(theta, device=DEV)
 
 
-def test_batched_triaged_rows_equal_exhaustive_batched_rows():
+@pytest.mark.parametrize("amp,count", [(0, False), (4, False), (0, True)])
+def test_batched_triaged_rows_equal_exhaustive_batched_rows(amp, count):
     """tcw_search_batched_triaged with every template: each event's chosen
     patches (ceil(frac * n_patch) of them) are searched in one launch and
-    their rows equal tcw_search_batched's rows bit for bit; the other rows
-    are empty."""
+    their rows equal tcw_search_batched's rows (the amplitude weighting and the
+    number count apply to both); the other rows are empty.  Bit for bit with
+    unit weights and counts; with amplitude weights the chosen sky subset's
+    chunk width, and with it the segments per ring stage, differs from the
+    full batch's, so the per-template weight sums are added in another order:
+    Psi within 2 ulp."""
     evs, bank = _batch([91, 92, 93], [150, 90, 200], [120, 208, 64])
     mlp = _hand_network()
     s = tcw.Search(0)
+    s.set_option(tcw.OPT_AMPLITUDE_POWER, amp)
+    if count:
+        s.set_statistic(tcw.STAT_NUMBER_COUNT, 1.6)
     s.define_bank(bank.f0, bank.tau, bank.n, 0.0)
     s.load_events(evs, evs[0].f_min, evs[0].df)
     k = 6
@@ -341,8 +352,12 @@ def test_batched_triaged_rows_equal_exhaustive_batched_rows():
     assert info["skies_searched"] == rows.sum() and 0 < rows.sum() < rows.shape[0]
     assert info["lookups_full"] == sum(e.nhat.shape[0] * len(bank) * 2 * e.rho.shape[1] for e in evs)
     assert info["templates_searched"] == len(evs) * len(bank)
-    np.testing.assert_array_equal(it[rows], ix[rows])
-    np.testing.assert_array_equal(pt[rows], vx[rows])
+    if amp == 0:
+        np.testing.assert_array_equal(it[rows], ix[rows])
+        np.testing.assert_array_equal(pt[rows], vx[rows])
+    else:
+        np.testing.assert_array_max_ulp(pt[rows], vx[rows], maxulp=2)
+        assert (it[rows] == ix[rows]).mean() > 0.99
     assert np.all(it[~rows] == -1) and np.all(np.isneginf(pt[~rows]))
     # every event has whole patches searched
     row = 0
