@@ -482,8 +482,14 @@ __global__ void __launch_bounds__(kSweepThreads, 4) coarse_sweep_kernel(CoarseSw
             }
           }
         } else if (uns || (k1 >= 0 && k0 < nbin)) {
-          // band edge, or factors out of order: every representative's own bin
-          edge = true;
+          // band edge, or factors out of order: every representative's own bin.  When
+          // every representative's bin is in the band (|offset| <= 5: |frac5| <= 2.5,
+          // Doppler term <= 2.9 bins) the weight sums are the same for all of them
+          const bool inband = base - 5 >= 0 && base + 5 < nbin;
+          if (inband)
+            W2b = fmaf(w, w, W2b);
+          else
+            edge = true;
           const double w2 = (double)w * (double)w;
           for (int r = 0; r < p.P; ++r) {
             const int kr = base + __float2int_rd(fmaf(F, dr[r], frac5));
@@ -491,6 +497,7 @@ __global__ void __launch_bounds__(kSweepThreads, 4) coarse_sweep_kernel(CoarseSw
             const float v = w * (load_rho(row, kr) - 1.f);
             col[r * kSweepThreads] += v;
             col[(r + 1) * kSweepThreads] -= v;
+            if (inband) continue;
             // other segment ranges of this template may add to the same entries
             atomicAdd(p.w2edge + (int64_t)r * p.Bpad + b, w2);
             atomicAdd(p.w2edge + (int64_t)(r + 1) * p.Bpad + b, -w2);
