@@ -547,7 +547,7 @@ tcw_status tcw::coarse_pass(tcw_ctx* c, const CoarseEvent& ev, int patch_size, f
     {
       TCW_CUDA(c, upload(c, c->tri_seg, sp.seg.data(), sp.seg.size() * sizeof(float4), TCW_HOST), "triage buffers");
       TCW_CUDA(c, upload(c, c->tri_ta, sp.ta.data(), sp.ta.size() * sizeof(double), TCW_HOST), "triage buffers");
-      TCW_CUDA(c, c->tri_coef.ensure((size_t)sp.nt64 * c->Bpad * sizeof(double)), "triage buffers");
+      TCW_CUDA(c, c->tri_coef.ensure((size_t)(sp.nt64 + 3) * c->Bpad * sizeof(double)), "triage buffers");
       TCW_CUDA(c, c->tri_w2e.ensure((size_t)(P + 1) * c->Bpad * sizeof(double)), "triage buffers");
       TCW_CUDA(c, c->tri_ne.ensure((size_t)(P + 1) * c->Bpad * sizeof(int)), "triage buffers");
       CoarseSweepParams cs{};
@@ -566,6 +566,8 @@ tcw_status tcw::coarse_pass(tcw_ctx* c, const CoarseEvent& ev, int patch_size, f
       cs.T0 = ev.T0;
       cs.f_min = ev.f_min;
       cs.df = ev.df;
+      cs.inv_df = 1.0 / ev.df;
+      cs.xmin = ev.f_min * cs.inv_df;
       cs.dop = sd.dop;
       cs.unsorted = sd.unsorted;
       cs.P = P;

@@ -293,6 +293,7 @@ struct CoarseSweepParams {
   const double* ta;         // [n_tiles] anchor times, NaN for tiles without a segment at or after T0
   int tile_shift, n_tiles, nt64;
   double T0, f_min, df;
+  double inv_df, xmin;      // 1/df and f_min/df
   const float* dop;         // [D][n_seg][P2] from SweepDopplerParams
   const int* unsorted;      // [D][n_seg] from SweepDopplerParams: those lookups take every
                             // representative one by one
@@ -301,7 +302,8 @@ struct CoarseSweepParams {
   const double* tau;
   const double* nbr;
   int B, Bpad;
-  double* coef64;           // [nt64][Bpad] scratch: binomial coefficients of each template
+  double* coef64;           // [nt64 + 3][Bpad] scratch: binomial coefficients C(e, k) of each
+                            // template, then 1/tau, e and C(e, 2)
   double* w2edge;           // [P + 1][Bpad] zero at launch: W2 steps of band-edge lookups
   int* nedge;               // [P + 1][Bpad] zero at launch: valid-lookup count steps of them
   int parts;                // segment ranges per template (a multiple of 64 segments each)

@@ -281,7 +281,7 @@ __global__ void sweep_doppler_kernel(SweepDopplerParams p) {
   }
 }
 
-constexpr int kSweepChunk = 32;   // segments staged per block step of the sweep form
+constexpr int kSweepChunk = 64;   // segments staged per block step of the sweep form
 
 // shared memory of coarse_sweep_kernel: the staged chunk and the difference arrays
 inline int sweep_smem_bytes(int P, int P2, int D) {
@@ -319,9 +319,14 @@ __device__ __forceinline__ void sweep_store(const CoarseSweepParams& p, int r, i
 // some representatives leave the band, and lookups at a (detector, segment)
 // whose factors are out of order, take every representative one by one and
 // record their W2 and count steps in global scratch.  Psi (Eq. 4) =
-// (S - W1)/sqrt(W2), accumulated as sum w (rho - 1).
+// (S - W1)/sqrt(W2), accumulated as sum w (rho - 1).  Three resident blocks:
+// two leave too few warps to cover the kernel's dependent chains (42 ms
+// against 31 on the 2e5-template event), four take so much shared memory that
+// the L1 cache left over no longer holds the gathered lines until the
+// neighbouring bins are read (55 ms).
 template <typename RhoT, int D, int NC>
-__global__ void __launch_bounds__(kSweepThreads, 4) coarse_sweep_kernel(CoarseSweepParams p) {
+__global__ void __launch_bounds__(kSweepThreads, 3) coarse_sweep_kernel(CoarseSweepParams p) {
+  static_assert(kSweepChunk == 64 && D * kSweepChunk <= kSweepThreads, "staging maps one thread per (d, segment)");
   extern __shared__ float4 s_sweep[];
   float4* s_seg = s_sweep;                                              // [kSweepChunk]
   float* s_w = reinterpret_cast<float*>(s_seg + kSweepChunk);           // [D][kSweepChunk]
@@ -337,15 +342,19 @@ __global__ void __launch_bounds__(kSweepThreads, 4) coarse_sweep_kernel(CoarseSw
   for (int r = 0; r <= p.P; ++r) col[r * kSweepThreads] = 0.f;
   const RhoT* rho = static_cast<const RhoT*>(p.rho);
   const int bb = live ? b : 0;
-  const double tau = p.tau[bb], e = -1.0 / (p.nbr[bb] - 1.0);
+  const double e = -1.0 / (p.nbr[bb] - 1.0);
+  const double c2 = 0.5 * e * (e - 1.0);
   if (live) {
     double c = 1.0;
     for (int k = 0; k < p.nt64; ++k) {
       p.coef64[(int64_t)k * p.Bpad + b] = c;   // C(e, k)
       c = c * (e - k) / (k + 1);
     }
+    // the template's constants, read back at each anchor (no registers held between)
+    p.coef64[(int64_t)p.nt64 * p.Bpad + b] = 1.0 / p.tau[b];
+    p.coef64[(int64_t)(p.nt64 + 1) * p.Bpad + b] = e;
+    p.coef64[(int64_t)(p.nt64 + 2) * p.Bpad + b] = c2;
   }
-  const double c2 = 0.5 * e * (e - 1.0);
   float cf[NC];   // C(e, k + 3)
   {
     double c = c2;
@@ -355,13 +364,12 @@ __global__ void __launch_bounds__(kSweepThreads, 4) coarse_sweep_kernel(CoarseSw
       cf[k] = (float)c;
     }
   }
-  const double inv_tau = 1.0 / tau, inv_df = 1.0 / p.df, xmin = p.f_min * inv_df;
   double fa = 0.0, ua = 0.0, inv_ua = 0.0;
   bool have = false, edge = false, tile_ok = false;
   int base_a = 0;
   float frac_a = 0.f, A_hi = 0.f, A_lo = 0.f, Q_hi = 0.f, Q_lo = 0.f, Xf = 0.f, sg = 0.f;
   float Sb = 0.f, W2b = 0.f;
-  const int P2 = p.P2;
+  const int P2 = p.P2, lg_p2 = __ffs(P2) - 1;
   const int nbin = (int)p.n_bin;
   const int64_t plane = (int64_t)p.n_seg_full * p.n_bin;   // one detector's map
   // segment range blockIdx.y of p.parts (whole multiples of 64 segments)
@@ -370,22 +378,36 @@ __global__ void __launch_bounds__(kSweepThreads, 4) coarse_sweep_kernel(CoarseSw
   for (int c0 = jb; c0 < je; c0 += kSweepChunk) {
     const int cn = min(kSweepChunk, je - c0);
     __syncthreads();
-    for (int i = tid; i < cn; i += kSweepThreads) s_seg[i] = p.seg[c0 + i];
-    for (int i = tid; i < D * cn; i += kSweepThreads) {
-      const int d = i / cn, jj = i % cn;
-      s_w[d * kSweepChunk + jj] = p.weights[(int64_t)d * p.n_seg_full + (int64_t)(c0 + jj) * p.stride];
+    // index arithmetic by shifts and masks: the chunk is 64 segments, P2 a power of two
+    if (tid < cn) s_seg[tid] = p.seg[c0 + tid];
+    if (tid < D * kSweepChunk) {
+      const int d = tid >> 6, jj = tid & (kSweepChunk - 1);
+      if (jj < cn) {
+        const int64_t dj = (int64_t)d * p.n_seg + c0 + jj;
+        const float* dr = p.dop + dj * P2;
+        const float span = dr[p.P - 1] - dr[0];
+        s_w[d * kSweepChunk + jj] = p.weights[(int64_t)d * p.n_seg_full + (int64_t)(c0 + jj) * p.stride];
+        s_step[jj * D + d] = span > 0.f ? (float)(p.P - 1) / span : 0.f;
+        s_rng[jj * D + d] = make_float2(dr[0], dr[p.P - 1]);
+        s_uns[jj * D + d] = p.unsorted[dj];
+      }
     }
-    for (int i = tid; i < D * cn * P2; i += kSweepThreads) {
-      const int q = i % P2, dj = i / P2, d = dj / cn, jj = dj % cn;
-      s_dop[(jj * D + d) * P2 + q] = p.dop[((int64_t)d * p.n_seg + c0 + jj) * P2 + q];
-    }
-    for (int i = tid; i < D * cn; i += kSweepThreads) {
-      const int d = i / cn, jj = i % cn;
-      const float* dr = p.dop + ((int64_t)d * p.n_seg + c0 + jj) * P2;
-      const float span = dr[p.P - 1] - dr[0];
-      s_step[jj * D + d] = span > 0.f ? (float)(p.P - 1) / span : 0.f;
-      s_rng[jj * D + d] = make_float2(dr[0], dr[p.P - 1]);
-      s_uns[jj * D + d] = p.unsorted[(int64_t)d * p.n_seg + c0 + jj];
+    if (P2 >= 4) {
+      // 16-byte copies: the rows of P2 factors start 16-byte aligned on both sides
+      const int sh = lg_p2 - 2;
+      for (int i = tid; i < (D * kSweepChunk * P2) >> 2; i += kSweepThreads) {
+        const int q4 = i & ((P2 >> 2) - 1), t = i >> sh;
+        const int d = t >> 6, jj = t & (kSweepChunk - 1);
+        if (jj < cn)
+          reinterpret_cast<float4*>(s_dop + (jj * D + d) * P2)[q4] =
+              reinterpret_cast<const float4*>(p.dop + ((int64_t)d * p.n_seg + c0 + jj) * P2)[q4];
+      }
+    } else {
+      for (int i = tid; i < D * kSweepChunk * P2; i += kSweepThreads) {
+        const int q = i & (P2 - 1), t = i >> lg_p2;
+        const int d = t >> 6, jj = t & (kSweepChunk - 1);
+        if (jj < cn) s_dop[(jj * D + d) * P2 + q] = p.dop[((int64_t)d * p.n_seg + c0 + jj) * P2 + q];
+      }
     }
     __syncthreads();
     if (!live) continue;
@@ -396,6 +418,9 @@ __global__ void __launch_bounds__(kSweepThreads, 4) coarse_sweep_kernel(CoarseSw
         const double ta = p.ta[j >> p.tile_shift];
         tile_ok = false;
         if (!isnan(ta)) {
+          const double inv_tau = p.coef64[(int64_t)p.nt64 * p.Bpad + b];
+          const double e = p.coef64[(int64_t)(p.nt64 + 1) * p.Bpad + b];
+          const double c2 = p.coef64[(int64_t)(p.nt64 + 2) * p.Bpad + b];
           const double u = fma(ta - p.T0, inv_tau, 1.0);
           if (!have) {
             fa = p.f0[b] * pow(u, e);
@@ -408,8 +433,8 @@ __global__ void __launch_bounds__(kSweepThreads, 4) coarse_sweep_kernel(CoarseSw
           }
           ua = u;
           inv_ua = 1.0 / u;
-          const double X = fa * inv_df;
-          const double xa = X - xmin;
+          const double X = fa * p.inv_df;
+          const double xa = X - p.xmin;
           const double xr = rint(xa);
           if (fabs(xr) < 1.0e9) {
             tile_ok = true;
@@ -465,18 +490,30 @@ __global__ void __launch_bounds__(kSweepThreads, 4) coarse_sweep_kernel(CoarseSw
           Sb = fmaf(w, rp - 1.f, Sb);
           W2b = fmaf(w, w, W2b);
           if (ohi[d] > olo[d]) {
-            const float step = s_step[jj * D + d], d0 = dr[0], rF = __frcp_rn(F);
-            for (int o = olo[d] + 1; o <= ohi[d]; ++o) {
+            // guess of the first representative at offset o from the nearly even
+            // spacing of the factors: ((o - frac5)/F - v_0/c) step + 1 = o ga + gc
+            const float step = s_step[jj * D + d], rF = __frcp_rn(F);
+            const float ga = rF * step, gc = fmaf(-fmaf(frac5, rF, dr[0]), step, 1.f);
+            float thr = (float)(olo[d] + 1);
+            for (int o = olo[d] + 1; o <= ohi[d]; ++o, thr += 1.f) {
               const float r1 = load_rho(row, base + o);
               // first representative q with fmaf(F, v_q/c, frac5) >= o: q is in
               // [1, P-1] (representative 0 is below o, the last one reaches it);
-              // guessed from the nearly even spacing of the factors, then moved
-              // until representative q-1 is below o and q is not
-              const float thr = (float)o;
-              int q = (int)(((thr - frac5) * rF - d0) * step) + 1;
+              // from the guess, moved until representative q-1 is below o and q is
+              // not (both neighbours read at once: the guess is right for ~9 in 10
+              // steps and otherwise off by one)
+              int q = (int)fmaf(thr, ga, gc);
               q = min(max(q, 1), p.P - 1);
-              while (q > 1 && fmaf(F, dr[q - 1], frac5) >= thr) --q;
-              while (q < p.P - 1 && fmaf(F, dr[q], frac5) < thr) ++q;
+              {
+                const float a1 = fmaf(F, dr[q - 1], frac5), a2 = fmaf(F, dr[q], frac5);
+                if (a1 >= thr) {
+                  --q;
+                  while (q > 1 && fmaf(F, dr[q - 1], frac5) >= thr) --q;
+                } else if (a2 < thr) {
+                  ++q;
+                  while (q < p.P - 1 && fmaf(F, dr[q], frac5) < thr) ++q;
+                }
+              }
               col[q * kSweepThreads] += w * (r1 - rp);
               rp = r1;
             }
