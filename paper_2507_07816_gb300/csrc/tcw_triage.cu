@@ -282,6 +282,10 @@ __global__ void sweep_doppler_kernel(SweepDopplerParams p) {
 }
 
 constexpr int kSweepChunk = 64;   // segments staged per block step of the sweep form
+// steps of the step function taken straight-line per lookup: most lookups
+// take one or two (about 1.4 on average at 500-3000 Hz); three straight-line
+// steps waste work where fewer are needed, one leaves the second in the loop
+constexpr int kSweepSteps = 2;
 
 // shared memory of coarse_sweep_kernel: the staged chunk and the difference arrays
 inline int sweep_smem_bytes(int P, int P2, int D) {
@@ -489,31 +493,57 @@ __global__ void __launch_bounds__(kSweepThreads, 3) coarse_sweep_kernel(CoarseSw
           float rp = r0[d];
           Sb = fmaf(w, rp - 1.f, Sb);
           W2b = fmaf(w, w, W2b);
-          if (ohi[d] > olo[d]) {
+          const int nst = ohi[d] - olo[d];
+          if (nst > 0) {
             // guess of the first representative at offset o from the nearly even
             // spacing of the factors: ((o - frac5)/F - v_0/c) step + 1 = o ga + gc
             const float step = s_step[jj * D + d], rF = __frcp_rn(F);
             const float ga = rF * step, gc = fmaf(-fmaf(frac5, rF, dr[0]), step, 1.f);
-            float thr = (float)(olo[d] + 1);
-            for (int o = olo[d] + 1; o <= ohi[d]; ++o, thr += 1.f) {
+            // the first kSweepSteps steps straight-line, so that their chains overlap
+            // (a step past nst reads the last in-band bin and adds nothing).  Step i:
+            // bin offset o = olo + i and the first representative q with
+            // fmaf(F, v_q/c, frac5) >= o, in [1, P-1] (representative 0 is below o,
+            // the last one reaches it).  The guess is right for ~9 in 10 steps and
+            // otherwise off by one: representatives q-2 .. q+1 are compared at once
+            // and moves of more than one are finished after the steps
+            int qs[kSweepSteps];
+            float vs[kSweepSteps];
+            bool far = false;
+#pragma unroll
+            for (int i = 1; i <= kSweepSteps; ++i) {
+              const int o = olo[d] + min(i, nst);
+              const float thr = (float)o;
               const float r1 = load_rho(row, base + o);
-              // first representative q with fmaf(F, v_q/c, frac5) >= o: q is in
-              // [1, P-1] (representative 0 is below o, the last one reaches it);
-              // from the guess, moved until representative q-1 is below o and q is
-              // not (both neighbours read at once: the guess is right for ~9 in 10
-              // steps and otherwise off by one)
-              int q = (int)fmaf(thr, ga, gc);
-              q = min(max(q, 1), p.P - 1);
-              {
-                const float a1 = fmaf(F, dr[q - 1], frac5), a2 = fmaf(F, dr[q], frac5);
-                if (a1 >= thr) {
-                  --q;
-                  while (q > 1 && fmaf(F, dr[q - 1], frac5) >= thr) --q;
-                } else if (a2 < thr) {
-                  ++q;
-                  while (q < p.P - 1 && fmaf(F, dr[q], frac5) < thr) ++q;
-                }
+              int q = min(max((int)fmaf(thr, ga, gc), 1), p.P - 1);
+              const float a0 = fmaf(F, dr[max(q - 2, 0)], frac5), a1 = fmaf(F, dr[q - 1], frac5);
+              const float a2 = fmaf(F, dr[q], frac5), a3 = fmaf(F, dr[min(q + 1, p.P - 1)], frac5);
+              const bool dn = a1 >= thr, up = a2 < thr;
+              far = far || (i <= nst && ((dn && a0 >= thr) || (up && a3 < thr)));
+              qs[i - 1] = q + (up ? 1 : 0) - (dn ? 1 : 0);
+              vs[i - 1] = w * (r1 - rp);
+              rp = r1;
+            }
+            if (far) {
+#pragma unroll
+              for (int i = 1; i <= kSweepSteps; ++i) {
+                if (i > nst) break;
+                const float thr = (float)(olo[d] + i);
+                int q = qs[i - 1];
+                while (q > 1 && fmaf(F, dr[q - 1], frac5) >= thr) --q;
+                while (q < p.P - 1 && fmaf(F, dr[q], frac5) < thr) ++q;
+                qs[i - 1] = q;
               }
+            }
+#pragma unroll
+            for (int i = 1; i <= kSweepSteps; ++i)
+              if (i <= nst) col[qs[i - 1] * kSweepThreads] += vs[i - 1];
+            // the steps after the first kSweepSteps, one by one
+            for (int i = kSweepSteps + 1; i <= nst; ++i) {
+              const float thr = (float)(olo[d] + i);
+              const float r1 = load_rho(row, base + olo[d] + i);
+              int q = min(max((int)fmaf(thr, ga, gc), 1), p.P - 1);
+              while (q > 1 && fmaf(F, dr[q - 1], frac5) >= thr) --q;
+              while (q < p.P - 1 && fmaf(F, dr[q], frac5) < thr) ++q;
               col[q * kSweepThreads] += w * (r1 - rp);
               rp = r1;
             }
