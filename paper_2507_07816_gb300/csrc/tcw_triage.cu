@@ -324,10 +324,10 @@ __device__ __forceinline__ void sweep_store(const CoarseSweepParams& p, int r, i
 // whose factors are out of order, take every representative one by one and
 // record their W2 and count steps in global scratch.  Psi (Eq. 4) =
 // (S - W1)/sqrt(W2), accumulated as sum w (rho - 1).  Three resident blocks:
-// two leave too few warps to cover the kernel's dependent chains (42 ms
-// against 31 on the 2e5-template event), four take so much shared memory that
-// the L1 cache left over no longer holds the gathered lines until the
-// neighbouring bins are read (55 ms).
+// two leave too few warps to cover the kernel's dependent chains (a third
+// slower on the 2e5-template event), four take so much shared memory that the
+// L1 cache left over no longer holds the gathered lines until the
+// neighbouring bins are read (almost twice as slow).
 template <typename RhoT, int D, int NC>
 __global__ void __launch_bounds__(kSweepThreads, 3) coarse_sweep_kernel(CoarseSweepParams p) {
   static_assert(kSweepChunk == 64 && D * kSweepChunk <= kSweepThreads, "staging maps one thread per (d, segment)");
