@@ -35,13 +35,19 @@ def small_event(seed, n_det=2, n_seg=150, n_bin=1200, n_sky=120, n_tmpl=96, n_in
 # form; neighbouring skies' factors cross, so many (detector, segment) pairs take
 # every representative's own bin) and 200 patches (the per-(template, patch) kernel)
 # (the 1100-segment event splits every template's segments into 4 ranges); one
-# detector; an FP16 map (the oracle reads the same half values widened)
-@pytest.mark.parametrize("P_SIZE,N_SKY,N_SEG,SWEEP,PARTS,N_DET,DTYPE",
-                         [(8, 120, 150, 1, 1, 2, np.float32), (1, 120, 150, 1, 1, 2, np.float32),
-                          (1, 200, 150, 0, 0, 2, np.float32), (8, 120, 1100, 1, 4, 2, np.float32),
-                          (8, 120, 150, 1, 1, 1, np.float32), (8, 120, 150, 1, 1, 2, np.float16)])
-def test_coarse_features_match_oracle(P_SIZE, N_SKY, N_SEG, SWEEP, PARTS, N_DET, DTYPE):
-    ev, bank = small_event(81, n_inj=2, n_sky=N_SKY, n_seg=N_SEG, n_det=N_DET, dtype=DTYPE)
+# detector; an FP16 map (the oracle reads the same half values widened); 32 s
+# segments (F = f/df up to 25 600: the representatives' bins of a lookup span up
+# to 5 bins, so lookups take more steps than the straight-line ones, and the
+# guessed representative is off by more than one more often)
+@pytest.mark.parametrize("P_SIZE,N_SKY,N_SEG,SWEEP,PARTS,N_DET,DTYPE,T_SFT",
+                         [(8, 120, 150, 1, 1, 2, np.float32, 4.0), (1, 120, 150, 1, 1, 2, np.float32, 4.0),
+                          (1, 200, 150, 0, 0, 2, np.float32, 4.0), (8, 120, 1100, 1, 4, 2, np.float32, 4.0),
+                          (8, 120, 150, 1, 1, 1, np.float32, 4.0), (8, 120, 150, 1, 1, 2, np.float16, 4.0),
+                          (8, 120, 150, 1, 1, 2, np.float32, 32.0), (3, 120, 150, 1, 1, 2, np.float32, 32.0)])
+def test_coarse_features_match_oracle(P_SIZE, N_SKY, N_SEG, SWEEP, PARTS, N_DET, DTYPE, T_SFT):
+    n_bin = 1200 if T_SFT == 4.0 else 9600
+    ev, bank = small_event(81, n_inj=2, n_sky=N_SKY, n_seg=N_SEG, n_det=N_DET, dtype=DTYPE, t_sft=T_SFT,
+                           n_bin=n_bin)
     LO, HI = -4.0, 12.0
     s = tcw.Search(0)
     TR.load_event(s, ev, bank)
