@@ -48,6 +48,20 @@ def test_coarse_features_match_oracle(P_SIZE, N_SKY, N_SEG, SWEEP, PARTS, N_DET,
     n_bin = 1200 if T_SFT == 4.0 else 9600
     ev, bank = small_event(81, n_inj=2, n_sky=N_SKY, n_seg=N_SEG, n_det=N_DET, dtype=DTYPE, t_sft=T_SFT,
                            n_bin=n_bin)
+    _check_coarse(ev, bank, P_SIZE, SWEEP, PARTS)
+
+
+def test_coarse_pass_with_segments_before_T0_matches_oracle():
+    """T0 inside the observation (Eq. 1 starts there; earlier segments add
+    nothing): the 64-segment tiles wholly before T0 take no anchor, the tile
+    holding T0 is anchored at T0 itself (its middle lies before T0), and the
+    second segment range starts its anchor chain with pow on a later tile."""
+    ev, bank = small_event(85, n_inj=1, n_seg=600)
+    ev.T0 = float(ev.t_mid[230] + 1.0)
+    _check_coarse(ev, bank, 8, 1, 2)
+
+
+def _check_coarse(ev, bank, P_SIZE, SWEEP, PARTS):
     LO, HI = -4.0, 12.0
     s = tcw.Search(0)
     TR.load_event(s, ev, bank)
