@@ -322,13 +322,13 @@ def test_parameter_regions_search_a_template_subset():
 
 
 
-def _batch(seeds, n_segs, n_skies, n_bin=1200, n_tmpl=96):
+def _batch(seeds, n_segs, n_skies, n_bin=1200, n_tmpl=96, n_det=2, dtype=np.float32):
     r = syn.rng(seeds[0] + 7)
     f_min, t_sft = 500.0, 4.0
     bank = syn.random_bank(r, n_tmpl, f0_range=(f_min - 3, f_min + n_bin / t_sft + 3),
                            tau_range=(3500.0, 35000.0))
-    evs = [syn.training_event(sd, bank, n_det=2, n_seg=ns, n_bin=n_bin, n_sky=S, n_inj=2,
-                              snr_range=(12.0, 16.0), t_sft=t_sft)
+    evs = [syn.training_event(sd, bank, n_det=n_det, n_seg=ns, n_bin=n_bin, n_sky=S, n_inj=2,
+                              snr_range=(12.0, 16.0), t_sft=t_sft, dtype=dtype)
            for sd, ns, S in zip(seeds, n_segs, n_skies)]
     return evs, bank
 
@@ -396,6 +396,29 @@ def test_batched_triaged_rows_equal_exhaustive_batched_rows(amp, count):
     assert (it0[r0][:, 0] == ix[r0][:, 0]).mean() > 0.95
     with pytest.raises(tcw.TcwError):
         s.search_batched_triaged(mlp, -1, -4.0, 12.0, 0.3, k)
+    s.close()
+
+
+@pytest.mark.parametrize("n_det,dtype", [(1, np.float32), (2, np.float16)])
+def test_batched_triaged_one_detector_and_fp16_rows_equal_exhaustive_batched_rows(n_det, dtype):
+    """tcw_search_batched_triaged on one-detector events and on FP16 maps (the
+    coarse pass reads the half values, the group kernel's FP16 instance searches
+    the chosen skies): with every template the searched rows equal
+    tcw_search_batched's rows bit for bit."""
+    evs, bank = _batch([96, 97], [130, 170], [100, 150], n_det=n_det, dtype=dtype)
+    mlp = _hand_network()
+    s = tcw.Search(0)
+    s.define_bank(bank.f0, bank.tau, bank.n, 0.0)
+    s.load_events(evs, evs[0].f_min, evs[0].df)
+    k = 5
+    vx, ix = s.search_batched(k)
+    pt, it, searched = s.search_batched_triaged(mlp, 16, -4.0, 12.0, 0.3, k)
+    rows = searched.astype(bool)
+    assert 0 < rows.sum() < rows.shape[0]
+    assert s.triage_info()["coarse_kernel"] == 1
+    np.testing.assert_array_equal(it[rows], ix[rows])
+    np.testing.assert_array_equal(pt[rows], vx[rows])
+    assert np.all(it[~rows] == -1) and np.all(np.isneginf(pt[~rows]))
     s.close()
 
 
