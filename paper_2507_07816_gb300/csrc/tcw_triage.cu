@@ -354,7 +354,8 @@ __global__ void __launch_bounds__(kSweepThreads, 3) coarse_sweep_kernel(CoarseSw
       p.coef64[(int64_t)k * p.Bpad + b] = c;   // C(e, k)
       c = c * (e - k) / (k + 1);
     }
-    // the template's constants, read back at each anchor (no registers held between)
+    // the template's constants, read back at each anchor (no registers held between);
+    // the blocks of a template's other segment ranges write the same values
     p.coef64[(int64_t)p.nt64 * p.Bpad + b] = 1.0 / p.tau[b];
     p.coef64[(int64_t)(p.nt64 + 1) * p.Bpad + b] = e;
     p.coef64[(int64_t)(p.nt64 + 2) * p.Bpad + b] = c2;
