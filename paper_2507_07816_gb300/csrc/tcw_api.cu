@@ -552,6 +552,14 @@ tcw_status tcw::coarse_pass(tcw_ctx* c, const CoarseEvent& ev, int patch_size, f
       TCW_CUDA(c, c->tri_ne.ensure((size_t)(P + 1) * c->Bpad * sizeof(int)), "triage buffers");
       CoarseSweepParams cs{};
       cs.rho = ev.rho;
+      if (ev.D == 2) {
+        const size_t esz = ev.half ? 2 : 4;
+        TCW_CUDA(c, c->tri_rhoi.ensure((size_t)n_cs * ev.n_bin * 2 * esz), "triage buffers");
+        TCW_CUDA(c, launch_interleave(ev.rho, ev.half, ev.n_bin, n_cs, stride, (int)ev.n_seg, c->tri_rhoi.p,
+                                      c->stream),
+                 "interleave_kernel launch");
+        cs.rho_i = c->tri_rhoi.p;
+      }
       cs.n_bin = ev.n_bin;
       cs.n_det = ev.D;
       cs.n_seg = n_cs;

@@ -105,7 +105,7 @@ struct tcw_ctx {
   std::vector<int32_t> h_sky_perm, h_bank_perm;  // sorted -> caller (host copies)
   tcw::DevBuf tri_tmid;   // coarse-pass segment times (every stride-th segment)
   tcw::DevBuf tri_dop, tri_hist, tri_feat, tri_psi, tri_anchor, tri_h1, tri_h2, tri_score, tri_sel, tri_part;
-  tcw::DevBuf tri_seg, tri_ta, tri_coef, tri_w2e, tri_ne, tri_flag, tri_pS, tri_pW;   // sweep form
+  tcw::DevBuf tri_seg, tri_ta, tri_coef, tri_w2e, tri_ne, tri_flag, tri_pS, tri_pW, tri_rhoi;   // sweep form
   tcw::DevBuf tri_keep, tri_sub;   // template regions: keep mask and chosen rows; the subset's parameters
   tcw_triage_info tri_info{};
 };

@@ -285,6 +285,7 @@ struct SweepDopplerParams {
 
 struct CoarseSweepParams {
   const void* rho;          // [D][n_seg_full][n_bin]
+  const void* rho_i;        // two detectors: [n_seg][n_bin][2], the coarse segments interleaved
   int64_t n_bin;
   int n_det, n_seg, stride, n_seg_full;   // n_seg: coarse segments
   const float* weights;     // [D][n_seg_full]
@@ -316,6 +317,8 @@ struct CoarseSweepParams {
 };
 
 cudaError_t launch_sweep_doppler(const SweepDopplerParams& p, cudaStream_t st);
+cudaError_t launch_interleave(const void* rho, bool half, int64_t n_bin, int n_seg, int stride, int n_seg_full,
+                              void* out, cudaStream_t st);
 // Template regions of a triaged search: for each listed row r of the coarse
 // Psi [P][Bpad] (sorted bank, first B valid), keep[b] = 1 for its M best
 // templates by (Psi desc, index asc); rows OR into one keep [B].

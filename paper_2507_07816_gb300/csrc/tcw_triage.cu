@@ -6,6 +6,9 @@
 //   sweep_doppler_kernel  Eq. 2 factor v.nhat/c of each patch representative,
 //                         padded to a power of two, and a flag for every
 //                         (detector, segment) whose factors are out of order
+//   interleave_kernel     a two-detector map's coarse segments with the
+//                         detectors interleaved per bin, so that the sweep's
+//                         gathers of both detectors share cache lines
 //   coarse_sweep_kernel   Psi (Eq. 4) of every template at every patch
 //                         representative, one thread per template walking the
 //                         segments (or a range of them): the representatives'
@@ -281,6 +284,22 @@ __global__ void sweep_doppler_kernel(SweepDopplerParams p) {
   }
 }
 
+// The coarse segments of a two-detector map with the detectors interleaved per
+// bin: out[jc][k][d] = rho[d][jc * stride][k].
+template <typename RhoT>
+__global__ void interleave_kernel(const RhoT* rho, int64_t n_bin, int n_seg, int stride, int n_seg_full,
+                                  RhoT* out) {
+  const int64_t total = (int64_t)n_seg * n_bin;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t jc = i / n_bin, k = i % n_bin;
+    const RhoT a = rho[(jc * stride) * n_bin + k];
+    const RhoT c = rho[((int64_t)n_seg_full + jc * stride) * n_bin + k];
+    out[2 * i] = a;
+    out[2 * i + 1] = c;
+  }
+}
+
 constexpr int kSweepChunk = 64;   // segments staged per block step of the sweep form
 // steps of the step function taken straight-line per lookup: most lookups
 // take one or two (about 1.4 on average at 500-3000 Hz); three straight-line
@@ -473,6 +492,12 @@ __global__ void __launch_bounds__(kSweepThreads, 3) coarse_sweep_kernel(CoarseSw
       // both detectors' first gathers before either is used (bins as int32: |base| < 1e9,
       // n_bin <= 2^30)
       const RhoT* row0 = rho + (int64_t)j * p.stride * p.n_bin;
+      // two detectors: the coarse copy of the map with the detectors interleaved per bin
+      // ([coarse segment][bin][2]), so both detectors' gathers of a lookup share L1 lines
+      const RhoT* rowi = D == 2 ? static_cast<const RhoT*>(p.rho_i) + (int64_t)j * p.n_bin * 2 : nullptr;
+      auto at = [&](int d, int k) {
+        return D == 2 ? load_rho(rowi, (int64_t)k * 2 + d) : load_rho(row0 + d * plane, k);
+      };
       int olo[D], ohi[D];
       float r0[D];
 #pragma unroll
@@ -481,14 +506,13 @@ __global__ void __launch_bounds__(kSweepThreads, 3) coarse_sweep_kernel(CoarseSw
         olo[d] = __float2int_rd(fmaf(F, rg.x, frac5));
         ohi[d] = __float2int_rd(fmaf(F, rg.y, frac5));
         const int kc = min(max(base + olo[d], 0), nbin - 1);
-        r0[d] = load_rho(row0 + d * plane, kc);
+        r0[d] = at(d, kc);
       }
 #pragma unroll
       for (int d = 0; d < D; ++d) {
         const float w = s_w[d * kSweepChunk + jj];
         const float* dr = s_dop + (jj * D + d) * P2;
         const int k0 = base + olo[d], k1 = base + ohi[d];
-        const RhoT* row = row0 + d * plane;
         const bool uns = s_uns[jj * D + d] != 0;
         if (!uns && k0 >= 0 && k1 < nbin) {
           float rp = r0[d];
@@ -514,7 +538,7 @@ __global__ void __launch_bounds__(kSweepThreads, 3) coarse_sweep_kernel(CoarseSw
             for (int i = 1; i <= kSweepSteps; ++i) {
               const int o = olo[d] + min(i, nst);
               const float thr = (float)o;
-              const float r1 = load_rho(row, base + o);
+              const float r1 = at(d, base + o);
               int q = min(max((int)fmaf(thr, ga, gc), 1), p.P - 1);
               const float a0 = fmaf(F, dr[max(q - 2, 0)], frac5), a1 = fmaf(F, dr[q - 1], frac5);
               const float a2 = fmaf(F, dr[q], frac5), a3 = fmaf(F, dr[min(q + 1, p.P - 1)], frac5);
@@ -541,7 +565,7 @@ __global__ void __launch_bounds__(kSweepThreads, 3) coarse_sweep_kernel(CoarseSw
             // the steps after the first kSweepSteps, one by one
             for (int i = kSweepSteps + 1; i <= nst; ++i) {
               const float thr = (float)(olo[d] + i);
-              const float r1 = load_rho(row, base + olo[d] + i);
+              const float r1 = at(d, base + olo[d] + i);
               int q = min(max((int)fmaf(thr, ga, gc), 1), p.P - 1);
               while (q > 1 && fmaf(F, dr[q - 1], frac5) >= thr) --q;
               while (q < p.P - 1 && fmaf(F, dr[q], frac5) < thr) ++q;
@@ -562,7 +586,7 @@ __global__ void __launch_bounds__(kSweepThreads, 3) coarse_sweep_kernel(CoarseSw
           for (int r = 0; r < p.P; ++r) {
             const int kr = base + __float2int_rd(fmaf(F, dr[r], frac5));
             if (kr < 0 || kr >= nbin) continue;
-            const float v = w * (load_rho(row, kr) - 1.f);
+            const float v = w * (at(d, kr) - 1.f);
             col[r * kSweepThreads] += v;
             col[(r + 1) * kSweepThreads] -= v;
             if (inband) continue;
@@ -935,6 +959,19 @@ cudaError_t launch_gather_rows(const int32_t* src, const int32_t* idx, int64_t n
 cudaError_t launch_fill_empty(float* psi, int64_t* idx, int64_t n, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   fill_empty_kernel<<<blocks_for(n, 256), 256, 0, st>>>(psi, idx, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_interleave(const void* rho, bool half, int64_t n_bin, int n_seg, int stride, int n_seg_full,
+                              void* out, cudaStream_t st) {
+  const int64_t total = (int64_t)n_seg * n_bin;
+  const int blocks = (int)std::min<int64_t>((total + 255) / 256, 152LL * 8);
+  if (half)
+    interleave_kernel<__half><<<blocks, 256, 0, st>>>(static_cast<const __half*>(rho), n_bin, n_seg, stride,
+                                                      n_seg_full, static_cast<__half*>(out));
+  else
+    interleave_kernel<float><<<blocks, 256, 0, st>>>(static_cast<const float*>(rho), n_bin, n_seg, stride,
+                                                     n_seg_full, static_cast<float*>(out));
   return cudaGetLastError();
 }
 
